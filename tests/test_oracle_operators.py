@@ -1,0 +1,155 @@
+"""Pins of the oracle residual / Jacobian / constrained system (oracle/operators.py)
+against closed forms, invariants and finite differences."""
+import numpy as np
+import pytest
+
+from oracle import operators as ops
+from oracle.mesh import LeafMesh, build_recipe
+from paper_2404_03265_gb300 import synth
+
+
+def mesh(name, k):
+    return LeafMesh(build_recipe(synth.recipe(name)), k)
+
+
+def random_state(m, seed=0, u_std=1e-1, E_cells=None):
+    xy = m.node_xy()
+    u, phi, phit = synth.linearisation(m.X, m.Y, m.Xmax, m.Ymax, seed=seed, u_std=u_std)
+    return ops.State(m, u, phi, phit, E_cells)
+
+
+def const_state(m, ufun=None, phi=1.0, phit=1.0):
+    x, y = m.node_xy()
+    u = np.zeros((m.nn, 2)) if ufun is None else ufun(x, y)
+    return ops.State(m, u, np.full(m.nn, phi), np.full(m.nn, phit))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_elastic_energy_linear_field(k):
+    """u = A x: u^T G_uu u = |Omega| (2 mu e:e + lam tr(e)^2), e = sym(A), with g = 1."""
+    m = mesh("tiny", k)
+    mat = ops.Material(E=1.3, nu=0.2, Gc=1.0, eps=0.5, kappa=0.0, p=0.0)
+    A = np.array([[0.3, -0.7], [0.2, 0.5]])
+    x, y = m.node_xy()
+    u = np.stack([A[0, 0] * x + A[0, 1] * y, A[1, 0] * x + A[1, 1] * y], axis=1)
+    st = const_state(m)
+    G = ops.assemble_jacobian(m, mat, st)
+    nn = m.nn
+    v = np.concatenate([m.C @ u[:, 0], m.C @ u[:, 1], np.zeros(nn)])
+    e = 0.5 * (A + A.T)
+    exact = 400.0 * (2 * mat.mu * np.sum(e * e) + mat.lam * np.trace(e) ** 2)
+    assert abs(v @ (G @ v) - exact) < 1e-10 * exact
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_rigid_modes_and_patch_test(k):
+    """Rigid motions are in the kernel of C^T G_uu C; a linear field leaves zero
+    residual on every free interior row (patch test on a mesh with hanging nodes)."""
+    m = mesh("small", k)
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.0, eps=0.5, kappa=0.0, p=0.0)
+    st = const_state(m)
+    G = ops.assemble_jacobian(m, mat, st)
+    C = ops.C3(m)
+    nn = m.nn
+    x, y = m.node_xy()
+    for vec in (np.concatenate([np.ones(nn), np.zeros(2 * nn)]),
+                np.concatenate([np.zeros(nn), np.ones(nn), np.zeros(nn)]),
+                np.concatenate([-y, x, np.zeros(nn)])):
+        r = C.T @ (G @ (C @ vec))
+        assert np.abs(r[:2 * nn]).max() < 1e-12
+    lin = np.concatenate([0.3 * x - 0.1 * y, 0.2 * x + 0.4 * y, np.zeros(nn)])
+    r = C.T @ (G @ (C @ lin))
+    interior = ~m.dirichlet & ~m.is_hanging
+    assert np.abs(r[:nn][interior]).max() < 1e-12
+    assert np.abs(r[nn:2 * nn][interior]).max() < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_pure_elasticity_limit(k):
+    """phi = phi~ = 1, u = 0: (p, div psi) = 0 for psi in H^1_0 and 1 - phi = 0, so the
+    condensed residual vanishes on every free row (U = (0, 1) solves the discrete system)."""
+    m = mesh("small", k)
+    mat = ops.Material(eps=0.4)
+    st = const_state(m)
+    A = ops.residual_form(m, mat, st)
+    R = ops.condense(m, -A)
+    free = ops.free_dofs(m, np.zeros(m.nn, bool))
+    assert np.abs(R[free]).max() < 1e-15
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("withE", [False, True])
+def test_jacobian_is_derivative_of_residual(k, withE):
+    """A(U + t V) is a cubic polynomial in t: the Richardson-extrapolated central
+    difference equals G C V up to rounding.  Pins every Jacobian term and the sign
+    of the G_c / l term."""
+    m = mesh("tiny", k)
+    E = None
+    if withE:
+        E = synth.cell_modulus(m.cells[:, 0], m.cells[:, 1], m.cells[:, 2], seed=4, sigma_log=0.3)
+    mat = ops.Material(E=1.0, nu=0.3, Gc=1.7, eps=0.8, kappa=1e-3, p=0.3)
+    x, y = m.node_xy()
+    u0, phi0, phit = synth.linearisation(m.X, m.Y, m.Xmax, m.Ymax, seed=7, u_std=0.3)
+    st = ops.State(m, u0, phi0, phit, E)
+    G = ops.assemble_jacobian(m, mat, st)
+    rng = np.random.default_rng(11)
+    V = rng.normal(size=(m.nn, 3))
+
+    def A_at(t):
+        s = ops.State(m, u0 + t * V[:, :2], phi0 + t * V[:, 2], phit, E)
+        return ops.residual_form(m, mat, s)
+
+    def D(e):
+        return (A_at(e) - A_at(-e)) / (2 * e)
+
+    eps = 1e-2
+    fd = (4 * D(eps / 2) - D(eps)) / 3
+    v = np.concatenate([V[:, 0], V[:, 1], V[:, 2]])
+    gv = G @ (ops.C3(m) @ v)
+    assert np.abs(fd - gv).max() < 1e-9 * np.abs(gv).max()
+
+
+def test_block_structure():
+    """Upper-right block (u rows, phi columns) is zero; diagonal blocks symmetric."""
+    m = mesh("small", 1)
+    mat = ops.Material(eps=0.4, p=1e-2)
+    st = random_state(m)
+    G = ops.assemble_jacobian(m, mat, st).toarray()
+    nn = m.nn
+    assert np.abs(G[:2 * nn, 2 * nn:]).max() == 0.0
+    Guu = G[:2 * nn, :2 * nn]
+    Gpp = G[2 * nn:, 2 * nn:]
+    assert np.abs(Guu - Guu.T).max() < 1e-14 * np.abs(Guu).max()
+    assert np.abs(Gpp - Gpp.T).max() < 1e-14 * np.abs(Gpp).max()
+    assert np.abs(G[2 * nn:, :2 * nn]).max() > 0
+
+
+def test_constrained_operator_structure():
+    m = mesh("small", 1)
+    mat = ops.Material(eps=0.4)
+    st = random_state(m)
+    G = ops.assemble_jacobian(m, mat, st)
+    active = np.zeros(m.nn, bool)
+    active[::17] = True
+    active &= ~m.is_hanging
+    Gt = ops.constrained_operator(m, G, active).toarray()
+    nn = m.nn
+    fixed = ops.fixed_dofs(m, active)
+    hang = np.tile(m.is_hanging, 3)
+    assert np.allclose(Gt[fixed][:, fixed], np.eye(fixed.sum()))
+    assert np.abs(Gt[fixed][:, ~fixed]).max() == 0.0
+    assert np.abs(Gt[~fixed][:, fixed]).max() == 0.0
+    assert np.abs(Gt[hang]).max() == 0.0 and np.abs(Gt[:, hang]).max() == 0.0
+
+
+def test_lumped_mass_and_tcv():
+    m = mesh("small", 1)
+    B = ops.lumped_mass(m)
+    assert abs(B.sum() - 400.0) < 1e-10
+    assert np.all(B[m.is_hanging] == 0.0) and np.all(B[~m.is_hanging] > 0)
+    # u = (x + 10, 0), phi = x: u . grad phi = x + 10, integral 20 * 200 = 4000
+    x, y = m.node_xy()
+    st = ops.State(m, np.stack([x + 10, 0 * x], 1), x.copy(), np.ones(m.nn))
+    assert abs(ops.tcv(m, st) - 4000.0) < 1e-9
+    st = ops.State(m, np.stack([0 * x, y], 1), y.copy(), np.ones(m.nn))
+    assert abs(ops.tcv(m, st)) < 1e-9

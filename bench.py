@@ -1,0 +1,343 @@
+"""Benchmark: matrix-free Jacobian apply throughput (GDoF/s and fraction of the
+HBM roofline) on the operator-apply workload of the pressurised-crack test
+(16x16 coarse cells on (-10,10)^2, 6 global refinements, 2 refinements of the
+box |x|<=2, |y|<=1; Q1 u and phi: 4,096,509 DoFs; Q2: 16,368,207 DoFs).
+
+One step = one application of the constrained Jacobian y = G~ x (Sec. 3.1,
+matrix-free cell loop of Sec. 3.3) over the whole mesh in FP32 (headline), with
+inputs resident in HBM.  Rotating input sets keep the footprint above L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only (one independent problem per GPU, no collective on
+the data path); value = DoFs processed by all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian apply GDoF/s & %HBM peak; solve s/load step, FP32-MG vs FP64 MG"
+WORKLOAD = "apply"
+L2_BYTES = 129 * 2 ** 20
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if os.environ.get("PFF_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_sets(mesh, n_sets, dtype, seed=0):
+    """n_sets independent (problem, x, y) triples with the workload's random inputs."""
+    import torch
+    from paper_2404_03265_gb300 import Problem, synth
+    X, Y, F = mesh.slots()
+    valid = (F & 1) == 1
+    info = mesh.info
+    Xv, Yv = X[valid], Y[valid]
+    u, phi, phit = synth.linearisation(Xv, Yv, info["x_max"], info["y_max"], seed=seed, u_std=1e-3)
+    xin = synth.vector(Xv, Yv, seed=seed + 1)
+    ns = info["n_slots"]
+
+    def slots(a):
+        out = np.zeros((ns,) + a.shape[1:])
+        out[valid] = a
+        return out
+
+    dev = torch.device("cuda")
+    us, ps, pts = (torch.tensor(slots(a), device=dev) for a in (u, phi, phit))
+    xs = slots(xin)
+    sets = []
+    eps = 2.0 * info["h_min"]
+    for r in range(n_sets):
+        pb = Problem(mesh, E=1.0, nu=0.2, Gc=1.0, eps=eps, kappa=1e-10, p=1e-3)
+        pb.set_state(us, ps, pts)
+        xu = torch.tensor(xs[:, :2], device=dev, dtype=dtype)
+        xp = torch.tensor(xs[:, 2], device=dev, dtype=dtype)
+        sets.append((pb, xu, xp, torch.empty_like(xu), torch.empty_like(xp)))
+    return sets
+
+
+def time_applies(sets, steps, warmup, ws):
+    import torch
+    from paper_2404_03265_gb300 import PFF_OP_JACOBIAN
+    n = len(sets)
+    for i in range(warmup):
+        pb, xu, xp, yu, yp = sets[i % n]
+        pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(steps):
+        pb, xu, xp, yu, yp = sets[i % n]
+        pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def time_e2e(mesh, dtype, steps, warmup):
+    """Same metric through the C-ABI with HOST buffers: H2D of x, apply, D2H of y per step."""
+    import torch
+    from paper_2404_03265_gb300 import PFF_OP_JACOBIAN
+    pb, xu, xp, yu, yp = build_sets(mesh, 1, dtype, seed=0)[0]
+    hxu = xu.cpu().pin_memory()
+    hxp = xp.cpu().pin_memory()
+    hyu = torch.empty_like(hxu).pin_memory()
+    hyp = torch.empty_like(hxp).pin_memory()
+    s = torch.cuda.current_stream()
+
+    def step():
+        xu.copy_(hxu, non_blocking=True)
+        xp.copy_(hxp, non_blocking=True)
+        pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+        hyu.copy_(yu, non_blocking=True)
+        hyp.copy_(yp, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    nb = hxu.numel() * hxu.element_size() + hxp.numel() * hxp.element_size()
+    return t, nb, hyu.numel() * hyu.element_size() + hyp.numel() * hyp.element_size()
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle as it stands (explicit assembly of G~ + CSR matvec, FP64), on
+    host cores, on a bounded sample: the 65,001-DoF Q1 mesh of the same box-refined
+    crack recipe (4x4 coarse, 5 global, 2 box steps), repeated within budget_s."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle import operators as ops
+    from oracle.mesh import LeafMesh, build_recipe
+    from paper_2404_03265_gb300 import synth
+    om = LeafMesh(build_recipe(synth.recipe("adjoint")), 1)
+    u, phi, phit = synth.linearisation(om.X, om.Y, om.Xmax, om.Ymax, seed=0, u_std=1e-3)
+    x = synth.vector(om.X, om.Y, seed=1)
+    v = np.concatenate([x[:, 0], x[:, 1], x[:, 2]])
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.0, eps=2.0 * om.h_min_diag(), kappa=1e-10, p=1e-3)
+    active = np.zeros(om.nn, bool)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        st = ops.State(om, u, phi, phit)
+        G = ops.assemble_jacobian(om, mat, st)
+        y = ops.constrained_operator(om, G, active) @ v
+        reps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = 1
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max([d.get("num_threads", 1) for d in info] + [1])
+    except Exception:
+        pass
+    return {"value": 3 * om.nn * reps / dt / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle G~x (FP64 element assembly + CSR matvec) on the 65,001-DoF Q1 mesh of the same "
+                      "box-refined crack recipe, %d repetitions in %.1f s; os.cpu_count()=%d"
+                      % (reps, dt, os.cpu_count() or 0)}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(budget_s=max(5.0, 1.0 * max(args.steps, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GDoF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle on the 65,001-DoF sample of the box-refined crack recipe"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2404_03265_gb300 import Mesh, synth
+    from paper_2404_03265_gb300 import _lib
+
+    mesh = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(1)
+    info = mesh.info
+    dofs = 3 * info["n_nodes"]
+    n_slots = info["n_slots"]
+    per_set_bytes = n_slots * (16 + 12 + 12)
+    n_sets = max(2, int(np.ceil(2.2 * L2_BYTES / per_set_bytes)))
+    sets = build_sets(mesh, n_sets, torch.float32, seed=0)
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t = time_applies(sets, args.steps, args.warmup, ws)
+    clocks = sampler.stop() if sampler else None
+    t = max_over_ranks(ws, t)
+    value = ws * dofs * args.steps / t / 1e9
+    ms = 1e3 * t / args.steps
+    del sets
+
+    # FP64 apply (FP64-ALU bound on GB300), fewer steps
+    sets64 = build_sets(mesh, max(2, n_sets // 2), torch.float64, seed=0)
+    k64 = max(5, args.steps // 10)
+    t64 = time_applies(sets64, k64, 3, 1)
+    g64 = dofs * k64 / t64 / 1e9
+    del sets64
+
+    te, bi, bo = time_e2e(mesh, torch.float32, max(10, args.steps // 4), 3)
+    e2e = ws * dofs * max(10, args.steps // 4) / max_over_ranks(ws, te) / 1e9
+
+    if rank != 0:
+        return
+    hbm, peak_kind = load_peaks()
+    alg_bytes = info["n_nodes"] * 10 * 4  # x (3), y (3), linearisation (4) per node, FP32
+    achieved = alg_bytes / (t / args.steps) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "apply_q1_f32_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "apply: 16x16 coarse on (-10,10)^2, 6 global + 2 box refinements (|x|<=2,|y|<=1), "
+                               "Q1 u and phi, %d DoFs; phi~U[0,1], u~N(0,1e-3), x~N(0,1), seed 0" % dofs,
+                   "fe_degree": 1, "dofs": dofs, "op": "constrained Jacobian y = G~ x",
+                   "l2": "%d rotating input sets of %.0f MB (> L2 129 MB)" % (n_sets, per_set_bytes / 1e6),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "note": "achieved = 40 B/node x nodes per launch / avg pff_apply duration (apply kernel + "
+                             "interface fix-up kernel)"},
+        "f64_apply": {"value": g64, "unit": "GDoF/s", "steps": k64,
+                      "hbm_frac": info["n_nodes"] * 80 / (t64 / k64) / 1e9 / hbm},
+        "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

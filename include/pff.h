@@ -1,0 +1,145 @@
+/*
+ * libpff: GB300-native hot path of the matrix-free, GMG-preconditioned
+ * Newton-GMRES solver for quasi-static phase-field fracture of Kolditz & Wick,
+ * "Matrix-free geometric multigrid preconditioning of combined Newton-GMRES for
+ * solving phase-field fracture with local mesh refinement" (arXiv 2404.03265).
+ *
+ * Conventions
+ * -----------
+ * - Every call returns pff_status (0 = PFF_OK).  No exception crosses the ABI.
+ *   pff_last_error() returns a thread-local message for the last failure.
+ * - Handles (pff_mesh, pff_problem) are owned by the library; destroy them with
+ *   the matching *_destroy call.  Device tables of a mesh are allocated by the
+ *   library (cudaMalloc) on the CUDA device current at pff_problem_create.
+ * - Vectors are caller-owned DEVICE pointers in the library's node layout:
+ *   n_slots entries (pff_mesh_info.n_slots), one per node slot.  Slots that hold
+ *   no node ("holes", pff_mesh_slots flags bit0 clear) are ignored on input and
+ *   written as 0 on output.  A displacement vector is interleaved (u_x, u_y) per
+ *   slot (2*n_slots values), a phase-field vector has one value per slot.
+ *   Values of hanging nodes are ignored on input (they follow from the
+ *   constraint) and written as 0 by operators.
+ * - stream is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *   device work is stream-ordered and asynchronous unless stated otherwise.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pff_status;
+enum {
+  PFF_OK = 0,
+  PFF_ERR_INVALID_ARG = 1,
+  PFF_ERR_CUDA = 2,
+  PFF_ERR_OOM = 3,
+  PFF_ERR_NOT_CONVERGED = 4,
+  PFF_ERR_GMRES_BREAKDOWN = 5,
+  PFF_ERR_NONFINITE = 6,
+  PFF_ERR_LINESEARCH = 7,
+  PFF_ERR_TIMEOUT = 8,
+  PFF_ERR_STATE = 9
+};
+
+enum { PFF_F64 = 0, PFF_F32 = 1 };
+
+/* Operator selector of pff_apply. */
+enum {
+  PFF_OP_JACOBIAN = 0,   /* y = G~ x  (constrained Jacobian, Sec. 3.1 / 3.2)           */
+  PFF_OP_TRANSPOSE = 1,  /* y = G~^T x (vector-Jacobian product)                        */
+  PFF_OP_CONDENSED = 2   /* y = M_f C^T G C x: fixed inputs NOT masked, fixed rows 0     */
+};
+
+typedef struct pff_mesh pff_mesh;
+typedef struct pff_problem pff_problem;
+
+typedef struct pff_mesh_info {
+  int64_t n_slots;       /* length of a node vector                                   */
+  int64_t n_nodes;       /* leaf-mesh nodes (incl. hanging); DoFs = 3 * n_nodes        */
+  int64_t n_leaf_cells;
+  int64_t n_hanging;
+  int64_t n_partials;    /* interface partial sums of one apply                       */
+  int64_t n_bricks;
+  int64_t n_irregular;   /* bricks that read explicit index tables                    */
+  int64_t x_max, y_max;  /* integer node coordinates run over 0..x_max, 0..y_max       */
+  double h_min;          /* diagonal of the finest leaf cell                          */
+  int32_t fe_degree;
+  int32_t finest_level;  /* levels 0..finest_level                                    */
+} pff_mesh_info;
+
+/* Material and solver parameters (Table 1 of the paper; Problems 1 and 2). */
+typedef struct pff_params {
+  double E;       /* Young's modulus                                       */
+  double nu;      /* Poisson ratio (plane strain Lame constants)            */
+  double Gc;      /* critical energy release rate G_c                        */
+  double eps;     /* length scale l                                          */
+  double kappa;   /* regularisation in g(phi) = (1-kappa) phi^2 + kappa      */
+  double p;       /* pressure                                                */
+  double c;       /* primal-dual active set constant                        */
+} pff_params;
+
+const char* pff_last_error(void);
+
+/* ---- mesh (host) ----------------------------------------------------------
+ * Quadtree on [x0,x1] x [y0,y1] with ncx x ncy coarse cells (level 0).
+ * Refinement keeps a 2:1 face balance (Sec. 3: hanging nodes).  Marks refer to
+ * leaves in canonical order: ascending (level, j, i).
+ * rule 0: refine leaves whose centre x0 + (i + 1/2) hx_l lies in the closed box;
+ * rule 1: refine leaves whose closed cell meets the closed box.
+ * pff_mesh_finalize builds nodes, hanging constraints, the brick layout and the
+ * multigrid level meshes for Q_k elements, k = fe_degree in {1, 2}.
+ * Errors: PFF_ERR_INVALID_ARG on bad sizes, PFF_ERR_STATE on refine after
+ * finalize.                                                                   */
+pff_status pff_mesh_create(double x0, double x1, double y0, double y1, int32_t ncx, int32_t ncy,
+                           pff_mesh** out);
+pff_status pff_mesh_refine_global(pff_mesh* m, int32_t times);
+pff_status pff_mesh_refine_box(pff_mesh* m, int32_t rule, double bx0, double bx1, double by0,
+                               double by1);
+pff_status pff_mesh_refine_marked(pff_mesh* m, const uint8_t* marks_host, int64_t n_leaves);
+pff_status pff_mesh_n_leaves(const pff_mesh* m, int64_t* n);
+pff_status pff_mesh_finalize(pff_mesh* m, int32_t fe_degree);
+pff_status pff_mesh_info_get(const pff_mesh* m, pff_mesh_info* out);
+/* Host arrays of n_slots entries: integer node coordinates (-1 for holes) and
+ * flags (bit0 node, bit1 on the boundary (Dirichlet u), bit2 hanging).         */
+pff_status pff_mesh_slots(const pff_mesh* m, int32_t* X, int32_t* Y, uint8_t* flags);
+/* Host array 3*n_leaf_cells: (level, i, j) per leaf cell, canonical order.       */
+pff_status pff_mesh_leaf_cells(const pff_mesh* m, int32_t* lij);
+void pff_mesh_destroy(pff_mesh* m);
+
+/* ---- problem --------------------------------------------------------------
+ * Binds parameters to a finalized mesh and uploads its device tables.          */
+pff_status pff_problem_create(pff_mesh* m, const pff_params* prm, pff_problem** out);
+void pff_problem_destroy(pff_problem* pb);
+
+/* Linearisation point U^k = (u, phi) and phi_tilde (Sec. 2: the degradation of
+ * the u-equation uses phi_tilde).  u: 2*n_slots doubles, phi, phi_tilde:
+ * n_slots doubles (device).  Hanging entries are replaced by their constraint.
+ * The library keeps FP64 and FP32 copies.                                      */
+pff_status pff_set_state(pff_problem* pb, const double* u, const double* phi, const double* phi_tilde,
+                         void* stream);
+
+/* Active set of the phase field (Algorithm 2): active[s] != 0 marks the phi DoF
+ * of slot s as fixed (identity row and column).  Device array of n_slots bytes;
+ * entries on hanging nodes and holes are ignored.                              */
+pff_status pff_set_active(pff_problem* pb, const uint8_t* active, void* stream);
+
+/* Matrix-free operator (Sec. 3.1 Jacobian, Sec. 3.3 matrix-free cell loop):
+ *   PFF_OP_JACOBIAN  y = G~ x,   G~ = M_f C^T G C M_f + I_fixed
+ *   PFF_OP_TRANSPOSE y = G~^T x
+ *   PFF_OP_CONDENSED y = M_f C^T G C x
+ * G: unconstrained Jacobian at the state; C: hanging-node constraints; M_f:
+ * free (not Dirichlet, not active, not hanging) DoFs; I_fixed: identity on
+ * Dirichlet u and active phi DoFs.  precision PFF_F64: double vectors, PFF_F32:
+ * float vectors (state cast to float).  xu/yu: 2*n_slots, xp/yp: n_slots.
+ * x and y must not overlap.                                                    */
+pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
+                     void* yu, void* yp, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFF_H */

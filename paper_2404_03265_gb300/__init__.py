@@ -1,0 +1,107 @@
+"""GB300-native hot path of the matrix-free, GMG-preconditioned Newton-GMRES
+phase-field fracture solver of Kolditz & Wick (arXiv 2404.03265).
+
+The compute path is ``libpff.so`` (hand-written CUDA for sm_103a behind the
+C-ABI of ``include/pff.h``).  ``Mesh`` and ``Problem`` below only marshal
+arguments; torch supplies device memory and streams.
+"""
+import numpy as np
+
+from . import _lib
+from ._lib import PFF_F32, PFF_F64, PFF_OP_CONDENSED, PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, PffError
+
+
+class Mesh:
+    """Quadtree mesh with 2:1 balance (libpff host side)."""
+
+    def __init__(self, x0, x1, y0, y1, ncx, ncy):
+        L = _lib.lib()
+        h = _lib.ctypes.c_void_p()
+        _lib.check(L.pff_mesh_create(x0, x1, y0, y1, ncx, ncy, _lib.ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_recipe(cls, rec):
+        d = rec["domain"]
+        m = cls(d[0], d[1], d[2], d[3], rec["ncx"], rec["ncy"])
+        m.refine_global(rec["n_global"])
+        for step in rec["steps"]:
+            m.refine_box(0 if step[0] == "box" else 1, *step[1:])
+        return m
+
+    def refine_global(self, times=1):
+        _lib.check(_lib.lib().pff_mesh_refine_global(self._h, times))
+
+    def refine_box(self, rule, bx0, bx1, by0, by1):
+        _lib.check(_lib.lib().pff_mesh_refine_box(self._h, rule, bx0, bx1, by0, by1))
+
+    def refine_marked(self, marks):
+        m = np.ascontiguousarray(marks, dtype=np.uint8)
+        _lib.check(_lib.lib().pff_mesh_refine_marked(self._h, _lib.ptr(m), m.size))
+
+    def n_leaves(self):
+        n = _lib.ctypes.c_int64()
+        _lib.check(_lib.lib().pff_mesh_n_leaves(self._h, _lib.ctypes.byref(n)))
+        return n.value
+
+    def finalize(self, fe_degree=1):
+        _lib.check(_lib.lib().pff_mesh_finalize(self._h, fe_degree))
+        self.info = self.get_info()
+        return self
+
+    def get_info(self):
+        inf = _lib.MeshInfo()
+        _lib.check(_lib.lib().pff_mesh_info_get(self._h, _lib.ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def slots(self):
+        n = self.info["n_slots"]
+        X = np.empty(n, np.int32)
+        Y = np.empty(n, np.int32)
+        F = np.empty(n, np.uint8)
+        _lib.check(_lib.lib().pff_mesh_slots(self._h, _lib.ptr(X), _lib.ptr(Y), _lib.ptr(F)))
+        return X, Y, F
+
+    def leaf_cells(self):
+        n = self.info["n_leaf_cells"]
+        a = np.empty((n, 3), np.int32)
+        _lib.check(_lib.lib().pff_mesh_leaf_cells(self._h, _lib.ptr(a)))
+        return a
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.lib().pff_mesh_destroy(h)
+            self._h = None
+
+
+class Problem:
+    """Parameters bound to a mesh; owns the linearisation and constraint masks on the GPU."""
+
+    def __init__(self, mesh, E=1.0, nu=0.2, Gc=1.0, eps=1.0, kappa=1e-10, p=1e-3, c=1e4):
+        self.mesh = mesh
+        prm = _lib.Params(E, nu, Gc, eps, kappa, p, c)
+        h = _lib.ctypes.c_void_p()
+        _lib.check(_lib.lib().pff_problem_create(mesh._h, _lib.ctypes.byref(prm), _lib.ctypes.byref(h)))
+        self._h = h
+        self.n_slots = mesh.info["n_slots"]
+
+    def set_state(self, u, phi, phit, stream=None):
+        """u: float64 (n_slots, 2), phi, phit: float64 (n_slots,) CUDA tensors."""
+        _lib.check(_lib.lib().pff_set_state(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phit),
+                                            _lib.stream_ptr(stream)))
+
+    def set_active(self, active, stream=None):
+        _lib.check(_lib.lib().pff_set_active(self._h, _lib.ptr(active), _lib.stream_ptr(stream)))
+
+    def apply(self, xu, xp, yu, yp, op=PFF_OP_JACOBIAN, stream=None):
+        import torch
+        prec = PFF_F64 if xu.dtype == torch.float64 else PFF_F32
+        _lib.check(_lib.lib().pff_apply(self._h, prec, op, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(yu),
+                                        _lib.ptr(yp), _lib.stream_ptr(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.lib().pff_problem_destroy(h)
+            self._h = None

@@ -1,0 +1,99 @@
+"""ctypes binding of libpff (include/pff.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library; this module converts
+Python / torch arguments into plain pointers and sizes.  If ``libpff.so`` has
+not been built the import of the binding fails loudly (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libpff.so")
+
+PFF_OK = 0
+PFF_F64, PFF_F32 = 0, 1
+PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, PFF_OP_CONDENSED = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "GMRES_BREAKDOWN",
+                6: "NONFINITE", 7: "LINESEARCH", 8: "TIMEOUT", 9: "STATE"}
+
+
+class PffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libpff %s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_leaf_cells", ctypes.c_int64),
+                ("n_hanging", ctypes.c_int64), ("n_partials", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
+                ("n_irregular", ctypes.c_int64), ("x_max", ctypes.c_int64), ("y_max", ctypes.c_int64),
+                ("h_min", ctypes.c_double), ("fe_degree", ctypes.c_int32), ("finest_level", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("Gc", ctypes.c_double), ("eps", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("p", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = [
+    ("pff_last_error", ctypes.c_char_p, []),
+    ("pff_mesh_create", ctypes.c_int32, [ctypes.c_double] * 4 + [ctypes.c_int32] * 2 + [ctypes.POINTER(_P)]),
+    ("pff_mesh_refine_global", ctypes.c_int32, [_P, ctypes.c_int32]),
+    ("pff_mesh_refine_box", ctypes.c_int32, [_P, ctypes.c_int32] + [ctypes.c_double] * 4),
+    ("pff_mesh_refine_marked", ctypes.c_int32, [_P, _P, ctypes.c_int64]),
+    ("pff_mesh_n_leaves", ctypes.c_int32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    ("pff_mesh_finalize", ctypes.c_int32, [_P, ctypes.c_int32]),
+    ("pff_mesh_info_get", ctypes.c_int32, [_P, ctypes.POINTER(MeshInfo)]),
+    ("pff_mesh_slots", ctypes.c_int32, [_P, _P, _P, _P]),
+    ("pff_mesh_leaf_cells", ctypes.c_int32, [_P, _P]),
+    ("pff_mesh_destroy", None, [_P]),
+    ("pff_problem_create", ctypes.c_int32, [_P, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    ("pff_problem_destroy", None, [_P]),
+    ("pff_set_state", ctypes.c_int32, [_P, _P, _P, _P, _P]),
+    ("pff_set_active", ctypes.c_int32, [_P, _P, _P]),
+    ("pff_apply", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P]),
+]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise ImportError("libpff.so is not built: run `python -c \"import __graft_entry__ as g; g.build()\"`")
+        L = ctypes.CDLL(LIBPATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def check(status):
+    if status != PFF_OK:
+        raise PffError(status, lib().pff_last_error().decode())
+
+
+def ptr(t):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream

@@ -1,0 +1,266 @@
+// C-ABI entry points of libpff (declared in include/pff.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pff.h"
+#include "kernels.cuh"
+#include "mesh.h"
+#include "state.h"
+
+using namespace pff;
+
+namespace {
+thread_local std::string g_err;
+
+pff_status fail(pff_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define PFF_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? PFF_ERR_OOM : PFF_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+#define PFF_TRY(...)                                               \
+  try {                                                            \
+    __VA_ARGS__                                                    \
+  } catch (const std::bad_alloc&) {                                \
+    return fail(PFF_ERR_OOM, "host allocation failed");            \
+  } catch (const std::exception& ex) {                             \
+    return fail(PFF_ERR_INVALID_ARG, ex.what());                   \
+  } catch (...) {                                                  \
+    return fail(PFF_ERR_INVALID_ARG, "unknown exception");         \
+  }
+
+}  // namespace
+
+extern "C" const char* pff_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ mesh
+extern "C" pff_status pff_mesh_create(double x0, double x1, double y0, double y1, int32_t ncx, int32_t ncy,
+                                      pff_mesh** out) {
+  PFF_TRY({
+    if (!out) return fail(PFF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(x1 > x0) || !(y1 > y0) || ncx <= 0 || ncy <= 0 || ncx > 4096 || ncy > 4096)
+      return fail(PFF_ERR_INVALID_ARG, "invalid domain or coarse grid");
+    auto* m = new pff_mesh();
+    Tree& t = m->m.tree;
+    t.x0 = x0; t.x1 = x1; t.y0 = y0; t.y1 = y1; t.ncx = ncx; t.ncy = ncy;
+    t.lev.emplace_back();
+    for (int j = 0; j < ncy; ++j)
+      for (int i = 0; i < ncx; ++i) t.lev[0].insert(cell_key(i, j));
+    *out = m;
+    return PFF_OK;
+  })
+}
+
+static pff_status check_refinable(pff_mesh* m) {
+  if (!m) return fail(PFF_ERR_INVALID_ARG, "mesh is NULL");
+  if (m->m.finalized) return fail(PFF_ERR_STATE, "mesh already finalized");
+  if (m->m.tree.finest() >= 24) return fail(PFF_ERR_INVALID_ARG, "more than 24 refinement levels");
+  return PFF_OK;
+}
+
+extern "C" pff_status pff_mesh_refine_global(pff_mesh* m, int32_t times) {
+  PFF_TRY({
+    pff_status st = check_refinable(m);
+    if (st) return st;
+    if (times < 0) return fail(PFF_ERR_INVALID_ARG, "times < 0");
+    for (int r = 0; r < times; ++r) {
+      auto lv = m->m.tree.leaves();
+      for (auto& c : lv) m->m.tree.split(int(c[0]), c[1], c[2]);
+      m->m.tree.balance();
+      if (m->m.tree.finest() >= 24) return fail(PFF_ERR_INVALID_ARG, "more than 24 refinement levels");
+    }
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_refine_box(pff_mesh* m, int32_t rule, double bx0, double bx1, double by0,
+                                          double by1) {
+  PFF_TRY({
+    pff_status st = check_refinable(m);
+    if (st) return st;
+    if (rule != 0 && rule != 1) return fail(PFF_ERR_INVALID_ARG, "rule must be 0 or 1");
+    Tree& t = m->m.tree;
+    auto lv = t.leaves();
+    std::vector<std::array<int64_t, 3>> marks;
+    for (auto& c : lv) {
+      const int l = int(c[0]);
+      const double hx = t.hx(l), hy = t.hy(l);
+      bool hit;
+      if (rule == 0) {
+        const double xc = t.x0 + (double(c[1]) + 0.5) * hx, yc = t.y0 + (double(c[2]) + 0.5) * hy;
+        hit = bx0 <= xc && xc <= bx1 && by0 <= yc && yc <= by1;
+      } else {
+        const double xa = t.x0 + double(c[1]) * hx, xb = t.x0 + double(c[1] + 1) * hx;
+        const double ya = t.y0 + double(c[2]) * hy, yb = t.y0 + double(c[2] + 1) * hy;
+        hit = xa <= bx1 && xb >= bx0 && ya <= by1 && yb >= by0;
+      }
+      if (hit) marks.push_back(c);
+    }
+    for (auto& c : marks) t.split(int(c[0]), c[1], c[2]);
+    t.balance();
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_refine_marked(pff_mesh* m, const uint8_t* marks, int64_t n_leaves) {
+  PFF_TRY({
+    pff_status st = check_refinable(m);
+    if (st) return st;
+    auto lv = m->m.tree.leaves();
+    if (!marks || n_leaves != int64_t(lv.size())) return fail(PFF_ERR_INVALID_ARG, "marks length != leaves");
+    for (size_t q = 0; q < lv.size(); ++q)
+      if (marks[q]) m->m.tree.split(int(lv[q][0]), lv[q][1], lv[q][2]);
+    m->m.tree.balance();
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_n_leaves(const pff_mesh* m, int64_t* n) {
+  PFF_TRY({
+    if (!m || !n) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    *n = m->m.finalized ? int64_t(m->m.leaves.size()) : int64_t(m->m.tree.leaves().size());
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_finalize(pff_mesh* m, int32_t fe_degree) {
+  PFF_TRY({
+    if (!m) return fail(PFF_ERR_INVALID_ARG, "mesh is NULL");
+    if (m->m.finalized) return fail(PFF_ERR_STATE, "mesh already finalized");
+    if (fe_degree != 1 && fe_degree != 2) return fail(PFF_ERR_INVALID_ARG, "fe_degree must be 1 or 2");
+    std::string e = finalize_mesh(m->m, fe_degree);
+    if (!e.empty()) return fail(PFF_ERR_INVALID_ARG, e);
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_info_get(const pff_mesh* m, pff_mesh_info* out) {
+  PFF_TRY({
+    if (!m || !out) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!m->m.finalized) return fail(PFF_ERR_STATE, "mesh not finalized");
+    const Mesh& M = m->m;
+    std::memset(out, 0, sizeof(*out));
+    out->n_slots = M.lay.n_slots;
+    out->n_nodes = M.n_nodes();
+    out->n_leaf_cells = int64_t(M.leaves.size());
+    out->n_hanging = int64_t(M.hang.size());
+    out->n_partials = M.n_partials;
+    out->n_bricks = int64_t(M.lay.bricks.size());
+    out->n_irregular = M.lay.n_irregular();
+    out->x_max = M.Xmax;
+    out->y_max = M.Ymax;
+    out->h_min = M.hmin_diag();
+    out->fe_degree = M.k;
+    out->finest_level = M.Lf;
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_slots(const pff_mesh* m, int32_t* X, int32_t* Y, uint8_t* flags) {
+  PFF_TRY({
+    if (!m) return fail(PFF_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->m.finalized) return fail(PFF_ERR_STATE, "mesh not finalized");
+    const Mesh& M = m->m;
+    for (int64_t s = 0; s < M.lay.n_slots; ++s) {
+      const int32_t n = M.slot_node[s];
+      if (X) X[s] = n < 0 ? -1 : M.nX[n];
+      if (Y) Y[s] = n < 0 ? -1 : M.nY[n];
+      if (flags) flags[s] = M.slot_flags[s] & 7;
+    }
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mesh_leaf_cells(const pff_mesh* m, int32_t* lij) {
+  PFF_TRY({
+    if (!m || !lij) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!m->m.finalized) return fail(PFF_ERR_STATE, "mesh not finalized");
+    for (size_t q = 0; q < m->m.leaves.size(); ++q)
+      for (int r = 0; r < 3; ++r) lij[3 * q + r] = int32_t(m->m.leaves[q][r]);
+    return PFF_OK;
+  })
+}
+
+extern "C" void pff_mesh_destroy(pff_mesh* m) {
+  if (!m) return;
+  m->dev.release();
+  delete m;
+}
+
+// ------------------------------------------------------------------ problem
+extern "C" pff_status pff_problem_create(pff_mesh* m, const pff_params* prm, pff_problem** out) {
+  PFF_TRY({
+    if (!m || !prm || !out) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!m->m.finalized) return fail(PFF_ERR_STATE, "mesh not finalized");
+    if (!(prm->E > 0) || !(prm->nu > -1.0 && prm->nu < 0.5) || !(prm->Gc > 0) || !(prm->eps > 0) ||
+        !(prm->kappa >= 0 && prm->kappa < 1))
+      return fail(PFF_ERR_INVALID_ARG, "invalid material parameters");
+    std::string e = upload_mesh(*m);
+    if (!e.empty()) return fail(PFF_ERR_CUDA, e);
+    auto* pb = new pff_problem();
+    pb->mesh = m;
+    pb->prm = *prm;
+    e = alloc_problem(*pb);
+    if (!e.empty()) {
+      delete pb;
+      return fail(PFF_ERR_OOM, e);
+    }
+    *out = pb;
+    return PFF_OK;
+  })
+}
+
+extern "C" void pff_problem_destroy(pff_problem* pb) {
+  if (!pb) return;
+  pb->bufs.release();
+  delete pb;
+}
+
+extern "C" pff_status pff_set_state(pff_problem* pb, const double* u, const double* phi, const double* phit,
+                                    void* stream) {
+  PFF_TRY({
+    if (!pb || !u || !phi || !phit) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    const Mesh& M = pb->mesh->m;
+    const DevMesh& D = pb->mesh->dev;
+    PFF_CUDA(launch_set_lin(M.lay.n_slots, u, phi, phit, D.hang, D.nhang, M.k, pb->lin64, pb->lin32,
+                            cudaStream_t(stream)));
+    pb->has_state = true;
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_set_active(pff_problem* pb, const uint8_t* active, void* stream) {
+  PFF_TRY({
+    if (!pb || !active) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    PFF_CUDA(launch_leaf_cmask(pb->mesh->m.lay.n_slots, pb->mesh->dev.slot_flags, active, pb->cmask,
+                               cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
+                                void* yu, void* yp, void* stream) {
+  PFF_TRY({
+    if (!pb || !xu || !xp || !yu || !yp) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (precision != PFF_F64 && precision != PFF_F32) return fail(PFF_ERR_INVALID_ARG, "bad precision");
+    if (op < 0 || op > 2) return fail(PFF_ERR_INVALID_ARG, "bad operator");
+    if (!pb->has_state) return fail(PFF_ERR_STATE, "pff_set_state has not been called");
+    if (xu == yu || xp == yp) return fail(PFF_ERR_INVALID_ARG, "x and y overlap");
+    PFF_CUDA(leaf_apply(*pb, precision, op, xu, xp, yu, yp, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}

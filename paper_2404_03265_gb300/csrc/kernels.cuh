@@ -1,0 +1,90 @@
+// Device-side argument blocks and launch wrappers of libpff's CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "mesh.h"
+
+namespace pff {
+
+constexpr int kMaxLevels = 32;
+
+// four doubles, 32-byte aligned (linearisation (u_x, u_y, phi, phi_tilde) per slot)
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+
+// Operator selector of the brick kernels.
+enum OpKind : int {
+  OP_FULL = 0,     // leaf Jacobian A'(U) (Sec. 3.1), 3 components, block lower triangular
+  OP_FULL_T = 1,   // its transpose (VJP)
+  OP_UU = 2,       // diagonal block uu of a level operator (Sec. 3.2)
+  OP_PP = 3,       // diagonal block phi-phi of a level operator
+  OP_UU_DIAG = 4,  // diagonal of the uu block (Chebyshev-Jacobi, Sec. 3.2)
+  OP_PP_DIAG = 5,  // diagonal of the phi-phi block
+};
+
+// mode bits
+constexpr int MODE_MASK_INPUT = 1;   // fixed components of x read as 0
+constexpr int MODE_IDENTITY = 2;     // fixed rows: y = x (else y = 0)
+
+struct DevHanging {
+  int32_t slot;
+  int32_t parent[3];
+  double weight[3];
+};
+
+struct DevLayout {
+  const BrickDesc* bricks = nullptr;
+  int32_t nbricks = 0;
+  const int32_t* win = nullptr;
+  const int32_t* own_part = nullptr;
+  const uint8_t* own_act = nullptr;
+  const uint32_t* cellmask = nullptr;
+};
+
+struct ApplyArgs {
+  DevLayout lay;
+  const DevHanging* hang;
+  const uint8_t* cmask;   // per slot: bit0/bit1 u_x/u_y fixed, bit2 phi fixed
+  const void* lin;        // T4 per slot: (u_x, u_y, phi, phi_tilde), hanging entries resolved
+  const void* xu;         // T2 per slot
+  const void* xp;         // T per slot
+  void* yu;
+  void* yp;
+  void* ibuf;             // 3 T per partial slot
+  double hx[kMaxLevels], hy[kMaxLevels];
+  double mu, lam;         // Lame constants (E already applied)
+  double kappa, p, gc_over_l, gc_times_l;
+  int mode;
+  int fe_degree;
+};
+
+struct FixupArgs {
+  int32_t n;
+  const int32_t* slot;
+  const int32_t* ptr;
+  const int32_t* part;
+  const double* w;
+  const uint8_t* cmask;
+  const void* xu;
+  const void* xp;
+  void* yu;
+  void* yp;
+  const void* ibuf;
+  int mode;
+};
+
+// launchers (return cudaError_t of the launch)
+template <typename T>
+cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fixup(const FixupArgs& a, cudaStream_t s);
+
+// state conversion: lin64/lin32[slot] = (u_x, u_y, phi, phi_t) with hanging entries from parents
+cudaError_t launch_set_lin(int64_t n_slots, const double* u, const double* phi, const double* phit,
+                           const DevHanging* hang, int32_t nhang, int fe_degree,
+                           double* lin64, float* lin32, cudaStream_t s);
+
+}  // namespace pff

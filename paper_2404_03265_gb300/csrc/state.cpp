@@ -1,0 +1,123 @@
+// Device uploads and operator dispatch behind the C-ABI.
+#include "state.h"
+
+#include <cstring>
+
+namespace pff {
+
+static DevLayout upload_layout(DevAllocs& mem, const Layout& L) {
+  DevLayout d;
+  d.bricks = mem.upload(L.bricks);
+  d.nbricks = int32_t(L.bricks.size());
+  d.win = mem.upload(L.win);
+  d.own_part = mem.upload(L.own_part);
+  d.own_act = mem.upload(L.own_act);
+  d.cellmask = mem.upload(L.cellmask);
+  return d;
+}
+
+std::string upload_mesh(pff_mesh& pm) {
+  DevMesh& D = pm.dev;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+  if (D.uploaded) {
+    if (D.device != dev) return "mesh tables live on another device";
+    return "";
+  }
+  const Mesh& M = pm.m;
+  D.leaf = upload_layout(D.mem, M.lay);
+  std::vector<DevHanging> hh(M.hang.size());
+  for (size_t h = 0; h < M.hang.size(); ++h) {
+    hh[h].slot = M.hang[h].slot;
+    for (int b = 0; b < 3; ++b) {
+      hh[h].parent[b] = M.hang[h].parent[b];
+      hh[h].weight[b] = M.hang[h].weight[b];
+    }
+  }
+  D.hang = D.mem.upload(hh);
+  D.nhang = int32_t(hh.size());
+  D.nfix = int32_t(M.fix_slot.size());
+  D.fix_slot = D.mem.upload(M.fix_slot);
+  D.fix_ptr = D.mem.upload(M.fix_ptr);
+  D.fix_part = D.mem.upload(M.fix_part);
+  D.fix_w = D.mem.upload(M.fix_w);
+  D.slot_flags = D.mem.upload(M.slot_flags);
+  if (!D.mem.err.empty()) {
+    std::string err = D.mem.err;
+    D.release();
+    return err;
+  }
+  D.uploaded = true;
+  D.device = dev;
+  return "";
+}
+
+std::string alloc_problem(pff_problem& pb) {
+  const Mesh& M = pb.mesh->m;
+  const int64_t ns = M.lay.n_slots;
+  pb.lin64 = pb.bufs.alloc<double>(4 * ns);
+  pb.lin32 = pb.bufs.alloc<float>(4 * ns);
+  pb.cmask = pb.bufs.alloc<uint8_t>(ns);
+  pb.ibuf64 = pb.bufs.alloc<double>(3 * M.n_partials);
+  pb.ibuf32 = pb.bufs.alloc<float>(3 * M.n_partials);
+  if (!pb.bufs.err.empty()) {
+    std::string err = pb.bufs.err;
+    pb.bufs.release();
+    return err;
+  }
+  cudaMemset(pb.lin64, 0, 4 * ns * sizeof(double));
+  cudaMemset(pb.lin32, 0, 4 * ns * sizeof(float));
+  const cudaError_t e = launch_leaf_cmask(ns, pb.mesh->dev.slot_flags, nullptr, pb.cmask, 0);
+  if (e != cudaSuccess) return std::string("cmask: ") + cudaGetErrorString(e);
+  cudaError_t e2 = cudaDeviceSynchronize();
+  if (e2 != cudaSuccess) return std::string("sync: ") + cudaGetErrorString(e2);
+  return "";
+}
+
+void fill_material(const pff_params& prm, ApplyArgs& a) {
+  a.mu = prm.E / (2.0 * (1.0 + prm.nu));
+  a.lam = prm.E * prm.nu / ((1.0 + prm.nu) * (1.0 - 2.0 * prm.nu));
+  a.kappa = prm.kappa;
+  a.p = prm.p;
+  a.gc_over_l = prm.Gc / prm.eps;
+  a.gc_times_l = prm.Gc * prm.eps;
+}
+
+cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, const void* xp, void* yu,
+                       void* yp, cudaStream_t s) {
+  const Mesh& M = pb.mesh->m;
+  const DevMesh& D = pb.mesh->dev;
+  ApplyArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.lay = D.leaf;
+  a.hang = D.hang;
+  a.cmask = pb.cmask;
+  a.lin = precision == PFF_F64 ? static_cast<const void*>(pb.lin64) : static_cast<const void*>(pb.lin32);
+  a.xu = xu; a.xp = xp; a.yu = yu; a.yp = yp;
+  a.ibuf = precision == PFF_F64 ? static_cast<void*>(pb.ibuf64) : static_cast<void*>(pb.ibuf32);
+  for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) {
+    a.hx[l] = M.tree.hx(l);
+    a.hy[l] = M.tree.hy(l);
+  }
+  fill_material(pb.prm, a);
+  a.fe_degree = M.k;
+  int kop = OP_FULL;
+  if (op == PFF_OP_JACOBIAN) { kop = OP_FULL; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }
+  else if (op == PFF_OP_TRANSPOSE) { kop = OP_FULL_T; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }
+  else { kop = OP_FULL; a.mode = 0; }
+  FixupArgs f;
+  f.n = D.nfix; f.slot = D.fix_slot; f.ptr = D.fix_ptr; f.part = D.fix_part; f.w = D.fix_w;
+  f.cmask = pb.cmask; f.xu = xu; f.xp = xp; f.yu = yu; f.yp = yp; f.ibuf = a.ibuf; f.mode = a.mode;
+  cudaError_t e;
+  if (precision == PFF_F64) {
+    e = launch_apply<double>(a, kop, s);
+    if (e == cudaSuccess) e = launch_fixup<double>(f, s);
+  } else {
+    e = launch_apply<float>(a, kop, s);
+    if (e == cudaSuccess) e = launch_fixup<float>(f, s);
+  }
+  return e;
+}
+
+}  // namespace pff

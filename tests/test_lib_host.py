@@ -1,0 +1,69 @@
+"""Host-side checks of libpff (no GPU): the C-ABI library loads, exports every
+symbol that include/pff.h declares, and its quadtree / node / constraint
+construction agrees with the independent oracle mesh."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "pff.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(pff_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_03265_gb300 import _lib
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2404_03265_gb300 import _lib
+    assert set(names) <= set(_lib.exported_names()) | {"pff_params_default"}
+
+
+@pytest.mark.parametrize("name,k", [("tiny", 1), ("small", 1), ("tiny", 2), ("small", 2), ("band4_2_4", 1),
+                                    ("band4_2_4", 2)])
+def test_mesh_matches_oracle(name, k):
+    from harness import Pair
+    P = Pair(name, k)
+    om, lm = P.om, P.lm
+    inf = lm.info
+    assert inf["n_nodes"] == om.nn
+    assert inf["n_leaf_cells"] == len(om.cells)
+    assert inf["n_hanging"] == len(om.hanging)
+    assert inf["x_max"] == om.Xmax and inf["y_max"] == om.Ymax
+    assert abs(inf["h_min"] - om.h_min_diag()) < 1e-15
+    F = P.slot_F[P.slots]
+    # hanging and boundary flags agree node by node
+    assert np.array_equal((F & 4) != 0, om.is_hanging[P.onode])
+    assert np.array_equal((F & 2) != 0, om.dirichlet[P.onode])
+    # leaf cells in canonical order
+    assert np.array_equal(lm.leaf_cells(), om.cells.astype(np.int32))
+
+
+def test_refine_marked_and_errors():
+    from paper_2404_03265_gb300 import Mesh, PffError
+    m = Mesh(-1, 1, -1, 1, 2, 2)
+    m.refine_global(1)
+    n = m.n_leaves()
+    marks = np.zeros(n, np.uint8)
+    marks[0] = 1
+    m.refine_marked(marks)
+    with pytest.raises(PffError):
+        m.refine_marked(np.zeros(3, np.uint8))
+    m.finalize(1)
+    with pytest.raises(PffError):
+        m.refine_global(1)
+    with pytest.raises(PffError):
+        Mesh(1, -1, 0, 1, 1, 1)

@@ -115,17 +115,6 @@ __device__ __forceinline__ void q1_test_val(const T fv[2][2], T w, T r[4]) {
   r[3] += w * pt;
 }
 
-template <typename T>
-struct CellConst {
-  T ihx, ihy;          // 1/hx, 1/hy
-  T c2ml, cl, cm;      // 2 mu + lambda, lambda, mu
-  T omk, kap, p;       // 1 - kappa, kappa, p
-  T gcl, gcL;          // G_c / l, G_c l
-  T jxw;               // hx hy / 4
-  T wx, wy;            // JxW / hx, JxW / hy
-  T wpx, wpy;          // 2 G_c l JxW / hx^2, 2 G_c l JxW / hy^2
-};
-
 // One Q1 cell.  Window node indices n0 (0,0), n0+1, n0+WN, n0+WN+1.
 // out[3*A + c] (c: 0 u_x, 1 u_y, 2 phi) for OP_FULL/OP_FULL_T; for OP_UU the
 // first two components, for OP_PP only component 2 is meaningful.
@@ -253,7 +242,7 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
         gx[q1][q2] = fxp.dxi[q2];
         gy[q1][q2] = fxp.deta[q1];
       }
-    q1_test_grad(gx, gy, T(0.5) * c.wpx, T(0.5) * c.wpy, rp);
+    q1_test_grad(gx, gy, c.wpx, c.wpy, rp);
   }
 #pragma unroll
   for (int A = 0; A < 4; ++A) {
@@ -264,8 +253,15 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
   (void)needU; (void)needP;
 }
 
+template <typename T>
+__device__ __forceinline__ const CellConst<T>& cconst(const ApplyArgs& a, int level);
+template <>
+__device__ __forceinline__ const CellConst<float>& cconst<float>(const ApplyArgs& a, int level) { return a.cf[level]; }
+template <>
+__device__ __forceinline__ const CellConst<double>& cconst<double>(const ApplyArgs& a, int level) { return a.cd[level]; }
+
 template <typename T, int OP>
-__global__ void __launch_bounds__(NTHREADS) apply_q1_kernel(const ApplyArgs a) {
+__global__ void __launch_bounds__(NTHREADS) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
   using T2 = typename VT<T>::T2;
   using T4 = typename VT<T>::T4;
   constexpr bool inU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU);
@@ -346,15 +342,7 @@ __global__ void __launch_bounds__(NTHREADS) apply_q1_kernel(const ApplyArgs a) {
     if (irr >= 0) active = (a.lay.cellmask[irr * 8 + (tid >> 5)] >> (tid & 31)) & 1u;
     T out[12];
     if (active) {
-      CellConst<T> c;
-      const double hx = a.hx[level], hy = a.hy[level];
-      c.ihx = T(1.0 / hx); c.ihy = T(1.0 / hy);
-      c.c2ml = T(2.0 * a.mu + a.lam); c.cl = T(a.lam); c.cm = T(a.mu);
-      c.omk = T(1.0 - a.kappa); c.kap = T(a.kappa); c.p = T(a.p);
-      c.gcl = T(a.gc_over_l); c.gcL = T(a.gc_times_l);
-      c.jxw = T(0.25 * hx * hy);
-      c.wx = T(0.25 * hy); c.wy = T(0.25 * hx);
-      c.wpx = T(0.5 * a.gc_times_l * hy / hx); c.wpy = T(0.5 * a.gc_times_l * hx / hy);
+      const CellConst<T>& c = cconst<T>(a, level);
       q1_cell<T, OP>(s_x0, s_x1, s_xp, s_lin, ci + WN * cj, c, out);
     } else {
 #pragma unroll
@@ -470,7 +458,25 @@ __global__ void set_lin_hanging_kernel(int32_t nh, const DevHanging* __restrict_
   lin32[e.slot] = make_float4(float(v.x), float(v.y), float(v.z), float(v.w));
 }
 
+template <typename T>
+void fill_cc(CellConst<T>& c, const ApplyArgs& a, double hx, double hy) {
+  c.ihx = T(1.0 / hx); c.ihy = T(1.0 / hy);
+  c.c2ml = T(2.0 * a.mu + a.lam); c.cl = T(a.lam); c.cm = T(a.mu);
+  c.omk = T(1.0 - a.kappa); c.kap = T(a.kappa); c.p = T(a.p);
+  c.gcl = T(a.gc_over_l); c.gcL = T(a.gc_times_l);
+  c.jxw = T(0.25 * hx * hy);
+  c.wx = T(0.25 * hy); c.wy = T(0.25 * hx);
+  c.wpx = T(0.25 * a.gc_times_l * hy / hx); c.wpy = T(0.25 * a.gc_times_l * hx / hy);
+}
+
 }  // namespace
+
+void fill_cell_constants(ApplyArgs& a, int nlevels) {
+  for (int l = 0; l < nlevels && l < kMaxLevels; ++l) {
+    fill_cc(a.cf[l], a, a.hx[l], a.hy[l]);
+    fill_cc(a.cd[l], a, a.hx[l], a.hy[l]);
+  }
+}
 
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {

@@ -44,6 +44,19 @@ struct DevLayout {
   const uint32_t* cellmask = nullptr;
 };
 
+// Per-level cell constants of the Q1 kernels, precomputed on the host in the
+// kernel's precision (no double arithmetic inside FP32 kernels).
+template <typename T>
+struct CellConst {
+  T ihx, ihy;          // 1/hx, 1/hy
+  T c2ml, cl, cm;      // 2 mu + lambda, lambda, mu
+  T omk, kap, p;       // 1 - kappa, kappa, p
+  T gcl, gcL;          // G_c / l, G_c l
+  T jxw;               // hx hy / 4 (2x2 Gauss weight times cell area)
+  T wx, wy;            // JxW / hx, JxW / hy
+  T wpx, wpy;          // G_c l JxW / hx^2, G_c l JxW / hy^2
+};
+
 struct ApplyArgs {
   DevLayout lay;
   const DevHanging* hang;
@@ -57,6 +70,8 @@ struct ApplyArgs {
   double hx[kMaxLevels], hy[kMaxLevels];
   double mu, lam;         // Lame constants (E already applied)
   double kappa, p, gc_over_l, gc_times_l;
+  CellConst<float> cf[kMaxLevels];
+  CellConst<double> cd[kMaxLevels];
   int mode;
   int fe_degree;
 };
@@ -75,6 +90,9 @@ struct FixupArgs {
   const void* ibuf;
   int mode;
 };
+
+// fills cf / cd from hx, hy and the material
+void fill_cell_constants(ApplyArgs& a, int nlevels);
 
 // launchers (return cudaError_t of the launch)
 template <typename T>

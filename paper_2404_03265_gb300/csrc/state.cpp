@@ -101,6 +101,7 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
     a.hy[l] = M.tree.hy(l);
   }
   fill_material(pb.prm, a);
+  fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
   int kop = OP_FULL;
   if (op == PFF_OP_JACOBIAN) { kop = OP_FULL; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }

@@ -9,17 +9,18 @@
 // The u-rows do not see dphi (block lower triangular, Sec. 3.2); the diagonal
 // blocks are the multigrid level operators (Sec. 3.2).
 //
-// One CTA of 256 threads per brick of 15x15 owned node slots:
-//   1. gather the 17x17 node window (input x with hanging-node constraints
-//      resolved on the fly and fixed components masked; linearisation) into
-//      shared memory;
-//   2. one thread per cell of the 16x16 cell window: sum-factorised 2x2 Gauss
-//      evaluation and test, 12 (or fewer) nodal contributions to shared memory;
-//   3. one thread per owned node sums its four cells in a fixed order and
-//      writes its output once.  Nodes shared with another level, hanging nodes
-//      and their parents write partial sums; a small fix-up kernel condenses
-//      them (x_full = C x on input, C^T y on output).
-// No atomics: every output is produced by exactly one thread in a fixed order.
+// One warp per strip of RSEG node rows of a brick of 30x30 owned node slots
+// (a "row sweep"): lane l owns node column l-1 of the brick window (columns
+// -1..30), computes cell (l-1, c) of every cell row c of the strip (sum-factorised
+// 2x2 Gauss evaluation and test) and exchanges node values and nodal
+// contributions with its neighbour lanes by warp shuffles.  Rows are loaded
+// straight from HBM into registers (coalesced: a row of a brick is 30
+// consecutive slots) one row ahead of the arithmetic; there is no shared memory
+// and no block barrier.  Input x has its hanging-node constraints resolved on
+// the fly and fixed components masked.  Each owned node is written once, by
+// one lane, in a fixed summation order.  Nodes shared with another level,
+// hanging nodes and their parents write partial sums; a small fix-up kernel
+// condenses them (x_full = C x on input, C^T y on output).  No atomics.
 #include "kernels.cuh"
 
 namespace pff {
@@ -30,13 +31,12 @@ template <typename T> struct VT;
 template <> struct VT<float> { using T2 = float2; using T4 = float4; };
 template <> struct VT<double> { using T2 = double2; using T4 = dbl4; };
 
-constexpr int NB = 15;          // owned node slots per brick side
-constexpr int WN = 17;          // window nodes per side
-constexpr int WC = 16;          // window cells per side
-constexpr int NWIN = WN * WN;   // 289
-constexpr int NCELL = WC * WC;  // 256
-constexpr int NOWN = NB * NB;   // 225
-constexpr int NTHREADS = 256;
+constexpr int NB = 30;          // owned node slots per brick side
+constexpr int WN = 32;          // window nodes per side (columns -1..30)
+constexpr int NCW = 31;         // window cells per side (cells -1..29)
+constexpr int RSEG = 10;        // node rows per warp strip
+constexpr int NSEG = NB / RSEG;
+constexpr int WARPS = 4;        // warps per CTA (independent strips)
 
 // 2-point Gauss rule on [0, 1]
 constexpr double GA = 0.21132486540518711775;
@@ -115,43 +115,49 @@ __device__ __forceinline__ void q1_test_val(const T fv[2][2], T w, T r[4]) {
   r[3] += w * pt;
 }
 
-// One Q1 cell.  Window node indices n0 (0,0), n0+1, n0+WN, n0+WN+1.
-// out[3*A + c] (c: 0 u_x, 1 u_y, 2 phi) for OP_FULL/OP_FULL_T; for OP_UU the
-// first two components, for OP_PP only component 2 is meaningful.
+// Node data of one window slot held in registers: input x (masked, hanging
+// resolved) and the linearisation.
+template <typename T>
+struct NodeVal {
+  T x0, x1, xp;
+  typename VT<T>::T4 L;
+};
+
+// Which node fields an operator reads.
+template <int OP> struct Needs {
+  static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU);
+  static constexpr bool xp = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP);
+  static constexpr bool linU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
+  static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T);
+  static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG);
+};
+
+// One Q1 cell with nodes v[0] (0,0), v[1] (1,0), v[2] (0,1), v[3] (1,1).
+// out[3*A + c] (c: 0 u_x, 1 u_y, 2 phi).  OP_UU fills components 0, 1;
+// OP_PP component 2; the *_DIAG operators the diagonal entries.
 template <typename T, int OP>
-__device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __restrict__ s1,
-                                        const T* __restrict__ sp, const typename VT<T>::T4* __restrict__ sl,
-                                        int n0, const CellConst<T>& c, T out[12]) {
-  const int nd[4] = {n0, n0 + 1, n0 + WN, n0 + WN + 1};
+__device__ __forceinline__ void q1_cell(const NodeVal<T> v[4], const CellConst<T>& c, T out[12]) {
+  using N = Needs<OP>;
   T rux[4] = {0, 0, 0, 0}, ruy[4] = {0, 0, 0, 0}, rp[4] = {0, 0, 0, 0};
-  constexpr bool needU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG);
-  constexpr bool needP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
-  constexpr bool needLinU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
-  constexpr bool needG = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG);
-  constexpr bool needPhi = (OP == OP_FULL || OP == OP_FULL_T);
-  typename VT<T>::T4 L[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) L[a] = sl[nd[a]];
   // ---- linearisation at the Gauss points
   Q1Field<T> fux, fuy;
   T phiq[2][2], phitq[2][2];
-  if (needLinU) {
-    fux.grads(L[0].x, L[1].x, L[2].x, L[3].x);
-    fuy.grads(L[0].y, L[1].y, L[2].y, L[3].y);
+  if (N::linU) {
+    fux.grads(v[0].L.x, v[1].L.x, v[2].L.x, v[3].L.x);
+    fuy.grads(v[0].L.y, v[1].L.y, v[2].L.y, v[3].L.y);
   }
-  if (needPhi) q1_values(L[0].z, L[1].z, L[2].z, L[3].z, phiq);
-  if (needG) q1_values(L[0].w, L[1].w, L[2].w, L[3].w, phitq);
+  if (N::phi) q1_values(v[0].L.z, v[1].L.z, v[2].L.z, v[3].L.z, phiq);
+  if (N::phit) q1_values(v[0].L.w, v[1].L.w, v[2].L.w, v[3].L.w, phitq);
   // ---- input
   Q1Field<T> fxu, fxv, fxp;
   T xpq[2][2];
-  if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU) {
-    fxu.grads(s0[nd[0]], s0[nd[1]], s0[nd[2]], s0[nd[3]]);
-    fxv.grads(s1[nd[0]], s1[nd[1]], s1[nd[2]], s1[nd[3]]);
+  if (N::xu) {
+    fxu.grads(v[0].x0, v[1].x0, v[2].x0, v[3].x0);
+    fxv.grads(v[0].x1, v[1].x1, v[2].x1, v[3].x1);
   }
-  if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP) {
-    const T v0 = sp[nd[0]], v1 = sp[nd[1]], v2 = sp[nd[2]], v3 = sp[nd[3]];
-    fxp.grads(v0, v1, v2, v3);
-    q1_values(v0, v1, v2, v3, xpq);
+  if (N::xp) {
+    fxp.grads(v[0].xp, v[1].xp, v[2].xp, v[3].xp);
+    q1_values(v[0].xp, v[1].xp, v[2].xp, v[3].xp, xpq);
   }
   T fux_x[2][2], fux_y[2][2], fuy_x[2][2], fuy_y[2][2], fv[2][2];
 #pragma unroll
@@ -159,11 +165,11 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
 #pragma unroll
     for (int q2 = 0; q2 < 2; ++q2) {
       T g = 0, T11 = 0, T22 = 0, T12 = 0, m = 0;
-      if (needG) {
+      if (N::phit) {
         const T pt = phitq[q1][q2];
         g = c.omk * pt * pt + c.kap;
       }
-      if (needLinU) {
+      if (N::linU) {
         const T e11 = fux.dxi[q2] * c.ihx;
         const T e22 = fuy.deta[q1] * c.ihy;
         const T ge12 = fux.deta[q1] * c.ihy + fuy.dxi[q2] * c.ihx;   // 2 e12
@@ -172,14 +178,14 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
         const T s12 = c.cm * ge12;
         const T se = s11 * e11 + s22 * e22 + s12 * ge12;
         m = c.omk * se + T(2) * c.p * (e11 + e22) + c.gcl;
-        if (needPhi) {
+        if (N::phi) {
           const T tp = T(2) * phiq[q1][q2];
           T11 = tp * (c.omk * s11 + c.p);
           T22 = tp * (c.omk * s22 + c.p);
           T12 = tp * (c.omk * s12);
         }
       }
-      if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU) {
+      if (N::xu) {
         const T a = fxu.dxi[q2] * c.ihx;                             // d du_x / dx
         const T d = fxv.deta[q1] * c.ihy;                            // d du_y / dy
         const T bc = fxu.deta[q1] * c.ihy + fxv.dxi[q2] * c.ihx;     // d du_x/dy + d du_y/dx
@@ -198,13 +204,12 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
         fuy_y[q1][q2] = S22;
         if (OP == OP_FULL) fv[q1][q2] = T11 * a + T22 * d + T12 * bc;
       }
-      if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP) {
+      if (N::xp) {
         const T mv = m * xpq[q1][q2];
         if (OP == OP_FULL) fv[q1][q2] += mv; else fv[q1][q2] = mv;
       }
       if (OP == OP_UU_DIAG) {
         // diag of (g sigma(N e_i), e(N e_i)): (2mu+lam)(dN/dx_i)^2 + mu (dN/dx_j)^2
-        // qp contributions accumulated directly
         const T xi = q1 ? T(GB) : T(GA), eta = q2 ? T(GB) : T(GA);
         const T dxs[4] = {-(1 - eta), (1 - eta), -eta, eta};
         const T dys[4] = {-(1 - xi), -xi, (1 - xi), xi};
@@ -227,11 +232,11 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
         }
       }
     }
-  if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU) {
+  if (N::xu) {
     q1_test_grad(fux_x, fux_y, c.wx, c.wy, rux);
     q1_test_grad(fuy_x, fuy_y, c.wx, c.wy, ruy);
   }
-  if (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP) {
+  if (N::xp) {
     q1_test_val(fv, c.jxw, rp);
     // G_c l (grad dphi, grad psi): reference fluxes are constant along one direction
     T gx[2][2], gy[2][2];
@@ -250,7 +255,6 @@ __device__ __forceinline__ void q1_cell(const T* __restrict__ s0, const T* __res
     out[3 * A + 1] = ruy[A];
     out[3 * A + 2] = rp[A];
   }
-  (void)needU; (void)needP;
 }
 
 template <typename T>
@@ -260,145 +264,171 @@ __device__ __forceinline__ const CellConst<float>& cconst<float>(const ApplyArgs
 template <>
 __device__ __forceinline__ const CellConst<double>& cconst<double>(const ApplyArgs& a, int level) { return a.cd[level]; }
 
+// Loads window slot (n, r) (brick-relative node coordinates, -1..30) into v.
 template <typename T, int OP>
-__global__ void __launch_bounds__(NTHREADS) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
+__device__ __forceinline__ void load_node(const ApplyArgs& a, int irr, int nbase, int n, int r, NodeVal<T>& v) {
+  using N = Needs<OP>;
   using T2 = typename VT<T>::T2;
   using T4 = typename VT<T>::T4;
-  constexpr bool inU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU);
-  constexpr bool inP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP);
-  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
-  constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
-  constexpr int NOUT = 12;
-  __shared__ T s_x0[NWIN], s_x1[NWIN], s_xp[NWIN];
-  __shared__ T4 s_lin[NWIN];
-  __shared__ T s_out[NOUT][NCELL];
-  __shared__ int s_nb[9];
-  __shared__ int s_irr, s_level;
-
-  const int tid = threadIdx.x;
-  const BrickDesc* bd = a.lay.bricks + blockIdx.x;
-  if (tid < 9) s_nb[tid] = bd->nbr_base[tid];
-  if (tid == 9) s_irr = bd->irr;
-  if (tid == 10) s_level = bd->level;
-  __syncthreads();
-  const int irr = s_irr;
-  const int level = s_level;
+  int32_t code;
+  if (irr < 0) {
+    const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
+    const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
+    const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1);
+    code = base + (n - dx * NB) + NB * (r - dy * NB);
+  } else {
+    code = a.lay.win[irr * (WN * WN) + (n + 1) + WN * (r + 1)];
+  }
   const T2* xu = reinterpret_cast<const T2*>(a.xu);
   const T* xp = reinterpret_cast<const T*>(a.xp);
   const T4* lin = reinterpret_cast<const T4*>(a.lin);
   const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
-
-  // ---- 1. window gather
-  for (int s = tid; s < NWIN; s += NTHREADS) {
-    int32_t code;
-    if (irr < 0) {
-      const int oi = s % WN - 1, oj = s / WN - 1;
-      const int dx = oi < 0 ? -1 : (oi >= NB ? 1 : 0);
-      const int dy = oj < 0 ? -1 : (oj >= NB ? 1 : 0);
-      code = s_nb[(dy + 1) * 3 + dx + 1] + (oi - dx * NB) + NB * (oj - dy * NB);
-    } else {
-      code = a.lay.win[irr * NWIN + s];
+  v.x0 = 0; v.x1 = 0; v.xp = 0;
+  v.L.x = 0; v.L.y = 0; v.L.z = 0; v.L.w = 0;
+  if (code >= 0) {
+    if (N::xu) { const T2 q = ldg(xu + code); v.x0 = q.x; v.x1 = q.y; }
+    if (N::xp) v.xp = ldg(xp + code);
+    v.L = ldg4(lin + code);
+    if (mask) {
+      const uint8_t cm = ldg(a.cmask + code);
+      if (cm) {
+        if (cm & 1) v.x0 = 0;
+        if (cm & 2) v.x1 = 0;
+        if (cm & 4) v.xp = 0;
+      }
     }
-    T v0 = 0, v1 = 0, vp = 0;
-    T4 L = {0, 0, 0, 0};
-    if (code >= 0) {
-      if (inU) { const T2 v = ldg(xu + code); v0 = v.x; v1 = v.y; }
-      if (inP) vp = ldg(xp + code);
-      L = ldg4(lin + code);
+  } else if (code <= -2) {
+    const DevHanging& h = a.hang[-2 - code];
+    v.L = ldg4(lin + h.slot);
+    const int np = a.fe_degree + 1;
+    for (int b = 0; b < np; ++b) {
+      const int ps = h.parent[b];
+      const T w = T(h.weight[b]);
+      T p0 = 0, p1 = 0, pp = 0;
+      if (N::xu) { const T2 q = ldg(xu + ps); p0 = q.x; p1 = q.y; }
+      if (N::xp) pp = ldg(xp + ps);
       if (mask) {
-        const uint8_t cm = ldg(a.cmask + code);
-        if (cm & 1) v0 = 0;
-        if (cm & 2) v1 = 0;
-        if (cm & 4) vp = 0;
+        const uint8_t cm = ldg(a.cmask + ps);
+        if (cm & 1) p0 = 0;
+        if (cm & 2) p1 = 0;
+        if (cm & 4) pp = 0;
       }
-    } else if (code <= -2) {
-      const DevHanging& h = a.hang[-2 - code];
-      L = ldg4(lin + h.slot);
-      const int np = a.fe_degree + 1;
-      for (int b = 0; b < np; ++b) {
-        const int ps = h.parent[b];
-        const T w = T(h.weight[b]);
-        T p0 = 0, p1 = 0, pp = 0;
-        if (inU) { const T2 v = ldg(xu + ps); p0 = v.x; p1 = v.y; }
-        if (inP) pp = ldg(xp + ps);
-        if (mask) {
-          const uint8_t cm = ldg(a.cmask + ps);
-          if (cm & 1) p0 = 0;
-          if (cm & 2) p1 = 0;
-          if (cm & 4) pp = 0;
-        }
-        v0 += w * p0; v1 += w * p1; vp += w * pp;
-      }
+      v.x0 += w * p0; v.x1 += w * p1; v.xp += w * pp;
     }
-    s_x0[s] = v0; s_x1[s] = v1; s_xp[s] = vp;
-    s_lin[s] = L;
   }
-  __syncthreads();
+}
 
-  // ---- 2. cells
-  {
-    const int ci = tid % WC, cj = tid / WC;
-    bool active = true;
-    if (irr >= 0) active = (a.lay.cellmask[irr * 8 + (tid >> 5)] >> (tid & 31)) & 1u;
+template <typename T, int OP>
+__device__ __forceinline__ NodeVal<T> shfl_down_node(const NodeVal<T>& v) {
+  using N = Needs<OP>;
+  NodeVal<T> r;
+  const unsigned FULL = 0xffffffffu;
+  r.x0 = N::xu ? __shfl_down_sync(FULL, v.x0, 1) : T(0);
+  r.x1 = N::xu ? __shfl_down_sync(FULL, v.x1, 1) : T(0);
+  r.xp = N::xp ? __shfl_down_sync(FULL, v.xp, 1) : T(0);
+  r.L.x = N::linU ? __shfl_down_sync(FULL, v.L.x, 1) : T(0);
+  r.L.y = N::linU ? __shfl_down_sync(FULL, v.L.y, 1) : T(0);
+  r.L.z = N::phi ? __shfl_down_sync(FULL, v.L.z, 1) : T(0);
+  r.L.w = N::phit ? __shfl_down_sync(FULL, v.L.w, 1) : T(0);
+  return r;
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(32 * WARPS) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
+  using T2 = typename VT<T>::T2;
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
+  constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
+  constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  if (unit >= a.lay.nbricks * NSEG) return;  // uniform per warp
+  const int b = unit / NSEG;
+  const int r0 = (unit % NSEG) * RSEG;
+  const BrickDesc* bd = a.lay.bricks + b;
+  const int nbase = lane < 9 ? __ldg(bd->nbr_base + lane) : 0;
+  const int irr = __ldg(&bd->irr);
+  const int level = __ldg(&bd->level);
+  const CellConst<T>& cc = cconst<T>(a, level);
+  const int n = lane - 1;  // node column of this lane (-1..30)
+  const int own_base = __shfl_sync(FULL, nbase, 4);
+  T2* yu = reinterpret_cast<T2*>(a.yu);
+  T* yp = reinterpret_cast<T*>(a.yp);
+
+  NodeVal<T> cur, nxt, curR;
+  load_node<T, OP>(a, irr, nbase, n, r0 - 1, cur);
+  load_node<T, OP>(a, irr, nbase, n, r0, nxt);
+  curR = shfl_down_node<T, OP>(cur);
+  T carry[3] = {0, 0, 0};
+#pragma unroll 1
+  for (int c = r0 - 1; c < r0 + RSEG; ++c) {
+    // prefetch node row c + 2
+    NodeVal<T> pre = nxt;
+    if (c + 2 <= r0 + RSEG) load_node<T, OP>(a, irr, nbase, n, c + 2, pre);
+    const NodeVal<T> nxtR = shfl_down_node<T, OP>(nxt);
+    bool act = lane < NCW;
+    if (irr >= 0 && act) {
+      const int ci = (c + 1) * NCW + lane;  // window cell (n, c) -> (lane, c+1)
+      act = (__ldg(a.lay.cellmask + irr * 31 + (ci >> 5)) >> (ci & 31)) & 1u;
+    }
     T out[12];
-    if (active) {
-      const CellConst<T>& c = cconst<T>(a, level);
-      q1_cell<T, OP>(s_x0, s_x1, s_xp, s_lin, ci + WN * cj, c, out);
+    if (act) {
+      NodeVal<T> v[4] = {cur, curR, nxt, nxtR};
+      q1_cell<T, OP>(v, cc, out);
     } else {
 #pragma unroll
       for (int q = 0; q < 12; ++q) out[q] = 0;
     }
+    // contributions of the left neighbour's cell (n-1, c): its BR (node (n, c)) and TR (node (n, c+1))
+    T brL[3], trL[3];
 #pragma unroll
-    for (int q = 0; q < NOUT; ++q) s_out[q][tid] = out[q];
-  }
-  __syncthreads();
-
-  // ---- 3. owned nodes
-  if (tid < NOWN) {
-    const int oi = tid % NB, oj = tid / NB;
-    const int c00 = oi + WC * oj;  // this node is local node 3 of c00, 2 of c00+1, 1 of c00+WC, 0 of c00+WC+1
-    T y[3];
+    for (int q = 0; q < 3; ++q) {
+      brL[q] = __shfl_up_sync(FULL, out[3 + q], 1);
+      trL[q] = __shfl_up_sync(FULL, out[9 + q], 1);
+    }
+    if (c >= r0 && lane >= 1 && lane <= NB) {
+      // node (n, c) complete: cells (n-1, c-1) TR + (n, c-1) TL (carry), (n-1, c) BR, (n, c) BL
+      T y[3];
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp)
-      y[comp] = s_out[9 + comp][c00] + s_out[6 + comp][c00 + 1] + s_out[3 + comp][c00 + WC] +
-                s_out[0 + comp][c00 + WC + 1];
-    int act = kActFinal;
-    int part = -1;
-    if (irr >= 0) {
-      act = a.lay.own_act[irr * NOWN + tid];
-      part = a.lay.own_part[irr * NOWN + tid];
-    }
-    const int slot = s_nb[4] + oi + NB * oj;
-    T2* yu = reinterpret_cast<T2*>(a.yu);
-    T* yp = reinterpret_cast<T*>(a.yp);
-    if (part >= 0) {
-      T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
-      ib[0] = y[0]; ib[1] = y[1]; ib[2] = y[2];
-    }
-    if (act == kActFinal) {
-      if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
-        // diagonal entries; fixed rows get 0 (their inverse is set to 0 too)
-        const uint8_t cm = ldg(a.cmask + slot);
-        if (outU) {
-          T2 o; o.x = (cm & 1) ? T(0) : y[0]; o.y = (cm & 2) ? T(0) : y[1];
-          yu[slot] = o;
-        }
-        if (outP) yp[slot] = (cm & 4) ? T(0) : y[2];
-      } else {
-        const uint8_t cm = ldg(a.cmask + slot);
-        if (cm) {
-          const bool ident = (a.mode & MODE_IDENTITY) != 0;
-          if (cm & 1) y[0] = ident ? ldg(xu + slot).x : T(0);
-          if (cm & 2) y[1] = ident ? ldg(xu + slot).y : T(0);
-          if (cm & 4) y[2] = ident ? ldg(xp + slot) : T(0);
-        }
-        if (outU) { T2 o; o.x = y[0]; o.y = y[1]; yu[slot] = o; }
-        if (outP) yp[slot] = y[2];
+      for (int q = 0; q < 3; ++q) y[q] = (carry[q] + brL[q]) + out[q];
+      const int o = n + NB * c;  // owned slot
+      int act_s = kActFinal, part = -1;
+      if (irr >= 0) {
+        act_s = __ldg(a.lay.own_act + irr * (NB * NB) + o);
+        part = __ldg(a.lay.own_part + irr * (NB * NB) + o);
       }
-    } else if (act == kActZero) {
-      if (outU) { T2 o; o.x = 0; o.y = 0; yu[slot] = o; }
-      if (outP) yp[slot] = 0;
+      const int slot = own_base + o;
+      if (part >= 0) {
+        T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
+        ib[0] = y[0]; ib[1] = y[1]; ib[2] = y[2];
+      }
+      if (act_s == kActFinal) {
+        const uint8_t cm = ldg(a.cmask + slot);
+        if (isDiag) {
+          if (outU) { T2 o2; o2.x = (cm & 1) ? T(0) : y[0]; o2.y = (cm & 2) ? T(0) : y[1]; yu[slot] = o2; }
+          if (outP) yp[slot] = (cm & 4) ? T(0) : y[2];
+        } else {
+          if (cm) {
+            const bool ident = (a.mode & MODE_IDENTITY) != 0;
+            const T2* xu = reinterpret_cast<const T2*>(a.xu);
+            const T* xp = reinterpret_cast<const T*>(a.xp);
+            if (cm & 1) y[0] = ident ? ldg(xu + slot).x : T(0);
+            if (cm & 2) y[1] = ident ? ldg(xu + slot).y : T(0);
+            if (cm & 4) y[2] = ident ? ldg(xp + slot) : T(0);
+          }
+          if (outU) { T2 o2; o2.x = y[0]; o2.y = y[1]; yu[slot] = o2; }
+          if (outP) yp[slot] = y[2];
+        }
+      } else if (act_s == kActZero) {
+        if (outU) { T2 o2; o2.x = 0; o2.y = 0; yu[slot] = o2; }
+        if (outP) yp[slot] = 0;
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) carry[q] = out[6 + q] + trL[q];
+    cur = nxt;
+    curR = nxtR;
+    nxt = pre;
   }
 }
 
@@ -482,13 +512,15 @@ template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
+  const unsigned grid = unsigned((a.lay.nbricks * NSEG + WARPS - 1) / WARPS);
+  const unsigned blk = 32 * WARPS;
   switch (op) {
-    case OP_FULL: apply_q1_kernel<T, OP_FULL><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
-    case OP_FULL_T: apply_q1_kernel<T, OP_FULL_T><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
-    case OP_UU: apply_q1_kernel<T, OP_UU><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
-    case OP_PP: apply_q1_kernel<T, OP_PP><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
-    case OP_UU_DIAG: apply_q1_kernel<T, OP_UU_DIAG><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
-    case OP_PP_DIAG: apply_q1_kernel<T, OP_PP_DIAG><<<a.lay.nbricks, NTHREADS, 0, s>>>(a); break;
+    case OP_FULL: apply_q1_kernel<T, OP_FULL><<<grid, blk, 0, s>>>(a); break;
+    case OP_FULL_T: apply_q1_kernel<T, OP_FULL_T><<<grid, blk, 0, s>>>(a); break;
+    case OP_UU: apply_q1_kernel<T, OP_UU><<<grid, blk, 0, s>>>(a); break;
+    case OP_PP: apply_q1_kernel<T, OP_PP><<<grid, blk, 0, s>>>(a); break;
+    case OP_UU_DIAG: apply_q1_kernel<T, OP_UU_DIAG><<<grid, blk, 0, s>>>(a); break;
+    case OP_PP_DIAG: apply_q1_kernel<T, OP_PP_DIAG><<<grid, blk, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -195,7 +195,7 @@ std::string finalize_mesh(Mesh& m, int k) {
   // ---- leaf layout bricks
   Layout& L = m.lay;
   L.k = k;
-  L.B = (k == 1) ? 15 : 8;
+  L.B = (k == 1) ? 30 : 15;
   L.NB = L.B * k;
   L.W = L.NB + k + 1;
   const int NB = L.NB, W = L.W, B = L.B, NB2 = NB * NB;

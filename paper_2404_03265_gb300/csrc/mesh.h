@@ -6,7 +6,7 @@
 //
 // Storage ("brick layout").  Every refinement level l has a structured node grid
 // (spacing h_l / k).  It is cut into square bricks of NB x NB node slots
-// (NB = B * k; B = 15 cells for Q1, 8 for Q2).  A node vector is the
+// (NB = B * k = 30; B = 30 cells for Q1, 15 for Q2).  A node vector is the
 // concatenation of the bricks of all levels, NB*NB slots each; a mesh node
 // lives in exactly one slot ("home"), the other slots are holes (kept at zero).
 //   * leaf mesh: a node's home is the coarsest level among the leaf cells that
@@ -65,7 +65,7 @@ inline int32_t hanging_code(int32_t h) { return -2 - h; }
 constexpr uint8_t kActNone = 0, kActFinal = 1, kActZero = 2;
 
 struct Layout {
-  int k = 1, B = 15, NB = 15, W = 17;
+  int k = 1, B = 30, NB = 30, W = 32;
   std::vector<BrickDesc> bricks;
   int64_t n_slots = 0;
   std::vector<int32_t> win;       // per irregular brick W*W codes

@@ -10,7 +10,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIBPATH = os.path.join(HERE, "libpff.so")
+LIBPATH = os.environ.get("PFF_LIBPATH") or os.path.join(HERE, "libpff.so")
 
 PFF_OK = 0
 PFF_F64, PFF_F32 = 0, 1

@@ -23,6 +23,9 @@
 // condenses them (x_full = C x on input, C^T y on output).  No atomics.
 #include "kernels.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace pff {
 
 namespace {
@@ -34,9 +37,19 @@ template <> struct VT<double> { using T2 = double2; using T4 = dbl4; };
 constexpr int NB = 30;          // owned node slots per brick side
 constexpr int WN = 32;          // window nodes per side (columns -1..30)
 constexpr int NCW = 31;         // window cells per side (cells -1..29)
-constexpr int RSEG = 10;        // node rows per warp strip
+#ifndef PFF_RSEG
+#define PFF_RSEG 10
+#endif
+#ifndef PFF_WARPS
+#define PFF_WARPS 4
+#endif
+#ifndef PFF_MINB
+#define PFF_MINB 1
+#endif
+constexpr int RSEG = PFF_RSEG;  // node rows per warp strip (divides NB)
 constexpr int NSEG = NB / RSEG;
-constexpr int WARPS = 4;        // warps per CTA (independent strips)
+constexpr int WARPS = PFF_WARPS;  // warps per CTA (independent strips)
+static_assert(NB % RSEG == 0, "strip height must divide the brick");
 
 // 2-point Gauss rule on [0, 1]
 constexpr double GA = 0.21132486540518711775;
@@ -132,122 +145,189 @@ template <int OP> struct Needs {
   static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG);
 };
 
+// ---- packed pairs: two Gauss points (eta = GA, GB at one xi) per operation.
+// FP32 uses Blackwell's paired FP32 instructions (FFMA2 / FADD2 / FMUL2);
+// FP64 falls back to two scalar operations.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pbc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 pbc(double s) { return make_double2(s, s); }
+
 // One Q1 cell with nodes v[0] (0,0), v[1] (1,0), v[2] (0,1), v[3] (1,1).
 // out[3*A + c] (c: 0 u_x, 1 u_y, 2 phi).  OP_UU fills components 0, 1;
 // OP_PP component 2; the *_DIAG operators the diagonal entries.
+//
+// Reference-cell fields (sum factorisation on 2x2 Gauss points, eta_q = GA, GB):
+//   d/dxi at the two eta points is a pair P (same for both xi points),
+//   d/deta at xi point q1 is a scalar, values at (xi_q1, eta_*) a pair.
 template <typename T, int OP>
 __device__ __forceinline__ void q1_cell(const NodeVal<T> v[4], const CellConst<T>& c, T out[12]) {
   using N = Needs<OP>;
+  using P = typename VT<T>::T2;
+  const P G2 = {T(GA), T(GB)};
   T rux[4] = {0, 0, 0, 0}, ruy[4] = {0, 0, 0, 0}, rp[4] = {0, 0, 0, 0};
-  // ---- linearisation at the Gauss points
-  Q1Field<T> fux, fuy;
-  T phiq[2][2], phitq[2][2];
-  if (N::linU) {
-    fux.grads(v[0].L.x, v[1].L.x, v[2].L.x, v[3].L.x);
-    fuy.grads(v[0].L.y, v[1].L.y, v[2].L.y, v[3].L.y);
-  }
-  if (N::phi) q1_values(v[0].L.z, v[1].L.z, v[2].L.z, v[3].L.z, phiq);
-  if (N::phit) q1_values(v[0].L.w, v[1].L.w, v[2].L.w, v[3].L.w, phitq);
-  // ---- input
-  Q1Field<T> fxu, fxv, fxp;
-  T xpq[2][2];
-  if (N::xu) {
-    fxu.grads(v[0].x0, v[1].x0, v[2].x0, v[3].x0);
-    fxv.grads(v[0].x1, v[1].x1, v[2].x1, v[3].x1);
-  }
-  if (N::xp) {
-    fxp.grads(v[0].xp, v[1].xp, v[2].xp, v[3].xp);
-    q1_values(v[0].xp, v[1].xp, v[2].xp, v[3].xp, xpq);
-  }
-  T fux_x[2][2], fux_y[2][2], fuy_x[2][2], fuy_y[2][2], fv[2][2];
-#pragma unroll
-  for (int q1 = 0; q1 < 2; ++q1)
-#pragma unroll
-    for (int q2 = 0; q2 < 2; ++q2) {
-      T g = 0, T11 = 0, T22 = 0, T12 = 0, m = 0;
-      if (N::phit) {
-        const T pt = phitq[q1][q2];
-        g = c.omk * pt * pt + c.kap;
-      }
-      if (N::linU) {
-        const T e11 = fux.dxi[q2] * c.ihx;
-        const T e22 = fuy.deta[q1] * c.ihy;
-        const T ge12 = fux.deta[q1] * c.ihy + fuy.dxi[q2] * c.ihx;   // 2 e12
-        const T s11 = c.c2ml * e11 + c.cl * e22;
-        const T s22 = c.cl * e11 + c.c2ml * e22;
-        const T s12 = c.cm * ge12;
-        const T se = s11 * e11 + s22 * e22 + s12 * ge12;
-        m = c.omk * se + T(2) * c.p * (e11 + e22) + c.gcl;
-        if (N::phi) {
-          const T tp = T(2) * phiq[q1][q2];
-          T11 = tp * (c.omk * s11 + c.p);
-          T22 = tp * (c.omk * s22 + c.p);
-          T12 = tp * (c.omk * s12);
-        }
-      }
-      if (N::xu) {
-        const T a = fxu.dxi[q2] * c.ihx;                             // d du_x / dx
-        const T d = fxv.deta[q1] * c.ihy;                            // d du_y / dy
-        const T bc = fxu.deta[q1] * c.ihy + fxv.dxi[q2] * c.ihx;     // d du_x/dy + d du_y/dx
-        T S11 = g * (c.c2ml * a + c.cl * d);
-        T S22 = g * (c.cl * a + c.c2ml * d);
-        T S12 = g * (c.cm * bc);
-        if (OP == OP_FULL_T) {
-          const T dp = xpq[q1][q2];
-          S11 += dp * T11;
-          S22 += dp * T22;
-          S12 += dp * T12;
-        }
-        fux_x[q1][q2] = S11;  // u_x test: (S11, S12) . grad psi
-        fux_y[q1][q2] = S12;
-        fuy_x[q1][q2] = S12;  // u_y test: (S12, S22) . grad psi
-        fuy_y[q1][q2] = S22;
-        if (OP == OP_FULL) fv[q1][q2] = T11 * a + T22 * d + T12 * bc;
-      }
-      if (N::xp) {
-        const T mv = m * xpq[q1][q2];
-        if (OP == OP_FULL) fv[q1][q2] += mv; else fv[q1][q2] = mv;
-      }
-      if (OP == OP_UU_DIAG) {
-        // diag of (g sigma(N e_i), e(N e_i)): (2mu+lam)(dN/dx_i)^2 + mu (dN/dx_j)^2
-        const T xi = q1 ? T(GB) : T(GA), eta = q2 ? T(GB) : T(GA);
-        const T dxs[4] = {-(1 - eta), (1 - eta), -eta, eta};
-        const T dys[4] = {-(1 - xi), -xi, (1 - xi), xi};
-#pragma unroll
-        for (int A = 0; A < 4; ++A) {
-          const T dx = dxs[A] * c.ihx, dy = dys[A] * c.ihy;
-          rux[A] += c.jxw * g * (c.c2ml * dx * dx + c.cm * dy * dy);
-          ruy[A] += c.jxw * g * (c.cm * dx * dx + c.c2ml * dy * dy);
-        }
-      }
-      if (OP == OP_PP_DIAG) {
-        const T xi = q1 ? T(GB) : T(GA), eta = q2 ? T(GB) : T(GA);
-        const T Ns[4] = {(1 - xi) * (1 - eta), xi * (1 - eta), (1 - xi) * eta, xi * eta};
-        const T dxs[4] = {-(1 - eta), (1 - eta), -eta, eta};
-        const T dys[4] = {-(1 - xi), -xi, (1 - xi), xi};
-#pragma unroll
-        for (int A = 0; A < 4; ++A) {
-          const T dx = dxs[A] * c.ihx, dy = dys[A] * c.ihy;
-          rp[A] += c.jxw * (m * Ns[A] * Ns[A] + c.gcL * (dx * dx + dy * dy));
-        }
-      }
+  if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
+    // diagonal entries, once per Newton step: plain scalar quadrature
+    Q1Field<T> fux, fuy;
+    T phitq[2][2];
+    if (N::linU) {
+      fux.grads(v[0].L.x, v[1].L.x, v[2].L.x, v[3].L.x);
+      fuy.grads(v[0].L.y, v[1].L.y, v[2].L.y, v[3].L.y);
     }
-  if (N::xu) {
-    q1_test_grad(fux_x, fux_y, c.wx, c.wy, rux);
-    q1_test_grad(fuy_x, fuy_y, c.wx, c.wy, ruy);
-  }
-  if (N::xp) {
-    q1_test_val(fv, c.jxw, rp);
-    // G_c l (grad dphi, grad psi): reference fluxes are constant along one direction
-    T gx[2][2], gy[2][2];
+    if (N::phit) q1_values(v[0].L.w, v[1].L.w, v[2].L.w, v[3].L.w, phitq);
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
       for (int q2 = 0; q2 < 2; ++q2) {
-        gx[q1][q2] = fxp.dxi[q2];
-        gy[q1][q2] = fxp.deta[q1];
+        const T xi = q1 ? T(GB) : T(GA), eta = q2 ? T(GB) : T(GA);
+        const T dxs[4] = {-(1 - eta), (1 - eta), -eta, eta};
+        const T dys[4] = {-(1 - xi), -xi, (1 - xi), xi};
+        if (OP == OP_UU_DIAG) {
+          const T pt = phitq[q1][q2];
+          const T g = c.omk * pt * pt + c.kap;
+#pragma unroll
+          for (int A = 0; A < 4; ++A) {
+            const T dx = dxs[A] * c.ihx, dy = dys[A] * c.ihy;
+            rux[A] += c.jxw * g * (c.c2ml * dx * dx + c.cm * dy * dy);
+            ruy[A] += c.jxw * g * (c.cm * dx * dx + c.c2ml * dy * dy);
+          }
+        } else {
+          const T e11 = fux.dxi[q2] * c.ihx, e22 = fuy.deta[q1] * c.ihy;
+          const T ge12 = fux.deta[q1] * c.ihy + fuy.dxi[q2] * c.ihx;
+          const T s11 = c.c2ml * e11 + c.cl * e22, s22 = c.cl * e11 + c.c2ml * e22, s12 = c.cm * ge12;
+          const T m = c.omk * (s11 * e11 + s22 * e22 + s12 * ge12) + T(2) * c.p * (e11 + e22) + c.gcl;
+          const T Ns[4] = {(1 - xi) * (1 - eta), xi * (1 - eta), (1 - xi) * eta, xi * eta};
+#pragma unroll
+          for (int A = 0; A < 4; ++A) {
+            const T dx = dxs[A] * c.ihx, dy = dys[A] * c.ihy;
+            rp[A] += c.jxw * (m * Ns[A] * Ns[A] + c.gcL * (dx * dx + dy * dy));
+          }
+        }
       }
-    q1_test_grad(gx, gy, c.wpx, c.wpy, rp);
+  } else {
+    // ---- linearisation: d/dxi pairs (eta points), d/deta scalars per xi point
+    P e11 = pbc(T(0)), uyxi = pbc(T(0));
+    T uxeta[2] = {0, 0}, e22s[2] = {0, 0};
+    if (N::linU) {
+      const T ax0 = v[1].L.x - v[0].L.x, ay0 = v[2].L.x - v[0].L.x, aX = (v[3].L.x - v[2].L.x) - ax0;
+      const T bx0 = v[1].L.y - v[0].L.y, by0 = v[2].L.y - v[0].L.y, bX = (v[3].L.y - v[2].L.y) - bx0;
+      e11 = pmul(pfma(G2, pbc(aX), pbc(ax0)), pbc(c.ihx));    // du_x/dx at the eta points
+      uyxi = pmul(pfma(G2, pbc(bX), pbc(bx0)), pbc(c.ihx));   // du_y/dx
+      uxeta[0] = (ay0 + T(GA) * aX) * c.ihy;                   // du_x/dy at xi points
+      uxeta[1] = (ay0 + T(GB) * aX) * c.ihy;
+      e22s[0] = (by0 + T(GA) * bX) * c.ihy;                    // du_y/dy
+      e22s[1] = (by0 + T(GB) * bX) * c.ihy;
+    }
+    // values of a field at (xi_q1, eta_*): pair per q1
+    auto vals = [&](T v0, T v1, T v2, T v3, P out2[2]) {
+      const T dx0 = v1 - v0, dy0 = v2 - v0, X = (v3 - v2) - dx0;
+      const T de0 = dy0 + T(GA) * X, de1 = dy0 + T(GB) * X;
+      const T vb0 = v0 + T(GA) * dx0, vb1 = v0 + T(GB) * dx0;
+      out2[0] = pfma(G2, pbc(de0), pbc(vb0));
+      out2[1] = pfma(G2, pbc(de1), pbc(vb1));
+    };
+    P phiP[2], phitP[2];
+    if (N::phi) vals(v[0].L.z, v[1].L.z, v[2].L.z, v[3].L.z, phiP);
+    if (N::phit) vals(v[0].L.w, v[1].L.w, v[2].L.w, v[3].L.w, phitP);
+    // ---- input
+    P axi = pbc(T(0)), cxi = pbc(T(0)), pxi = pbc(T(0));
+    T beta[2] = {0, 0}, deta[2] = {0, 0}, peta[2] = {0, 0};
+    P xpP[2];
+    if (N::xu) {
+      const T ax0 = v[1].x0 - v[0].x0, ay0 = v[2].x0 - v[0].x0, aX = (v[3].x0 - v[2].x0) - ax0;
+      const T bx0 = v[1].x1 - v[0].x1, by0 = v[2].x1 - v[0].x1, bX = (v[3].x1 - v[2].x1) - bx0;
+      axi = pmul(pfma(G2, pbc(aX), pbc(ax0)), pbc(c.ihx));   // d dux/dx (pair over eta)
+      cxi = pmul(pfma(G2, pbc(bX), pbc(bx0)), pbc(c.ihx));   // d duy/dx
+      beta[0] = (ay0 + T(GA) * aX) * c.ihy;                   // d dux/dy (per xi)
+      beta[1] = (ay0 + T(GB) * aX) * c.ihy;
+      deta[0] = (by0 + T(GA) * bX) * c.ihy;                   // d duy/dy
+      deta[1] = (by0 + T(GB) * bX) * c.ihy;
+    }
+    if (N::xp) {
+      const T px0 = v[1].xp - v[0].xp, py0 = v[2].xp - v[0].xp, pX = (v[3].xp - v[2].xp) - px0;
+      pxi = pfma(G2, pbc(pX), pbc(px0));                      // reference d dphi/dxi (pair over eta)
+      peta[0] = py0 + T(GA) * pX;                              // reference d dphi/deta (per xi)
+      peta[1] = py0 + T(GB) * pX;
+      vals(v[0].xp, v[1].xp, v[2].xp, v[3].xp, xpP);
+    }
+    // per xi point: the pair of eta points
+    P Fux_x[2], Fux_y[2], Fuy_y[2], Fv[2];
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1) {
+      P g = pbc(T(0)), T11 = pbc(T(0)), T22 = pbc(T(0)), T12 = pbc(T(0)), m = pbc(T(0));
+      if (N::phit) g = pfma(pbc(c.omk), pmul(phitP[q1], phitP[q1]), pbc(c.kap));
+      if (N::linU) {
+        const P ge12 = padd(pbc(uxeta[q1]), uyxi);   // 2 e12
+        const P e22 = pbc(e22s[q1]);
+        const P s11 = pfma(pbc(c.c2ml), e11, pbc(c.cl * e22s[q1]));
+        const P s22 = pfma(pbc(c.cl), e11, pbc(c.c2ml * e22s[q1]));
+        const P s12 = pmul(pbc(c.cm), ge12);
+        const P se = pfma(s11, e11, pfma(s22, e22, pmul(s12, ge12)));
+        m = pfma(pbc(c.omk), se, pfma(pbc(T(2) * c.p), padd(e11, e22), pbc(c.gcl)));
+        if (N::phi) {
+          const P tp = padd(phiP[q1], phiP[q1]);
+          T11 = pmul(tp, pfma(pbc(c.omk), s11, pbc(c.p)));
+          T22 = pmul(tp, pfma(pbc(c.omk), s22, pbc(c.p)));
+          T12 = pmul(tp, pmul(pbc(c.omk), s12));
+        }
+      }
+      if (N::xu) {
+        const P bcp = padd(pbc(beta[q1]), cxi);          // d dux/dy + d duy/dx
+        const P d = pbc(deta[q1]);
+        P S11 = pmul(g, pfma(pbc(c.c2ml), axi, pbc(c.cl * deta[q1])));
+        P S22 = pmul(g, pfma(pbc(c.cl), axi, pbc(c.c2ml * deta[q1])));
+        P S12 = pmul(g, pmul(pbc(c.cm), bcp));
+        if (OP == OP_FULL_T) {
+          S11 = pfma(xpP[q1], T11, S11);
+          S22 = pfma(xpP[q1], T22, S22);
+          S12 = pfma(xpP[q1], T12, S12);
+        }
+        Fux_x[q1] = S11;
+        Fux_y[q1] = S12;   // also the d/dxi flux of the u_y test
+        Fuy_y[q1] = S22;
+        if (OP == OP_FULL) Fv[q1] = pfma(T11, axi, pfma(T22, d, pfma(T12, bcp, pmul(m, xpP[q1]))));
+      }
+      if (N::xp && OP != OP_FULL) Fv[q1] = pmul(m, xpP[q1]);
+    }
+    // ---- test.  d/dxi flux pairs (per eta point, summed over xi) and d/deta
+    // fluxes (per xi point, summed over eta):
+    //   dN/dxi: N0 -(1-eta), N1 (1-eta), N2 -eta, N3 eta
+    //   dN/deta: N0 -(1-xi), N1 -xi, N2 (1-xi), N3 xi
+    auto test_grad = [&](P fxi0, P fxi1, T fe0, T fe1, T wx, T wy, T r[4]) {
+      const P sx = padd(fxi0, fxi1);                  // sum over xi, per eta
+      const T px = T(GA) * sx.x + T(GB) * sx.y;       // eta-weighted
+      const T qx = (sx.x + sx.y) - px;                // (1-eta)-weighted
+      const T py = T(GA) * fe0 + T(GB) * fe1;         // xi-weighted
+      const T qy = (fe0 + fe1) - py;
+      r[0] += -wx * qx - wy * qy;
+      r[1] += wx * qx - wy * py;
+      r[2] += -wx * px + wy * qy;
+      r[3] += wx * px + wy * py;
+    };
+    if (N::xu) {
+      // u_x test: (S11, S12) . grad psi;  u_y test: (S12, S22) . grad psi
+      test_grad(Fux_x[0], Fux_x[1], Fux_y[0].x + Fux_y[0].y, Fux_y[1].x + Fux_y[1].y, c.wx, c.wy, rux);
+      test_grad(Fux_y[0], Fux_y[1], Fuy_y[0].x + Fuy_y[0].y, Fuy_y[1].x + Fuy_y[1].y, c.wx, c.wy, ruy);
+    }
+    if (N::xp) {
+      // value test against N_A = L_a(xi) L_b(eta)
+      const T s0 = Fv[0].x + Fv[0].y, s1 = Fv[1].x + Fv[1].y;
+      const T t0 = T(GA) * Fv[0].x + T(GB) * Fv[0].y, t1 = T(GA) * Fv[1].x + T(GB) * Fv[1].y;
+      const T b0 = s0 - t0, b1 = s1 - t1;
+      const T pb = T(GA) * b0 + T(GB) * b1, pt = T(GA) * t0 + T(GB) * t1;
+      rp[0] += c.jxw * ((b0 + b1) - pb);
+      rp[1] += c.jxw * pb;
+      rp[2] += c.jxw * ((t0 + t1) - pt);
+      rp[3] += c.jxw * pt;
+      // G_c l (grad dphi, grad psi): the d/dxi flux is the same at both xi points
+      test_grad(pxi, pxi, T(2) * peta[0], T(2) * peta[1], c.wpx, c.wpy, rp);
+    }
   }
 #pragma unroll
   for (int A = 0; A < 4; ++A) {
@@ -334,15 +414,16 @@ __device__ __forceinline__ NodeVal<T> shfl_down_node(const NodeVal<T>& v) {
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(32 * WARPS) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
+__global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
   using T2 = typename VT<T>::T2;
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
   constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int unit = blockIdx.x * WARPS + (threadIdx.x >> 5);
-  if (unit >= a.lay.nbricks * NSEG) return;  // uniform per warp
+  const int nunits = a.lay.nbricks * NSEG;
+  // persistent warps: grid-stride over strips (unit is uniform per warp)
+  for (int unit = blockIdx.x * WARPS + (threadIdx.x >> 5); unit < nunits; unit += gridDim.x * WARPS) {
   const int b = unit / NSEG;
   const int r0 = (unit % NSEG) * RSEG;
   const BrickDesc* bd = a.lay.bricks + b;
@@ -430,6 +511,7 @@ __global__ void __launch_bounds__(32 * WARPS) apply_q1_kernel(const __grid_const
     curR = nxtR;
     nxt = pre;
   }
+  }  // unit
 }
 
 template <typename T>
@@ -501,6 +583,22 @@ void fill_cc(CellConst<T>& c, const ApplyArgs& a, double hx, double hy) {
 
 }  // namespace
 
+// Blocks of `threads` threads of kernel fn that fit on all SMs at once (cached per kernel).
+int resident_blocks(const void* fn, int threads) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(fn);
+  if (it != cache.end()) return it->second;
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const int n = sms * per_sm;
+  cache[fn] = n;
+  return n;
+}
+
 void fill_cell_constants(ApplyArgs& a, int nlevels) {
   for (int l = 0; l < nlevels && l < kMaxLevels; ++l) {
     fill_cc(a.cf[l], a, a.hx[l], a.hy[l]);
@@ -512,15 +610,27 @@ template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
-  const unsigned grid = unsigned((a.lay.nbricks * NSEG + WARPS - 1) / WARPS);
+  const int units = a.lay.nbricks * NSEG;
   const unsigned blk = 32 * WARPS;
+  auto grid_of = [&](const void* fn) -> unsigned {
+    const int full = resident_blocks(fn, int(blk));
+    const int need = (units + WARPS - 1) / WARPS;
+    return unsigned(need < full ? need : full);
+  };
   switch (op) {
-    case OP_FULL: apply_q1_kernel<T, OP_FULL><<<grid, blk, 0, s>>>(a); break;
-    case OP_FULL_T: apply_q1_kernel<T, OP_FULL_T><<<grid, blk, 0, s>>>(a); break;
-    case OP_UU: apply_q1_kernel<T, OP_UU><<<grid, blk, 0, s>>>(a); break;
-    case OP_PP: apply_q1_kernel<T, OP_PP><<<grid, blk, 0, s>>>(a); break;
-    case OP_UU_DIAG: apply_q1_kernel<T, OP_UU_DIAG><<<grid, blk, 0, s>>>(a); break;
-    case OP_PP_DIAG: apply_q1_kernel<T, OP_PP_DIAG><<<grid, blk, 0, s>>>(a); break;
+#define PFF_LAUNCH(OPV)                                                                        \
+    case OPV: {                                                                                \
+      const void* fn = reinterpret_cast<const void*>(&apply_q1_kernel<T, OPV>);               \
+      apply_q1_kernel<T, OPV><<<grid_of(fn), blk, 0, s>>>(a);                                  \
+      break;                                                                                   \
+    }
+    PFF_LAUNCH(OP_FULL)
+    PFF_LAUNCH(OP_FULL_T)
+    PFF_LAUNCH(OP_UU)
+    PFF_LAUNCH(OP_PP)
+    PFF_LAUNCH(OP_UU_DIAG)
+    PFF_LAUNCH(OP_PP_DIAG)
+#undef PFF_LAUNCH
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

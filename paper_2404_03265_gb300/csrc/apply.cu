@@ -344,42 +344,97 @@ __device__ __forceinline__ const CellConst<float>& cconst<float>(const ApplyArgs
 template <>
 __device__ __forceinline__ const CellConst<double>& cconst<double>(const ApplyArgs& a, int level) { return a.cd[level]; }
 
-// Loads window slot (n, r) (brick-relative node coordinates, -1..30) into v.
+// ---- asynchronous global -> shared copies (Ampere+ cp.async), per lane
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+template <typename X>
+__device__ __forceinline__ void cp_async_x(X* dst, const X* src) {
+  if constexpr (sizeof(X) == 4) cp_async4(dst, src);
+  else if constexpr (sizeof(X) == 8) cp_async8(dst, src);
+  else if constexpr (sizeof(X) == 16) cp_async16(dst, src);
+  else { cp_async16(dst, src); cp_async16(reinterpret_cast<char*>(dst) + 16, reinterpret_cast<const char*>(src) + 16); }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+#ifndef PFF_DEPTH
+#define PFF_DEPTH 4
+#endif
+constexpr int DEPTH = PFF_DEPTH;  // ring stages per warp (rows in flight: DEPTH-1)
+constexpr int NROWS = RSEG + 2;   // node rows a strip reads
+
+// One ring stage: one node row of the window for the 32 lanes of a warp.
+template <typename T>
+struct __align__(16) Stage {
+  typename VT<T>::T4 lin[32];
+  typename VT<T>::T2 xu[32];
+  T xp[32];
+  uint32_t cm[32];   // the 4-byte word of the constraint mask holding this slot's byte
+};
+
+template <typename T>
+struct WarpSmem {
+  Stage<T> st[DEPTH];
+  int32_t code[NROWS][32];
+};
+
+// Storage code of window slot (n, r) of a regular brick.
+__device__ __forceinline__ int32_t regular_code(int nbase, int n, int r) {
+  const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
+  const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
+  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1);
+  return base + (n - dx * NB) + NB * (r - dy * NB);
+}
+
+// Issue the copies of one node row (code per lane) into a ring stage.
 template <typename T, int OP>
-__device__ __forceinline__ void load_node(const ApplyArgs& a, int irr, int nbase, int n, int r, NodeVal<T>& v) {
+__device__ __forceinline__ void issue_row(const ApplyArgs& a, int32_t code, Stage<T>& st, int lane) {
   using N = Needs<OP>;
   using T2 = typename VT<T>::T2;
   using T4 = typename VT<T>::T4;
-  int32_t code;
-  if (irr < 0) {
-    const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
-    const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
-    const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1);
-    code = base + (n - dx * NB) + NB * (r - dy * NB);
-  } else {
-    code = a.lay.win[irr * (WN * WN) + (n + 1) + WN * (r + 1)];
+  if (code >= 0) {
+    cp_async_x(&st.lin[lane], reinterpret_cast<const T4*>(a.lin) + code);
+    if (N::xu) cp_async_x(&st.xu[lane], reinterpret_cast<const T2*>(a.xu) + code);
+    if (N::xp) cp_async_x(&st.xp[lane], reinterpret_cast<const T*>(a.xp) + code);
+    cp_async4(&st.cm[lane], reinterpret_cast<const uint32_t*>(a.cmask + (code & ~3)));
   }
-  const T2* xu = reinterpret_cast<const T2*>(a.xu);
-  const T* xp = reinterpret_cast<const T*>(a.xp);
-  const T4* lin = reinterpret_cast<const T4*>(a.lin);
+}
+
+// Node value of window slot with storage code `code` from the ring stage
+// (regular slots) or from global memory (hanging nodes: constraint applied).
+template <typename T, int OP>
+__device__ __forceinline__ void take_node(const ApplyArgs& a, int32_t code, const Stage<T>& st, int lane,
+                                          NodeVal<T>& v, uint8_t& cmv) {
+  using N = Needs<OP>;
+  using T2 = typename VT<T>::T2;
+  using T4 = typename VT<T>::T4;
   const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
   v.x0 = 0; v.x1 = 0; v.xp = 0;
   v.L.x = 0; v.L.y = 0; v.L.z = 0; v.L.w = 0;
+  cmv = 0;
   if (code >= 0) {
-    if (N::xu) { const T2 q = ldg(xu + code); v.x0 = q.x; v.x1 = q.y; }
-    if (N::xp) v.xp = ldg(xp + code);
-    v.L = ldg4(lin + code);
-    if (mask) {
-      const uint8_t cm = ldg(a.cmask + code);
-      if (cm) {
-        if (cm & 1) v.x0 = 0;
-        if (cm & 2) v.x1 = 0;
-        if (cm & 4) v.xp = 0;
-      }
+    v.L = st.lin[lane];
+    if (N::xu) { const T2 q = st.xu[lane]; v.x0 = q.x; v.x1 = q.y; }
+    if (N::xp) v.xp = st.xp[lane];
+    cmv = uint8_t(st.cm[lane] >> (8 * (code & 3)));
+    if (mask && cmv) {
+      if (cmv & 1) v.x0 = 0;
+      if (cmv & 2) v.x1 = 0;
+      if (cmv & 4) v.xp = 0;
     }
   } else if (code <= -2) {
+    const T2* xu = reinterpret_cast<const T2*>(a.xu);
+    const T* xp = reinterpret_cast<const T*>(a.xp);
     const DevHanging& h = a.hang[-2 - code];
-    v.L = ldg4(lin + h.slot);
+    v.L = ldg4(reinterpret_cast<const T4*>(a.lin) + h.slot);
     const int np = a.fe_degree + 1;
     for (int b = 0; b < np; ++b) {
       const int ps = h.parent[b];
@@ -420,97 +475,120 @@ __global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __
   constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<T>& ws = reinterpret_cast<WarpSmem<T>*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int nunits = a.lay.nbricks * NSEG;
-  // persistent warps: grid-stride over strips (unit is uniform per warp)
-  for (int unit = blockIdx.x * WARPS + (threadIdx.x >> 5); unit < nunits; unit += gridDim.x * WARPS) {
-  const int b = unit / NSEG;
-  const int r0 = (unit % NSEG) * RSEG;
-  const BrickDesc* bd = a.lay.bricks + b;
-  const int nbase = lane < 9 ? __ldg(bd->nbr_base + lane) : 0;
-  const int irr = __ldg(&bd->irr);
-  const int level = __ldg(&bd->level);
-  const CellConst<T>& cc = cconst<T>(a, level);
-  const int n = lane - 1;  // node column of this lane (-1..30)
-  const int own_base = __shfl_sync(FULL, nbase, 4);
   T2* yu = reinterpret_cast<T2*>(a.yu);
   T* yp = reinterpret_cast<T*>(a.yp);
-
-  NodeVal<T> cur, nxt, curR;
-  load_node<T, OP>(a, irr, nbase, n, r0 - 1, cur);
-  load_node<T, OP>(a, irr, nbase, n, r0, nxt);
-  curR = shfl_down_node<T, OP>(cur);
-  T carry[3] = {0, 0, 0};
+  // persistent warps: grid-stride over strips (unit is uniform per warp)
+  for (int unit = blockIdx.x * WARPS + (threadIdx.x >> 5); unit < nunits; unit += gridDim.x * WARPS) {
+    const int b = unit / NSEG;
+    const int r0 = (unit % NSEG) * RSEG;
+    const BrickDesc* bd = a.lay.bricks + b;
+    const int nbase = lane < 9 ? __ldg(bd->nbr_base + lane) : 0;
+    const int irr = __ldg(&bd->irr);
+    const int level = __ldg(&bd->level);
+    const CellConst<T>& cc = cconst<T>(a, level);
+    const int n = lane - 1;  // node column of this lane (-1..30)
+    const int own_base = __shfl_sync(FULL, nbase, 4);
+    // storage codes of the strip's window column
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NROWS; ++i) {
+      const int r = r0 - 1 + i;
+      ws.code[i][lane] = irr < 0 ? regular_code(nbase, n, r) : __ldg(a.lay.win + irr * (WN * WN) + (n + 1) + WN * (r + 1));
+    }
+    // prologue: rows 0 .. DEPTH-2 in flight
+#pragma unroll
+    for (int i = 0; i < DEPTH - 1; ++i) {
+      issue_row<T, OP>(a, ws.code[i][lane], ws.st[i], lane);
+      cp_async_commit();
+    }
+    NodeVal<T> cur, curR;
+    uint8_t cmcur = 0;
+    T carry[3] = {0, 0, 0};
 #pragma unroll 1
-  for (int c = r0 - 1; c < r0 + RSEG; ++c) {
-    // prefetch node row c + 2
-    NodeVal<T> pre = nxt;
-    if (c + 2 <= r0 + RSEG) load_node<T, OP>(a, irr, nbase, n, c + 2, pre);
-    const NodeVal<T> nxtR = shfl_down_node<T, OP>(nxt);
-    bool act = lane < NCW;
-    if (irr >= 0 && act) {
-      const int ci = (c + 1) * NCW + lane;  // window cell (n, c) -> (lane, c+1)
-      act = (__ldg(a.lay.cellmask + irr * 31 + (ci >> 5)) >> (ci & 31)) & 1u;
-    }
-    T out[12];
-    if (act) {
-      NodeVal<T> v[4] = {cur, curR, nxt, nxtR};
-      q1_cell<T, OP>(v, cc, out);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) out[q] = 0;
-    }
-    // contributions of the left neighbour's cell (n-1, c): its BR (node (n, c)) and TR (node (n, c+1))
-    T brL[3], trL[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      brL[q] = __shfl_up_sync(FULL, out[3 + q], 1);
-      trL[q] = __shfl_up_sync(FULL, out[9 + q], 1);
-    }
-    if (c >= r0 && lane >= 1 && lane <= NB) {
-      // node (n, c) complete: cells (n-1, c-1) TR + (n, c-1) TL (carry), (n-1, c) BR, (n, c) BL
-      T y[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) y[q] = (carry[q] + brL[q]) + out[q];
-      const int o = n + NB * c;  // owned slot
-      int act_s = kActFinal, part = -1;
-      if (irr >= 0) {
-        act_s = __ldg(a.lay.own_act + irr * (NB * NB) + o);
-        part = __ldg(a.lay.own_part + irr * (NB * NB) + o);
+    for (int i = 0; i < NROWS; ++i) {
+      if (i + DEPTH - 1 < NROWS) issue_row<T, OP>(a, ws.code[i + DEPTH - 1][lane], ws.st[(i + DEPTH - 1) % DEPTH], lane);
+      cp_async_commit();
+      cp_async_wait<DEPTH - 1>();
+      NodeVal<T> nxt;
+      uint8_t cmnxt;
+      const int32_t codei = ws.code[i][lane];
+      take_node<T, OP>(a, codei, ws.st[i % DEPTH], lane, nxt, cmnxt);
+      const NodeVal<T> nxtR = shfl_down_node<T, OP>(nxt);
+      if (i == 0) {
+        cur = nxt; curR = nxtR; cmcur = cmnxt;
+        continue;
       }
-      const int slot = own_base + o;
-      if (part >= 0) {
-        T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
-        ib[0] = y[0]; ib[1] = y[1]; ib[2] = y[2];
+      const int c = r0 - 2 + i;  // cell row between node rows c (cur) and c + 1 (nxt)
+      bool act = lane < NCW;
+      if (irr >= 0 && act) {
+        const int ci = (c + 1) * NCW + lane;
+        act = (__ldg(a.lay.cellmask + irr * 31 + (ci >> 5)) >> (ci & 31)) & 1u;
       }
-      if (act_s == kActFinal) {
-        const uint8_t cm = ldg(a.cmask + slot);
-        if (isDiag) {
-          if (outU) { T2 o2; o2.x = (cm & 1) ? T(0) : y[0]; o2.y = (cm & 2) ? T(0) : y[1]; yu[slot] = o2; }
-          if (outP) yp[slot] = (cm & 4) ? T(0) : y[2];
-        } else {
-          if (cm) {
-            const bool ident = (a.mode & MODE_IDENTITY) != 0;
-            const T2* xu = reinterpret_cast<const T2*>(a.xu);
-            const T* xp = reinterpret_cast<const T*>(a.xp);
-            if (cm & 1) y[0] = ident ? ldg(xu + slot).x : T(0);
-            if (cm & 2) y[1] = ident ? ldg(xu + slot).y : T(0);
-            if (cm & 4) y[2] = ident ? ldg(xp + slot) : T(0);
-          }
-          if (outU) { T2 o2; o2.x = y[0]; o2.y = y[1]; yu[slot] = o2; }
-          if (outP) yp[slot] = y[2];
+      T out[12];
+      if (act) {
+        NodeVal<T> v[4] = {cur, curR, nxt, nxtR};
+        q1_cell<T, OP>(v, cc, out);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) out[q] = 0;
+      }
+      // the left neighbour's cell (n-1, c) contributes BR to node (n, c) and TR to node (n, c+1)
+      T brL[3], trL[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        brL[q] = __shfl_up_sync(FULL, out[3 + q], 1);
+        trL[q] = __shfl_up_sync(FULL, out[9 + q], 1);
+      }
+      if (c >= r0 && lane >= 1 && lane <= NB) {
+        // node (n, c) is complete: carry (cells (n-1,c-1) TR, (n,c-1) TL) + (n-1,c) BR + (n,c) BL
+        T y[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) y[q] = (carry[q] + brL[q]) + out[q];
+        const int o = n + NB * c;  // owned slot
+        int act_s = kActFinal, part = -1;
+        if (irr >= 0) {
+          act_s = __ldg(a.lay.own_act + irr * (NB * NB) + o);
+          part = __ldg(a.lay.own_part + irr * (NB * NB) + o);
         }
-      } else if (act_s == kActZero) {
-        if (outU) { T2 o2; o2.x = 0; o2.y = 0; yu[slot] = o2; }
-        if (outP) yp[slot] = 0;
+        const int slot = own_base + o;
+        if (part >= 0) {
+          T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
+          ib[0] = y[0]; ib[1] = y[1]; ib[2] = y[2];
+        }
+        if (act_s == kActFinal) {
+          // a home, single-level node: its slot is the window slot (n, c), whose mask is cmcur
+          const uint8_t cm = cmcur;
+          if (isDiag) {
+            if (outU) { T2 o2; o2.x = (cm & 1) ? T(0) : y[0]; o2.y = (cm & 2) ? T(0) : y[1]; yu[slot] = o2; }
+            if (outP) yp[slot] = (cm & 4) ? T(0) : y[2];
+          } else {
+            if (cm) {
+              const bool ident = (a.mode & MODE_IDENTITY) != 0;
+              const T2* xu = reinterpret_cast<const T2*>(a.xu);
+              const T* xp = reinterpret_cast<const T*>(a.xp);
+              if (cm & 1) y[0] = ident ? ldg(xu + slot).x : T(0);
+              if (cm & 2) y[1] = ident ? ldg(xu + slot).y : T(0);
+              if (cm & 4) y[2] = ident ? ldg(xp + slot) : T(0);
+            }
+            if (outU) { T2 o2; o2.x = y[0]; o2.y = y[1]; yu[slot] = o2; }
+            if (outP) yp[slot] = y[2];
+          }
+        } else if (act_s == kActZero) {
+          if (outU) { T2 o2; o2.x = 0; o2.y = 0; yu[slot] = o2; }
+          if (outP) yp[slot] = 0;
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) carry[q] = out[6 + q] + trL[q];
-    cur = nxt;
-    curR = nxtR;
-    nxt = pre;
-  }
+      for (int q = 0; q < 3; ++q) carry[q] = out[6 + q] + trL[q];
+      cur = nxt;
+      curR = nxtR;
+      cmcur = cmnxt;
+    }
+    cp_async_wait<0>();
   }  // unit
 }
 
@@ -584,7 +662,7 @@ void fill_cc(CellConst<T>& c, const ApplyArgs& a, double hx, double hy) {
 }  // namespace
 
 // Blocks of `threads` threads of kernel fn that fit on all SMs at once (cached per kernel).
-int resident_blocks(const void* fn, int threads) {
+int resident_blocks(const void* fn, int threads, size_t smem) {
   static std::mutex mu;
   static std::unordered_map<const void*, int> cache;
   std::lock_guard<std::mutex> lock(mu);
@@ -593,7 +671,8 @@ int resident_blocks(const void* fn, int threads) {
   int dev = 0, sms = 1, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   const int n = sms * per_sm;
   cache[fn] = n;
   return n;
@@ -612,8 +691,9 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
   const int units = a.lay.nbricks * NSEG;
   const unsigned blk = 32 * WARPS;
+  const size_t smem = sizeof(WarpSmem<T>) * WARPS;
   auto grid_of = [&](const void* fn) -> unsigned {
-    const int full = resident_blocks(fn, int(blk));
+    const int full = resident_blocks(fn, int(blk), smem);
     const int need = (units + WARPS - 1) / WARPS;
     return unsigned(need < full ? need : full);
   };
@@ -621,7 +701,7 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
 #define PFF_LAUNCH(OPV)                                                                        \
     case OPV: {                                                                                \
       const void* fn = reinterpret_cast<const void*>(&apply_q1_kernel<T, OPV>);               \
-      apply_q1_kernel<T, OPV><<<grid_of(fn), blk, 0, s>>>(a);                                  \
+      apply_q1_kernel<T, OPV><<<grid_of(fn), blk, smem, s>>>(a);                               \
       break;                                                                                   \
     }
     PFF_LAUNCH(OP_FULL)

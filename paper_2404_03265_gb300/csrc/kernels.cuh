@@ -44,17 +44,22 @@ struct DevLayout {
   const uint32_t* cellmask = nullptr;
 };
 
-// Per-level cell constants of the Q1 kernels, precomputed on the host in the
-// kernel's precision (no double arithmetic inside FP32 kernels).
+// Material constants of the cell kernels (level independent), precomputed on
+// the host in the kernel's precision (no double arithmetic in FP32 kernels).
 template <typename T>
-struct CellConst {
-  T ihx, ihy;          // 1/hx, 1/hy
+struct MatConst {
   T c2ml, cl, cm;      // 2 mu + lambda, lambda, mu
-  T omk, kap, p;       // 1 - kappa, kappa, p
+  T omk, kap, p, p2;   // 1 - kappa, kappa, p, 2 p
   T gcl, gcL;          // G_c / l, G_c l
-  T jxw;               // hx hy / 4 (2x2 Gauss weight times cell area)
+};
+
+// Geometry of a Cartesian hx x hy cell of one refinement level.
+template <typename T>
+struct LevGeom {
+  T ihx, ihy;          // 1/hx, 1/hy
+  T jxw;               // hx hy / 4: 2x2 Gauss weight times cell area
   T wx, wy;            // JxW / hx, JxW / hy
-  T wpx, wpy;          // G_c l JxW / hx^2, G_c l JxW / hy^2
+  T wpx, wpy;          // 2 G_c l JxW / hx^2, 2 G_c l JxW / hy^2
 };
 
 struct ApplyArgs {
@@ -70,8 +75,10 @@ struct ApplyArgs {
   double hx[kMaxLevels], hy[kMaxLevels];
   double mu, lam;         // Lame constants (E already applied)
   double kappa, p, gc_over_l, gc_times_l;
-  CellConst<float> cf[kMaxLevels];
-  CellConst<double> cd[kMaxLevels];
+  MatConst<float> mf;
+  MatConst<double> md;
+  LevGeom<float> gf[kMaxLevels];
+  LevGeom<double> gd[kMaxLevels];
   int mode;
   int fe_degree;
 };
@@ -91,7 +98,7 @@ struct FixupArgs {
   int mode;
 };
 
-// fills cf / cd from hx, hy and the material
+// fills mf / md / gf / gd from hx, hy and the material
 void fill_cell_constants(ApplyArgs& a, int nlevels);
 
 // launchers (return cudaError_t of the launch)

@@ -499,11 +499,11 @@ __global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __
 #pragma unroll
     for (int i = 0; i < NROWS; ++i) {
       const int r = r0 - 1 + i;
-      int32_t cA, cB;
-      if (irr < 0) {
-        cA = regular_code(nbase, nA, r);
-        cB = regular_code(nbase, nB, r);
-      } else {
+      // the shuffles in regular_code run on all 32 lanes (the two half-warps may
+      // hold a regular and an irregular brick)
+      int32_t cA = regular_code(nbase, nA, r);
+      int32_t cB = regular_code(nbase, nB, r);
+      if (irr >= 0) {
         const int32_t* w = a.lay.win + irr * (WN * WN) + WN * (r + 1);
         cA = __ldg(w + colA);
         cB = __ldg(w + colB);

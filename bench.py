@@ -136,14 +136,15 @@ def build_sets(mesh, n_sets, dtype, seed=0):
         return out
 
     dev = torch.device("cuda")
-    us, ps, pts = (torch.tensor(slots(a), device=dev) for a in (u, phi, phit))
+    us = torch.tensor(slots(u).T.copy(), device=dev)
+    ps, pts = (torch.tensor(slots(a), device=dev) for a in (phi, phit))
     xs = slots(xin)
     sets = []
     eps = 2.0 * info["h_min"]
     for r in range(n_sets):
         pb = Problem(mesh, E=1.0, nu=0.2, Gc=1.0, eps=eps, kappa=1e-10, p=1e-3)
         pb.set_state(us, ps, pts)
-        xu = torch.tensor(xs[:, :2], device=dev, dtype=dtype)
+        xu = torch.tensor(xs[:, :2].T.copy(), device=dev, dtype=dtype)
         xp = torch.tensor(xs[:, 2], device=dev, dtype=dtype)
         sets.append((pb, xu, xp, torch.empty_like(xu), torch.empty_like(xp)))
     return sets

@@ -14,8 +14,9 @@
  * - Vectors are caller-owned DEVICE pointers in the library's node layout:
  *   n_slots entries (pff_mesh_info.n_slots), one per node slot.  Slots that hold
  *   no node ("holes", pff_mesh_slots flags bit0 clear) are ignored on input and
- *   written as 0 on output.  A displacement vector is interleaved (u_x, u_y) per
- *   slot (2*n_slots values), a phase-field vector has one value per slot.
+ *   written as 0 on output.  A displacement vector is stored in block layout:
+ *   n_slots values of u_x followed by n_slots values of u_y (2*n_slots values);
+ *   a phase-field vector has one value per slot.
  *   Values of hanging nodes are ignored on input (they follow from the
  *   constraint) and written as 0 by operators.
  * - stream is a cudaStream_t passed as void* (NULL = legacy default stream);

@@ -87,7 +87,7 @@ class Problem:
         self.n_slots = mesh.info["n_slots"]
 
     def set_state(self, u, phi, phit, stream=None):
-        """u: float64 (n_slots, 2), phi, phit: float64 (n_slots,) CUDA tensors."""
+        """u: float64 (2, n_slots) (u_x block, u_y block), phi, phit: float64 (n_slots,) CUDA tensors."""
         _lib.check(_lib.lib().pff_set_state(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phit),
                                             _lib.stream_ptr(stream)))
 

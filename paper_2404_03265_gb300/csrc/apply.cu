@@ -39,23 +39,25 @@ constexpr int NB = 30;          // owned node slots per brick side
 constexpr int WN = 32;          // window nodes per side (columns -1..30)
 constexpr int NCW = 31;         // window cells per side (cells -1..29)
 #ifndef PFF_RSEG
-#define PFF_RSEG 10
+#define PFF_RSEG 15
 #endif
 #ifndef PFF_WARPS
 #define PFF_WARPS 4
 #endif
 #ifndef PFF_MINB
-#define PFF_MINB 1
+#define PFF_MINB 4
+#endif
+#ifndef PFF_MINB64
+#define PFF_MINB64 2
 #endif
 #ifndef PFF_DEPTH
 #define PFF_DEPTH 4
 #endif
-constexpr int RSEG = PFF_RSEG;    // node rows per strip (divides NB)
-constexpr int NSEG = NB / RSEG;
-constexpr int WARPS = PFF_WARPS;  // warps per CTA; each warp sweeps two strips
+constexpr int RSEG = PFF_RSEG;    // node rows per half-warp strip (two strips per brick)
+constexpr int WARPS = PFF_WARPS;  // warps per CTA; one brick per warp
 constexpr int DEPTH = PFF_DEPTH;  // ring stages (rows in flight: DEPTH-1)
 constexpr int NROWS = RSEG + 2;   // node rows a strip reads
-static_assert(NB % RSEG == 0, "strip height must divide the brick");
+static_assert(2 * RSEG == NB, "a brick is two half-warp strips");
 
 // 2-point Gauss rule on [0, 1]
 constexpr double GA = 0.21132486540518711775;
@@ -310,132 +312,170 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
 }
-template <typename X>
-__device__ __forceinline__ void cp_async_x(X* dst, const X* src) {
-  if constexpr (sizeof(X) == 4) cp_async4(dst, src);
-  else if constexpr (sizeof(X) == 8) cp_async8(dst, src);
-  else if constexpr (sizeof(X) == 16) cp_async16(dst, src);
-  else { cp_async16(dst, src); cp_async16(reinterpret_cast<char*>(dst) + 16, reinterpret_cast<const char*>(src) + 16); }
+// copies of one value / one adjacent pair of values of type T
+template <typename T>
+__device__ __forceinline__ void cp_one(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+}
+template <typename T>
+__device__ __forceinline__ void cp_pair(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4) cp_async8(dst, src); else cp_async16(dst, src);
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
-// One ring stage: one node row of the window (32 columns) for a half-warp.
+// Node fields in a ring stage (structure of arrays over the 32 columns of a
+// half-warp; lane l holds columns 2l, 2l+1, so its pair is one aligned load).
+enum Field : int { F_XU = 0, F_XV = 1, F_XP = 2, F_LU = 3, F_LV = 4, F_LP = 5, F_LT = 6, NF = 7 };
+
+template <int OP>
+__device__ __forceinline__ constexpr bool field_used(int f) {
+  using N = Needs<OP>;
+  return f == F_XU || f == F_XV ? N::xu : f == F_XP ? N::xp : f == F_LU || f == F_LV ? N::linU
+         : f == F_LP ? N::phi : N::phit;
+}
+
 template <typename T>
 struct __align__(16) Stage {
-  typename VT<T>::T4 lin[32];
-  typename VT<T>::T2 xu[32];
-  T xp[32];
-  uint32_t cm[32];   // the 4-byte word of the constraint mask holding the slot's byte
+  T f[NF][32];
+  uint32_t cm[32];   // constraint-mask words (4 slots per word) of the columns' slots
 };
 
 template <typename T>
 struct HalfSmem {
   Stage<T> st[DEPTH];
-  int32_t code[NROWS][32];
+  int32_t code[NROWS][32];   // storage codes of the lane columns per strip row
 };
 
-// Storage code of window slot (n, r) of a regular brick (half-warp shuffle of
-// the 3x3 neighbour bases held by lanes 0..8 of the half-warp).
+template <typename T>
+__device__ __forceinline__ const T* field_ptr(const ApplyArgs& a, int f) {
+  const T* xu = reinterpret_cast<const T*>(a.xu);
+  const T* lin = reinterpret_cast<const T*>(a.lin);
+  switch (f) {
+    case F_XU: return xu;
+    case F_XV: return xu + a.n_slots;
+    case F_XP: return reinterpret_cast<const T*>(a.xp);
+    default: return lin + (f - F_LU) * a.n_slots;
+  }
+}
+
+// Storage code of node (n, r) (brick-relative, -1..30) of a regular brick; the
+// 3x3 neighbour bases are held by lanes 0..8 of the warp.  All lanes call it.
 __device__ __forceinline__ int32_t regular_code(int nbase, int n, int r) {
   const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
   const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
-  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1, 16);
+  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1);
   return base + (n - dx * NB) + NB * (r - dy * NB);
 }
 
+// Issue the copies of the lane's two columns of one strip row.
 template <typename T, int OP>
-__device__ __forceinline__ void issue_slot(const ApplyArgs& a, int32_t code, Stage<T>& st, int col) {
-  using N = Needs<OP>;
-  using T2 = typename VT<T>::T2;
-  using T4 = typename VT<T>::T4;
-  if (code >= 0) {
-    cp_async_x(&st.lin[col], reinterpret_cast<const T4*>(a.lin) + code);
-    if (N::xu) cp_async_x(&st.xu[col], reinterpret_cast<const T2*>(a.xu) + code);
-    if (N::xp) cp_async_x(&st.xp[col], reinterpret_cast<const T*>(a.xp) + code);
-    cp_async4(&st.cm[col], reinterpret_cast<const uint32_t*>(a.cmask + (code & ~3)));
+__device__ __forceinline__ void issue_row(const ApplyArgs& a, bool pairwise, int32_t cA, int32_t cB, Stage<T>& st,
+                                          int hl) {
+  const int jA = 2 * hl, jB = 2 * hl + 1;
+  if (pairwise) {  // both slots present, adjacent and 2-aligned
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (field_used<OP>(f)) cp_pair(&st.f[f][jA], field_ptr<T>(a, f) + cA);
+    cp_async4(&st.cm[jA], reinterpret_cast<const uint32_t*>(a.cmask + (cA & ~3)));
+  } else {
+    if (cA >= 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if (field_used<OP>(f)) cp_one(&st.f[f][jA], field_ptr<T>(a, f) + cA);
+      cp_async4(&st.cm[jA], reinterpret_cast<const uint32_t*>(a.cmask + (cA & ~3)));
+    }
+    if (cB >= 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if (field_used<OP>(f)) cp_one(&st.f[f][jB], field_ptr<T>(a, f) + cB);
+      cp_async4(&st.cm[jB], reinterpret_cast<const uint32_t*>(a.cmask + (cB & ~3)));
+    }
   }
 }
 
-// Node value of a window slot from the ring stage (stored slots) or from
-// global memory (hanging nodes: constraint x_h = sum w x_parent).
+// Make the landed row usable: masked components zeroed, absent slots zeroed,
+// hanging slots filled from their constraint x_h = sum w x_parent.  Returns
+// the constraint-mask byte of the column.
 template <typename T, int OP>
-__device__ __forceinline__ void take_slot(const ApplyArgs& a, int32_t code, const Stage<T>& st, int col, T& x0, T& x1,
-                                          T& xp, typename VT<T>::T4& L, uint8_t& cmv) {
+__device__ __forceinline__ uint8_t settle_slot(const ApplyArgs& a, int32_t code, Stage<T>& st, int j, uint32_t cmw,
+                                               int byte) {
   using N = Needs<OP>;
-  using T2 = typename VT<T>::T2;
-  using T4 = typename VT<T>::T4;
   const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
-  x0 = 0; x1 = 0; xp = 0;
-  L.x = 0; L.y = 0; L.z = 0; L.w = 0;
-  cmv = 0;
   if (code >= 0) {
-    L = st.lin[col];
-    if (N::xu) { const T2 q = st.xu[col]; x0 = q.x; x1 = q.y; }
-    if (N::xp) xp = st.xp[col];
-    cmv = uint8_t(st.cm[col] >> (8 * (code & 3)));
-    if (mask && cmv) {
-      if (cmv & 1) x0 = 0;
-      if (cmv & 2) x1 = 0;
-      if (cmv & 4) xp = 0;
+    const uint8_t cm = uint8_t(cmw >> (8 * byte));
+    if (mask && cm) {
+      if (N::xu && (cm & 1)) st.f[F_XU][j] = T(0);
+      if (N::xu && (cm & 2)) st.f[F_XV][j] = T(0);
+      if (N::xp && (cm & 4)) st.f[F_XP][j] = T(0);
     }
-  } else if (code <= -2) {
-    const T2* xu = reinterpret_cast<const T2*>(a.xu);
-    const T* xpp = reinterpret_cast<const T*>(a.xp);
-    const DevHanging& h = a.hang[-2 - code];
-    L = ldg4(reinterpret_cast<const T4*>(a.lin) + h.slot);
-    const int np = a.fe_degree + 1;
-    for (int b = 0; b < np; ++b) {
-      const int ps = h.parent[b];
-      const T w = T(h.weight[b]);
-      T p0 = 0, p1 = 0, pp = 0;
-      if (N::xu) { const T2 q = ldg(xu + ps); p0 = q.x; p1 = q.y; }
-      if (N::xp) pp = ldg(xpp + ps);
-      if (mask) {
-        const uint8_t cm = ldg(a.cmask + ps);
-        if (cm & 1) p0 = 0;
-        if (cm & 2) p1 = 0;
-        if (cm & 4) pp = 0;
-      }
-      x0 += w * p0; x1 += w * p1; xp += w * pp;
-    }
+    return cm;
   }
+  if (code == kAbsent) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (field_used<OP>(f)) st.f[f][j] = T(0);
+    return 0;
+  }
+  const DevHanging& h = a.hang[-2 - code];
+#pragma unroll
+  for (int f = F_LU; f < NF; ++f)
+    if (field_used<OP>(f)) st.f[f][j] = ldg(field_ptr<T>(a, f) + h.slot);
+  T v0 = 0, v1 = 0, vp = 0;
+  const int np = a.fe_degree + 1;
+  for (int b = 0; b < np; ++b) {
+    const int ps = h.parent[b];
+    const T w = T(h.weight[b]);
+    T p0 = 0, p1 = 0, pp = 0;
+    if (N::xu) { p0 = ldg(field_ptr<T>(a, F_XU) + ps); p1 = ldg(field_ptr<T>(a, F_XV) + ps); }
+    if (N::xp) pp = ldg(field_ptr<T>(a, F_XP) + ps);
+    if (mask) {
+      const uint8_t cm = ldg(a.cmask + ps);
+      if (cm & 1) p0 = 0;
+      if (cm & 2) p1 = 0;
+      if (cm & 4) pp = 0;
+    }
+    v0 += w * p0; v1 += w * p1; vp += w * pp;
+  }
+  if (N::xu) { st.f[F_XU][j] = v0; st.f[F_XV][j] = v1; }
+  if (N::xp) st.f[F_XP][j] = vp;
+  return 0;
 }
 
-// (own B, right neighbour's A): the right-hand nodes of the two cells
+// The lane's node pair of a settled row, and the right-hand pair (own B, next lane's A).
 template <typename T, int OP>
-__device__ __forceinline__ NodePair<T> right_pair(const NodePair<T>& v) {
-  using N = Needs<OP>;
+__device__ __forceinline__ void read_row(const Stage<T>& st, int hl, int right_lane, NodePair<T>& v, NodePair<T>& r) {
   using P = typename VT<T>::T2;
   const unsigned FULL = 0xffffffffu;
-  NodePair<T> r;
-  auto rp = [&](const P& q, bool need) -> P {
-    P o;
-    o.x = q.y;
-    o.y = need ? __shfl_down_sync(FULL, q.x, 1, 16) : T(0);
-    return o;
-  };
-  r.x0 = rp(v.x0, N::xu);
-  r.x1 = rp(v.x1, N::xu);
-  r.xp = rp(v.xp, N::xp);
-  r.lx = rp(v.lx, N::linU);
-  r.ly = rp(v.ly, N::linU);
-  r.lz = rp(v.lz, N::phi);
-  r.lw = rp(v.lw, N::phit);
-  return r;
+  P* dst[NF] = {&v.x0, &v.x1, &v.xp, &v.lx, &v.ly, &v.lz, &v.lw};
+  P* dsr[NF] = {&r.x0, &r.x1, &r.xp, &r.lx, &r.ly, &r.lz, &r.lw};
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (field_used<OP>(f)) {
+      const P q = *reinterpret_cast<const P*>(&st.f[f][2 * hl]);
+      *dst[f] = q;
+      P o;
+      o.x = q.y;
+      o.y = __shfl_sync(FULL, q.x, right_lane);
+      *dsr[f] = o;
+    } else {
+      *dst[f] = pbc(T(0));
+      *dsr[f] = pbc(T(0));
+    }
+  }
 }
 
-// Final write of owned node (n, c) of the brick: storage action, partial sum,
-// constraint rows.
+// Final write of owned node (n, c) of an irregular brick: storage action,
+// partial sum, constraint rows.
 template <typename T, int OP>
 __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_base, int n, int c, uint8_t cm,
                                            T y0, T y1, T y2) {
-  using T2 = typename VT<T>::T2;
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
   constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
-  T2* yu = reinterpret_cast<T2*>(a.yu);
+  T* yu = reinterpret_cast<T*>(a.yu);
+  T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
   const int o = n + NB * c;
   int act_s = kActFinal, part = -1;
@@ -449,110 +489,100 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
     ib[0] = y0; ib[1] = y1; ib[2] = y2;
   }
   if (act_s == kActFinal) {
-    // a home, single-level node: its storage slot is this window slot, mask cm
     if (isDiag) {
-      if (outU) { T2 o2; o2.x = (cm & 1) ? T(0) : y0; o2.y = (cm & 2) ? T(0) : y1; yu[slot] = o2; }
-      if (outP) yp[slot] = (cm & 4) ? T(0) : y2;
-    } else {
-      if (cm) {
-        const bool ident = (a.mode & MODE_IDENTITY) != 0;
-        const T2* xu = reinterpret_cast<const T2*>(a.xu);
-        const T* xp = reinterpret_cast<const T*>(a.xp);
-        if (cm & 1) y0 = ident ? ldg(xu + slot).x : T(0);
-        if (cm & 2) y1 = ident ? ldg(xu + slot).y : T(0);
-        if (cm & 4) y2 = ident ? ldg(xp + slot) : T(0);
-      }
-      if (outU) { T2 o2; o2.x = y0; o2.y = y1; yu[slot] = o2; }
-      if (outP) yp[slot] = y2;
+      if (cm & 1) y0 = T(0);
+      if (cm & 2) y1 = T(0);
+      if (cm & 4) y2 = T(0);
+    } else if (cm) {
+      const bool ident = (a.mode & MODE_IDENTITY) != 0;
+      const T* xu = reinterpret_cast<const T*>(a.xu);
+      if (cm & 1) y0 = ident ? ldg(xu + slot) : T(0);
+      if (cm & 2) y1 = ident ? ldg(xu + a.n_slots + slot) : T(0);
+      if (cm & 4) y2 = ident ? ldg(reinterpret_cast<const T*>(a.xp) + slot) : T(0);
     }
+    if (outU) { yu[slot] = y0; yv[slot] = y1; }
+    if (outP) yp[slot] = y2;
   } else if (act_s == kActZero) {
-    if (outU) { T2 o2; o2.x = 0; o2.y = 0; yu[slot] = o2; }
-    if (outP) yp[slot] = 0;
+    if (outU) { yu[slot] = T(0); yv[slot] = T(0); }
+    if (outP) yp[slot] = T(0);
   }
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
+__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MINB64) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
   using P = typename VT<T>::T2;
-  using T4 = typename VT<T>::T4;
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
+  constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
+  constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int half = lane >> 4, hl = lane & 15;
   HalfSmem<T>& sm = reinterpret_cast<HalfSmem<T>*>(smem_raw)[(threadIdx.x >> 5) * 2 + half];
-  const int nunits = a.lay.nbricks * NSEG;
+  const int right_lane = (half << 4) | ((hl + 1) & 15);
+  const int left_lane = (half << 4) | ((hl + 15) & 15);
   const MatConst<T>& mc = matc<T>(a);
-  const int colA = 2 * hl, colB = 2 * hl + 1;   // window columns (node n = col - 1)
-  const int nA = colA - 1, nB = colB - 1;
-  // persistent warps: each warp sweeps two strips (one per half-warp) per round
-  for (int ubase = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2; ubase < nunits; ubase += gridDim.x * WARPS * 2) {
-    const int unit = ubase + half;
-    const bool valid = unit < nunits;
-    const int b = valid ? unit / NSEG : 0;
-    const int r0 = valid ? (unit % NSEG) * RSEG : 0;
+  // lane columns: nodes (2hl, 2hl+1) for hl < 15; lane 15 holds the halo nodes (30, -1)
+  const int nA = hl < 15 ? 2 * hl : NB, nB = hl < 15 ? 2 * hl + 1 : -1;
+  const int r0 = half * RSEG;
+  T* yu = reinterpret_cast<T*>(a.yu);
+  T* yv = yu + a.n_slots;
+  T* yp = reinterpret_cast<T*>(a.yp);
+  // persistent warps, one brick per warp and round (half-warp h sweeps rows 15h..15h+14)
+  for (int b = blockIdx.x * WARPS + (threadIdx.x >> 5); b < a.lay.nbricks; b += gridDim.x * WARPS) {
     const BrickDesc* bd = a.lay.bricks + b;
-    const int nbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
-    const int irr = valid ? __ldg(&bd->irr) : 0;
+    const int nbase = lane < 9 ? __ldg(bd->nbr_base + lane) : 0;
+    const int irr = __ldg(&bd->irr);
     const LevGeom<T> gq = geom<T>(a, __ldg(&bd->level));
-    const int own_base = __shfl_sync(FULL, nbase, 4, 16);
-    // storage codes of the strip's window rows
+    const int own_base = __shfl_sync(FULL, nbase, 4);
+    const bool pairwise = irr < 0 && hl < 15;
 #pragma unroll
     for (int i = 0; i < NROWS; ++i) {
       const int r = r0 - 1 + i;
-      // the shuffles in regular_code run on all 32 lanes (the two half-warps may
-      // hold a regular and an irregular brick)
       int32_t cA = regular_code(nbase, nA, r);
       int32_t cB = regular_code(nbase, nB, r);
       if (irr >= 0) {
         const int32_t* w = a.lay.win + irr * (WN * WN) + WN * (r + 1);
-        cA = __ldg(w + colA);
-        cB = __ldg(w + colB);
+        cA = __ldg(w + nA + 1);
+        cB = __ldg(w + nB + 1);
       }
-      if (!valid) { cA = kAbsent; cB = kAbsent; }
-      sm.code[i][colA] = cA;
-      sm.code[i][colB] = cB;
+      sm.code[i][2 * hl] = cA;
+      sm.code[i][2 * hl + 1] = cB;
     }
 #pragma unroll
     for (int i = 0; i < DEPTH - 1; ++i) {
-      issue_slot<T, OP>(a, sm.code[i][colA], sm.st[i], colA);
-      issue_slot<T, OP>(a, sm.code[i][colB], sm.st[i], colB);
+      issue_row<T, OP>(a, pairwise, sm.code[i][2 * hl], sm.code[i][2 * hl + 1], sm.st[i], hl);
       cp_async_commit();
     }
-    NodePair<T> cur, curR;
     uint8_t cmA = 0, cmB = 0;
     P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
 #pragma unroll 1
     for (int i = 0; i < NROWS; ++i) {
-      if (i + DEPTH - 1 < NROWS) {
-        Stage<T>& sn = sm.st[(i + DEPTH - 1) % DEPTH];
-        issue_slot<T, OP>(a, sm.code[i + DEPTH - 1][colA], sn, colA);
-        issue_slot<T, OP>(a, sm.code[i + DEPTH - 1][colB], sn, colB);
-      }
-      cp_async_commit();
-      cp_async_wait<DEPTH - 1>();
-      const Stage<T>& si = sm.st[i % DEPTH];
-      NodePair<T> nxt;
+      cp_async_wait<DEPTH - 2>();
+      Stage<T>& si = sm.st[i % DEPTH];
+      const int32_t cA = sm.code[i][2 * hl], cB = sm.code[i][2 * hl + 1];
       uint8_t nmA, nmB;
-      {
-        T a0, a1, ap, b0, b1, bp;
-        T4 La, Lb;
-        take_slot<T, OP>(a, sm.code[i][colA], si, colA, a0, a1, ap, La, nmA);
-        take_slot<T, OP>(a, sm.code[i][colB], si, colB, b0, b1, bp, Lb, nmB);
-        nxt.x0 = P{a0, b0}; nxt.x1 = P{a1, b1}; nxt.xp = P{ap, bp};
-        nxt.lx = P{La.x, Lb.x}; nxt.ly = P{La.y, Lb.y}; nxt.lz = P{La.z, Lb.z}; nxt.lw = P{La.w, Lb.w};
+      if (pairwise) {
+        const uint32_t w = si.cm[2 * hl];
+        nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, w, cA & 3);
+        nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, w, cB & 3);
+      } else {
+        nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, si.cm[2 * hl], cA & 3);
+        nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, si.cm[2 * hl + 1], cB & 3);
       }
-      const NodePair<T> nxtR = right_pair<T, OP>(nxt);
       if (i > 0) {
-        const int c = r0 - 2 + i;  // cell row between node rows c (cur) and c + 1 (nxt)
-        bool actA = true, actB = hl < 15;  // cell columns -1..29 exist in the window
+        const int c = r0 - 2 + i;  // cell row between node rows c and c + 1
+        NodePair<T> v[4];
+        read_row<T, OP>(sm.st[(i - 1) % DEPTH], hl, right_lane, v[0], v[1]);
+        read_row<T, OP>(si, hl, right_lane, v[2], v[3]);
+        bool actA = hl < 15, actB = true;
         if (irr >= 0) {
           const uint32_t* cmw = a.lay.cellmask + irr * 31;
-          const int ia = (c + 1) * NCW + colA, ib = ia + 1;
-          actA = (__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u;
-          actB = actB && ((__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u);
+          const int ib = (c + 1) * NCW + (nB + 1), ia = ib - 1;  // window cells of cells nA (if hl<15) and nB
+          actA = actA && ((__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u);
+          actB = (__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u;
         }
         P out[12];
-        const NodePair<T> v[4] = {cur, curR, nxt, nxtR};
         q1_cell_pair<T, OP>(v, mc, gq, out);
         if (!actA || !actB) {
 #pragma unroll
@@ -561,20 +591,32 @@ __global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __
             if (!actB) out[q].y = T(0);
           }
         }
-        // left lane's cell B contributes BR to our node A (row c), TR to node A (row c+1)
+        // the left lane's cell B contributes BR to our node A (row c) and TR to node A (row c+1)
         T brL[3], trL[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          brL[q] = __shfl_up_sync(FULL, out[3 + q].y, 1, 16);
-          trL[q] = __shfl_up_sync(FULL, out[9 + q].y, 1, 16);
+          brL[q] = __shfl_sync(FULL, out[3 + q].y, left_lane);
+          trL[q] = __shfl_sync(FULL, out[9 + q].y, left_lane);
         }
-        if (c >= r0 && valid) {
-          if (hl >= 1)   // node A: column nA in 0..29
-            write_node<T, OP>(a, irr, own_base, nA, c, cmA, (carry[0].x + brL[0]) + out[0].x,
-                              (carry[1].x + brL[1]) + out[1].x, (carry[2].x + brL[2]) + out[2].x);
-          if (hl <= 14)  // node B: column nB in 0..29
-            write_node<T, OP>(a, irr, own_base, nB, c, cmB, (carry[0].y + out[3].x) + out[0].y,
-                              (carry[1].y + out[4].x) + out[1].y, (carry[2].y + out[5].x) + out[2].y);
+        if (c >= r0 && hl < 15) {
+          T yA[3], yB[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            yA[q] = (carry[q].x + brL[q]) + out[q].x;
+            yB[q] = (carry[q].y + out[3 + q].x) + out[q].y;
+          }
+          if (irr < 0 && !(cmA | cmB)) {
+            // regular brick, unconstrained pair: one aligned pair store per output field
+            const int slot = own_base + nA + NB * c;
+            if (outU) {
+              *reinterpret_cast<P*>(yu + slot) = P{yA[0], yB[0]};
+              *reinterpret_cast<P*>(yv + slot) = P{yA[1], yB[1]};
+            }
+            if (outP) *reinterpret_cast<P*>(yp + slot) = P{yA[2], yB[2]};
+          } else {
+            write_node<T, OP>(a, irr, own_base, nA, c, cmA, yA[0], yA[1], yA[2]);
+            write_node<T, OP>(a, irr, own_base, nB, c, cmB, yB[0], yB[1], yB[2]);
+          }
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -582,19 +624,22 @@ __global__ void __launch_bounds__(32 * WARPS, PFF_MINB) apply_q1_kernel(const __
           carry[q].y = out[6 + q].y + out[9 + q].x;
         }
       }
-      cur = nxt;
-      curR = nxtR;
       cmA = nmA;
       cmB = nmB;
+      // refill the stage of row i-1 (no longer read) with row i+DEPTH-1
+      if (i + DEPTH - 1 < NROWS)
+        issue_row<T, OP>(a, pairwise, sm.code[i + DEPTH - 1][2 * hl], sm.code[i + DEPTH - 1][2 * hl + 1],
+                         sm.st[(i + DEPTH - 1) % DEPTH], hl);
+      cp_async_commit();
     }
     cp_async_wait<0>();
     __syncwarp();
+    (void)isDiag;
   }
 }
 
 template <typename T>
 __global__ void fixup_kernel(const FixupArgs a) {
-  using T2 = typename VT<T>::T2;
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= a.n) return;
   const int slot = a.slot[f];
@@ -608,46 +653,50 @@ __global__ void fixup_kernel(const FixupArgs a) {
     y2 += w * ib[3 * p + 2];
   }
   const uint8_t cm = a.cmask[slot];
+  const T* xu = reinterpret_cast<const T*>(a.xu);
+  const T* xp = reinterpret_cast<const T*>(a.xp);
   if (cm) {
     const bool ident = (a.mode & MODE_IDENTITY) != 0;
-    const T2* xu = reinterpret_cast<const T2*>(a.xu);
-    const T* xp = reinterpret_cast<const T*>(a.xp);
-    if (cm & 1) y0 = ident ? xu[slot].x : T(0);
-    if (cm & 2) y1 = ident ? xu[slot].y : T(0);
+    if (cm & 1) y0 = ident ? xu[slot] : T(0);
+    if (cm & 2) y1 = ident ? xu[a.n_slots + slot] : T(0);
     if (cm & 4) y2 = ident ? xp[slot] : T(0);
   }
-  T2 o; o.x = y0; o.y = y1;
-  reinterpret_cast<T2*>(a.yu)[slot] = o;
+  T* yu = reinterpret_cast<T*>(a.yu);
+  yu[slot] = y0;
+  yu[a.n_slots + slot] = y1;
   reinterpret_cast<T*>(a.yp)[slot] = y2;
 }
 
-__global__ void set_lin_kernel(int64_t n, const double2* __restrict__ u, const double* __restrict__ phi,
-                               const double* __restrict__ phit, dbl4* lin64, float4* lin32) {
+// lin blocks (u_x, u_y, phi, phi_tilde) in FP64 and FP32 from the state
+__global__ void set_lin_kernel(int64_t n, const double* __restrict__ u, const double* __restrict__ phi,
+                               const double* __restrict__ phit, double* lin64, float* lin32) {
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const double2 uu = u[s];
-  dbl4 v;
-  v.x = uu.x; v.y = uu.y; v.z = phi[s]; v.w = phit[s];
-  lin64[s] = v;
-  lin32[s] = make_float4(float(v.x), float(v.y), float(v.z), float(v.w));
+  const double v[4] = {u[s], u[n + s], phi[s], phit[s]};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lin64[k * n + s] = v[k];
+    lin32[k * n + s] = float(v[k]);
+  }
 }
 
-__global__ void set_lin_hanging_kernel(int32_t nh, const DevHanging* __restrict__ hang, int np,
-                                       dbl4* lin64, float4* lin32) {
+__global__ void set_lin_hanging_kernel(int32_t nh, int64_t n, const DevHanging* __restrict__ hang, int np,
+                                       double* lin64, float* lin32) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= nh) return;
   const DevHanging e = hang[h];
-  dbl4 v;
-  v.x = 0; v.y = 0; v.z = 0; v.w = 0;
-  for (int b = 0; b < np; ++b) {
-    const dbl4 p = lin64[e.parent[b]];
-    v.x += e.weight[b] * p.x; v.y += e.weight[b] * p.y;
-    v.z += e.weight[b] * p.z; v.w += e.weight[b] * p.w;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = 0;
+    for (int b = 0; b < np; ++b) v += e.weight[b] * lin64[k * n + e.parent[b]];
+    lin64[k * n + e.slot] = v;
+    lin32[k * n + e.slot] = float(v);
   }
-  lin64[e.slot] = v;
-  lin32[e.slot] = make_float4(float(v.x), float(v.y), float(v.z), float(v.w));
 }
 
+}  // namespace
+
+namespace {
 template <typename T>
 void fill_mat(MatConst<T>& c, const ApplyArgs& a) {
   c.c2ml = T(2.0 * a.mu + a.lam); c.cl = T(a.lam); c.cm = T(a.mu);
@@ -694,7 +743,7 @@ template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
-  const int units = (a.lay.nbricks * NSEG + 1) / 2;  // strip pairs
+  const int units = a.lay.nbricks;  // one brick per warp
   const unsigned blk = 32 * WARPS;
   const size_t smem = sizeof(HalfSmem<T>) * 2 * WARPS;
   auto grid_of = [&](const void* fn) -> unsigned {
@@ -732,13 +781,9 @@ cudaError_t launch_set_lin(int64_t n_slots, const double* u, const double* phi, 
                            const DevHanging* hang, int32_t nhang, int fe_degree,
                            double* lin64, float* lin32, cudaStream_t s) {
   if (n_slots > 0)
-    set_lin_kernel<<<unsigned((n_slots + 255) / 256), 256, 0, s>>>(
-        n_slots, reinterpret_cast<const double2*>(u), phi, phit, reinterpret_cast<dbl4*>(lin64),
-        reinterpret_cast<float4*>(lin32));
+    set_lin_kernel<<<unsigned((n_slots + 255) / 256), 256, 0, s>>>(n_slots, u, phi, phit, lin64, lin32);
   if (nhang > 0)
-    set_lin_hanging_kernel<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, hang, fe_degree + 1,
-                                                                reinterpret_cast<dbl4*>(lin64),
-                                                                reinterpret_cast<float4*>(lin32));
+    set_lin_hanging_kernel<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, n_slots, hang, fe_degree + 1, lin64, lin32);
   return cudaGetLastError();
 }
 

@@ -66,12 +66,13 @@ struct ApplyArgs {
   DevLayout lay;
   const DevHanging* hang;
   const uint8_t* cmask;   // per slot: bit0/bit1 u_x/u_y fixed, bit2 phi fixed
-  const void* lin;        // T4 per slot: (u_x, u_y, phi, phi_tilde), hanging entries resolved
-  const void* xu;         // T2 per slot
-  const void* xp;         // T per slot
+  const void* lin;        // 4 blocks of n_slots T: u_x, u_y, phi, phi_tilde (hanging entries resolved)
+  const void* xu;         // 2 blocks of n_slots T: u_x, u_y
+  const void* xp;         // n_slots T
   void* yu;
   void* yp;
   void* ibuf;             // 3 T per partial slot
+  int64_t n_slots;
   double hx[kMaxLevels], hy[kMaxLevels];
   double mu, lam;         // Lame constants (E already applied)
   double kappa, p, gc_over_l, gc_times_l;
@@ -85,6 +86,7 @@ struct ApplyArgs {
 
 struct FixupArgs {
   int32_t n;
+  int64_t n_slots;
   const int32_t* slot;
   const int32_t* ptr;
   const int32_t* part;
@@ -107,7 +109,8 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fixup(const FixupArgs& a, cudaStream_t s);
 
-// state conversion: lin64/lin32[slot] = (u_x, u_y, phi, phi_t) with hanging entries from parents
+// state conversion: lin64/lin32 blocks (u_x, u_y, phi, phi_t), hanging entries from parents;
+// u is the displacement in block layout (u_x block, u_y block)
 cudaError_t launch_set_lin(int64_t n_slots, const double* u, const double* phi, const double* phit,
                            const DevHanging* hang, int32_t nhang, int fe_degree,
                            double* lin64, float* lin32, cudaStream_t s);

@@ -96,6 +96,7 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
   a.lin = precision == PFF_F64 ? static_cast<const void*>(pb.lin64) : static_cast<const void*>(pb.lin32);
   a.xu = xu; a.xp = xp; a.yu = yu; a.yp = yp;
   a.ibuf = precision == PFF_F64 ? static_cast<void*>(pb.ibuf64) : static_cast<void*>(pb.ibuf32);
+  a.n_slots = M.lay.n_slots;
   for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) {
     a.hx[l] = M.tree.hx(l);
     a.hy[l] = M.tree.hy(l);
@@ -108,7 +109,7 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
   else if (op == PFF_OP_TRANSPOSE) { kop = OP_FULL_T; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }
   else { kop = OP_FULL; a.mode = 0; }
   FixupArgs f;
-  f.n = D.nfix; f.slot = D.fix_slot; f.ptr = D.fix_ptr; f.part = D.fix_part; f.w = D.fix_w;
+  f.n = D.nfix; f.n_slots = M.lay.n_slots; f.slot = D.fix_slot; f.ptr = D.fix_ptr; f.part = D.fix_part; f.w = D.fix_w;
   f.cmask = pb.cmask; f.xu = xu; f.xp = xp; f.yu = yu; f.yp = yp; f.ibuf = a.ibuf; f.mode = a.mode;
   cudaError_t e;
   if (precision == PFF_F64) {

@@ -33,7 +33,7 @@ def run_lib(P, mat, u, phi, phit, active, x, prec, op):
     from paper_2404_03265_gb300 import PFF_OP_CONDENSED, PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, Problem
     dev = torch.device("cuda:0")
     pb = Problem(P.lm, **mat)
-    us = torch.tensor(P.to_slots(u), device=dev)
+    us = torch.tensor(P.to_slots(u).T.copy(), device=dev)
     ps = torch.tensor(P.to_slots(phi), device=dev)
     pts = torch.tensor(P.to_slots(phit), device=dev)
     pb.set_state(us, ps, pts)
@@ -45,14 +45,14 @@ def run_lib(P, mat, u, phi, phit, active, x, prec, op):
     xs[holes] = 1e30
     hang = P.slots[(P.slot_F[P.slots] & 4) != 0]
     xs[hang] = 7.0
-    xu = torch.tensor(xs[:, :2].copy(), device=dev, dtype=dt)
+    xu = torch.tensor(xs[:, :2].T.copy(), device=dev, dtype=dt)
     xp = torch.tensor(xs[:, 2].copy(), device=dev, dtype=dt)
     yu = torch.full_like(xu, float("nan"))
     yp = torch.full_like(xp, float("nan"))
     opc = {"jacobian": PFF_OP_JACOBIAN, "transpose": PFF_OP_TRANSPOSE, "condensed": PFF_OP_CONDENSED}[op]
     pb.apply(xu, xp, yu, yp, op=opc)
     torch.cuda.synchronize()
-    ys = np.concatenate([yu.cpu().double().numpy(), yp.cpu().double().numpy()[:, None]], axis=1)
+    ys = np.concatenate([yu.cpu().double().numpy().T, yp.cpu().double().numpy()[:, None]], axis=1)
     return ys
 
 

@@ -53,11 +53,12 @@ constexpr int NCW = 31;         // window cells per side (cells -1..29)
 #ifndef PFF_DEPTH
 #define PFF_DEPTH 4
 #endif
-constexpr int RSEG = PFF_RSEG;    // node rows per half-warp strip (two strips per brick)
-constexpr int WARPS = PFF_WARPS;  // warps per CTA; one brick per warp
+constexpr int RSEG = PFF_RSEG;    // node rows per half-warp strip
+constexpr int NSEG = NB / RSEG;   // strips per brick
+constexpr int WARPS = PFF_WARPS;  // warps per CTA; a half-warp sweeps one strip per round
 constexpr int DEPTH = PFF_DEPTH;  // ring stages (rows in flight: DEPTH-1)
 constexpr int NROWS = RSEG + 2;   // node rows a strip reads
-static_assert(2 * RSEG == NB, "a brick is two half-warp strips");
+static_assert(NB % RSEG == 0, "strip height must divide the brick");
 
 // 2-point Gauss rule on [0, 1]
 constexpr double GA = 0.21132486540518711775;
@@ -361,11 +362,12 @@ __device__ __forceinline__ const T* field_ptr(const ApplyArgs& a, int f) {
 }
 
 // Storage code of node (n, r) (brick-relative, -1..30) of a regular brick; the
-// 3x3 neighbour bases are held by lanes 0..8 of the warp.  All lanes call it.
+// 3x3 neighbour bases are held by lanes 0..8 of each half-warp.  All 32 lanes
+// call it (the two half-warps may hold different bricks).
 __device__ __forceinline__ int32_t regular_code(int nbase, int n, int r) {
   const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
   const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
-  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1);
+  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1, 16);
   return base + (n - dx * NB) + NB * (r - dy * NB);
 }
 
@@ -524,18 +526,22 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   const MatConst<T>& mc = matc<T>(a);
   // lane columns: nodes (2hl, 2hl+1) for hl < 15; lane 15 holds the halo nodes (30, -1)
   const int nA = hl < 15 ? 2 * hl : NB, nB = hl < 15 ? 2 * hl + 1 : -1;
-  const int r0 = half * RSEG;
   T* yu = reinterpret_cast<T*>(a.yu);
   T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
-  // persistent warps, one brick per warp and round (half-warp h sweeps rows 15h..15h+14)
-  for (int b = blockIdx.x * WARPS + (threadIdx.x >> 5); b < a.lay.nbricks; b += gridDim.x * WARPS) {
+  const int nunits = a.lay.nbricks * NSEG;
+  // persistent warps; per round a half-warp sweeps one strip (brick, RSEG rows)
+  for (int ubase = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2; ubase < nunits; ubase += gridDim.x * WARPS * 2) {
+    const int unit = ubase + half;
+    const bool valid = unit < nunits;
+    const int b = valid ? unit / NSEG : 0;
+    const int r0 = valid ? (unit % NSEG) * RSEG : 0;
     const BrickDesc* bd = a.lay.bricks + b;
-    const int nbase = lane < 9 ? __ldg(bd->nbr_base + lane) : 0;
+    const int nbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
     const int irr = __ldg(&bd->irr);
     const LevGeom<T> gq = geom<T>(a, __ldg(&bd->level));
-    const int own_base = __shfl_sync(FULL, nbase, 4);
-    const bool pairwise = irr < 0 && hl < 15;
+    const int own_base = __shfl_sync(FULL, nbase, 4, 16);
+    const bool pairwise = valid && irr < 0 && hl < 15;
 #pragma unroll
     for (int i = 0; i < NROWS; ++i) {
       const int r = r0 - 1 + i;
@@ -546,6 +552,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
         cA = __ldg(w + nA + 1);
         cB = __ldg(w + nB + 1);
       }
+      if (!valid) { cA = kAbsent; cB = kAbsent; }
       sm.code[i][2 * hl] = cA;
       sm.code[i][2 * hl + 1] = cB;
     }
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
           brL[q] = __shfl_sync(FULL, out[3 + q].y, left_lane);
           trL[q] = __shfl_sync(FULL, out[9 + q].y, left_lane);
         }
-        if (c >= r0 && hl < 15) {
+        if (c >= r0 && hl < 15 && valid) {
           T yA[3], yB[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -743,7 +750,7 @@ template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
-  const int units = a.lay.nbricks;  // one brick per warp
+  const int units = (a.lay.nbricks * NSEG + 1) / 2;  // two strips per warp
   const unsigned blk = 32 * WARPS;
   const size_t smem = sizeof(HalfSmem<T>) * 2 * WARPS;
   auto grid_of = [&](const void* fn) -> unsigned {

@@ -346,7 +346,7 @@ struct __align__(16) Stage {
 template <typename T>
 struct HalfSmem {
   Stage<T> st[DEPTH];
-  int32_t code[NROWS][32];   // storage codes of the lane columns per strip row
+  int32_t code[2][NROWS][32];   // storage codes of the lane columns per strip row (two strips)
 };
 
 template <typename T>
@@ -530,18 +530,24 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
   const int nunits = a.lay.nbricks * NSEG;
-  // persistent warps; per round a half-warp sweeps one strip (brick, RSEG rows)
-  for (int ubase = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2; ubase < nunits; ubase += gridDim.x * WARPS * 2) {
-    const int unit = ubase + half;
+  // Persistent warps.  Half-warp h of warp w sweeps the strips (units)
+  // 2w + h + k * stride, k = 0, 1, ...; their node rows form one continuous
+  // stream j = k * NROWS + i, kept DEPTH-1 rows ahead in the cp.async ring
+  // across strip boundaries.
+  const int stride = gridDim.x * WARPS * 2;
+  const int ubase0 = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2;
+  if (ubase0 >= nunits) return;  // warp-uniform
+  const int nrounds = (nunits - ubase0 + stride - 1) / stride;
+  const int nstream = nrounds * NROWS;
+  // codes of strip k into table k & 1 (all 32 lanes: shuffles); returns its pairwise flag
+  auto build_codes = [&](int k) -> bool {
+    const int unit = ubase0 + k * stride + half;
     const bool valid = unit < nunits;
     const int b = valid ? unit / NSEG : 0;
     const int r0 = valid ? (unit % NSEG) * RSEG : 0;
     const BrickDesc* bd = a.lay.bricks + b;
     const int nbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
     const int irr = __ldg(&bd->irr);
-    const LevGeom<T> gq = geom<T>(a, __ldg(&bd->level));
-    const int own_base = __shfl_sync(FULL, nbase, 4, 16);
-    const bool pairwise = valid && irr < 0 && hl < 15;
 #pragma unroll
     for (int i = 0; i < NROWS; ++i) {
       const int r = r0 - 1 + i;
@@ -553,96 +559,117 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
         cB = __ldg(w + nB + 1);
       }
       if (!valid) { cA = kAbsent; cB = kAbsent; }
-      sm.code[i][2 * hl] = cA;
-      sm.code[i][2 * hl + 1] = cB;
+      sm.code[k & 1][i][2 * hl] = cA;
+      sm.code[k & 1][i][2 * hl + 1] = cB;
     }
-#pragma unroll
-    for (int i = 0; i < DEPTH - 1; ++i) {
-      issue_row<T, OP>(a, pairwise, sm.code[i][2 * hl], sm.code[i][2 * hl + 1], sm.st[i], hl);
-      cp_async_commit();
+    return valid && irr < 0 && hl < 15;
+  };
+  bool pw_issue = build_codes(0);   // pairwise flag of the strip being issued
+  int k_issue = 0;
+  auto issue_stream = [&](int j) {
+    if (j < nstream) {
+      const int k = j / NROWS, i = j - k * NROWS;
+      if (k != k_issue) { pw_issue = build_codes(k); k_issue = k; }
+      issue_row<T, OP>(a, pw_issue, sm.code[k & 1][i][2 * hl], sm.code[k & 1][i][2 * hl + 1], sm.st[j % DEPTH], hl);
     }
-    uint8_t cmA = 0, cmB = 0;
-    P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
+    cp_async_commit();
+  };
 #pragma unroll 1
-    for (int i = 0; i < NROWS; ++i) {
-      cp_async_wait<DEPTH - 2>();
-      Stage<T>& si = sm.st[i % DEPTH];
-      const int32_t cA = sm.code[i][2 * hl], cB = sm.code[i][2 * hl + 1];
-      uint8_t nmA, nmB;
-      if (pairwise) {
-        const uint32_t w = si.cm[2 * hl];
-        nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, w, cA & 3);
-        nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, w, cB & 3);
-      } else {
-        nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, si.cm[2 * hl], cA & 3);
-        nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, si.cm[2 * hl + 1], cB & 3);
-      }
-      if (i > 0) {
-        const int c = r0 - 2 + i;  // cell row between node rows c and c + 1
-        NodePair<T> v[4];
-        read_row<T, OP>(sm.st[(i - 1) % DEPTH], hl, right_lane, v[0], v[1]);
-        read_row<T, OP>(si, hl, right_lane, v[2], v[3]);
-        bool actA = hl < 15, actB = true;
-        if (irr >= 0) {
-          const uint32_t* cmw = a.lay.cellmask + irr * 31;
-          const int ib = (c + 1) * NCW + (nB + 1), ia = ib - 1;  // window cells of cells nA (if hl<15) and nB
-          actA = actA && ((__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u);
-          actB = (__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u;
-        }
-        P out[12];
-        q1_cell_pair<T, OP>(v, mc, gq, out);
-        if (!actA || !actB) {
-#pragma unroll
-          for (int q = 0; q < 12; ++q) {
-            if (!actA) out[q].x = T(0);
-            if (!actB) out[q].y = T(0);
-          }
-        }
-        // the left lane's cell B contributes BR to our node A (row c) and TR to node A (row c+1)
-        T brL[3], trL[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          brL[q] = __shfl_sync(FULL, out[3 + q].y, left_lane);
-          trL[q] = __shfl_sync(FULL, out[9 + q].y, left_lane);
-        }
-        if (c >= r0 && hl < 15 && valid) {
-          T yA[3], yB[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            yA[q] = (carry[q].x + brL[q]) + out[q].x;
-            yB[q] = (carry[q].y + out[3 + q].x) + out[q].y;
-          }
-          if (irr < 0 && !(cmA | cmB)) {
-            // regular brick, unconstrained pair: one aligned pair store per output field
-            const int slot = own_base + nA + NB * c;
-            if (outU) {
-              *reinterpret_cast<P*>(yu + slot) = P{yA[0], yB[0]};
-              *reinterpret_cast<P*>(yv + slot) = P{yA[1], yB[1]};
-            }
-            if (outP) *reinterpret_cast<P*>(yp + slot) = P{yA[2], yB[2]};
-          } else {
-            write_node<T, OP>(a, irr, own_base, nA, c, cmA, yA[0], yA[1], yA[2]);
-            write_node<T, OP>(a, irr, own_base, nB, c, cmB, yB[0], yB[1], yB[2]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          carry[q].x = out[6 + q].x + trL[q];
-          carry[q].y = out[6 + q].y + out[9 + q].x;
-        }
-      }
-      cmA = nmA;
-      cmB = nmB;
-      // refill the stage of row i-1 (no longer read) with row i+DEPTH-1
-      if (i + DEPTH - 1 < NROWS)
-        issue_row<T, OP>(a, pairwise, sm.code[i + DEPTH - 1][2 * hl], sm.code[i + DEPTH - 1][2 * hl + 1],
-                         sm.st[(i + DEPTH - 1) % DEPTH], hl);
-      cp_async_commit();
+  for (int j = 0; j < DEPTH - 1; ++j) issue_stream(j);
+
+  // per-strip state of the strip being computed
+  bool valid = false, pairwise = false;
+  int irr = 0, r0 = 0, own_base = 0;
+  LevGeom<T> gq = geom<T>(a, 0);
+  uint8_t cmA = 0, cmB = 0;
+  P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
+#pragma unroll 1
+  for (int j = 0; j < nstream; ++j) {
+    const int k = j / NROWS, i = j - k * NROWS;
+    if (i == 0) {
+      const int unit = ubase0 + k * stride + half;
+      valid = unit < nunits;
+      const int b = valid ? unit / NSEG : 0;
+      r0 = valid ? (unit % NSEG) * RSEG : 0;
+      const BrickDesc* bd = a.lay.bricks + b;
+      irr = __ldg(&bd->irr);
+      own_base = __ldg(bd->nbr_base + 4);
+      gq = geom<T>(a, __ldg(&bd->level));
+      pairwise = valid && irr < 0 && hl < 15;
     }
-    cp_async_wait<0>();
-    __syncwarp();
-    (void)isDiag;
+    cp_async_wait<DEPTH - 2>();
+    Stage<T>& si = sm.st[j % DEPTH];
+    const int32_t cA = sm.code[k & 1][i][2 * hl], cB = sm.code[k & 1][i][2 * hl + 1];
+    uint8_t nmA, nmB;
+    if (pairwise) {
+      const uint32_t w = si.cm[2 * hl];
+      nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, w, cA & 3);
+      nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, w, cB & 3);
+    } else {
+      nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, si.cm[2 * hl], cA & 3);
+      nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, si.cm[2 * hl + 1], cB & 3);
+    }
+    if (i > 0) {
+      const int c = r0 - 2 + i;  // cell row between node rows c and c + 1
+      NodePair<T> v[4];
+      read_row<T, OP>(sm.st[(j - 1) % DEPTH], hl, right_lane, v[0], v[1]);
+      read_row<T, OP>(si, hl, right_lane, v[2], v[3]);
+      bool actA = hl < 15, actB = true;
+      if (irr >= 0) {
+        const uint32_t* cmw = a.lay.cellmask + irr * 31;
+        const int ib = (c + 1) * NCW + (nB + 1), ia = ib - 1;  // window cells of cells nA (if hl<15) and nB
+        actA = actA && ((__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u);
+        actB = (__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u;
+      }
+      P out[12];
+      q1_cell_pair<T, OP>(v, mc, gq, out);
+      if (!actA || !actB) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          if (!actA) out[q].x = T(0);
+          if (!actB) out[q].y = T(0);
+        }
+      }
+      // the left lane's cell B contributes BR to our node A (row c) and TR to node A (row c+1)
+      T brL[3], trL[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        brL[q] = __shfl_sync(FULL, out[3 + q].y, left_lane);
+        trL[q] = __shfl_sync(FULL, out[9 + q].y, left_lane);
+      }
+      if (c >= r0 && hl < 15 && valid) {
+        T yA[3], yB[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          yA[q] = (carry[q].x + brL[q]) + out[q].x;
+          yB[q] = (carry[q].y + out[3 + q].x) + out[q].y;
+        }
+        if (irr < 0 && !(cmA | cmB)) {
+          // regular brick, unconstrained pair: one aligned pair store per output field
+          const int slot = own_base + nA + NB * c;
+          if (outU) {
+            *reinterpret_cast<P*>(yu + slot) = P{yA[0], yB[0]};
+            *reinterpret_cast<P*>(yv + slot) = P{yA[1], yB[1]};
+          }
+          if (outP) *reinterpret_cast<P*>(yp + slot) = P{yA[2], yB[2]};
+        } else {
+          write_node<T, OP>(a, irr, own_base, nA, c, cmA, yA[0], yA[1], yA[2]);
+          write_node<T, OP>(a, irr, own_base, nB, c, cmB, yB[0], yB[1], yB[2]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        carry[q].x = out[6 + q].x + trL[q];
+        carry[q].y = out[6 + q].y + out[9 + q].x;
+      }
+    }
+    cmA = nmA;
+    cmB = nmB;
+    // refill the stage of stream row j-1 (no longer read) with row j+DEPTH-1
+    issue_stream(j + DEPTH - 1);
   }
+  cp_async_wait<0>();
+  (void)isDiag;
 }
 
 template <typename T>

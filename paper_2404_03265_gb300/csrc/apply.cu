@@ -39,7 +39,7 @@ constexpr int NB = 30;          // owned node slots per brick side
 constexpr int WN = 32;          // window nodes per side (columns -1..30)
 constexpr int NCW = 31;         // window cells per side (cells -1..29)
 #ifndef PFF_RSEG
-#define PFF_RSEG 15
+#define PFF_RSEG 3
 #endif
 #ifndef PFF_WARPS
 #define PFF_WARPS 4

@@ -1,0 +1,122 @@
+"""Pins of the oracle multigrid (oracle/mg.py): Chebyshev polynomial, eigenvalue
+estimate bounds, and the local-smoothing V-cycle against an independent
+multiplicative subspace correction."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from numpy.polynomial import chebyshev as C
+
+from oracle import mg
+from oracle import operators as ops
+from oracle.mesh import LeafMesh, build_recipe
+from paper_2404_03265_gb300 import synth
+
+
+def test_chebyshev_error_polynomial():
+    """For D^-1 A = diag(lam): x_m = (1 - T_m((theta - lam)/delta) / T_m(sigma)) * x_true."""
+    lam = np.linspace(0.01, 1.5, 40)
+    lmax = 1.3
+    for degree in (1, 2, 3, 5):
+        a, b = 0.08 * lmax, 1.2 * lmax
+        theta, delta = (a + b) / 2, (b - a) / 2
+        xs = np.random.default_rng(1).normal(size=lam.size)
+        x = mg.chebyshev(lambda v: lam * v, np.ones_like(lam), lam * xs, lmax, degree)
+        Tm = C.Chebyshev.basis(degree)
+        factor = Tm((theta - lam) / delta) / Tm(theta / delta)
+        assert np.allclose(x, (1 - factor) * xs, rtol=1e-12, atol=1e-13)
+
+
+def test_splitmix64_known_values():
+    # SplitMix64 of 0 and 1 (published reference outputs of the finaliser with seed increment)
+    assert mg.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert mg.splitmix64(1) == 0x910A2DEC89025CC1
+
+
+def build(name, k, active_frac=0.0, u_std=0.0, phit_one=True, seed=3):
+    leaf = LeafMesh(build_recipe(synth.recipe(name)), k)
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.0, eps=0.5, kappa=1e-10, p=1e-3)
+    u, phi, phit = synth.linearisation(leaf.X, leaf.Y, leaf.Xmax, leaf.Ymax, seed=seed, u_std=max(u_std, 1e-300))
+    if u_std == 0.0:
+        u[:] = 0.0
+    if phit_one:
+        phit[:] = 1.0
+    rng = np.random.default_rng(seed)
+    active = (rng.uniform(size=leaf.nn) < active_frac) & ~leaf.is_hanging
+    return leaf, mat, u, phi, phit, active
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_lambda_estimate_bounds(k):
+    leaf, mat, u, phi, phit, active = build("tiny", k, u_std=1e-1, phit_one=False)
+    M = mg.MG(leaf, mat, u, phi, phit, active)
+    for name in ("uu", "pp"):
+        for l, blk in enumerate(M.B[name][1:], start=1):
+            I = np.nonzero(blk.interior)[0]
+            if len(I) < 2:
+                continue
+            A = blk.A[I][:, I].toarray()
+            D = np.diag(np.diag(A))
+            true = sla.eigh(A, D, eigvals_only=True).max()
+            assert blk.lam <= true * (1 + 1e-10)
+            assert blk.lam >= 0.9 * true
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("name,frac", [("tiny", 0.0), ("small", 0.0), ("small", 0.1)])
+def test_vcycle_equals_subspace_correction(k, name, frac):
+    """Constant coefficients (u = 0, phi~ = 1): level operators are Galerkin and the
+    local-smoothing V-cycle equals the multiplicative subspace correction computed
+    from the leaf matrix and the level-to-leaf interpolations."""
+    leaf, mat, u, phi, phit, active = build(name, k, active_frac=frac)
+    M = mg.MG(leaf, mat, u, phi, phit, active)
+    st = ops.State(leaf, u, phi, phit)
+    Gt = ops.constrained_operator(leaf, ops.assemble_jacobian(leaf, mat, st), active)
+    nn = leaf.nn
+    rng = np.random.default_rng(7)
+    for blk, sl, free in (("uu", slice(0, 2 * nn), np.tile(~leaf.dirichlet & ~leaf.is_hanging, 2)),
+                          ("pp", slice(2 * nn, 3 * nn), ~active & ~leaf.is_hanging)):
+        A = Gt[sl, sl]
+        r = rng.normal(size=A.shape[0])
+        z = M.vcycle(blk, r)
+        e = M.msc(blk, A, r)
+        err = np.abs(z[free] - e[free]).max() / np.abs(e[free]).max()
+        assert err < 1e-11, (blk, err)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_vcycle_symmetric_and_contracting(k):
+    leaf, mat, u, phi, phit, active = build("small", k, active_frac=0.05, u_std=1e-3, phit_one=False)
+    M = mg.MG(leaf, mat, u, phi, phit, active)
+    st = ops.State(leaf, u, phi, phit)
+    Gt = ops.constrained_operator(leaf, ops.assemble_jacobian(leaf, mat, st), active)
+    nn = leaf.nn
+    rng = np.random.default_rng(2)
+    for blk, sl, free in (("uu", slice(0, 2 * nn), np.tile(~leaf.dirichlet & ~leaf.is_hanging, 2)),
+                          ("pp", slice(2 * nn, 3 * nn), ~active & ~leaf.is_hanging)):
+        A = Gt[sl, sl]
+        a = rng.normal(size=A.shape[0]) * free
+        b = rng.normal(size=A.shape[0]) * free
+        za, zb = M.vcycle(blk, a) * free, M.vcycle(blk, b) * free
+        assert abs(a @ zb - b @ za) < 1e-10 * abs(a @ zb)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_vcycle_contracts(k):
+    """Stationary iteration x <- x + MG(f - A x) converges fast (no active set: a
+    scattered random active set makes coarse levels active by the pessimistic
+    level rule, which is the paper's rule, not a defect)."""
+    leaf, mat, u, phi, phit, active = build("small", k, active_frac=0.0, u_std=1e-3, phit_one=True)
+    M = mg.MG(leaf, mat, u, phi, phit, active)
+    st = ops.State(leaf, u, phi, phit)
+    Gt = ops.constrained_operator(leaf, ops.assemble_jacobian(leaf, mat, st), active)
+    nn = leaf.nn
+    rng = np.random.default_rng(2)
+    for blk, sl, free in (("uu", slice(0, 2 * nn), np.tile(~leaf.dirichlet & ~leaf.is_hanging, 2)),
+                          ("pp", slice(2 * nn, 3 * nn), ~active & ~leaf.is_hanging)):
+        A = Gt[sl, sl]
+        f = rng.normal(size=A.shape[0]) * free
+        x = np.zeros_like(f)
+        res0 = np.linalg.norm(f)
+        for _ in range(8):
+            x = x + M.vcycle(blk, f - A @ x) * free
+        assert np.linalg.norm((f - A @ x) * free) < 0.05 * res0

@@ -121,7 +121,8 @@ def max_over_ranks(ws, v):
 def build_sets(mesh, n_sets, dtype, seed=0):
     """n_sets independent (problem, x, y) triples with the workload's random inputs."""
     import torch
-    from paper_2404_03265_gb300 import Problem, synth
+    from paper_2404_03265_gb300 import Problem
+    import synthetic as synth
     X, Y, F = mesh.slots()
     valid = (F & 1) == 1
     info = mesh.info
@@ -214,7 +215,7 @@ def cpu_baseline(budget_s=12.0):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from oracle import operators as ops
     from oracle.mesh import LeafMesh, build_recipe
-    from paper_2404_03265_gb300 import synth
+    import synthetic as synth
     om = LeafMesh(build_recipe(synth.recipe("adjoint")), 1)
     u, phi, phit = synth.linearisation(om.X, om.Y, om.Xmax, om.Ymax, seed=0, u_std=1e-3)
     x = synth.vector(om.X, om.Y, seed=1)
@@ -275,7 +276,8 @@ def main():
     import torch
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
-    from paper_2404_03265_gb300 import Mesh, synth
+    from paper_2404_03265_gb300 import Mesh
+    import synthetic as synth
     from paper_2404_03265_gb300 import _lib
 
     mesh = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(1)

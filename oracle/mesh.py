@@ -147,7 +147,7 @@ class QuadTree:
 
 
 def build_recipe(recipe):
-    """Build a QuadTree from a recipe dict (see paper_2404_03265_gb300.synth)."""
+    """Build a QuadTree from a recipe dict (see synthetic.py)."""
     d = recipe["domain"]
     t = QuadTree(d[0], d[1], d[2], d[3], recipe["ncx"], recipe["ncy"])
     for _ in range(recipe["n_global"]):

@@ -16,7 +16,10 @@ Readings where the paper is silent:
 * level linearisation = injection of the (constraint-resolved) leaf nodal
   values; per-cell modulus of a refined cell = mean of its four children;
 * level active set: level-l nodes that coincide with an active leaf node, or
-  that interpolate onto an active node of level l+1;
+  that lie below their home level (the coarsest level among the node's leaf
+  cells) and interpolate onto an active node of level l+1 (pessimistic
+  coarsening); on its home level a DoF keeps its leaf state, since it is
+  smoothed on no other level;
 * Chebyshev: textbook three-term recurrence for D^-1 A on [a, b];
   lambda_max: largest Ritz value of 12 steps of Jacobi-preconditioned CG from a
   fixed start vector 1 + 0.01 * (splitmix64(key) mod 1000) / 1000;
@@ -260,22 +263,28 @@ class MG:
             lm.leaf_node = ln
             Ec = None if E_cells is None else level_cell_modulus(leaf, E_cells, lm)
             lin.append(ops.State(lm, uf[ln], pf[ln], ptf[ln], Ec))
-        # level active sets (phi block), finest to coarsest
-        act = [None] * (Lf + 1)
-        for l in range(Lf, -1, -1):
-            lm = self.levels[l]
-            a = self.active_leaf[lm.leaf_node] & ~leaf.is_hanging[lm.leaf_node]
-            if l < Lf:
-                Pf = self.P[l + 1]   # fine(l+1) x coarse(l)
-                child_active = (abs(Pf).T @ act[l + 1].astype(np.float64)) > 0
-                a = a | child_active
-            act[l] = a
-        self.act = act
-        # copy map: leaf node -> coarsest level among its leaf cells
+        # copy map: leaf node -> coarsest level among its leaf cells ("home" level)
         lmin = np.full(leaf.nn, 10 ** 6)
         for c, (l, i, j) in enumerate(leaf.cells):
             lmin[leaf.cell_nodes[c]] = np.minimum(lmin[leaf.cell_nodes[c]], l)
         self.lmin = lmin
+        # level active sets (phi block), finest to coarsest: a level node is
+        # active if the leaf node at its position is active, or if it lies below
+        # its home level and interpolates onto an active node of the next finer
+        # level (pessimistic coarsening).  On its home level a DoF keeps its own
+        # leaf state, else it would be smoothed on no level at all.
+        act = [None] * (Lf + 1)
+        for l in range(Lf, -1, -1):
+            lm = self.levels[l]
+            ln = lm.leaf_node
+            a = self.active_leaf[ln] & ~leaf.is_hanging[ln]
+            if l < Lf:
+                Pf = self.P[l + 1]   # fine(l+1) x coarse(l)
+                child_active = (abs(Pf).T @ act[l + 1].astype(np.float64)) > 0
+                home = (lmin[ln] == l) & ~leaf.is_hanging[ln]
+                a = a | (child_active & ~home)
+            act[l] = a
+        self.act = act
         self.copy_idx = {}
         for l, lm in enumerate(self.levels):
             nodes = np.nonzero((lmin == l) & ~leaf.is_hanging)[0]

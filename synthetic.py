@@ -49,6 +49,9 @@ def recipe(name):
         return dict(domain=DOMAIN, ncx=14, ncy=14, n_global=6, steps=[_band(14, 6, 9)] * 9)
     if name == "table2_0":
         return dict(domain=DOMAIN, ncx=10, ncy=10, n_global=2, steps=[])
+    if name.startswith("box"):  # box<ncx>_<global>_<steps>: box |x|<=2, |y|<=1 refined <steps> times
+        a, b, c = name[3:].split("_")
+        return dict(domain=DOMAIN, ncx=int(a), ncy=int(a), n_global=int(b), steps=[box] * int(c))
     if name.startswith("band"):  # band<ncx>_<global>_<steps>, e.g. band4_2_3
         a, b, c = name[4:].split("_")
         ncx, g, s = int(a), int(b), int(c)

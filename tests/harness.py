@@ -8,7 +8,7 @@ import numpy as np
 
 from oracle import operators as ops
 from oracle.mesh import LeafMesh, build_recipe
-from paper_2404_03265_gb300 import synth
+import synthetic as synth
 
 
 class Pair:

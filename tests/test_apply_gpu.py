@@ -66,7 +66,7 @@ def test_apply_parity_q1(name, prec, op, params):
     mat = P.material(**kw)
     u, phi, phit = random_linearisation(P, seed=0, u_std=ustd)
     active = random_active(P, seed=5, frac=0.05)
-    from paper_2404_03265_gb300 import synth
+    import synthetic as synth
     x = synth.vector(P.om.X, P.om.Y, seed=1)
     ref = oracle_apply(P, mat, u, phi, phit, active, x, op=op)
     ys = run_lib(P, mat, u, phi, phit, active, x, prec, op)

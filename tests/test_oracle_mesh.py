@@ -6,7 +6,7 @@ import pytest
 
 from oracle.fe import lagrange1d
 from oracle.mesh import LeafMesh, QuadTree, build_recipe
-from paper_2404_03265_gb300 import synth
+import synthetic as synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

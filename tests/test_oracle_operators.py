@@ -5,7 +5,7 @@ import pytest
 
 from oracle import operators as ops
 from oracle.mesh import LeafMesh, build_recipe
-from paper_2404_03265_gb300 import synth
+import synthetic as synth
 
 
 def mesh(name, k):

@@ -1,0 +1,95 @@
+"""Pins of the oracle GMRES and Newton / PDAS load step (oracle/solvers.py)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import operators as ops
+from oracle import solvers
+from oracle.mesh import LeafMesh, build_recipe
+import synthetic as synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TCV_REF_P1E3 = 2.0 * np.pi * 1e-3 * (1.0 - 0.2 ** 2)   # Sec. 4: 2 pi p l0^2 / E', E' = E / (1 - nu^2)
+
+
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    n = 60
+    A = np.eye(n) * 4 + rng.normal(size=(n, n)) * 0.3
+    b = rng.normal(size=n)
+    d = 1.0 / np.diag(A)
+    for restart in (50, 7):
+        x, its, est, b0 = solvers.gmres(lambda v: A @ v, lambda v: d * v, b, rtol=1e-12, restart=restart)
+        xe = np.linalg.solve(A, b)
+        assert np.linalg.norm(x - xe) < 1e-9 * np.linalg.norm(xe)
+        assert its <= 200
+    # the reported estimate is the true preconditioned residual within rounding
+    x, its, est, b0 = solvers.gmres(lambda v: A @ v, lambda v: d * v, b, rtol=1e-4, restart=50)
+    assert abs(np.linalg.norm(d * (b - A @ x)) - est) < 1e-10 * b0
+
+
+def sneddon(name, k=1, p=1e-3, kappa=1e-10):
+    m = LeafMesh(build_recipe(synth.recipe(name)), k)
+    h = m.h_min_diag()
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.0, eps=2 * h, kappa=kappa, p=p)
+    u, phi_old = solvers.sneddon_initial(m, h)
+    return m, mat, u, phi_old, h
+
+
+def test_pure_elasticity_limit_solves_in_zero_steps():
+    """No crack (phi_old = 1): U = (0, 1) solves the system.  R~ vanishes up to
+    rounding; every active-set indicator is 0 in exact arithmetic, so rounding
+    decides the (irrelevant) set for a few iterations while U stays at (0, 1)."""
+    m, mat, u, phi_old, h = sneddon("small")
+    phi_old = np.ones(m.nn)
+    u1, phi1, act, info = solvers.load_step(m, mat, 1e4, u, phi_old.copy(), phi_old)
+    assert info.converged and info.newton <= 8
+    assert max(info.res) < 1e-14
+    assert np.abs(u1).max() < 1e-12 and np.abs(phi1 - 1.0).max() < 1e-12
+
+
+def test_load_step_kkt_and_tcv():
+    """Sneddon load step: converged, KKT conditions of the complementarity
+    reformulation (Problem 2), stable active set, TCV near the closed form."""
+    m, mat, u, phi_old, h = sneddon("small")
+    u1, phi1, act, info = solvers.load_step(m, mat, 1e4, u, phi_old.copy(), phi_old)
+    assert info.converged
+    assert info.linesearch_failed == 0
+    nn = m.nn
+    st = ops.State(m, u1, phi1, phi_old)
+    R = ops.condense(m, -ops.residual_form(m, mat, st))
+    B = ops.lumped_mass(m)
+    free_u = np.tile(~m.dirichlet & ~m.is_hanging, 2)
+    scale = np.abs(R).max()
+    assert np.abs(R[:2 * nn][free_u]).max() <= 1e-6 * scale + 1e-14
+    inactive = ~act & ~m.is_hanging
+    assert np.abs(R[2 * nn:][inactive]).max() <= 1e-6 * scale + 1e-14
+    # irreversibility phi <= phi_old, equality on the active set with lambda >= 0
+    assert np.all(phi1 <= phi_old + 1e-10)
+    assert np.all(phi1[act] == phi_old[act])
+    assert np.all(R[2 * nn:][act] / B[act] >= -1e-12)
+    # linear iteration counts of the size Table 2 reports (max 6-8 on coarse meshes)
+    assert max(info.gmres) <= 20
+    tcv = ops.tcv(m, st)
+    err = abs(tcv - TCV_REF_P1E3) / TCV_REF_P1E3
+    t2 = np.loadtxt(os.path.join(GOLDEN, "table2.txt"))
+    # Table 2 reports 45.9 % at h = 0.1768 (< this mesh's 0.221): the error here is not larger
+    assert err < t2[2, 2] / 100
+    assert tcv > 0
+
+
+def test_tcv_converges_under_refinement():
+    """TCV error drops from h = 0.110 to h = 0.055 (Sec. 4) and stays within the
+    errors Table 2 reports at comparable h (18.7 % at 0.0884, 7.67 % at 0.0442)."""
+    t2 = np.loadtxt(os.path.join(GOLDEN, "table2.txt"))
+    errs = []
+    for name in ("box4_4_2", "adjoint"):
+        m, mat, u, phi_old, h = sneddon(name)
+        u1, phi1, act, info = solvers.load_step(m, mat, 1e4, u, phi_old.copy(), phi_old)
+        assert info.converged
+        tcv = ops.tcv(m, ops.State(m, u1, phi1, phi_old))
+        errs.append((h, 100 * abs(tcv - TCV_REF_P1E3) / TCV_REF_P1E3))
+    assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1]
+    # h = 0.110 lies between Table 2's 0.1768 and 0.0884 rows, h = 0.055 between 0.0884 and 0.0442
+    assert errs[0][1] < t2[2, 2] and errs[1][1] < t2[3, 2]

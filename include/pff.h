@@ -56,6 +56,7 @@ enum {
 
 typedef struct pff_mesh pff_mesh;
 typedef struct pff_problem pff_problem;
+typedef struct pff_mg pff_mg;
 
 typedef struct pff_mesh_info {
   int64_t n_slots;       /* length of a node vector                                   */
@@ -138,6 +139,25 @@ pff_status pff_set_active(pff_problem* pb, const uint8_t* active, void* stream);
  * x and y must not overlap.                                                    */
 pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
                      void* yu, void* yp, void* stream);
+
+/* ---- multigrid preconditioner (Sec. 3.2) -----------------------------------
+ * One V-cycle per diagonal block of G~: block 0 = u-u (2 components, vectors of
+ * 2*n_slots doubles), block 1 = phi-phi (n_slots doubles).  Levels are all cells
+ * of one refinement level (local smoothing); Chebyshev-accelerated Jacobi
+ * smoothing of degree 3 on [0.08, 1.2] * lambda_max, lambda_max from 12 steps of
+ * Jacobi-preconditioned CG (FP64); inverse diagonal from cell-local assembly;
+ * direct FP64 solve on level 0.  precision selects the V-cycle arithmetic
+ * (PFF_F32: applies, smoothing and transfers in FP32).
+ * pff_mg_setup uses the problem's current state and active set (call it after
+ * pff_set_state / pff_set_active); it synchronises the stream.
+ * pff_vcycle: z = MG(r) for one block; fixed leaf DoFs (Dirichlet u, active phi)
+ * get z = r, hanging entries and holes 0.  r and z are device vectors.          */
+pff_status pff_mg_create(pff_problem* pb, int32_t precision, pff_mg** out);
+pff_status pff_mg_setup(pff_mg* mg, void* stream);
+pff_status pff_vcycle(pff_mg* mg, int32_t block, const double* r, double* z, void* stream);
+/* lambda_max estimates per level (host array of finest_level + 1 doubles; entry 0 unused) */
+pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam_host, int32_t n);
+void pff_mg_destroy(pff_mg* mg);
 
 #ifdef __cplusplus
 }

@@ -105,3 +105,32 @@ class Problem:
         if h is not None and h.value:
             _lib.lib().pff_problem_destroy(h)
             self._h = None
+
+
+class MG:
+    """Block-diagonal GMG preconditioner (u-u block 0, phi-phi block 1) of a Problem."""
+
+    def __init__(self, problem, precision=PFF_F32):
+        self.problem = problem
+        h = _lib.ctypes.c_void_p()
+        _lib.check(_lib.lib().pff_mg_create(problem._h, precision, _lib.ctypes.byref(h)))
+        self._h = h
+        self.n_levels = problem.mesh.info["finest_level"] + 1
+
+    def setup(self, stream=None):
+        _lib.check(_lib.lib().pff_mg_setup(self._h, _lib.stream_ptr(stream)))
+
+    def vcycle(self, block, r, z, stream=None):
+        """z = MG(r); block 0: r, z float64 (2, n_slots); block 1: (n_slots,)."""
+        _lib.check(_lib.lib().pff_vcycle(self._h, block, _lib.ptr(r), _lib.ptr(z), _lib.stream_ptr(stream)))
+
+    def lam(self, block):
+        out = np.zeros(self.n_levels)
+        _lib.check(_lib.lib().pff_mg_lambda(self._h, block, _lib.ptr(out), self.n_levels))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.lib().pff_mg_destroy(h)
+            self._h = None

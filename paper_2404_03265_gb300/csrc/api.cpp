@@ -264,3 +264,62 @@ extern "C" pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, 
     return PFF_OK;
   })
 }
+
+// ------------------------------------------------------------------ multigrid
+extern "C" pff_status pff_mg_create(pff_problem* pb, int32_t precision, pff_mg** out) {
+  PFF_TRY({
+    if (!pb || !out) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (precision != PFF_F64 && precision != PFF_F32) return fail(PFF_ERR_INVALID_ARG, "bad precision");
+    if (pb->mesh->m.Lf + 1 > kMaxLevels) return fail(PFF_ERR_INVALID_ARG, "too many levels");
+    auto* mg = new pff_mg();
+    mg->pb = pb;
+    mg->precision = precision;
+    std::string e = mg_alloc(*mg);
+    if (!e.empty()) {
+      mg->mem.release();
+      delete mg;
+      return fail(PFF_ERR_OOM, e);
+    }
+    *out = mg;
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mg_setup(pff_mg* mg, void* stream) {
+  PFF_TRY({
+    if (!mg) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!mg->pb->has_state) return fail(PFF_ERR_STATE, "pff_set_state has not been called");
+    std::string e = mg_setup(*mg, cudaStream_t(stream));
+    if (!e.empty()) return fail(PFF_ERR_CUDA, e);
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_vcycle(pff_mg* mg, int32_t block, const double* r, double* z, void* stream) {
+  PFF_TRY({
+    if (!mg || !r || !z) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (block != 0 && block != 1) return fail(PFF_ERR_INVALID_ARG, "block must be 0 (u) or 1 (phi)");
+    if (!mg->ready) return fail(PFF_ERR_STATE, "pff_mg_setup has not been called");
+    if (r == z) return fail(PFF_ERR_INVALID_ARG, "r and z overlap");
+    PFF_CUDA(mg_vcycle(*mg, block, r, z, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam, int32_t n) {
+  PFF_TRY({
+    if (!mg || !lam) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (block != 0 && block != 1) return fail(PFF_ERR_INVALID_ARG, "bad block");
+    const auto& v = mg->blk[block].lam;
+    if (n < int32_t(v.size())) return fail(PFF_ERR_INVALID_ARG, "lam array too short");
+    for (size_t i = 0; i < v.size(); ++i) lam[i] = v[i];
+    return PFF_OK;
+  })
+}
+
+extern "C" void pff_mg_destroy(pff_mg* mg) {
+  if (!mg) return;
+  mg->mem.release();
+  delete mg;
+}

@@ -405,6 +405,7 @@ std::string finalize_mesh(Mesh& m, int k) {
       const int64_t ln = m.find_node(X, Y);
       if (ln < 0) return "level node without a leaf node at its position";
       lm.slot_leaf[slot] = m.nslot[ln];
+      if (m.nhang[ln] < 0 && m.nminlev[ln] == l) lm.slot_flags[slot] |= 16;  // home level of a leaf DoF
     }
     auto lfind = [&](int64_t gx, int64_t gy) -> int32_t {
       if (gx < 0 || gy < 0 || gx > gnx || gy > gny) return -1;

@@ -87,7 +87,7 @@ struct LevelMesh {
   Layout lay;
   int64_t n_nodes = 0;
   std::vector<int32_t> slot_X, slot_Y;   // finest-grid integer coordinates, -1 for holes
-  std::vector<uint8_t> slot_flags;       // bit0 node, bit1 Dirichlet, bit3 refinement edge
+  std::vector<uint8_t> slot_flags;       // bit0 node, bit1 Dirichlet, bit3 refinement edge, bit4 home level of a leaf DoF
   std::vector<int32_t> slot_leaf;        // leaf storage slot at the same position (-1 holes)
   // prolongation P (this level <- level-1) as CSR over this level's slots
   std::vector<int32_t> P_ptr, P_col;

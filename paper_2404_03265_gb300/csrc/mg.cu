@@ -1,0 +1,417 @@
+// Multigrid kernels of libpff (see mg.cuh).  Level vectors of a block are
+// stored per level as ncomp consecutive blocks of the level's slot count.
+// Fixed rows (Dirichlet u for the u-block, active phi for the phi-block) and
+// holes carry zeros; the inverse diagonal is zero off the interior, so the
+// Chebyshev updates leave edge and fixed entries untouched.
+#include "mg.cuh"
+
+namespace pff {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned blocks_for(int64_t n) {
+  int64_t b = (n + TPB - 1) / TPB;
+  if (b > 65535 * 8) b = 65535 * 8;
+  return unsigned(b < 1 ? 1 : b);
+}
+
+#define GRID_STRIDE(i, n) for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
+
+template <typename T>
+__global__ void k_cheb_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0) {
+  GRID_STRIDE(i, n) {
+    x[i] = c0 * dinv[i] * d[i];
+    xprev[i] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_cheb_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d, const T* ax,
+                            T a, T b) {
+  GRID_STRIDE(i, n) {
+    const T xi = x[i];
+    xnew[i] = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
+  }
+}
+
+template <typename T>
+__global__ void k_residual(int64_t n, T* r, const T* d, const T* ax) {
+  GRID_STRIDE(i, n) r[i] = d[i] - ax[i];
+}
+
+template <typename T>
+__global__ void k_axpy(int64_t n, T* y, const T* x, T a) {
+  GRID_STRIDE(i, n) y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* __restrict__ ptr,
+                           const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ df,
+                           const T* __restrict__ axf, T* dc, const uint8_t* __restrict__ cmask_c, int fixbits) {
+  GRID_STRIDE(y, nc) {
+    const uint8_t cm = cmask_c[y];
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      T acc = dc[c * ncs + y];
+      for (int e = ptr[y]; e < ptr[y + 1]; ++e) {
+        const int z = col[e];
+        acc += T(val[e]) * (df[c * nfs + z] - axf[c * nfs + z]);
+      }
+      dc[c * ncs + y] = (cm & bit) ? T(0) : acc;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const int32_t* __restrict__ ptr,
+                          const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ xc,
+                          T* xf, const uint8_t* __restrict__ cmask_f, int fixbits) {
+  GRID_STRIDE(z, nf) {
+    const uint8_t cm = cmask_f[z];
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      T acc = xf[c * nfs + z];
+      for (int e = ptr[z]; e < ptr[z + 1]; ++e) acc += T(val[e]) * xc[c * ncs + col[e]];
+      xf[c * nfs + z] = (cm & bit) ? T(0) : acc;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_copy_in(int32_t n, int ncomp, const int32_t* __restrict__ ls, const int32_t* __restrict__ vs,
+                          const double* __restrict__ r, int64_t nsl, T* d, int64_t nsv,
+                          const uint8_t* __restrict__ lcm, int fixbits) {
+  GRID_STRIDE(i, n) {
+    const int a = ls[i], b = vs[i];
+    const uint8_t cm = lcm[a];
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      if (!(cm & bit)) d[c * nsv + b] = T(r[c * nsl + a]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_copy_out(int32_t n, int ncomp, const int32_t* __restrict__ ls, const int32_t* __restrict__ vs,
+                           const T* __restrict__ x, int64_t nsv, double* z, int64_t nsl,
+                           const uint8_t* __restrict__ lcm, int fixbits) {
+  GRID_STRIDE(i, n) {
+    const int a = ls[i], b = vs[i];
+    const uint8_t cm = lcm[a];
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      if (!(cm & bit)) z[c * nsl + a] = double(x[c * nsv + b]);
+    }
+  }
+}
+
+__global__ void k_leaf_init(int64_t ns, int ncomp, const double* __restrict__ r, double* z,
+                            const uint8_t* __restrict__ lcm, const uint8_t* __restrict__ lflags, int fixbits) {
+  GRID_STRIDE(s, ns) {
+    const uint8_t cm = lcm[s];
+    const bool node = (lflags[s] & 1) && !(lflags[s] & 4);
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      z[c * ns + s] = (node && (cm & bit)) ? r[c * ns + s] : 0.0;
+    }
+  }
+}
+
+// Dense FP64 coarse solve: tmp = d[idx] (to FP64), x[idx] = Ainv tmp; one block per row group.
+template <typename T>
+__global__ void k_coarse_gather(int32_t n, const int32_t* idx, const T* d, double* tmp) {
+  GRID_STRIDE(i, n) tmp[i] = double(d[idx[i]]);
+}
+
+template <typename T>
+__global__ void k_coarse_matvec(int32_t n, const int32_t* idx, const double* __restrict__ A,
+                                const double* __restrict__ tmp, T* x) {
+  // one warp per row, lanes stride the columns, fixed-order warp reduction
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += A[int64_t(warp) * n + j] * tmp[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[idx[warp]] = T(acc);
+}
+
+__global__ void k_inject_lin(int32_t nsl, const int32_t* __restrict__ sl, const double* __restrict__ lin,
+                             int64_t nsleaf, double* l64, float* l32) {
+  GRID_STRIDE(s, nsl) {
+    const int ls = sl[s];
+    for (int f = 0; f < 4; ++f) {
+      const double v = ls >= 0 ? lin[f * nsleaf + ls] : 0.0;
+      l64[f * int64_t(nsl) + s] = v;
+      l32[f * int64_t(nsl) + s] = float(v);
+    }
+  }
+}
+
+__global__ void k_level_cmask(int32_t nsl, const uint8_t* __restrict__ flags, const int32_t* __restrict__ sl,
+                              const uint8_t* __restrict__ lcm, const int32_t* __restrict__ Rp,
+                              const int32_t* __restrict__ Rc, const uint8_t* __restrict__ cmf, uint8_t* cm) {
+  GRID_STRIDE(s, nsl) {
+    const uint8_t f = flags[s];
+    uint8_t c = 0;
+    if ((f & 1) && (f & 2)) c |= 3;
+    if (f & 1) {
+      const int ls = sl[s];
+      bool act = ls >= 0 && (lcm[ls] & 4);
+      if (!act && Rp != nullptr && !(f & 16)) {
+        for (int e = Rp[s]; e < Rp[s + 1]; ++e)
+          if (cmf[Rc[e]] & 4) { act = true; break; }
+      }
+      if (act) c |= 4;
+    }
+    cm[s] = c;
+  }
+}
+
+__global__ void k_invert_diag(int32_t nsl, int ncomp, const double* __restrict__ diag,
+                              const uint8_t* __restrict__ flags, const uint8_t* __restrict__ cm, int fixbits,
+                              double* d64, float* d32) {
+  GRID_STRIDE(s, nsl) {
+    const uint8_t f = flags[s];
+    for (int c = 0; c < ncomp; ++c) {
+      const int bit = (fixbits == 4) ? 4 : (1 << c);
+      const int64_t i = c * int64_t(nsl) + s;
+      const double dg = diag[i];
+      const bool interior = (f & 1) && !(f & 8) && !(cm[s] & bit) && dg != 0.0;
+      const double v = interior ? 1.0 / dg : 0.0;
+      d64[i] = v;
+      d32[i] = float(v);
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_start_vector(int32_t nsl, int ncomp, const int32_t* __restrict__ gx, const int32_t* __restrict__ gy,
+                               const double* __restrict__ dinv, double* r) {
+  GRID_STRIDE(s, nsl) {
+    double v = 0.0;
+    if (gx[s] >= 0) {
+      const uint64_t h = splitmix64((uint64_t(uint32_t(gx[s])) << 32) | uint64_t(uint32_t(gy[s])));
+      v = 1.0 + 0.01 * double(h % 1000ull) / 1000.0;
+    }
+    for (int c = 0; c < ncomp; ++c) {
+      const int64_t i = c * int64_t(nsl) + s;
+      r[i] = dinv[i] != 0.0 ? v : 0.0;
+    }
+  }
+}
+
+constexpr int DOT_BLOCKS = 512;
+
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* part) {
+  __shared__ double sh[TPB];
+  double acc = 0.0;
+  GRID_STRIDE(i, n) acc += a[i] * b[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(int nb, const double* __restrict__ part, double* out) {
+  __shared__ double sh[TPB];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += TPB) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// sc: 0 rz, 1 pq, 2 rz_new, 3 alpha, 4 beta, 5 ok (1 while the iteration is healthy)
+__global__ void k_cg_alpha(double* sc) {
+  const double pq = sc[1];
+  const bool ok = sc[5] > 0.5 && pq > 0.0 && sc[0] > 0.0;
+  sc[3] = ok ? sc[0] / pq : 0.0;
+  if (!ok) sc[5] = 0.0;
+}
+
+__global__ void k_cg_beta(double* sc, double* hist, int step) {
+  const bool ok = sc[5] > 0.5;
+  const double beta = ok ? sc[2] / sc[0] : 0.0;
+  sc[4] = beta;
+  hist[2 * step + 0] = ok ? sc[3] : 0.0;   // alpha_j (0 marks a stop)
+  hist[2 * step + 1] = beta;
+  if (!(ok && sc[2] > 1e-300)) sc[5] = 0.0;
+  sc[0] = sc[2];
+}
+
+__global__ void k_cg_r(int64_t n, double* r, double* z, const double* __restrict__ q, const double* __restrict__ dinv,
+                       const double* __restrict__ sc) {
+  const double alpha = sc[3];
+  GRID_STRIDE(i, n) {
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    z[i] = dinv[i] * ri;
+  }
+}
+
+__global__ void k_cg_p(int64_t n, double* p, const double* __restrict__ z, const double* __restrict__ sc) {
+  const double beta = sc[4];
+  GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_fill64(int64_t n, double* x, double v) { GRID_STRIDE(i, n) x[i] = v; }
+__global__ void k_copy64(int64_t n, double* d, const double* s) { GRID_STRIDE(i, n) d[i] = s[i]; }
+
+}  // namespace
+
+template <typename T>
+cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0, cudaStream_t s) {
+  if (n > 0) k_cheb_first<T><<<blocks_for(n), TPB, 0, s>>>(n, x, xprev, dinv, d, c0);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d,
+                              const T* ax, T a, T b, cudaStream_t s) {
+  if (n > 0) k_cheb_step<T><<<blocks_for(n), TPB, 0, s>>>(n, xnew, x, xprev, dinv, d, ax, a, b);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_residual(int64_t n, T* r, const T* d, const T* ax, cudaStream_t s) {
+  if (n > 0) k_residual<T><<<blocks_for(n), TPB, 0, s>>>(n, r, d, ax);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_axpy(int64_t n, T* y, const T* x, T a, cudaStream_t s) {
+  if (n > 0) k_axpy<T><<<blocks_for(n), TPB, 0, s>>>(n, y, x, a);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* ptr, const int32_t* col,
+                        const float* val, const T* d_f, const T* ax_f, T* d_c, const uint8_t* cmask_c, int fixbits,
+                        cudaStream_t s) {
+  if (nc > 0) k_restrict<T><<<blocks_for(nc), TPB, 0, s>>>(nc, ncomp, ncs, nfs, ptr, col, val, d_f, ax_f, d_c,
+                                                           cmask_c, fixbits);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const int32_t* ptr, const int32_t* col,
+                       const float* val, const T* x_c, T* x_f, const uint8_t* cmask_f, int fixbits, cudaStream_t s) {
+  if (nf > 0) k_prolong<T><<<blocks_for(nf), TPB, 0, s>>>(nf, ncomp, nfs, ncs, ptr, col, val, x_c, x_f, cmask_f,
+                                                          fixbits);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_copy_in(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const double* r,
+                       int64_t ns_leaf, T* d, int64_t ns_l, const uint8_t* leaf_cmask, int fixbits, cudaStream_t s) {
+  if (n > 0) k_copy_in<T><<<blocks_for(n), TPB, 0, s>>>(n, ncomp, leaf_slot, lev_slot, r, ns_leaf, d, ns_l,
+                                                        leaf_cmask, fixbits);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_copy_out(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const T* x,
+                        int64_t ns_l, double* z, int64_t ns_leaf, const uint8_t* leaf_cmask, int fixbits,
+                        cudaStream_t s) {
+  if (n > 0) k_copy_out<T><<<blocks_for(n), TPB, 0, s>>>(n, ncomp, leaf_slot, lev_slot, x, ns_l, z, ns_leaf,
+                                                         leaf_cmask, fixbits);
+  return cudaGetLastError();
+}
+cudaError_t mg_leaf_init(int64_t ns_leaf, int ncomp, const double* r, double* z, const uint8_t* leaf_cmask,
+                         const uint8_t* leaf_flags, int fixbits, cudaStream_t s) {
+  if (ns_leaf > 0) k_leaf_init<<<blocks_for(ns_leaf), TPB, 0, s>>>(ns_leaf, ncomp, r, z, leaf_cmask, leaf_flags,
+                                                                   fixbits);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_coarse(int32_t n, const int32_t* idx, const double* Ainv, const T* d, T* x, double* tmp,
+                      cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_coarse_gather<T><<<blocks_for(n), TPB, 0, s>>>(n, idx, d, tmp);
+  const int warps_per_block = TPB / 32;
+  k_coarse_matvec<T><<<(n + warps_per_block - 1) / warps_per_block, TPB, 0, s>>>(n, idx, Ainv, tmp, x);
+  return cudaGetLastError();
+}
+
+cudaError_t mg_inject_lin(int32_t ns_l, const int32_t* slot_leaf, const double* lin64, int64_t ns_leaf,
+                          double* lev64, float* lev32, cudaStream_t s) {
+  if (ns_l > 0) k_inject_lin<<<blocks_for(ns_l), TPB, 0, s>>>(ns_l, slot_leaf, lin64, ns_leaf, lev64, lev32);
+  return cudaGetLastError();
+}
+cudaError_t mg_level_cmask(int32_t ns_l, const uint8_t* flags, const int32_t* slot_leaf, const uint8_t* leaf_cmask,
+                           const int32_t* R_ptr, const int32_t* R_col, const uint8_t* cmask_fine, uint8_t* cmask,
+                           cudaStream_t s) {
+  if (ns_l > 0) k_level_cmask<<<blocks_for(ns_l), TPB, 0, s>>>(ns_l, flags, slot_leaf, leaf_cmask, R_ptr, R_col,
+                                                                cmask_fine, cmask);
+  return cudaGetLastError();
+}
+cudaError_t mg_invert_diag(int32_t ns_l, int ncomp, const double* diag, const uint8_t* flags, const uint8_t* cmask,
+                           int fixbits, double* dinv64, float* dinv32, cudaStream_t s) {
+  if (ns_l > 0) k_invert_diag<<<blocks_for(ns_l), TPB, 0, s>>>(ns_l, ncomp, diag, flags, cmask, fixbits, dinv64,
+                                                                dinv32);
+  return cudaGetLastError();
+}
+cudaError_t mg_start_vector(int32_t ns_l, int ncomp, const int32_t* gx, const int32_t* gy, const double* dinv,
+                            double* r, cudaStream_t s) {
+  if (ns_l > 0) k_start_vector<<<blocks_for(ns_l), TPB, 0, s>>>(ns_l, ncomp, gx, gy, dinv, r);
+  return cudaGetLastError();
+}
+cudaError_t dot64(int64_t n, const double* a, const double* b, double* partial, double* out, cudaStream_t s) {
+  k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, a, b, partial);
+  k_dot_final<<<1, TPB, 0, s>>>(DOT_BLOCKS, partial, out);
+  return cudaGetLastError();
+}
+cudaError_t cg_update_r(int64_t n, double* r, double* z, const double* q, const double* dinv, const double* sc,
+                        cudaStream_t s) {
+  if (n > 0) k_cg_r<<<blocks_for(n), TPB, 0, s>>>(n, r, z, q, dinv, sc);
+  return cudaGetLastError();
+}
+cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* sc, cudaStream_t s) {
+  if (n > 0) k_cg_p<<<blocks_for(n), TPB, 0, s>>>(n, p, z, sc);
+  return cudaGetLastError();
+}
+cudaError_t cg_scalars_alpha(double* sc, cudaStream_t s) {
+  k_cg_alpha<<<1, 1, 0, s>>>(sc);
+  return cudaGetLastError();
+}
+cudaError_t cg_scalars_beta(double* sc, double* hist, int step, cudaStream_t s) {
+  k_cg_beta<<<1, 1, 0, s>>>(sc, hist, step);
+  return cudaGetLastError();
+}
+cudaError_t fill64(int64_t n, double* x, double v, cudaStream_t s) {
+  if (n > 0) k_fill64<<<blocks_for(n), TPB, 0, s>>>(n, x, v);
+  return cudaGetLastError();
+}
+cudaError_t copy64(int64_t n, double* dst, const double* src, cudaStream_t s) {
+  if (n > 0) k_copy64<<<blocks_for(n), TPB, 0, s>>>(n, dst, src);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                \
+  template cudaError_t mg_chebyshev_first<T>(int64_t, T*, T*, const T*, const T*, T, cudaStream_t);           \
+  template cudaError_t mg_chebyshev_step<T>(int64_t, T*, const T*, const T*, const T*, const T*, const T*, T,  \
+                                            T, cudaStream_t);                                                  \
+  template cudaError_t mg_residual<T>(int64_t, T*, const T*, const T*, cudaStream_t);                         \
+  template cudaError_t mg_axpy<T>(int64_t, T*, const T*, T, cudaStream_t);                                    \
+  template cudaError_t mg_restrict<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,          \
+                                      const float*, const T*, const T*, T*, const uint8_t*, int, cudaStream_t); \
+  template cudaError_t mg_prolong<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,           \
+                                     const float*, const T*, T*, const uint8_t*, int, cudaStream_t);           \
+  template cudaError_t mg_copy_in<T>(int32_t, int, const int32_t*, const int32_t*, const double*, int64_t, T*, \
+                                     int64_t, const uint8_t*, int, cudaStream_t);                              \
+  template cudaError_t mg_copy_out<T>(int32_t, int, const int32_t*, const int32_t*, const T*, int64_t, double*,\
+                                      int64_t, const uint8_t*, int, cudaStream_t);                             \
+  template cudaError_t mg_coarse<T>(int32_t, const int32_t*, const double*, const T*, T*, double*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace pff

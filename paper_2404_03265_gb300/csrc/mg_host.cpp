@@ -1,0 +1,390 @@
+// Host driver of the block-diagonal geometric multigrid preconditioner.
+//
+// Kolditz & Wick (arXiv 2404.03265), Sec. 3.2: one V-cycle per diagonal block
+// (u-u, phi-phi) of the Jacobian; Chebyshev-accelerated Jacobi smoothing with
+// the inverse diagonal from cell-local assembly and a CG-based estimate of the
+// largest eigenvalue, smoothing range [0.08, 1.2] * lambda_max; local
+// smoothing on the level meshes; coarse level solved directly (FP64).
+//
+// V-cycle of one block (levels L..1, coarse 0):
+//   copy the leaf defect to the coarsest level on which each DoF is interior;
+//   down: Chebyshev from zero, defect d - A x on interior and edge rows,
+//         restriction P^T into the next coarser level;
+//   coarse: x_0 = A_0^{-1} d_0 on the interior;
+//   up: x += P x_coarse on all level nodes, Chebyshev on d - A x;
+//   copy the level solutions back to the leaf DoFs (fixed leaf rows: z = r).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "state.h"
+
+namespace pff {
+
+namespace {
+
+inline int block_op(int b) { return b == 0 ? OP_UU : OP_PP; }
+inline int block_diag_op(int b) { return b == 0 ? OP_UU_DIAG : OP_PP_DIAG; }
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (d, e) by bisection on Sturm counts.
+double tridiag_max_eig(const std::vector<double>& d, const std::vector<double>& e) {
+  const int m = int(d.size());
+  if (m == 0) return 0.0;
+  double lo = d[0], hi = d[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < m - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      const double qq = (q == 0.0) ? 1e-300 : q;
+      q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), 1e-300); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) == m) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Dense Cholesky A = L L^T in place (lower), then A^{-1} via two triangular solves per column.
+bool dense_spd_inverse(int n, std::vector<double>& A, std::vector<double>& inv) {
+  for (int j = 0; j < n; ++j) {
+    double s = A[size_t(j) * n + j];
+    for (int k = 0; k < j; ++k) s -= A[size_t(j) * n + k] * A[size_t(j) * n + k];
+    if (!(s > 0)) return false;
+    const double ljj = std::sqrt(s);
+    A[size_t(j) * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[size_t(i) * n + j];
+      for (int k = 0; k < j; ++k) t -= A[size_t(i) * n + k] * A[size_t(j) * n + k];
+      A[size_t(i) * n + j] = t / ljj;
+    }
+  }
+  inv.assign(size_t(n) * n, 0.0);
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= A[size_t(i) * n + k] * y[k];
+      y[i] = t / A[size_t(i) * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= A[size_t(k) * n + i] * inv[size_t(k) * n + c];
+      inv[size_t(i) * n + c] = t / A[size_t(i) * n + i];
+    }
+  }
+  return true;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return std::string(#call) + ": " + cudaGetErrorString(e_); \
+  } while (0)
+
+}  // namespace
+
+template <typename T>
+cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s) {
+  pff_problem& pb = *mg.pb;
+  const Mesh& M = pb.mesh->m;
+  const DevMesh::Level& L = pb.mesh->dev.levels[level];
+  ApplyArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.lay = L.lay;
+  a.hang = nullptr;
+  a.cmask = mg.cmask + L.lv.off;
+  const int64_t n = L.lv.n_slots;
+  if (sizeof(T) == 8) a.lin = mg.lin64 + 4 * L.lv.off; else a.lin = mg.lin32 + 4 * L.lv.off;
+  a.xu = x; a.xp = x; a.yu = y; a.yp = y;
+  a.ibuf = nullptr;
+  a.n_slots = n;
+  for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) { a.hx[l] = M.tree.hx(l); a.hy[l] = M.tree.hy(l); }
+  fill_material(pb.prm, a);
+  fill_cell_constants(a, M.Lf + 1);
+  a.fe_degree = M.k;
+  a.mode = MODE_MASK_INPUT;
+  return launch_apply<T>(a, op, s);
+}
+
+std::string mg_alloc(pff_mg& mg) {
+  const DevMesh& D = mg.pb->mesh->dev;
+  const int64_t N = D.lev_total;
+  int64_t nmax = 0;
+  for (const auto& L : D.levels) nmax = std::max<int64_t>(nmax, L.lv.n_slots);
+  mg.lin64 = mg.mem.alloc<double>(4 * N);
+  mg.lin32 = mg.mem.alloc<float>(4 * N);
+  mg.cmask = mg.mem.alloc<uint8_t>(N);
+  const size_t esz = mg.precision == PFF_F64 ? sizeof(double) : sizeof(float);
+  for (int b = 0; b < 2; ++b) {
+    MGBlock& B = mg.blk[b];
+    B.ncomp = b == 0 ? 2 : 1;
+    B.fixbits = b == 0 ? 3 : 4;
+    const int64_t n = B.ncomp * N;
+    B.dinv64 = mg.mem.alloc<double>(n);
+    B.dinv32 = mg.mem.alloc<float>(n);
+    void** bufs[6] = {&B.d, &B.x, &B.r, &B.y, &B.yp, &B.t};
+    for (auto* p : bufs) *p = mg.mem.alloc<unsigned char>(n * esz);
+    B.lam.assign(D.levels.size(), 0.0);
+  }
+  mg.cg_r = mg.mem.alloc<double>(2 * nmax);
+  mg.cg_z = mg.mem.alloc<double>(2 * nmax);
+  mg.cg_p = mg.mem.alloc<double>(2 * nmax);
+  mg.cg_q = mg.mem.alloc<double>(2 * nmax);
+  mg.diag = mg.mem.alloc<double>(2 * nmax);
+  mg.partial = mg.mem.alloc<double>(1024);
+  mg.sc = mg.mem.alloc<double>(8);
+  mg.hist = mg.mem.alloc<double>(2 * 64);
+  if (!mg.mem.err.empty()) return mg.mem.err;
+  return "";
+}
+
+// Per Newton step: level linearisation, level constraint masks, inverse
+// diagonals, eigenvalue estimates and the coarse inverse of both blocks.
+std::string mg_setup(pff_mg& mg, cudaStream_t s) {
+  pff_problem& pb = *mg.pb;
+  const Mesh& M = pb.mesh->m;
+  const DevMesh& D = pb.mesh->dev;
+  const int nl = int(D.levels.size());
+  const int64_t nsleaf = M.lay.n_slots;
+  for (int l = 0; l < nl; ++l) {
+    const DevLevel& lv = D.levels[l].lv;
+    CK(mg_inject_lin(lv.n_slots, lv.slot_leaf, pb.lin64, nsleaf, mg.lin64 + 4 * lv.off, mg.lin32 + 4 * lv.off, s));
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    const DevLevel& lv = D.levels[l].lv;
+    const DevLevel* fine = (l + 1 < nl) ? &D.levels[l + 1].lv : nullptr;
+    CK(mg_level_cmask(lv.n_slots, lv.flags, lv.slot_leaf, pb.cmask, fine ? fine->R_ptr : nullptr,
+                      fine ? fine->R_col : nullptr, fine ? mg.cmask + fine->off : nullptr, mg.cmask + lv.off, s));
+  }
+  for (int b = 0; b < 2; ++b) {
+    MGBlock& B = mg.blk[b];
+    for (int l = 0; l < nl; ++l) {
+      const DevLevel& lv = D.levels[l].lv;
+      const int64_t n = lv.n_slots;
+      CK(level_apply<double>(mg, l, block_diag_op(b), mg.diag, mg.diag, s));
+      CK(mg_invert_diag(lv.n_slots, B.ncomp, mg.diag, lv.flags, mg.cmask + lv.off, B.fixbits,
+                        B.dinv64 + B.ncomp * lv.off, B.dinv32 + B.ncomp * lv.off, s));
+      B.lam[l] = 0.0;
+      if (l == 0) continue;
+      // lambda_max of D^-1 A on the interior: Jacobi-preconditioned CG from a fixed start vector
+      const int64_t nn = B.ncomp * n;
+      const double* dinv = B.dinv64 + B.ncomp * lv.off;
+      CK(mg_start_vector(lv.n_slots, B.ncomp, D.levels[l].gx, D.levels[l].gy, dinv, mg.cg_r, s));
+      CK(fill64(nn, mg.cg_q, 0.0, s));
+      // scalars {rz, pq, rz_new, alpha = 0, beta, ok = 1}; z = D^-1 r, p = z, rz = r.z
+      const double sc0[8] = {0, 0, 0, 0, 0, 1, 0, 0};
+      CK(cudaMemcpyAsync(mg.sc, sc0, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cg_update_r(nn, mg.cg_r, mg.cg_z, mg.cg_q, dinv, mg.sc, s));
+      CK(copy64(nn, mg.cg_p, mg.cg_z, s));
+      CK(dot64(nn, mg.cg_r, mg.cg_z, mg.partial, mg.sc + 0, s));
+      for (int j = 0; j < mg.lanczos_steps; ++j) {
+        CK(level_apply<double>(mg, l, block_op(b), mg.cg_p, mg.cg_q, s));
+        CK(dot64(nn, mg.cg_p, mg.cg_q, mg.partial, mg.sc + 1, s));
+        CK(cg_scalars_alpha(mg.sc, s));
+        CK(cg_update_r(nn, mg.cg_r, mg.cg_z, mg.cg_q, dinv, mg.sc, s));
+        CK(dot64(nn, mg.cg_r, mg.cg_z, mg.partial, mg.sc + 2, s));
+        CK(cg_scalars_beta(mg.sc, mg.hist, j, s));
+        CK(cg_update_p(nn, mg.cg_p, mg.cg_z, mg.sc, s));
+      }
+      std::vector<double> hist(2 * mg.lanczos_steps);
+      CK(cudaMemcpyAsync(hist.data(), mg.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<double> al, be;
+      for (int j = 0; j < mg.lanczos_steps; ++j) {
+        if (!(hist[2 * j] > 0)) break;
+        al.push_back(hist[2 * j]);
+        be.push_back(hist[2 * j + 1]);
+      }
+      const int m = int(al.size());
+      std::vector<double> dd(m), ee(m > 0 ? m - 1 : 0);
+      for (int j = 0; j < m; ++j) dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+      for (int j = 0; j + 1 < m; ++j) ee[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
+      B.lam[l] = tridiag_max_eig(dd, ee);
+    }
+    // coarse level: dense FP64 block by probing with (2k+1)^2 colours per component
+    const DevMesh::Level& L0 = D.levels[0];
+    const LevelMesh& lm0 = M.levels[0];
+    const int n0 = L0.lv.n_slots;
+    std::vector<uint8_t> cm0(n0);
+    CK(cudaMemcpyAsync(cm0.data(), mg.cmask + L0.lv.off, n0, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int k = M.k, Mc = 2 * k + 1;
+    std::unordered_map<int64_t, int32_t> pos;  // (gx, gy) -> slot
+    std::vector<int32_t> gx(n0, -1), gy(n0, -1);
+    for (int q = 0; q < n0; ++q)
+      if (lm0.slot_X[q] >= 0) {
+        gx[q] = lm0.slot_X[q] >> M.Lf;
+        gy[q] = lm0.slot_Y[q] >> M.Lf;
+        pos[(int64_t(gx[q]) << 32) | gy[q]] = q;
+      }
+    std::vector<int32_t> eidx;            // interior entries (comp * n0 + slot)
+    std::vector<int32_t> ent_of(size_t(B.ncomp) * n0, -1);
+    for (int q = 0; q < n0; ++q)
+      for (int c = 0; c < B.ncomp; ++c) {
+        const int bit = B.fixbits == 4 ? 4 : (1 << c);
+        if (gx[q] >= 0 && !(cm0[q] & bit)) {
+          ent_of[size_t(c) * n0 + q] = int32_t(eidx.size());
+          eidx.push_back(c * n0 + q);
+        }
+      }
+    const int nI = int(eidx.size());
+    std::vector<double> A(size_t(nI) * nI, 0.0), probe(size_t(B.ncomp) * n0), yv(size_t(B.ncomp) * n0);
+    for (int c = 0; c < B.ncomp; ++c)
+      for (int cy = 0; cy < Mc; ++cy)
+        for (int cx = 0; cx < Mc; ++cx) {
+          std::fill(probe.begin(), probe.end(), 0.0);
+          for (int q = 0; q < n0; ++q)
+            if (gx[q] >= 0 && gx[q] % Mc == cx && gy[q] % Mc == cy) probe[size_t(c) * n0 + q] = 1.0;
+          CK(cudaMemcpyAsync(mg.cg_p, probe.data(), probe.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+          CK(level_apply<double>(mg, 0, block_op(b), mg.cg_p, mg.cg_q, s));
+          CK(cudaMemcpyAsync(yv.data(), mg.cg_q, yv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          for (int q = 0; q < n0; ++q) {
+            if (gx[q] < 0) continue;
+            // the probed node within distance k of q in each direction
+            const int jx = gx[q] - k + ((cx - (gx[q] - k)) % Mc + Mc) % Mc;
+            const int jy = gy[q] - k + ((cy - (gy[q] - k)) % Mc + Mc) % Mc;
+            auto it = pos.find((int64_t(jx) << 32) | jy);
+            if (it == pos.end()) continue;
+            const int32_t col = ent_of[size_t(c) * n0 + it->second];
+            if (col < 0) continue;
+            for (int cr = 0; cr < B.ncomp; ++cr) {
+              const int32_t row = ent_of[size_t(cr) * n0 + q];
+              if (row < 0) continue;
+              A[size_t(row) * nI + col] = yv[size_t(cr) * n0 + q];
+            }
+          }
+        }
+    std::vector<double> inv;
+    if (nI > 0 && !dense_spd_inverse(nI, A, inv)) return "coarse level block is not positive definite";
+    if (B.n_coarse != nI || !B.coarse_idx) {
+      B.coarse_idx = mg.mem.alloc<int32_t>(std::max(nI, 1));
+      B.coarse_inv = mg.mem.alloc<double>(std::max<int64_t>(int64_t(nI) * nI, 1));
+      B.coarse_tmp = mg.mem.alloc<double>(std::max(nI, 1));
+      if (!mg.mem.err.empty()) return mg.mem.err;
+      B.n_coarse = nI;
+    }
+    if (nI > 0) {
+      CK(cudaMemcpyAsync(B.coarse_idx, eidx.data(), nI * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(B.coarse_inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  mg.ready = true;
+  return "";
+}
+
+namespace {
+
+template <typename T>
+cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t s) {
+  pff_problem& pb = *mg.pb;
+  const Mesh& M = pb.mesh->m;
+  const DevMesh& D = pb.mesh->dev;
+  MGBlock& B = mg.blk[b];
+  const int nc = B.ncomp, nl = int(D.levels.size());
+  const int64_t N = D.lev_total;
+  const int64_t nsleaf = M.lay.n_slots;
+  T* d = static_cast<T*>(B.d);
+  T* x = static_cast<T*>(B.x);
+  T* rr = static_cast<T*>(B.r);
+  T* y = static_cast<T*>(B.y);
+  T* yp = static_cast<T*>(B.yp);
+  T* t = static_cast<T*>(B.t);
+  const T* dinv = sizeof(T) == 8 ? reinterpret_cast<const T*>(B.dinv64) : reinterpret_cast<const T*>(B.dinv32);
+  cudaError_t e;
+#define VC(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+  VC(cudaMemsetAsync(d, 0, nc * N * sizeof(T), s));
+  VC(cudaMemsetAsync(x, 0, nc * N * sizeof(T), s));
+  for (int l = 0; l < nl; ++l) {
+    const DevLevel& lv = D.levels[l].lv;
+    VC(mg_copy_in<T>(lv.n_copy, nc, lv.copy_leaf, lv.copy_level, r, nsleaf, d + nc * lv.off, lv.n_slots,
+                     pb.cmask, B.fixbits, s));
+  }
+  // Chebyshev on level l: solve A v = rhs from v = 0 into out (buffers v, vp, t)
+  auto cheb = [&](int l, const T* rhs, T* out) -> cudaError_t {
+    const DevLevel& lv = D.levels[l].lv;
+    const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
+    const double lam = B.lam[l];
+    if (!(lam > 0)) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
+    const double a = mg.lo * lam, bb = mg.hi * lam;
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    T* v = out;
+    T* vp = yp + o;
+    T* tmp = y + o;
+    cudaError_t ee = mg_chebyshev_first<T>(n, v, vp, dinv + o, rhs, T(1.0 / theta), s);
+    if (ee != cudaSuccess) return ee;
+    double rho = 1.0 / sigma;
+    for (int j = 1; j < mg.degree; ++j) {
+      const double rho_n = 1.0 / (2.0 * sigma - rho);
+      ee = level_apply<T>(mg, l, block_op(b), v, t + o, s);
+      if (ee != cudaSuccess) return ee;
+      // tmp = v + rho_n rho (v - vp) + 2 rho_n / delta D^-1 (rhs - A v)
+      ee = mg_chebyshev_step<T>(n, tmp, v, vp, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
+      if (ee != cudaSuccess) return ee;
+      // rotate: vp <- v, v <- tmp (copies keep the buffer roles fixed)
+      ee = cudaMemcpyAsync(vp, v, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      if (ee != cudaSuccess) return ee;
+      ee = cudaMemcpyAsync(v, tmp, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      if (ee != cudaSuccess) return ee;
+      rho = rho_n;
+    }
+    return cudaSuccess;
+  };
+  // down sweep
+  for (int l = nl - 1; l >= 1; --l) {
+    const DevLevel& lv = D.levels[l].lv;
+    const DevLevel& lc = D.levels[l - 1].lv;
+    const int64_t o = nc * lv.off;
+    VC(cheb(l, d + o, x + o));
+    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s));
+    VC(mg_restrict<T>(lc.n_slots, nc, lc.n_slots, lv.n_slots, lv.R_ptr, lv.R_col, lv.R_val, d + o, t + o,
+                      d + nc * lc.off, mg.cmask + lc.off, B.fixbits, s));
+  }
+  // coarse
+  VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s));
+  // up sweep
+  for (int l = 1; l < nl; ++l) {
+    const DevLevel& lv = D.levels[l].lv;
+    const DevLevel& lc = D.levels[l - 1].lv;
+    const int64_t o = nc * lv.off, n = nc * int64_t(lv.n_slots);
+    VC(mg_prolong<T>(lv.n_slots, nc, lv.n_slots, lc.n_slots, lv.P_ptr, lv.P_col, lv.P_val, x + nc * lc.off, x + o,
+                     mg.cmask + lv.off, B.fixbits, s));
+    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s));
+    VC(mg_residual<T>(n, rr + o, d + o, t + o, s));
+    // post-smoothing correction; the level defect d is not needed any more and holds it
+    VC(cheb(l, rr + o, d + o));
+    VC(mg_axpy<T>(n, x + o, d + o, T(1), s));
+  }
+  VC(mg_leaf_init(nsleaf, nc, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s));
+  for (int l = 0; l < nl; ++l) {
+    const DevLevel& lv = D.levels[l].lv;
+    VC(mg_copy_out<T>(lv.n_copy, nc, lv.copy_leaf, lv.copy_level, x + nc * lv.off, lv.n_slots, z, nsleaf,
+                      pb.cmask, B.fixbits, s));
+  }
+#undef VC
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s) {
+  if (mg.precision == PFF_F64) return vcycle_t<double>(mg, block, r, z, s);
+  return vcycle_t<float>(mg, block, r, z, s);
+}
+
+template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t);
+template cudaError_t level_apply<double>(pff_mg&, int, int, const double*, double*, cudaStream_t);
+
+}  // namespace pff

@@ -43,6 +43,38 @@ std::string upload_mesh(pff_mesh& pm) {
   D.fix_part = D.mem.upload(M.fix_part);
   D.fix_w = D.mem.upload(M.fix_w);
   D.slot_flags = D.mem.upload(M.slot_flags);
+  D.levels.resize(M.levels.size());
+  int64_t off = 0;
+  for (size_t l = 0; l < M.levels.size(); ++l) {
+    const LevelMesh& lm = M.levels[l];
+    DevMesh::Level& L = D.levels[l];
+    L.lay = upload_layout(D.mem, lm.lay);
+    L.lv.n_slots = int32_t(lm.lay.n_slots);
+    L.lv.off = off;
+    off += lm.lay.n_slots;
+    L.lv.flags = D.mem.upload(lm.slot_flags);
+    L.lv.slot_leaf = D.mem.upload(lm.slot_leaf);
+    std::vector<float> pv(lm.P_val.begin(), lm.P_val.end()), rv(lm.R_val.begin(), lm.R_val.end());
+    if (l > 0) {
+      L.lv.P_ptr = D.mem.upload(lm.P_ptr);
+      L.lv.P_col = D.mem.upload(lm.P_col);
+      L.lv.P_val = D.mem.upload(pv);
+      L.lv.R_ptr = D.mem.upload(lm.R_ptr);
+      L.lv.R_col = D.mem.upload(lm.R_col);
+      L.lv.R_val = D.mem.upload(rv);
+    }
+    L.lv.n_copy = int32_t(lm.copy_leaf.size());
+    L.lv.copy_leaf = D.mem.upload(lm.copy_leaf);
+    L.lv.copy_level = D.mem.upload(lm.copy_level);
+    std::vector<int32_t> gx(lm.slot_X.size()), gy(lm.slot_Y.size());
+    for (size_t q = 0; q < gx.size(); ++q) {
+      gx[q] = lm.slot_X[q] < 0 ? -1 : (lm.slot_X[q] >> (M.Lf - int(l)));
+      gy[q] = lm.slot_Y[q] < 0 ? -1 : (lm.slot_Y[q] >> (M.Lf - int(l)));
+    }
+    L.gx = D.mem.upload(gx);
+    L.gy = D.mem.upload(gy);
+  }
+  D.lev_total = off;
   if (!D.mem.err.empty()) {
     std::string err = D.mem.err;
     D.release();

@@ -1,0 +1,77 @@
+"""Parity of the CUDA block multigrid (through the C-ABI) with the oracle V-cycle:
+eigenvalue estimates per level and the V-cycle output of both blocks, for the
+FP64 and the FP32 V-cycle (tolerances 1e-10 and 1e-5 relative)."""
+import numpy as np
+import pytest
+
+from harness import Pair, random_active, random_linearisation, rel_err
+from oracle import mg as omg
+from oracle import operators as ops
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def setup_pair(name, frac, seed=0):
+    key = (name, frac, seed)
+    if key in _cache:
+        return _cache[key]
+    P = Pair(name, 1)
+    mat = P.material(kappa=1e-3, p=0.05)
+    u, phi, phit = random_linearisation(P, seed=seed, u_std=1e-2)
+    active = random_active(P, seed=5, frac=frac) if frac > 0 else np.zeros(P.om.nn, bool)
+    M = omg.MG(P.om, ops.Material(**mat), u, phi, phit, active)
+    _cache[key] = (P, mat, u, phi, phit, active, M)
+    return _cache[key]
+
+
+def lib_mg(P, mat, u, phi, phit, active, prec):
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, Problem
+    dev = torch.device("cuda:0")
+    pb = Problem(P.lm, **mat)
+    pb.set_state(torch.tensor(P.to_slots(u).T.copy(), device=dev), torch.tensor(P.to_slots(phi), device=dev),
+                 torch.tensor(P.to_slots(phit), device=dev))
+    pb.set_active(torch.tensor(P.to_slots(active.astype(np.uint8)), device=dev))
+    mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
+    mg.setup()
+    return pb, mg
+
+
+@pytest.mark.parametrize("name,frac", [("tiny", 0.0), ("small", 0.0), ("small", 0.05), ("band4_2_4", 0.0)])
+def test_lambda_estimates(name, frac):
+    P, mat, u, phi, phit, active, M = setup_pair(name, frac)
+    pb, mg = lib_mg(P, mat, u, phi, phit, active, "f32")
+    for b, blk in ((0, "uu"), (1, "pp")):
+        lam = mg.lam(b)
+        ref = np.array([0.0] + [M.B[blk][l].lam for l in range(1, len(M.B[blk]))])
+        assert np.allclose(lam[1:], ref[1:], rtol=1e-9, atol=1e-300), (blk, lam, ref)
+
+
+@pytest.mark.parametrize("name,frac", [("tiny", 0.0), ("small", 0.0), ("small", 0.05), ("band4_2_4", 0.0)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_vcycle_parity(name, frac, prec, tol):
+    import torch
+    P, mat, u, phi, phit, active, M = setup_pair(name, frac)
+    pb, mg = lib_mg(P, mat, u, phi, phit, active, prec)
+    om = P.om
+    nn = om.nn
+    rng = np.random.default_rng(3)
+    for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
+        r = rng.normal(size=(nn, nc))
+        zref = M.vcycle(blk, np.concatenate([r[:, c] for c in range(nc)]))
+        zref = np.stack([zref[c * nn:(c + 1) * nn] for c in range(nc)], 1)
+        rs = P.to_slots(r)
+        rs[~P.valid] = 1e30   # holes must be ignored
+        rt = torch.tensor(rs.T.copy() if nc == 2 else rs[:, 0].copy(), device="cuda")
+        zt = torch.full_like(rt, float("nan"))
+        mg.vcycle(b, rt, zt)
+        torch.cuda.synchronize()
+        zs = zt.cpu().numpy()
+        zs = zs.T if nc == 2 else zs[:, None]
+        assert np.all(zs[~P.valid] == 0.0)
+        z = P.from_slots(zs)
+        assert np.all(z[om.is_hanging] == 0.0)
+        inf, two = rel_err(z, zref)
+        assert inf < tol and two < tol, (blk, prec, inf, two)

@@ -159,6 +159,59 @@ pff_status pff_vcycle(pff_mg* mg, int32_t block, const double* r, double* z, voi
 pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam_host, int32_t n);
 void pff_mg_destroy(pff_mg* mg);
 
+/* ---- residual, GMRES, Newton / primal-dual active set ---------------------
+ * Full vectors hold three blocks of n_slots doubles (u_x, u_y, phi).        */
+typedef struct pff_solve_info {
+  int32_t newton_iterations;
+  int32_t converged;           /* 1 if the stopping rule was met                */
+  int32_t linesearch_failures; /* Newton steps whose line search found no decrease */
+  int32_t gmres_total;         /* linear iterations, summed over Newton steps     */
+  int32_t gmres_max;
+  int32_t pad;
+  int64_t active_size;         /* size of the final active set                   */
+  double residual0;            /* ||R~(U^{n,0})|| (GMRES: initial preconditioned residual) */
+  double residual;             /* final ||R~|| (GMRES: final estimate)            */
+  double margin;               /* min |R_i / B_ii + c (phi_i - phi_i^old)| over DoFs */
+  int32_t gmres_per_newton[128];
+  double residual_history[129];
+} pff_solve_info;
+
+typedef struct pff_newton_opts {
+  double tol;         /* relative Newton tolerance on ||R~|| (1e-8)           */
+  double atol;        /* absolute floor (1e-13)                               */
+  double gmres_rtol;  /* GMRES tolerance on the preconditioned residual (1e-6) */
+  double omega;       /* line-search damping (0.5)                            */
+  int32_t restart;    /* GMRES restart length (50)                            */
+  int32_t gmres_maxiter;
+  int32_t max_newton; /* Newton iteration cap (100)                           */
+  int32_t ls_max;     /* line-search trials (10)                              */
+} pff_newton_opts;
+
+/* Pressure p of the current load step (Problem 1).                           */
+pff_status pff_set_pressure(pff_problem* pb, double p);
+/* R = -A(U)(psi) (Problem 2, residual form; sigma^+ read as sigma) for every
+ * basis function, hanging contributions condensed onto their parents,
+ * Dirichlet u rows 0.  u: 2*n_slots, phi, phi_tilde: n_slots (device).  R: 3 blocks. */
+pff_status pff_residual(pff_problem* pb, const double* u, const double* phi, const double* phi_tilde, double* R,
+                        void* stream);
+/* B: lumped phi mass, integral of each (constrained) basis function; n_slots.   */
+pff_status pff_lumped_mass(pff_problem* pb, double* B, void* stream);
+/* Total crack volume integral of u . grad phi (Sec. 4) into *out_host (synchronises). */
+pff_status pff_tcv(pff_problem* pb, const double* u, const double* phi, double* out_host, void* stream);
+/* Left-preconditioned GMRES on G~ x = rhs (transpose != 0: G~^T) with the block
+ * V-cycle preconditioner of mg, x0 = 0; synchronises.  Errors:
+ * PFF_ERR_NOT_CONVERGED, PFF_ERR_GMRES_BREAKDOWN, PFF_ERR_NONFINITE (info filled). */
+pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
+                           double rtol, int32_t restart, int32_t maxiter, pff_solve_info* info, void* stream);
+/* One load step of Algorithm 2 at the problem's pressure: Newton iterations with
+ * the primal-dual active set, multigrid-preconditioned GMRES and line search,
+ * phi_tilde = phi_old.  u, phi: updated in place; active: n_slots bytes, the
+ * previous step's final set on input, this step's on output.  opts may be NULL
+ * (defaults above).  Synchronises.  Errors: PFF_ERR_NOT_CONVERGED,
+ * PFF_ERR_NONFINITE, PFF_ERR_GMRES_BREAKDOWN (info filled).                   */
+pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* u, double* phi, const double* phi_old,
+                                uint8_t* active, const pff_newton_opts* opts, pff_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,6 +100,23 @@ class Problem:
         _lib.check(_lib.lib().pff_apply(self._h, prec, op, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(yu),
                                         _lib.ptr(yp), _lib.stream_ptr(stream)))
 
+    def set_pressure(self, p):
+        _lib.check(_lib.lib().pff_set_pressure(self._h, p))
+
+    def residual(self, u, phi, phit, R, stream=None):
+        """R (3, n_slots) float64 = -A(U) condensed, Dirichlet rows 0."""
+        _lib.check(_lib.lib().pff_residual(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phit), _lib.ptr(R),
+                                           _lib.stream_ptr(stream)))
+
+    def lumped_mass(self, B, stream=None):
+        _lib.check(_lib.lib().pff_lumped_mass(self._h, _lib.ptr(B), _lib.stream_ptr(stream)))
+
+    def tcv(self, u, phi, stream=None):
+        out = _lib.ctypes.c_double()
+        _lib.check(_lib.lib().pff_tcv(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ctypes.byref(out),
+                                      _lib.stream_ptr(stream)))
+        return out.value
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
@@ -134,3 +151,30 @@ class MG:
         if h is not None and h.value:
             _lib.lib().pff_mg_destroy(h)
             self._h = None
+
+
+def gmres(problem, mg, rhs, x, rtol=1e-6, restart=50, maxiter=500, transpose=False, stream=None, check=True):
+    """Left-preconditioned GMRES on the constrained Jacobian (full vectors (3, n_slots) float64)."""
+    info = _lib.SolveInfo()
+    st = _lib.lib().pff_gmres_solve(problem._h, mg._h, int(transpose), _lib.ptr(rhs), _lib.ptr(x), rtol, restart,
+                                    maxiter, _lib.ctypes.byref(info), _lib.stream_ptr(stream))
+    d = dict(iterations=info.gmres_total, converged=bool(info.converged), initial=info.residual0,
+             estimate=info.residual, status=st)
+    if check:
+        _lib.check(st)
+    return d
+
+
+def newton_step(problem, mg, u, phi, phi_old, active, tol=1e-8, atol=1e-13, gmres_rtol=1e-6, omega=0.5,
+                restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, stream=None, check=True):
+    """One load step of Algorithm 2 (u (2, n_slots), phi, phi_old (n_slots,) float64; active uint8)."""
+    o = _lib.NewtonOpts(tol, atol, gmres_rtol, omega, restart, gmres_maxiter, max_newton, ls_max)
+    info = _lib.SolveInfo()
+    st = _lib.lib().pff_newton_pdas_step(problem._h, mg._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phi_old),
+                                         _lib.ptr(active), _lib.ctypes.byref(o), _lib.ctypes.byref(info),
+                                         _lib.stream_ptr(stream))
+    d = info.to_dict()
+    d["status"] = st
+    if check:
+        _lib.check(st)
+    return d

@@ -37,6 +37,28 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("p", ctypes.c_double), ("c", ctypes.c_double)]
 
 
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("newton_iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("linesearch_failures", ctypes.c_int32), ("gmres_total", ctypes.c_int32),
+                ("gmres_max", ctypes.c_int32), ("pad", ctypes.c_int32), ("active_size", ctypes.c_int64),
+                ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("margin", ctypes.c_double),
+                ("gmres_per_newton", ctypes.c_int32 * 128), ("residual_history", ctypes.c_double * 129)]
+
+    def to_dict(self):
+        n = self.newton_iterations
+        return dict(newton=n, converged=bool(self.converged), linesearch_failures=self.linesearch_failures,
+                    gmres_total=self.gmres_total, gmres_max=self.gmres_max, active_size=self.active_size,
+                    residual0=self.residual0, residual=self.residual, margin=self.margin,
+                    gmres=list(self.gmres_per_newton[:min(n, 128)]),
+                    residual_history=list(self.residual_history[:min(n + 1, 129)]))
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
+                ("omega", ctypes.c_double), ("restart", ctypes.c_int32), ("gmres_maxiter", ctypes.c_int32),
+                ("max_newton", ctypes.c_int32), ("ls_max", ctypes.c_int32)]
+
+
 _lib = None
 
 # (name, restype, argtypes)
@@ -63,6 +85,14 @@ _SIGS = [
     ("pff_vcycle", ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
     ("pff_mg_lambda", ctypes.c_int32, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     ("pff_mg_destroy", None, [_P]),
+    ("pff_set_pressure", ctypes.c_int32, [_P, ctypes.c_double]),
+    ("pff_residual", ctypes.c_int32, [_P, _P, _P, _P, _P, _P]),
+    ("pff_lumped_mass", ctypes.c_int32, [_P, _P, _P]),
+    ("pff_tcv", ctypes.c_int32, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("pff_gmres_solve", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.POINTER(SolveInfo), _P]),
+    ("pff_newton_pdas_step", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(NewtonOpts),
+                                              ctypes.POINTER(SolveInfo), _P]),
 ]
 
 

@@ -1,6 +1,7 @@
 // C-ABI entry points of libpff (declared in include/pff.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -226,6 +227,7 @@ extern "C" pff_status pff_problem_create(pff_mesh* m, const pff_params* prm, pff
 
 extern "C" void pff_problem_destroy(pff_problem* pb) {
   if (!pb) return;
+  pb->ws.mem.release();
   pb->bufs.release();
   delete pb;
 }
@@ -322,4 +324,117 @@ extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (!mg) return;
   mg->mem.release();
   delete mg;
+}
+
+// ------------------------------------------------------------------ solvers
+extern "C" pff_status pff_set_pressure(pff_problem* pb, double p) {
+  PFF_TRY({
+    if (!pb || !std::isfinite(p)) return fail(PFF_ERR_INVALID_ARG, "bad argument");
+    pb->prm.p = p;
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_residual(pff_problem* pb, const double* u, const double* phi, const double* phi_tilde,
+                                   double* R, void* stream) {
+  PFF_TRY({
+    if (!pb || !u || !phi || !phi_tilde || !R) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    PFF_CUDA(leaf_residual(*pb, u, phi, phi_tilde, R, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_lumped_mass(pff_problem* pb, double* B, void* stream) {
+  PFF_TRY({
+    if (!pb || !B) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    PFF_CUDA(lumped_mass(*pb, B, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_tcv(pff_problem* pb, const double* u, const double* phi, double* out_host, void* stream) {
+  PFF_TRY({
+    if (!pb || !u || !phi || !out_host) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    PFF_CUDA(total_crack_volume(*pb, u, phi, out_host, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+static void fill_info(const NewtonInfo& in, pff_solve_info* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->newton_iterations = in.newton;
+  out->converged = in.converged ? 1 : 0;
+  out->linesearch_failures = in.linesearch_failures;
+  int tot = 0, mx = 0;
+  for (size_t i = 0; i < in.gmres.size(); ++i) {
+    tot += in.gmres[i];
+    mx = std::max(mx, in.gmres[i]);
+    if (i < 128) out->gmres_per_newton[i] = in.gmres[i];
+  }
+  out->gmres_total = tot;
+  out->gmres_max = mx;
+  out->active_size = in.active_size.empty() ? 0 : in.active_size.back();
+  out->residual0 = in.residual0;
+  out->residual = in.residual.empty() ? 0.0 : in.residual.back();
+  out->margin = in.margin;
+  for (size_t i = 0; i < in.residual.size() && i < 129; ++i) out->residual_history[i] = in.residual[i];
+}
+
+extern "C" pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
+                                      double rtol, int32_t restart, int32_t maxiter, pff_solve_info* info,
+                                      void* stream) {
+  PFF_TRY({
+    if (!pb || !mg || !rhs || !x) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (restart < 1 || restart > 500 || maxiter < 1 || !(rtol > 0)) return fail(PFF_ERR_INVALID_ARG, "bad options");
+    if (!mg->ready) return fail(PFF_ERR_STATE, "pff_mg_setup has not been called");
+    std::string e = ensure_workspace(*pb, restart);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    GmresResult gr;
+    PFF_CUDA(gmres_solve(*pb, *mg, transpose, rhs, x, rtol, restart, maxiter, gr, cudaStream_t(stream)));
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->gmres_total = gr.iterations;
+      info->gmres_max = gr.iterations;
+      info->converged = gr.converged ? 1 : 0;
+      info->residual0 = gr.initial;
+      info->residual = gr.estimate;
+    }
+    if (gr.breakdown) return fail(PFF_ERR_GMRES_BREAKDOWN, "GMRES breakdown");
+    if (!std::isfinite(gr.estimate)) return fail(PFF_ERR_NONFINITE, "non-finite residual in GMRES");
+    if (!gr.converged) return fail(PFF_ERR_NOT_CONVERGED, "GMRES did not reach the tolerance");
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* u, double* phi, const double* phi_old,
+                                           uint8_t* active, const pff_newton_opts* opts, pff_solve_info* info,
+                                           void* stream) {
+  PFF_TRY({
+    if (!pb || !mg || !u || !phi || !phi_old || !active) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    NewtonOpts o;
+    if (opts) {
+      o.tol = opts->tol; o.atol = opts->atol; o.gmres_rtol = opts->gmres_rtol; o.omega = opts->omega;
+      o.restart = opts->restart; o.gmres_maxiter = opts->gmres_maxiter; o.max_newton = opts->max_newton;
+      o.ls_max = opts->ls_max;
+    }
+    if (o.restart < 1 || o.restart > 500 || o.max_newton < 0 || o.ls_max < 1 || !(o.omega > 0 && o.omega <= 1))
+      return fail(PFF_ERR_INVALID_ARG, "bad Newton options");
+    std::string e = ensure_workspace(*pb, o.restart);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    NewtonInfo ni;
+    cudaError_t ce = newton_pdas_step(*pb, *mg, u, phi, phi_old, active, o, ni, cudaStream_t(stream));
+    if (info) fill_info(ni, info);
+    if (!ni.error.empty()) return fail(PFF_ERR_CUDA, ni.error);
+    PFF_CUDA(ce);
+    if (ni.nonfinite) return fail(PFF_ERR_NONFINITE, "non-finite Newton residual");
+    if (ni.gmres_breakdown) return fail(PFF_ERR_GMRES_BREAKDOWN, "GMRES breakdown inside Newton");
+    if (!ni.converged) return fail(PFF_ERR_NOT_CONVERGED, "Newton / active set did not converge");
+    return PFF_OK;
+  })
 }

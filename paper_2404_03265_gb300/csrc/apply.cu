@@ -93,9 +93,11 @@ __device__ __forceinline__ P psub(P a, P b) { return pfma(b, pbc(decltype(a.x)(-
 template <int OP> struct Needs {
   static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU);
   static constexpr bool xp = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP);
-  static constexpr bool linU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
-  static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T);
-  static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG);
+  static constexpr bool linU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG ||
+                                OP == OP_RESID || OP == OP_TCV);
+  static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_RESID || OP == OP_TCV);
+  static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG ||
+                                OP == OP_RESID);
 };
 
 // Node data of a column pair (A, B) of one window row, in registers.
@@ -192,7 +194,69 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
     }
   }
   if (N::xp) { fxp.init(v[0].xp, v[1].xp, v[2].xp, v[3].xp); fxp.values(v[0].xp, xpq); }
-  if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
+  if (OP == OP_RESID || OP == OP_MASS || OP == OP_TCV) {
+    // R = -A(U)(psi), Problem 2 with sigma^+ read as sigma:
+    //   A_u(psi)   = (g(phi~) sigma(u), e(psi)) + (phi~^2 p, div psi)
+    //   A_phi(psi) = ((1-kappa) phi sigma(u):e(u) + 2 p phi div u - G_c/l (1 - phi), psi)
+    //                + G_c l (grad phi, grad psi)
+    // MASS: (1, psi);  TCV: (u . grad phi, psi)
+    P S11[2][2], S12[2][2], S22[2][2], fv[2][2];
+    P uxq[2][2], uyq[2][2];
+    if (OP == OP_TCV) { fux.values(v[0].lx, uxq); fuy.values(v[0].ly, uyq); }
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+      for (int q2 = 0; q2 < 2; ++q2) {
+        if (OP == OP_MASS) { fv[q1][q2] = pbc(T(1)); continue; }
+        if (OP == OP_TCV) {
+          // u . grad phi, grad phi from the reference derivatives of phi
+          const P gpx = pmul(fphi.dxi[q2], ihx), gpy = pmul(fphi.deta[q1], ihy);
+          fv[q1][q2] = pfma(uxq[q1][q2], gpx, pmul(uyq[q1][q2], gpy));
+          continue;
+        }
+        const P gq = pfma(omk, pmul(phitq[q1][q2], phitq[q1][q2]), pbc(m.kap));
+        const P ge12 = padd(uxy[q1], uyx[q2]);
+        const P s11 = pfma(c2ml, e11[q2], pmul(cl, e22[q1]));
+        const P s22 = pfma(cl, e11[q2], pmul(c2ml, e22[q1]));
+        const P s12 = pmul(cm, ge12);
+        const P pt2 = pmul(pbc(m.p), pmul(phitq[q1][q2], phitq[q1][q2]));
+        S11[q1][q2] = pfma(gq, s11, pt2);
+        S22[q1][q2] = pfma(gq, s22, pt2);
+        S12[q1][q2] = pmul(gq, s12);
+        const P se = pfma(s11, e11[q2], pfma(s22, e22[q1], pmul(s12, ge12)));
+        const P ph = phiq[q1][q2];
+        // (1-kappa) phi se + 2 p phi div u - G_c/l (1 - phi)
+        const P a1 = pfma(pmul(omk, ph), se, pmul(pmul(pbc(m.p2), ph), padd(e11[q2], e22[q1])));
+        fv[q1][q2] = pfma(pbc(m.gcl), psub(ph, pbc(T(1))), a1);
+      }
+    const P wx = pbc(g.wx), wy = pbc(g.wy), nwx = pbc(-g.wx), nwy = pbc(-g.wy);
+    if (OP == OP_RESID) {
+      ptest_grad(padd(S11[0][0], S11[1][0]), padd(S11[0][1], S11[1][1]),
+                 padd(S12[0][0], S12[0][1]), padd(S12[1][0], S12[1][1]), wx, wy, nwx, nwy, rux);
+      ptest_grad(padd(S12[0][0], S12[1][0]), padd(S12[0][1], S12[1][1]),
+                 padd(S22[0][0], S22[0][1]), padd(S22[1][0], S22[1][1]), wx, wy, nwx, nwy, ruy);
+      ptest_grad(fphi.dxi[0], fphi.dxi[1], fphi.deta[0], fphi.deta[1], pbc(g.wpx), pbc(g.wpy), pbc(-g.wpx),
+                 pbc(-g.wpy), rp);
+    }
+    {
+      const P jxw = pbc(g.jxw);
+      const P s0 = padd(fv[0][0], fv[0][1]), s1 = padd(fv[1][0], fv[1][1]);
+      const P t0 = pfma(pbc(T(GA)), fv[0][0], pmul(pbc(T(GB)), fv[0][1]));
+      const P t1 = pfma(pbc(T(GA)), fv[1][0], pmul(pbc(T(GB)), fv[1][1]));
+      const P b0 = psub(s0, t0), b1 = psub(s1, t1);
+      const P pb = pfma(pbc(T(GA)), b0, pmul(pbc(T(GB)), b1));
+      const P pt = pfma(pbc(T(GA)), t0, pmul(pbc(T(GB)), t1));
+      rp[0] = pfma(jxw, psub(padd(b0, b1), pb), rp[0]);
+      rp[1] = pfma(jxw, pb, rp[1]);
+      rp[2] = pfma(jxw, psub(padd(t0, t1), pt), rp[2]);
+      rp[3] = pfma(jxw, pt, rp[3]);
+    }
+    if (OP == OP_RESID) {
+      const P neg = pbc(T(-1));
+#pragma unroll
+      for (int A = 0; A < 4; ++A) { rux[A] = pmul(rux[A], neg); ruy[A] = pmul(ruy[A], neg); rp[A] = pmul(rp[A], neg); }
+    }
+  } else if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
@@ -473,8 +537,8 @@ __device__ __forceinline__ void read_row(const Stage<T>& st, int hl, int right_l
 template <typename T, int OP>
 __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_base, int n, int c, uint8_t cm,
                                            T y0, T y1, T y2) {
-  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
-  constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV);
+  constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   T* yu = reinterpret_cast<T*>(a.yu);
   T* yv = yu + a.n_slots;
@@ -513,8 +577,8 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 template <typename T, int OP>
 __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MINB64) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
   using P = typename VT<T>::T2;
-  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG);
-  constexpr bool outP = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG);
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV);
+  constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -798,6 +862,9 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
     PFF_LAUNCH(OP_PP)
     PFF_LAUNCH(OP_UU_DIAG)
     PFF_LAUNCH(OP_PP_DIAG)
+    PFF_LAUNCH(OP_RESID)
+    PFF_LAUNCH(OP_MASS)
+    PFF_LAUNCH(OP_TCV)
 #undef PFF_LAUNCH
     default: return cudaErrorInvalidValue;
   }

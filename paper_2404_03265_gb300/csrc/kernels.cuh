@@ -23,6 +23,9 @@ enum OpKind : int {
   OP_PP = 3,       // diagonal block phi-phi of a level operator
   OP_UU_DIAG = 4,  // diagonal of the uu block (Chebyshev-Jacobi, Sec. 3.2)
   OP_PP_DIAG = 5,  // diagonal of the phi-phi block
+  OP_RESID = 6,    // residual R = -A(U)(psi) at the state held in `lin` (Problem 2)
+  OP_MASS = 7,     // integral of each basis function (lumped mass, phi component)
+  OP_TCV = 8,      // (u . grad phi, psi) per basis function (summed: total crack volume)
 };
 
 // mode bits

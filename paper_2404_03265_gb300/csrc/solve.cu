@@ -1,0 +1,255 @@
+// Element-wise kernels of the Newton / primal-dual active set loop (Algorithm 2
+// of Kolditz & Wick, arXiv 2404.03265) and the Krylov kernels of GMRES.
+//
+// A full vector has three blocks of n_slots doubles: u_x, u_y, phi.
+// Leaf slot flags: bit0 node, bit1 boundary (Dirichlet u), bit2 hanging.
+// All reductions are deterministic (fixed partition, fixed summation order).
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "solve.cuh"
+
+namespace pff {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int RED_BLOCKS = 512;
+
+inline unsigned blocks_for(int64_t n) {
+  int64_t b = (n + TPB - 1) / TPB;
+  if (b > 65535 * 8) b = 65535 * 8;
+  return unsigned(b < 1 ? 1 : b);
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
+
+__global__ void k_make_state(int64_t n, const double* __restrict__ u, const double* __restrict__ phi,
+                             const double* __restrict__ phit, const uint8_t* __restrict__ flags, double* st) {
+  GRID_STRIDE(s, n) {
+    const bool node = flags[s] & 1;
+    st[s] = node ? u[s] : 0.0;
+    st[n + s] = node ? u[n + s] : 0.0;
+    st[2 * n + s] = node ? phi[s] : 0.0;
+    st[3 * n + s] = node ? phit[s] : 0.0;
+  }
+}
+
+__global__ void k_state_hanging(int32_t nh, int64_t n, const DevHanging* __restrict__ hang, int np, int nblk,
+                                double* v) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nh) return;
+  const DevHanging e = hang[h];
+  for (int k = 0; k < nblk; ++k) {
+    double acc = 0.0;
+    for (int b = 0; b < np; ++b) acc += e.weight[b] * v[k * n + e.parent[b]];
+    v[k * n + e.slot] = acc;
+  }
+}
+
+// active set: ind = R_phi / B + c (phi - phi_old) > 0 on non-hanging nodes
+__global__ void k_active(int64_t n, const double* __restrict__ R, const double* __restrict__ B,
+                         const double* __restrict__ phi, const double* __restrict__ phio,
+                         const uint8_t* __restrict__ flags, double c, const uint8_t* __restrict__ prev,
+                         uint8_t* act, unsigned long long* stats) {
+  GRID_STRIDE(s, n) {
+    const uint8_t f = flags[s];
+    uint8_t a = 0;
+    if ((f & 1) && !(f & 4)) {
+      const double ind = R[2 * n + s] / B[s] + c * (phi[s] - phio[s]);
+      a = ind > 0.0 ? 1 : 0;
+      // |ind| as its IEEE bit pattern: ordered like the value for non-negative doubles
+      const double ai = fabs(ind);
+      atomicMin(stats + 2, (unsigned long long)__double_as_longlong(ai));
+      if (a) atomicAdd(stats + 1, 1ull);
+    }
+    if (a != (prev ? prev[s] : 0)) atomicAdd(stats + 0, 1ull);
+    act[s] = a;
+  }
+}
+
+// Newton residual: R on free rows, phi_old - phi on active phi rows, 0 on Dirichlet / hanging / holes
+__global__ void k_newton_res(int64_t n, const double* __restrict__ R, const uint8_t* __restrict__ act,
+                             const double* __restrict__ phi, const double* __restrict__ phio,
+                             const uint8_t* __restrict__ flags, double* out) {
+  GRID_STRIDE(s, n) {
+    const uint8_t f = flags[s];
+    const bool node = (f & 1) && !(f & 4);
+    const bool dir = f & 2;
+    out[s] = (node && !dir) ? R[s] : 0.0;
+    out[n + s] = (node && !dir) ? R[n + s] : 0.0;
+    out[2 * n + s] = node ? (act[s] ? phio[s] - phi[s] : R[2 * n + s]) : 0.0;
+  }
+}
+
+// rhs = (R - t) on free rows, dU0 = phi_old - phi on active phi rows, 0 elsewhere
+__global__ void k_newton_rhs(int64_t n, const double* __restrict__ R, const double* __restrict__ t,
+                             const uint8_t* __restrict__ act, const double* __restrict__ phi,
+                             const double* __restrict__ phio, const uint8_t* __restrict__ flags, double* rhs) {
+  GRID_STRIDE(s, n) {
+    const uint8_t f = flags[s];
+    const bool node = (f & 1) && !(f & 4);
+    const bool dir = f & 2;
+    rhs[s] = (node && !dir) ? R[s] - t[s] : 0.0;
+    rhs[n + s] = (node && !dir) ? R[n + s] - t[n + s] : 0.0;
+    rhs[2 * n + s] = node ? (act[s] ? phio[s] - phi[s] : R[2 * n + s] - t[2 * n + s]) : 0.0;
+  }
+}
+
+// dU0: phi_old - phi on active phi DoFs, 0 elsewhere
+__global__ void k_du0(int64_t n, const uint8_t* __restrict__ act, const double* __restrict__ phi,
+                      const double* __restrict__ phio, double* du0) {
+  GRID_STRIDE(s, n) {
+    du0[s] = 0.0;
+    du0[n + s] = 0.0;
+    du0[2 * n + s] = act[s] ? phio[s] - phi[s] : 0.0;
+  }
+}
+
+__global__ void k_axpby(int64_t n, double* out, const double* __restrict__ x, double a, const double* __restrict__ y,
+                        double b) {
+  GRID_STRIDE(i, n) out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale(int64_t n, double* out, const double* __restrict__ x, double a) {
+  GRID_STRIDE(i, n) out[i] = a * x[i];
+}
+
+// partial[b * k + j] = sum over this block's rows of V_j . w
+__global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ V, int64_t ld,
+                                   const double* __restrict__ w, double* partial) {
+  __shared__ double sh[TPB];
+  for (int j = 0; j < k; ++j) {
+    double acc = 0.0;
+    GRID_STRIDE(i, n) acc += V[j * ld + i] * w[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = TPB / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * k + j] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_multidot_final(int nb, int k, const double* __restrict__ partial, double* out) {
+  __shared__ double sh[TPB];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += TPB) acc += partial[int64_t(b) * k + j];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sh[0];
+}
+
+// w += sign * sum_j h_j V_j
+__global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
+                             double sign, double* w) {
+  GRID_STRIDE(i, n) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += h[j] * V[j * ld + i];
+    w[i] += sign * acc;
+  }
+}
+
+__global__ void k_sum_partial(int64_t n, const double* __restrict__ a, double* part) {
+  __shared__ double sh[TPB];
+  double acc = 0.0;
+  GRID_STRIDE(i, n) acc += a[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_all_finite(int64_t n, const double* __restrict__ a, int* bad) {
+  GRID_STRIDE(i, n) if (!isfinite(a[i])) atomicOr(bad, 1);
+}
+
+}  // namespace
+
+cudaError_t make_state(int64_t n, const double* u, const double* phi, const double* phit, const uint8_t* flags,
+                       const DevHanging* hang, int32_t nhang, int fe_degree, double* st, cudaStream_t s) {
+  if (n > 0) k_make_state<<<blocks_for(n), TPB, 0, s>>>(n, u, phi, phit, flags, st);
+  if (nhang > 0) k_state_hanging<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, n, hang, fe_degree + 1, 4, st);
+  return cudaGetLastError();
+}
+
+cudaError_t distribute_hanging(int64_t n, const DevHanging* hang, int32_t nhang, int fe_degree, int nblk, double* v,
+                               cudaStream_t s) {
+  if (nhang > 0) k_state_hanging<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, n, hang, fe_degree + 1, nblk, v);
+  return cudaGetLastError();
+}
+
+cudaError_t active_set(int64_t n, const double* R, const double* B, const double* phi, const double* phi_old,
+                       const uint8_t* flags, double c, const uint8_t* prev, uint8_t* act, unsigned long long* stats,
+                       cudaStream_t s) {
+  if (n > 0) k_active<<<blocks_for(n), TPB, 0, s>>>(n, R, B, phi, phi_old, flags, c, prev, act, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t newton_residual(int64_t n, const double* R, const uint8_t* act, const double* phi,
+                            const double* phi_old, const uint8_t* flags, double* out, cudaStream_t s) {
+  if (n > 0) k_newton_res<<<blocks_for(n), TPB, 0, s>>>(n, R, act, phi, phi_old, flags, out);
+  return cudaGetLastError();
+}
+
+cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_t* act, const double* phi,
+                       const double* phi_old, const uint8_t* flags, double* rhs, cudaStream_t s) {
+  if (n > 0) k_newton_rhs<<<blocks_for(n), TPB, 0, s>>>(n, R, t, act, phi, phi_old, flags, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
+                       cudaStream_t s) {
+  if (n > 0) k_du0<<<blocks_for(n), TPB, 0, s>>>(n, act, phi, phi_old, du0);
+  return cudaGetLastError();
+}
+
+cudaError_t axpby(int64_t n, double* out, const double* x, double a, const double* y, double b, cudaStream_t s) {
+  if (n > 0) k_axpby<<<blocks_for(n), TPB, 0, s>>>(n, out, x, a, y, b);
+  return cudaGetLastError();
+}
+
+cudaError_t scale(int64_t n, double* out, const double* x, double a, cudaStream_t s) {
+  if (n > 0) k_scale<<<blocks_for(n), TPB, 0, s>>>(n, out, x, a);
+  return cudaGetLastError();
+}
+
+int reduction_partials() { return RED_BLOCKS; }
+
+cudaError_t multidot(int64_t n, int k, const double* V, int64_t ld, const double* w, double* partial, double* out,
+                     cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_multidot_partial<<<RED_BLOCKS, TPB, 0, s>>>(n, k, V, ld, w, partial);
+  k_multidot_final<<<k, TPB, 0, s>>>(RED_BLOCKS, k, partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ld, const double* h, double sign, double* w,
+                       cudaStream_t s) {
+  if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ld, h, sign, w);
+  return cudaGetLastError();
+}
+
+cudaError_t vsum(int64_t n, const double* a, double* partial, double* out, cudaStream_t s) {
+  k_sum_partial<<<RED_BLOCKS, TPB, 0, s>>>(n, a, partial);
+  k_multidot_final<<<1, TPB, 0, s>>>(RED_BLOCKS, 1, partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t all_finite(int64_t n, const double* a, int* bad, cudaStream_t s) {
+  if (n > 0) k_all_finite<<<blocks_for(n), TPB, 0, s>>>(n, a, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace pff

@@ -1,0 +1,40 @@
+// Kernels of the Newton / PDAS loop and of GMRES (solve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace pff {
+
+// state (4 blocks: u_x, u_y, phi, phi_tilde) with hanging entries from their constraint
+cudaError_t make_state(int64_t n, const double* u, const double* phi, const double* phit, const uint8_t* flags,
+                       const DevHanging* hang, int32_t nhang, int fe_degree, double* st, cudaStream_t s);
+// v[h] = sum_b w_b v[parent_b] on the first nblk blocks of v
+cudaError_t distribute_hanging(int64_t n, const DevHanging* hang, int32_t nhang, int fe_degree, int nblk, double* v,
+                               cudaStream_t s);
+// stats[0] += changes vs prev, stats[1] += active count, stats[2] = min |indicator| (IEEE bits)
+cudaError_t active_set(int64_t n, const double* R, const double* B, const double* phi, const double* phi_old,
+                       const uint8_t* flags, double c, const uint8_t* prev, uint8_t* act, unsigned long long* stats,
+                       cudaStream_t s);
+cudaError_t newton_residual(int64_t n, const double* R, const uint8_t* act, const double* phi,
+                            const double* phi_old, const uint8_t* flags, double* out, cudaStream_t s);
+cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_t* act, const double* phi,
+                       const double* phi_old, const uint8_t* flags, double* rhs, cudaStream_t s);
+cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
+                       cudaStream_t s);
+cudaError_t axpby(int64_t n, double* out, const double* x, double a, const double* y, double b, cudaStream_t s);
+cudaError_t scale(int64_t n, double* out, const double* x, double a, cudaStream_t s);
+int reduction_partials();
+// out[j] = V_j . w, j < k (V_j = V + j * ld)
+cudaError_t multidot(int64_t n, int k, const double* V, int64_t ld, const double* w, double* partial, double* out,
+                     cudaStream_t s);
+// w += sign * sum_j h[j] V_j  (h on the device)
+cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ld, const double* h, double sign, double* w,
+                       cudaStream_t s);
+cudaError_t vsum(int64_t n, const double* a, double* partial, double* out, cudaStream_t s);
+cudaError_t all_finite(int64_t n, const double* a, int* bad, cudaStream_t s);
+
+}  // namespace pff

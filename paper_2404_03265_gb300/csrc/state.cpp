@@ -91,6 +91,7 @@ std::string alloc_problem(pff_problem& pb) {
   pb.lin64 = pb.bufs.alloc<double>(4 * ns);
   pb.lin32 = pb.bufs.alloc<float>(4 * ns);
   pb.cmask = pb.bufs.alloc<uint8_t>(ns);
+  pb.cmask_dir = pb.bufs.alloc<uint8_t>(ns);
   pb.ibuf64 = pb.bufs.alloc<double>(3 * M.n_partials);
   pb.ibuf32 = pb.bufs.alloc<float>(3 * M.n_partials);
   if (!pb.bufs.err.empty()) {
@@ -100,7 +101,8 @@ std::string alloc_problem(pff_problem& pb) {
   }
   cudaMemset(pb.lin64, 0, 4 * ns * sizeof(double));
   cudaMemset(pb.lin32, 0, 4 * ns * sizeof(float));
-  const cudaError_t e = launch_leaf_cmask(ns, pb.mesh->dev.slot_flags, nullptr, pb.cmask, 0);
+  cudaError_t e = launch_leaf_cmask(ns, pb.mesh->dev.slot_flags, nullptr, pb.cmask, 0);
+  if (e == cudaSuccess) e = launch_leaf_cmask(ns, pb.mesh->dev.slot_flags, nullptr, pb.cmask_dir, 0);
   if (e != cudaSuccess) return std::string("cmask: ") + cudaGetErrorString(e);
   cudaError_t e2 = cudaDeviceSynchronize();
   if (e2 != cudaSuccess) return std::string("sync: ") + cudaGetErrorString(e2);

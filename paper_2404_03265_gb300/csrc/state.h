@@ -73,6 +73,42 @@ struct DevMesh {
   }
 };
 
+// Work space of GMRES and the Newton loop (allocated on first use).
+struct SolverWS {
+  DevAllocs mem;
+  bool ready = false;
+  int restart = 0;
+  double *V = nullptr, *w = nullptr, *tmp = nullptr, *rhs = nullptr, *R = nullptr, *res = nullptr;
+  double *dU = nullptr, *du0 = nullptr, *st = nullptr, *ut = nullptr, *B = nullptr;
+  uint8_t *act = nullptr, *act_prev = nullptr;
+  unsigned long long* stats = nullptr;
+  double *partial = nullptr, *h = nullptr, *scal = nullptr;
+  int* bad = nullptr;
+};
+
+struct GmresResult {
+  int iterations = 0;
+  bool converged = false;
+  bool breakdown = false;
+  double initial = 0.0, estimate = 0.0;
+};
+
+struct NewtonOpts {
+  double tol = 1e-8, atol = 1e-13, gmres_rtol = 1e-6, omega = 0.5;
+  int restart = 50, gmres_maxiter = 500, max_newton = 100, ls_max = 10;
+};
+
+struct NewtonInfo {
+  int newton = 0;
+  bool converged = false, nonfinite = false, gmres_breakdown = false;
+  int linesearch_failures = 0;
+  double residual0 = 0.0, margin = 0.0;
+  std::vector<double> residual;
+  std::vector<int> gmres;
+  std::vector<int64_t> active_size, changes;
+  std::string error;
+};
+
 }  // namespace pff
 
 struct pff_mesh {
@@ -87,6 +123,8 @@ struct pff_problem {
   double* lin64 = nullptr;   // 4 per slot
   float* lin32 = nullptr;
   uint8_t* cmask = nullptr;  // leaf constraint mask: bit0/1 Dirichlet u, bit2 active phi
+  uint8_t* cmask_dir = nullptr;  // Dirichlet bits only (residual evaluation)
+  pff::SolverWS ws;
   double* ibuf64 = nullptr;  // 3 per partial slot
   float* ibuf32 = nullptr;
   bool has_state = false;
@@ -140,6 +178,18 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
                        void* yp, cudaStream_t s);
 cudaError_t launch_leaf_cmask(int64_t n, const uint8_t* slot_flags, const uint8_t* active, uint8_t* cmask,
                               cudaStream_t s);
+// solvers (solver.cpp)
+cudaError_t leaf_op(pff_problem& pb, int kop, int mode, const double* lin, const uint8_t* cmask, const double* xu,
+                    const double* xp, double* yu, double* yp, cudaStream_t s);
+std::string ensure_workspace(pff_problem& pb, int restart);
+cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double* b, double* x, double rtol,
+                        int restart, int maxiter, GmresResult& res, cudaStream_t s);
+cudaError_t leaf_residual(pff_problem& pb, const double* u, const double* phi, const double* phit, double* R,
+                          cudaStream_t s);
+cudaError_t lumped_mass(pff_problem& pb, double* B, cudaStream_t s);
+cudaError_t total_crack_volume(pff_problem& pb, const double* u, const double* phi, double* out_host, cudaStream_t s);
+cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi, const double* phi_old,
+                             uint8_t* active, const NewtonOpts& o, NewtonInfo& info, cudaStream_t s);
 // multigrid (mg_host.cpp)
 std::string mg_alloc(pff_mg& mg);
 std::string mg_setup(pff_mg& mg, cudaStream_t s);

@@ -1,0 +1,131 @@
+"""Parity of the CUDA residual, lumped mass, TCV, GMRES and Newton / PDAS load step
+with the oracle (through the C-ABI).  Tolerances: residual 1e-12 relative;
+GMRES solution vs a sparse direct solve 1e-7; converged u, phi 1e-7 relative L2;
+active set bit-identical."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from harness import Pair, random_active, random_linearisation, rel_err
+from oracle import operators as ops
+from oracle import solvers
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def problem(P, mat):
+    from paper_2404_03265_gb300 import Problem
+    return Problem(P.lm, **mat)
+
+
+def blocks(P, v3):
+    """oracle (nn, 3) -> library (3, n_slots)."""
+    return P.to_slots(v3).T.copy()
+
+
+def unblocks(P, s3):
+    return P.from_slots(np.asarray(s3).T)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "band4_2_4"])
+def test_residual_mass_tcv(name):
+    import torch
+    P = Pair(name, 1)
+    mat = P.material(kappa=1e-3, p=0.2)
+    u, phi, phit = random_linearisation(P, seed=2, u_std=0.05)
+    om = P.om
+    pb = problem(P, mat)
+    us, ps, pts = dev(P.to_slots(u).T), dev(P.to_slots(phi)), dev(P.to_slots(phit))
+    R = torch.full((3, P.n_slots), float("nan"), dtype=torch.float64, device="cuda")
+    pb.residual(us, ps, pts, R)
+    B = torch.full((P.n_slots,), float("nan"), dtype=torch.float64, device="cuda")
+    pb.lumped_mass(B)
+    torch.cuda.synchronize()
+    st = ops.State(om, u, phi, phit)
+    Rref = ops.condense(om, -ops.residual_form(om, ops.Material(**mat), st))
+    nn = om.nn
+    Rref = np.stack([Rref[:nn], Rref[nn:2 * nn], Rref[2 * nn:]], 1)
+    Rref[om.dirichlet, :2] = 0.0
+    Rg = unblocks(P, R.cpu().numpy())
+    inf, two = rel_err(Rg, Rref)
+    assert inf < 1e-12 and two < 1e-12, (inf, two)
+    Bg = P.from_slots(B.cpu().numpy())
+    Bref = ops.lumped_mass(om)
+    assert np.abs(Bg - Bref).max() < 1e-13 * Bref.max()
+    tcv = pb.tcv(us, ps)
+    tref = ops.tcv(om, ops.State(om, u, phi, phi))
+    assert abs(tcv - tref) <= 1e-12 * abs(tref)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_gmres_solves_constrained_system(prec):
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, gmres
+    P = Pair("small", 1)
+    mat = P.material(kappa=1e-3, p=0.05)
+    u, phi, phit = random_linearisation(P, seed=0, u_std=1e-2)
+    active = random_active(P, seed=5, frac=0.05)
+    om = P.om
+    pb = problem(P, mat)
+    pb.set_state(dev(P.to_slots(u).T), dev(P.to_slots(phi)), dev(P.to_slots(phit)))
+    pb.set_active(dev(P.to_slots(active.astype(np.uint8))))
+    mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
+    mg.setup()
+    rng = np.random.default_rng(9)
+    b = rng.normal(size=(om.nn, 3))
+    b[om.is_hanging] = 0.0
+    bs = dev(blocks(P, b))
+    x = torch.zeros_like(bs)
+    info = gmres(pb, mg, bs, x, rtol=1e-10, restart=50, maxiter=400)
+    assert info["converged"]
+    Gt = ops.constrained_operator(om, ops.assemble_jacobian(om, ops.Material(**mat), ops.State(om, u, phi, phit)),
+                                  active)
+    nn = om.nn
+    bv = np.concatenate([b[:, 0], b[:, 1], b[:, 2]])
+    free = ops.free_dofs(om, active) | ops.fixed_dofs(om, active)
+    xs = np.zeros(3 * nn)
+    idx = np.nonzero(free)[0]
+    xs[idx] = spla.spsolve(Gt[idx][:, idx].tocsc(), bv[idx])
+    xg = unblocks(P, x.cpu().numpy())
+    xg = np.concatenate([xg[:, 0], xg[:, 1], xg[:, 2]])
+    err = np.linalg.norm(xg - xs) / np.linalg.norm(xs)
+    assert err < 1e-7, err
+
+
+@pytest.mark.parametrize("name", ["small", "band4_3_3"])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_newton_pdas_load_step(name, prec):
+    """Sneddon load step on the GPU against the oracle load step (Algorithm 2)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, newton_step
+    P = Pair(name, 1)
+    om = P.om
+    h = om.h_min_diag()
+    mat = P.material()
+    u0, phi_old = solvers.sneddon_initial(om, h)
+    uo, po, ao, io = solvers.load_step(om, ops.Material(**mat), 1e4, u0, phi_old.copy(), phi_old)
+    assert io.converged
+    pb = problem(P, mat)
+    mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
+    us = dev(P.to_slots(u0).T)
+    ps = dev(P.to_slots(phi_old))
+    pos = dev(P.to_slots(phi_old))
+    act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
+    info = newton_step(pb, mg, us, ps, pos, act)
+    assert info["converged"], info
+    ug = P.from_slots(us.cpu().numpy().T)
+    pg = P.from_slots(ps.cpu().numpy())
+    ag = P.from_slots(act.cpu().numpy()).astype(bool)
+    assert np.array_equal(ag, ao), (ag.sum(), ao.sum(), (ag != ao).sum(), info["margin"])
+    eu = np.linalg.norm(ug - uo) / np.linalg.norm(uo)
+    ep = np.linalg.norm(pg - po) / np.linalg.norm(po)
+    assert eu < 1e-7 and ep < 1e-7, (eu, ep)
+    assert info["newton"] == io.newton
+    tcv = pb.tcv(us, ps)
+    tref = ops.tcv(om, ops.State(om, uo, po, po))
+    assert abs(tcv - tref) < 1e-7 * abs(tref)

@@ -187,6 +187,33 @@ typedef struct pff_newton_opts {
   int32_t ls_max;     /* line-search trials (10)                              */
 } pff_newton_opts;
 
+/* ---- allocation-free variant of pff_apply (no counterpart in the paper) ----
+ * Same operators, arguments, layout and results as pff_apply.  The difference is
+ * where the apply keeps its interface partial sums (one triple per interface
+ * node of an irregular brick, condensed by a second kernel): pff_apply uses
+ * buffers made by pff_problem_create, this call uses one fixed device array of
+ * PFF_NOALLOC_MAX_PARTIALS triples (1.5 MiB) that is part of the library image.
+ * No device or pinned memory is allocated by the call, directly or through a
+ * library.  It serves callers that must not allocate while they run: a host
+ * whose caching allocator has reserved nearly all device memory (a library
+ * cudaMalloc could fail at any time there), or a latency-bound loop that cannot
+ * afford cudaFree's implicit device synchronisation.
+ * Set-up: the first call on a device (that device current) looks up the array's
+ * address (cudaGetSymbolAddress) and caches it; make that first call outside any
+ * stream capture.
+ * Limits and hazards:
+ *  - a mesh with pff_mesh_info.n_partials > PFF_NOALLOC_MAX_PARTIALS is rejected
+ *    with PFF_ERR_INVALID_ARG (use pff_apply);
+ *  - the array is shared by all problems and streams of a device and keeps the
+ *    previous call's contents (nothing in it has to start at zero: every partial
+ *    that is read is written earlier in the same call); calls that may execute
+ *    at the same time on one device race on it, so order them on one stream or
+ *    with events;
+ *  - the problem must live on the current device.                              */
+#define PFF_NOALLOC_MAX_PARTIALS 65536
+pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
+                             void* yu, void* yp, void* stream);
+
 /* Pressure p of the current load step (Problem 1).                           */
 pff_status pff_set_pressure(pff_problem* pb, double p);
 /* R = -A(U)(psi) (Problem 2, residual form; sigma^+ read as sigma) for every

@@ -80,6 +80,7 @@ _SIGS = [
     ("pff_set_state", ctypes.c_int32, [_P, _P, _P, _P, _P]),
     ("pff_set_active", ctypes.c_int32, [_P, _P, _P]),
     ("pff_apply", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    ("pff_apply_noalloc", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P]),
     ("pff_mg_create", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("pff_mg_setup", ctypes.c_int32, [_P, _P]),
     ("pff_vcycle", ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),

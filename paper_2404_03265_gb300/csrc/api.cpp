@@ -44,6 +44,10 @@ pff_status fail(pff_status st, const std::string& msg) {
 
 }  // namespace
 
+namespace pff {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace pff
+
 extern "C" const char* pff_last_error(void) { return g_err.c_str(); }
 
 // ------------------------------------------------------------------ mesh

@@ -173,6 +173,8 @@ namespace pff {
 
 std::string upload_mesh(pff_mesh& m);
 std::string alloc_problem(pff_problem& pb);
+// message returned by pff_last_error on this thread
+void set_last_error(const std::string& msg);
 void fill_material(const pff_params& prm, ApplyArgs& a);
 cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, const void* xp, void* yu,
                        void* yp, cudaStream_t s);

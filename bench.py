@@ -208,6 +208,62 @@ def time_e2e(mesh, dtype, steps, warmup):
     return t, nb, hyu.numel() * hyu.element_size() + hyp.numel() * hyp.element_size()
 
 
+SOLVE_LOADS = (1e-3, 1.5e-3, 2e-3)
+
+
+def time_solve(precision, loads=SOLVE_LOADS):
+    """Load steps of Algorithm 2 on the 1,043,811-DoF band-refined crack mesh
+    (16x16 coarse, 5 global, 7 band steps; Q1): line-search Newton / PDAS with
+    FP64 GMRES preconditioned by the block V-cycle in the given precision.
+    Returns per-step wall time (CUDA events around pff_newton_pdas_step), Newton
+    and GMRES counts, TCV, and the final (u, phi) on the host."""
+    import torch
+    from paper_2404_03265_gb300 import MG, Mesh, Problem, newton_step
+    import synthetic as synth
+    mesh = Mesh.from_recipe(synth.recipe("solve")).finalize(1)
+    info = mesh.info
+    ns = info["n_slots"]
+    X, Y, F = mesh.slots()
+    valid = (F & 1) == 1
+    x, y = synth.node_xy(X[valid], Y[valid], info["x_max"], info["y_max"])
+    h = info["h_min"]
+    po_h = np.ones(ns)
+    po_h[valid] = synth.crack_phi_old(x, y, h)
+    m = synth.material(h_min=h)
+    pb = Problem(mesh, E=m["E"], nu=m["nu"], Gc=m["Gc"], eps=m["eps"], kappa=m["kappa"], p=loads[0], c=m["c"])
+    mg = MG(pb, precision)
+    dev = torch.device("cuda")
+    u = torch.zeros((2, ns), dtype=torch.float64, device=dev)
+    phi = torch.tensor(po_h, device=dev)
+    phi_old = phi.clone()
+    act = torch.zeros(ns, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    steps = []
+    for p in loads:
+        pb.set_pressure(p)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r = newton_step(pb, mg, u, phi, phi_old, act, check=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        tcv = pb.tcv(u, phi)
+        eprime = m["E"] / (1.0 - m["nu"] ** 2)
+        tcv_ref = 2.0 * np.pi * p * 1.0 ** 2 / eprime
+        k = max(r["newton"], 1)
+        steps.append({"p": p, "s": t, "newton": r["newton"], "gmres_mean": r["gmres_total"] / k,
+                      "gmres_max": r["gmres_max"], "gmres": r["gmres"], "linesearch_failures": r["linesearch_failures"],
+                      "active": r["active_size"], "converged": bool(r["converged"]), "status": r["status"],
+                      "residual": r["residual"], "tcv": tcv, "tcv_rel_err": abs(tcv - tcv_ref) / tcv_ref})
+        phi_old.copy_(phi)
+    uh = u.cpu().numpy()[:, valid]
+    ph = phi.cpu().numpy()[valid]
+    return {"dofs": 3 * info["n_nodes"], "steps": steps,
+            "s_per_load_step": float(np.mean([st["s"] for st in steps]))}, uh, ph
+
+
 def cpu_baseline(budget_s=12.0):
     """The oracle as it stands (explicit assembly of G~ + CSR matvec, FP64), on
     host cores, on a bounded sample: the 65,001-DoF Q1 mesh of the same box-refined
@@ -260,6 +316,27 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch of the FP32 apply kernel from the committed
+    ncu summary, or None when the kernel source has changed since it was captured."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "apply_q1_f32_apply_workload_ncu.md")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        text = f.read()
+    h = hashlib.sha256()
+    for name in ("apply.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_03265_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    m_hash = re.search(r"first 16 hex\): `([0-9a-f]{16})`", text)
+    m_bytes = re.search(r"^bytes_per_launch: (\d+)", text, re.M)
+    if not m_hash or not m_bytes or m_hash.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(m_bytes.group(1))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +344,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the load-step timing leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -313,11 +391,7 @@ def main():
     hbm, peak_kind = load_peaks()
     alg_bytes = info["n_nodes"] * 10 * 4  # x (3), y (3), linearisation (4) per node, FP32
     achieved = alg_bytes / (t / args.steps) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "apply_q1_f32_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -337,6 +411,20 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
+    if not args.no_solve:
+        from paper_2404_03265_gb300 import PFF_F32, PFF_F64
+        r32, u32, p32 = time_solve(PFF_F32)
+        r64, u64, p64 = time_solve(PFF_F64)
+        line["solve"] = {
+            "workload": "solve: 16x16 coarse on (-10,10)^2, 5 global + 7 band refinements toward the crack "
+                        "(|x|<=1+2h_min, |y|<=2h_min), Q1, %d DoFs; Sneddon crack, E=1, nu=0.2, G_c=1, "
+                        "l=2h_min, kappa=1e-10, c=1e4; p = %s" % (r32["dofs"], ", ".join("%g" % p for p in SOLVE_LOADS)),
+            "unit": "s/load step", "newton_tol": 1e-8, "gmres_rtol": 1e-6,
+            "fp32_mg": r32, "fp64_mg": r64,
+            "speedup_fp32_mg": r64["s_per_load_step"] / r32["s_per_load_step"],
+            "fp32_vs_fp64_rel_l2": {"u": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
+                                    "phi": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))},
+        }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -20,6 +20,9 @@ mg         level meshes, local-smoothing V-cycle with Chebyshev-Jacobi smoothing
            eigenvalue estimate, transfers, coarse solve (Sec. 3.2).
 solvers    left-preconditioned GMRES, Newton / primal-dual active set with line
            search (Algorithms 1 and 2).
+adjoint    gradient of the total crack volume of a converged load step with
+           respect to p, G_c and a per-cell Young's modulus (adjoint solve with
+           the transposed constrained Jacobian of Sec. 3.1).
 
 Parity status of each function is stated in its module header; the pins live
 in ``tests/test_oracle_*.py``.

@@ -239,6 +239,49 @@ pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const
 pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* u, double* phi, const double* phi_old,
                                 uint8_t* active, const pff_newton_opts* opts, pff_solve_info* info, void* stream);
 
+/* ---- differentiation: per-cell modulus, TCV gradient, adjoint --------------
+ * Sec. 4 quantity of interest J = TCV = integral of u . grad phi; parameters p,
+ * G_c (Problem 1) and a per-cell Young's modulus E_K (sigma = E_K sigma_1, the
+ * Lame constants of each cell scaled by E_K).                                  */
+
+/* Per-cell modulus: E_cells is a device array of n_leaf_cells doubles in the
+ * canonical leaf-cell order of pff_mesh_leaf_cells (positive values), or NULL to
+ * return to the uniform pff_params.E.  Level operators of the multigrid use the
+ * leaf value on leaf cells and the mean of the four children on refined cells;
+ * call pff_mg_setup again afterwards.  The array is copied (stream-ordered).   */
+pff_status pff_set_cell_modulus(pff_problem* pb, const double* E_cells, void* stream);
+
+/* Replace the problem's parameters (E is ignored while a cell modulus is set).
+ * Takes effect for later calls; an existing pff_mg needs pff_mg_setup again.   */
+pff_status pff_set_params(pff_problem* pb, const pff_params* prm);
+
+/* g = M_f C^T dJ/dU at U = (u, phi): 3 blocks of n_slots doubles (device),
+ * rows of Dirichlet u, active phi (pff_set_active) and hanging nodes 0.        */
+pff_status pff_tcv_gradient(pff_problem* pb, const double* u, const double* phi, double* g, void* stream);
+
+/* Vector-Jacobian product of the residual with respect to the parameters at the
+ * problem's state (pff_set_state: u, phi, phi_tilde) and active set:
+ *   g_theta = (C M_f w) . dR/dtheta,  R = -A (Problem 2),
+ * w: 3 blocks of n_slots doubles (device; fixed entries ignored, hanging entries
+ * taken from their parents).  gE_cells: device, n_leaf_cells doubles in
+ * canonical leaf order (may be NULL); g_host[0] = g_p, g_host[1] = g_Gc (host).
+ * Synchronises.                                                               */
+pff_status pff_param_vjp(pff_problem* pb, const double* w, double* gE_cells, double* g_host, void* stream);
+
+/* Adjoint gradient of J at a converged load step (u, phi, active from
+ * pff_newton_pdas_step, phi_old its obstacle and phi_tilde):
+ *   G~^T lambda = M_f C^T dJ/dU (left-preconditioned GMRES with the block V-cycle
+ *   of mg, relative tolerance rtol on the preconditioned residual),
+ *   dJ/dtheta = (C M_f lambda) . dR/dtheta.
+ * Sets the problem's state and active set to (u, phi, phi_old) / active and
+ * re-runs pff_mg_setup.  Outputs as in pff_param_vjp: gE_cells (device, may be
+ * NULL), g_host[0] = dJ/dp, g_host[1] = dJ/dG_c.  info: GMRES count and
+ * residuals.  Synchronises.  Errors: PFF_ERR_NOT_CONVERGED,
+ * PFF_ERR_GMRES_BREAKDOWN, PFF_ERR_NONFINITE.                                 */
+pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const double* phi, const double* phi_old,
+                           const uint8_t* active, double rtol, int32_t restart, int32_t maxiter, double* gE_cells,
+                           double* g_host, pff_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ class Problem:
         _lib.check(_lib.lib().pff_problem_create(mesh._h, _lib.ctypes.byref(prm), _lib.ctypes.byref(h)))
         self._h = h
         self.n_slots = mesh.info["n_slots"]
+        self.params = dict(E=E, nu=nu, Gc=Gc, eps=eps, kappa=kappa, p=p, c=c)
 
     def set_state(self, u, phi, phit, stream=None):
         """u: float64 (2, n_slots) (u_x block, u_y block), phi, phit: float64 (n_slots,) CUDA tensors."""
@@ -102,6 +103,31 @@ class Problem:
 
     def set_pressure(self, p):
         _lib.check(_lib.lib().pff_set_pressure(self._h, p))
+        self.params["p"] = p
+
+    def set_params(self, **kw):
+        """Update parameters (E, nu, Gc, eps, kappa, p, c); later calls use them."""
+        self.params.update(kw)
+        q = self.params
+        prm = _lib.Params(q["E"], q["nu"], q["Gc"], q["eps"], q["kappa"], q["p"], q["c"])
+        _lib.check(_lib.lib().pff_set_params(self._h, _lib.ctypes.byref(prm)))
+
+    def set_cell_modulus(self, E_cells, stream=None):
+        """Per-cell Young's modulus (float64 device tensor in leaf_cells() order), or None."""
+        _lib.check(_lib.lib().pff_set_cell_modulus(self._h, None if E_cells is None else _lib.ptr(E_cells),
+                                                   _lib.stream_ptr(stream)))
+
+    def tcv_gradient(self, u, phi, g, stream=None):
+        """g = M_f C^T dJ/dU of J = TCV (g: float64 (3, n_slots))."""
+        _lib.check(_lib.lib().pff_tcv_gradient(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(g),
+                                               _lib.stream_ptr(stream)))
+
+    def param_vjp(self, w, gE=None, stream=None):
+        """(C M_f w) . dR/dtheta at the current state: returns (g_p, g_Gc); fills gE (per leaf cell)."""
+        out = np.zeros(2)
+        _lib.check(_lib.lib().pff_param_vjp(self._h, _lib.ptr(w), None if gE is None else _lib.ptr(gE),
+                                            _lib.ptr(out), _lib.stream_ptr(stream)))
+        return float(out[0]), float(out[1])
 
     def residual(self, u, phi, phit, R, stream=None):
         """R (3, n_slots) float64 = -A(U) condensed, Dirichlet rows 0."""
@@ -178,3 +204,18 @@ def newton_step(problem, mg, u, phi, phi_old, active, tol=1e-8, atol=1e-13, gmre
     if check:
         _lib.check(st)
     return d
+
+
+def tcv_adjoint(problem, mg, u, phi, phi_old, active, gE=None, rtol=1e-10, restart=50, maxiter=2000, stream=None,
+                check=True):
+    """dJ/dp, dJ/dG_c (and dJ/dE_K into gE) of J = TCV at a converged load step, by one
+    adjoint solve with the transposed constrained Jacobian."""
+    out = np.zeros(2)
+    info = _lib.SolveInfo()
+    st = _lib.lib().pff_tcv_adjoint(problem._h, mg._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phi_old),
+                                    _lib.ptr(active), rtol, restart, maxiter, None if gE is None else _lib.ptr(gE),
+                                    _lib.ptr(out), _lib.ctypes.byref(info), _lib.stream_ptr(stream))
+    if check:
+        _lib.check(st)
+    return dict(p=float(out[0]), Gc=float(out[1]), iterations=info.gmres_total, converged=bool(info.converged),
+                status=st)

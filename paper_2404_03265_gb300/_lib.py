@@ -94,6 +94,12 @@ _SIGS = [
                                          ctypes.c_int32, ctypes.POINTER(SolveInfo), _P]),
     ("pff_newton_pdas_step", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(NewtonOpts),
                                               ctypes.POINTER(SolveInfo), _P]),
+    ("pff_set_cell_modulus", ctypes.c_int32, [_P, _P, _P]),
+    ("pff_set_params", ctypes.c_int32, [_P, ctypes.POINTER(Params)]),
+    ("pff_tcv_gradient", ctypes.c_int32, [_P, _P, _P, _P, _P]),
+    ("pff_param_vjp", ctypes.c_int32, [_P, _P, _P, _P, _P]),
+    ("pff_tcv_adjoint", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         _P, _P, ctypes.POINTER(SolveInfo), _P]),
 ]
 
 

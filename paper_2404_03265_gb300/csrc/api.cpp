@@ -442,3 +442,77 @@ extern "C" pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* 
     return PFF_OK;
   })
 }
+
+// ---- per-cell modulus, parameters, TCV gradient, adjoint ---------------------
+extern "C" pff_status pff_set_cell_modulus(pff_problem* pb, const double* E_cells, void* stream) {
+  PFF_TRY({
+    if (!pb) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = set_cell_modulus(*pb, E_cells, cudaStream_t(stream));
+    if (!e.empty()) return fail(PFF_ERR_CUDA, "pff_set_cell_modulus: " + e);
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_set_params(pff_problem* pb, const pff_params* prm) {
+  PFF_TRY({
+    if (!pb || !prm) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!(prm->E > 0) || !(prm->nu > -1.0 && prm->nu < 0.5) || !(prm->eps > 0) || !(prm->Gc >= 0))
+      return fail(PFF_ERR_INVALID_ARG, "bad material parameters");
+    pb->prm = *prm;
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_tcv_gradient(pff_problem* pb, const double* u, const double* phi, double* g,
+                                       void* stream) {
+  PFF_TRY({
+    if (!pb || !u || !phi || !g) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    PFF_CUDA(tcv_gradient(*pb, u, phi, g, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_param_vjp(pff_problem* pb, const double* w, double* gE_cells, double* g_host,
+                                    void* stream) {
+  PFF_TRY({
+    if (!pb || !w || !g_host) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!pb->has_state) return fail(PFF_ERR_STATE, "pff_set_state has not been called");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    PFF_CUDA(param_vjp(*pb, w, gE_cells, g_host, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const double* phi,
+                                      const double* phi_old, const uint8_t* active, double rtol, int32_t restart,
+                                      int32_t maxiter, double* gE_cells, double* g_host, pff_solve_info* info,
+                                      void* stream) {
+  PFF_TRY({
+    if (!pb || !mg || !u || !phi || !phi_old || !active || !g_host) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (mg->pb != pb) return fail(PFF_ERR_INVALID_ARG, "multigrid object of another problem");
+    if (restart < 1 || restart > 500 || maxiter < 1 || !(rtol > 0)) return fail(PFF_ERR_INVALID_ARG, "bad options");
+    std::string e = ensure_workspace(*pb, restart);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    GmresResult gr;
+    std::string err;
+    const cudaError_t ce = tcv_adjoint(*pb, *mg, u, phi, phi_old, active, rtol, restart, maxiter, gE_cells, g_host,
+                                       gr, err, cudaStream_t(stream));
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->gmres_total = gr.iterations;
+      info->gmres_max = gr.iterations;
+      info->converged = gr.converged ? 1 : 0;
+      info->residual0 = gr.initial;
+      info->residual = gr.estimate;
+    }
+    if (!err.empty()) return fail(PFF_ERR_CUDA, "pff_mg_setup: " + err);
+    PFF_CUDA(ce);
+    if (gr.breakdown) return fail(PFF_ERR_GMRES_BREAKDOWN, "GMRES breakdown in the adjoint solve");
+    if (!std::isfinite(gr.estimate)) return fail(PFF_ERR_NONFINITE, "non-finite residual in the adjoint solve");
+    if (!gr.converged) return fail(PFF_ERR_NOT_CONVERGED, "adjoint GMRES did not reach the tolerance");
+    return PFF_OK;
+  })
+}

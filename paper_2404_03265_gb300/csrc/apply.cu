@@ -91,13 +91,14 @@ __device__ __forceinline__ P psub(P a, P b) { return pfma(b, pbc(decltype(a.x)(-
 
 // Which node fields an operator reads.
 template <int OP> struct Needs {
-  static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU);
-  static constexpr bool xp = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP);
+  static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_VJP);
+  static constexpr bool xp = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_VJP);
   static constexpr bool linU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG ||
-                                OP == OP_RESID || OP == OP_TCV);
-  static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_RESID || OP == OP_TCV);
+                                OP == OP_RESID || OP == OP_TCV || OP == OP_TCV_GRAD || OP == OP_VJP);
+  static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_RESID || OP == OP_TCV ||
+                               OP == OP_TCV_GRAD || OP == OP_VJP);
   static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG ||
-                                OP == OP_RESID);
+                                OP == OP_RESID || OP == OP_VJP);
 };
 
 // Node data of a column pair (A, B) of one window row, in registers.
@@ -150,18 +151,36 @@ __device__ __forceinline__ void ptest_grad(P sx0, P sx1, P sy0, P sy1, P wx, P w
   r[3] = pfma(wx, px, pfma(wy, py, r[3]));
 }
 
+// Test a value f given per Gauss point [q1][q2] against N_A = L_a(xi) L_b(eta), into r[0..3].
+template <typename P>
+__device__ __forceinline__ void ptest_value(const P fv[2][2], P jxw, P r[4]) {
+  using T = decltype(jxw.x);
+  const P s0 = padd(fv[0][0], fv[0][1]), s1 = padd(fv[1][0], fv[1][1]);
+  const P t0 = pfma(pbc(T(GA)), fv[0][0], pmul(pbc(T(GB)), fv[0][1]));
+  const P t1 = pfma(pbc(T(GA)), fv[1][0], pmul(pbc(T(GB)), fv[1][1]));
+  const P b0 = psub(s0, t0), b1 = psub(s1, t1);
+  const P pb = pfma(pbc(T(GA)), b0, pmul(pbc(T(GB)), b1));
+  const P pt = pfma(pbc(T(GA)), t0, pmul(pbc(T(GB)), t1));
+  r[0] = pfma(jxw, psub(padd(b0, b1), pb), r[0]);
+  r[1] = pfma(jxw, pb, r[1]);
+  r[2] = pfma(jxw, psub(padd(t0, t1), pt), r[2]);
+  r[3] = pfma(jxw, pt, r[3]);
+}
+
 // Two Q1 cells at once.  v[0] = nodes (0,0) of cells A and B, v[1] = (1,0),
 // v[2] = (0,1), v[3] = (1,1).  out[3*N + c]: contribution to node N of
-// component c (0 u_x, 1 u_y, 2 phi), as a pair over the two cells.
+// component c (0 u_x, 1 u_y, 2 phi), as a pair over the two cells.  ec: the
+// cells' moduli E_K (the elastic constants in m are then those of unit E), or 1.
+// OP_VJP returns its three per-cell values in out[0..2].
 template <typename T, int OP>
 __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatConst<T>& m, const LevGeom<T>& g,
-                                             typename VT<T>::T2 out[12]) {
+                                             typename VT<T>::T2 ec, typename VT<T>::T2 out[12]) {
   using N = Needs<OP>;
   using P = typename VT<T>::T2;
   const P zero = pbc(T(0));
   P rux[4] = {zero, zero, zero, zero}, ruy[4] = {zero, zero, zero, zero}, rp[4] = {zero, zero, zero, zero};
   const P ihx = pbc(g.ihx), ihy = pbc(g.ihy);
-  const P c2ml = pbc(m.c2ml), cl = pbc(m.cl), cm = pbc(m.cm), omk = pbc(m.omk);
+  const P c2ml = pmul(pbc(m.c2ml), ec), cl = pmul(pbc(m.cl), ec), cm = pmul(pbc(m.cm), ec), omk = pbc(m.omk);
   // ---- linearisation
   PField<P> fux, fuy, fphi, fphit;
   P e11[2], e22[2], uyx[2], uxy[2];
@@ -256,6 +275,56 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
 #pragma unroll
       for (int A = 0; A < 4; ++A) { rux[A] = pmul(rux[A], neg); ruy[A] = pmul(ruy[A], neg); rp[A] = pmul(rp[A], neg); }
     }
+  } else if (OP == OP_TCV_GRAD) {
+    // J = integral of u . grad phi:  dJ/du_(A,i) = (dphi/dx_i, N_A),  dJ/dphi_A = (u, grad N_A)
+    P uxq[2][2], uyq[2][2], gpx[2][2], gpy[2][2];
+    fux.values(v[0].lx, uxq);
+    fuy.values(v[0].ly, uyq);
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+      for (int q2 = 0; q2 < 2; ++q2) {
+        gpx[q1][q2] = pmul(fphi.dxi[q2], ihx);
+        gpy[q1][q2] = pmul(fphi.deta[q1], ihy);
+      }
+    const P jxw = pbc(g.jxw);
+    ptest_value(gpx, jxw, rux);
+    ptest_value(gpy, jxw, ruy);
+    ptest_grad(padd(uxq[0][0], uxq[1][0]), padd(uxq[0][1], uxq[1][1]), padd(uyq[0][0], uyq[0][1]),
+               padd(uyq[1][0], uyq[1][1]), pbc(g.wx), pbc(g.wy), pbc(-g.wx), pbc(-g.wy), rp);
+  } else if (OP == OP_VJP) {
+    // x . dR/dtheta per cell (R = -A, Problem 2; x = (w_u, w_phi) after constraints):
+    //   E_K: -[(g(phi~) sigma_1(u), e(w_u)) + (1-kappa)(phi sigma_1(u):e(u), w_phi)]_K
+    //   p:   -[(phi~^2, div w_u) + 2 (phi div u, w_phi)]_K
+    //   G_c: -[-(1/l)(1 - phi, w_phi) + l (grad phi, grad w_phi)]_K
+    // sigma_1: stress of unit modulus (m holds unit-E constants for this operator)
+    const P uc2ml = pbc(m.c2ml), ucl = pbc(m.cl), ucm = pbc(m.cm);
+    const T ihx2 = g.ihx * g.ihx, ihy2 = g.ihy * g.ihy;
+    P sE = zero, sP = zero, sG = zero;
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+      for (int q2 = 0; q2 < 2; ++q2) {
+        const P pt2 = pmul(phitq[q1][q2], phitq[q1][q2]);
+        const P gq = pfma(omk, pt2, pbc(m.kap));
+        const P ge12 = padd(uxy[q1], uyx[q2]);
+        const P s11 = pfma(uc2ml, e11[q2], pmul(ucl, e22[q1]));
+        const P s22 = pfma(ucl, e11[q2], pmul(uc2ml, e22[q1]));
+        const P s12 = pmul(ucm, ge12);
+        const P se = pfma(s11, e11[q2], pfma(s22, e22[q1], pmul(s12, ge12)));
+        const P bc = padd(bxy[q1], cyx[q2]);
+        const P sw = pfma(s11, ax[q2], pfma(s22, dy[q1], pmul(s12, bc)));
+        const P ph = phiq[q1][q2], wp = xpq[q1][q2];
+        sE = padd(sE, pfma(gq, sw, pmul(pmul(omk, ph), pmul(se, wp))));
+        sP = padd(sP, pfma(pt2, padd(ax[q2], dy[q1]), pmul(padd(ph, ph), pmul(padd(e11[q2], e22[q1]), wp))));
+        const P gg = pfma(pmul(fphi.dxi[q2], fxp.dxi[q2]), pbc(ihx2),
+                          pmul(pmul(fphi.deta[q1], fxp.deta[q1]), pbc(ihy2)));
+        sG = padd(sG, pfma(pbc(m.l), gg, pmul(pbc(-m.il), pmul(psub(pbc(T(1)), ph), wp))));
+      }
+    const P njxw = pbc(-g.jxw);
+    rux[0] = pmul(njxw, sE);
+    ruy[0] = pmul(njxw, sP);
+    rp[0] = pmul(njxw, sG);
   } else if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
@@ -267,7 +336,7 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
         const T Ns[4] = {(1 - xi) * (1 - eta), xi * (1 - eta), (1 - xi) * eta, xi * eta};
         if (OP == OP_UU_DIAG) {
           const P gq = pfma(omk, pmul(phitq[q1][q2], phitq[q1][q2]), pbc(m.kap));
-          const P jg = pmul(pbc(g.jxw), gq);
+          const P jg = pmul(pmul(pbc(g.jxw), gq), ec);
 #pragma unroll
           for (int A = 0; A < 4; ++A) {
             const T dx = dxs[A] * g.ihx, dyy = dys[A] * g.ihy;
@@ -643,7 +712,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
 
   // per-strip state of the strip being computed
   bool valid = false, pairwise = false;
-  int irr = 0, r0 = 0, own_base = 0;
+  int irr = 0, r0 = 0, own_base = 0, cnbase = 0;
   LevGeom<T> gq = geom<T>(a, 0);
   uint8_t cmA = 0, cmB = 0;
   P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
@@ -658,6 +727,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
       const BrickDesc* bd = a.lay.bricks + b;
       irr = __ldg(&bd->irr);
       own_base = __ldg(bd->nbr_base + 4);
+      cnbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
       gq = geom<T>(a, __ldg(&bd->level));
       pairwise = valid && irr < 0 && hl < 15;
     }
@@ -685,8 +755,17 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
         actA = actA && ((__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u);
         actB = (__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u;
       }
+      // cell moduli: the cell slot of a cell is the slot of its lower-left node
+      // position in the bricks of this level (neighbour bricks for column/row -1)
+      P ec = pbc(T(1));
+      if (a.ecell != nullptr) {  // uniform: all 32 lanes take the shuffles in regular_code
+        const int32_t sA = regular_code(cnbase, nA, c), sB = regular_code(cnbase, nB, c);
+        const T* E = reinterpret_cast<const T*>(a.ecell);
+        if (valid && actA) ec.x = ldg(E + sA);
+        if (valid && actB) ec.y = ldg(E + sB);
+      }
       P out[12];
-      q1_cell_pair<T, OP>(v, mc, gq, out);
+      q1_cell_pair<T, OP>(v, mc, gq, ec, out);
       if (!actA || !actB) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
@@ -694,6 +773,18 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
           if (!actB) out[q].y = T(0);
         }
       }
+      if constexpr (OP == OP_VJP) {
+        // per-cell values of the cells owned by this strip (rows r0.., columns 0..29)
+        if (c >= r0 && hl < 15 && valid) {
+          T* co = reinterpret_cast<T*>(a.cell_out);
+          const int64_t sA = own_base + nA + NB * c;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if (actA) co[q * a.n_slots + sA] = out[q].x;
+            if (actB) co[q * a.n_slots + sA + 1] = out[q].y;
+          }
+        }
+      } else {
       // the left lane's cell B contributes BR to our node A (row c) and TR to node A (row c+1)
       T brL[3], trL[3];
 #pragma unroll
@@ -725,6 +816,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
       for (int q = 0; q < 3; ++q) {
         carry[q].x = out[6 + q].x + trL[q];
         carry[q].y = out[6 + q].y + out[9 + q].x;
+      }
       }
     }
     cmA = nmA;
@@ -800,6 +892,7 @@ void fill_mat(MatConst<T>& c, const ApplyArgs& a) {
   c.c2ml = T(2.0 * a.mu + a.lam); c.cl = T(a.lam); c.cm = T(a.mu);
   c.omk = T(1.0 - a.kappa); c.kap = T(a.kappa); c.p = T(a.p); c.p2 = T(2.0 * a.p);
   c.gcl = T(a.gc_over_l); c.gcL = T(a.gc_times_l);
+  c.il = T(1.0 / a.ell); c.l = T(a.ell);
 }
 template <typename T>
 void fill_geom(LevGeom<T>& c, const ApplyArgs& a, double hx, double hy) {
@@ -865,6 +958,8 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
     PFF_LAUNCH(OP_RESID)
     PFF_LAUNCH(OP_MASS)
     PFF_LAUNCH(OP_TCV)
+    PFF_LAUNCH(OP_TCV_GRAD)
+    PFF_LAUNCH(OP_VJP)
 #undef PFF_LAUNCH
     default: return cudaErrorInvalidValue;
   }

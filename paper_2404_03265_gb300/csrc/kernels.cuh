@@ -26,6 +26,8 @@ enum OpKind : int {
   OP_RESID = 6,    // residual R = -A(U)(psi) at the state held in `lin` (Problem 2)
   OP_MASS = 7,     // integral of each basis function (lumped mass, phi component)
   OP_TCV = 8,      // (u . grad phi, psi) per basis function (summed: total crack volume)
+  OP_TCV_GRAD = 9, // dJ/dU of J = TCV: (psi_u . grad phi) and (u . grad psi_phi) per basis function
+  OP_VJP = 10,     // per cell: x . dR/dtheta for theta = E_K, p, G_c (R = -A, x taken through C)
 };
 
 // mode bits
@@ -54,6 +56,7 @@ struct MatConst {
   T c2ml, cl, cm;      // 2 mu + lambda, lambda, mu
   T omk, kap, p, p2;   // 1 - kappa, kappa, p, 2 p
   T gcl, gcL;          // G_c / l, G_c l
+  T il, l;             // 1 / l, l
 };
 
 // Geometry of a Cartesian hx x hy cell of one refinement level.
@@ -75,9 +78,12 @@ struct ApplyArgs {
   void* yu;
   void* yp;
   void* ibuf;             // 3 T per partial slot
+  const void* ecell;      // per-cell modulus E_K (T, cell-slot layout) or nullptr: constants carry E
+  void* cell_out;         // OP_VJP: 3 blocks of n_slots T (E_K, p, G_c) at cell slots
   int64_t n_slots;
   double hx[kMaxLevels], hy[kMaxLevels];
-  double mu, lam;         // Lame constants (E already applied)
+  double mu, lam;         // Lame constants (E applied, or unit E when ecell is set)
+  double ell;             // length scale l
   double kappa, p, gc_over_l, gc_times_l;
   MatConst<float> mf;
   MatConst<double> md;

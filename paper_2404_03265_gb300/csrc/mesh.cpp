@@ -501,6 +501,57 @@ std::string finalize_mesh(Mesh& m, int k) {
     m.levels[l].copy_leaf.push_back(m.nslot[n]);
     m.levels[l].copy_level.push_back(it->second);
   }
+  // cell slots: the slot of a cell's lower-left node position in a brick of its level
+  auto cell_slot_in = [&](const std::vector<BrickIndex>& idx, int l, int64_t i, int64_t j) -> int32_t {
+    const int64_t gx = i * k, gy = j * k;
+    const int32_t b = idx[l].find(gx / NB, gy / NB);
+    if (b < 0) return -1;
+    return int32_t(int64_t(b) * NB2 + (gx % NB) + NB * (gy % NB));
+  };
+  std::vector<std::unordered_map<uint64_t, int32_t>> leaf_of(Lf + 1);
+  m.cell_slot.resize(m.leaves.size());
+  for (size_t c = 0; c < m.leaves.size(); ++c) {
+    const auto& lc = m.leaves[c];
+    const int32_t sl = cell_slot_in(bidx, int(lc[0]), lc[1], lc[2]);
+    if (sl < 0) return "leaf cell without a brick of its level";
+    m.cell_slot[c] = sl;
+    leaf_of[lc[0]][cell_key(lc[1], lc[2])] = int32_t(c);
+  }
+  for (int l = 0; l <= Lf; ++l) {
+    LevelMesh& lm = m.levels[l];
+    std::vector<std::array<int32_t, 6>> rows;  // dst, src, 4 children
+    rows.reserve(t.lev[l].size());
+    for (uint64_t c : t.lev[l]) {
+      const int64_t i = int64_t(c >> 32), j = int64_t(c & 0xffffffffu);
+      std::array<int32_t, 6> r{cell_slot_in(lbidx, l, i, j), 0, -1, -1, -1, -1};
+      if (r[0] < 0) return "level cell without a brick";
+      auto it = leaf_of[l].find(cell_key(i, j));
+      if (it != leaf_of[l].end()) {
+        r[1] = it->second;
+      } else {
+        r[1] = -1;
+        int q = 2;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            r[q] = cell_slot_in(lbidx, l + 1, 2 * i + a, 2 * j + b);
+            if (r[q] < 0) return "child cell without a brick";
+            ++q;
+          }
+      }
+      rows.push_back(r);
+    }
+    std::sort(rows.begin(), rows.end());
+    lm.cell_dst.clear(); lm.cell_src.clear(); lm.cell_child.clear();
+    for (const auto& r : rows) {
+      lm.cell_dst.push_back(r[0]);
+      if (r[1] >= 0) {
+        lm.cell_src.push_back(r[1]);
+      } else {
+        lm.cell_src.push_back(-1 - int32_t(lm.cell_child.size() / 4));
+        for (int q = 2; q < 6; ++q) lm.cell_child.push_back(r[q]);
+      }
+    }
+  }
   m.finalized = true;
   return "";
 }

@@ -98,6 +98,11 @@ struct LevelMesh {
   // leaf nodes whose coarsest level is this one: (leaf slot, level slot)
   std::vector<int32_t> copy_leaf, copy_level;
   int64_t n_cells = 0;
+  // per-cell values (modulus E_K, mean of the four children on refined cells):
+  // for every cell of this level, its cell slot in this layout, its source (leaf
+  // index >= 0, else -1 - q with children cell_child[4q..4q+3], cell slots of
+  // level l+1 in the order (2i,2j), (2i,2j+1), (2i+1,2j), (2i+1,2j+1)); sorted by slot
+  std::vector<int32_t> cell_dst, cell_src, cell_child;
 };
 
 struct Mesh {
@@ -124,7 +129,11 @@ struct Mesh {
   std::vector<int32_t> fix_slot;    // storage slot of every non-pure node (incl. hanging)
   std::vector<int32_t> fix_ptr, fix_part;
   std::vector<double> fix_w;
-  // per leaf cell: storage slot of its cell value (per-cell modulus), by canonical order
+  // per leaf cell (canonical order): its cell slot, the leaf-layout slot of the
+  // cell's lower-left node position in the brick of the cell's own level; each
+  // leaf cell has its own (the lower-left node of a level-l leaf cell lies in a
+  // level-l brick).  Per-cell data (modulus E_K, its gradient) use these slots.
+  std::vector<int32_t> cell_slot;
   std::vector<LevelMesh> levels;
 
   int64_t n_nodes() const { return int64_t(nkey.size()); }

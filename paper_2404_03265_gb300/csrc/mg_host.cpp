@@ -110,7 +110,10 @@ cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStr
   a.ibuf = nullptr;
   a.n_slots = n;
   for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) { a.hx[l] = M.tree.hx(l); a.hy[l] = M.tree.hy(l); }
-  fill_material(pb.prm, a);
+  fill_material(pb.prm, a, pb.has_ecell);
+  if (pb.has_ecell) {
+    if (sizeof(T) == 8) a.ecell = pb.lev_ecell64 + L.lv.off; else a.ecell = pb.lev_ecell32 + L.lv.off;
+  }
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
   a.mode = MODE_MASK_INPUT;

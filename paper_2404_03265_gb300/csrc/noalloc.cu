@@ -101,7 +101,7 @@ extern "C" pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int3
       a.hx[l] = M.tree.hx(l);
       a.hy[l] = M.tree.hy(l);
     }
-    fill_material(pb->prm, a);
+    leaf_modulus(*pb, precision, a);
     fill_cell_constants(a, M.Lf + 1);
     a.fe_degree = M.k;
     const int kop = op == PFF_OP_TRANSPOSE ? OP_FULL_T : OP_FULL;

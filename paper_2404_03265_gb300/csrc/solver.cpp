@@ -39,14 +39,17 @@ cudaError_t leaf_op(pff_problem& pb, int kop, int mode, const double* lin, const
   a.ibuf = pb.ibuf64;
   a.n_slots = M.lay.n_slots;
   for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) { a.hx[l] = M.tree.hx(l); a.hy[l] = M.tree.hy(l); }
-  fill_material(pb.prm, a);
+  leaf_modulus(pb, PFF_F64, a);
+  if (kop == OP_VJP) fill_material(pb.prm, a, true);
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
   a.mode = mode;
+  a.cell_out = pb.cell_out;
   FixupArgs f;
   f.n = D.nfix; f.n_slots = M.lay.n_slots; f.slot = D.fix_slot; f.ptr = D.fix_ptr; f.part = D.fix_part;
   f.w = D.fix_w; f.cmask = cmask; f.xu = xu; f.xp = xp; f.yu = yu; f.yp = yp; f.ibuf = a.ibuf; f.mode = mode;
   RET(launch_apply<double>(a, kop, s));
+  if (kop == OP_VJP) return cudaSuccess;  // per-cell outputs only
   return launch_fixup<double>(f, s);
 }
 

@@ -43,6 +43,8 @@ std::string upload_mesh(pff_mesh& pm) {
   D.fix_part = D.mem.upload(M.fix_part);
   D.fix_w = D.mem.upload(M.fix_w);
   D.slot_flags = D.mem.upload(M.slot_flags);
+  D.n_leaf_cells = int32_t(M.cell_slot.size());
+  D.cell_slot = D.mem.upload(M.cell_slot);
   D.levels.resize(M.levels.size());
   int64_t off = 0;
   for (size_t l = 0; l < M.levels.size(); ++l) {
@@ -73,6 +75,10 @@ std::string upload_mesh(pff_mesh& pm) {
     }
     L.gx = D.mem.upload(gx);
     L.gy = D.mem.upload(gy);
+    L.n_cells = int32_t(lm.cell_dst.size());
+    L.cell_dst = D.mem.upload(lm.cell_dst);
+    L.cell_src = D.mem.upload(lm.cell_src);
+    L.cell_child = D.mem.upload(lm.cell_child);
   }
   D.lev_total = off;
   if (!D.mem.err.empty()) {
@@ -109,13 +115,21 @@ std::string alloc_problem(pff_problem& pb) {
   return "";
 }
 
-void fill_material(const pff_params& prm, ApplyArgs& a) {
-  a.mu = prm.E / (2.0 * (1.0 + prm.nu));
-  a.lam = prm.E * prm.nu / ((1.0 + prm.nu) * (1.0 - 2.0 * prm.nu));
+void fill_material(const pff_params& prm, ApplyArgs& a, bool unit_E) {
+  const double E = unit_E ? 1.0 : prm.E;
+  a.mu = E / (2.0 * (1.0 + prm.nu));
+  a.lam = E * prm.nu / ((1.0 + prm.nu) * (1.0 - 2.0 * prm.nu));
+  a.ell = prm.eps;
   a.kappa = prm.kappa;
   a.p = prm.p;
   a.gc_over_l = prm.Gc / prm.eps;
   a.gc_times_l = prm.Gc * prm.eps;
+}
+
+void leaf_modulus(const pff_problem& pb, int precision, ApplyArgs& a) {
+  fill_material(pb.prm, a, pb.has_ecell);
+  a.ecell = !pb.has_ecell ? nullptr
+            : precision == PFF_F64 ? static_cast<const void*>(pb.ecell64) : static_cast<const void*>(pb.ecell32);
 }
 
 cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, const void* xp, void* yu,
@@ -135,7 +149,7 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
     a.hx[l] = M.tree.hx(l);
     a.hy[l] = M.tree.hy(l);
   }
-  fill_material(pb.prm, a);
+  leaf_modulus(pb, precision, a);
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
   int kop = OP_FULL;

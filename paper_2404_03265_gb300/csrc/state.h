@@ -57,12 +57,18 @@ struct DevMesh {
   int32_t* fix_part = nullptr;
   double* fix_w = nullptr;
   uint8_t* slot_flags = nullptr;
+  int32_t n_leaf_cells = 0;
+  int32_t* cell_slot = nullptr;   // per leaf cell (canonical order): its cell slot
   // multigrid level meshes
   struct Level {
     DevLayout lay;
     DevLevel lv;
     int32_t* gx = nullptr;   // level-grid coordinates (units h_l / k), -1 for holes
     int32_t* gy = nullptr;
+    int32_t n_cells = 0;     // cells of this level and their per-cell value sources
+    int32_t* cell_dst = nullptr;
+    int32_t* cell_src = nullptr;
+    int32_t* cell_child = nullptr;
   };
   std::vector<Level> levels;
   int64_t lev_total = 0;     // sum of level slot counts
@@ -128,6 +134,13 @@ struct pff_problem {
   double* ibuf64 = nullptr;  // 3 per partial slot
   float* ibuf32 = nullptr;
   bool has_state = false;
+  // per-cell modulus E_K (cell-slot layout; levels concatenated like level vectors)
+  bool has_ecell = false;
+  double* ecell64 = nullptr;      // n_slots
+  float* ecell32 = nullptr;
+  double* lev_ecell64 = nullptr;  // lev_total
+  float* lev_ecell32 = nullptr;
+  double* cell_out = nullptr;     // 3 * n_slots: per-cell VJP values
 };
 
 namespace pff {
@@ -175,7 +188,10 @@ std::string upload_mesh(pff_mesh& m);
 std::string alloc_problem(pff_problem& pb);
 // message returned by pff_last_error on this thread
 void set_last_error(const std::string& msg);
-void fill_material(const pff_params& prm, ApplyArgs& a);
+// material constants; unit_E: elastic constants of E = 1 (a per-cell modulus is applied in the kernel)
+void fill_material(const pff_params& prm, ApplyArgs& a, bool unit_E = false);
+// modulus source of a leaf operator: unit-E constants + the cell array when a modulus field is set
+void leaf_modulus(const pff_problem& pb, int precision, ApplyArgs& a);
 cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, const void* xp, void* yu,
                        void* yp, cudaStream_t s);
 cudaError_t launch_leaf_cmask(int64_t n, const uint8_t* slot_flags, const uint8_t* active, uint8_t* cmask,
@@ -192,6 +208,19 @@ cudaError_t lumped_mass(pff_problem& pb, double* B, cudaStream_t s);
 cudaError_t total_crack_volume(pff_problem& pb, const double* u, const double* phi, double* out_host, cudaStream_t s);
 cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi, const double* phi_old,
                              uint8_t* active, const NewtonOpts& o, NewtonInfo& info, cudaStream_t s);
+// per-cell modulus and the adjoint TCV gradient (adjoint.cpp)
+std::string set_cell_modulus(pff_problem& pb, const double* E_cells, cudaStream_t s);
+cudaError_t tcv_gradient(pff_problem& pb, const double* u, const double* phi, double* g, cudaStream_t s);
+cudaError_t param_vjp(pff_problem& pb, const double* w, double* gE_cells, double* g_host, cudaStream_t s);
+cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const double* phi, const double* phi_old,
+                        const uint8_t* active, double rtol, int restart, int maxiter, double* gE, double* g_host,
+                        GmresResult& gr, std::string& err, cudaStream_t s);
+// cell kernels (cells.cu)
+cudaError_t cells_scatter(int32_t n, const double* v, const int32_t* slot, double* out64, float* out32,
+                          cudaStream_t s);
+cudaError_t cells_level(int32_t n, const int32_t* dst, const int32_t* src, const int32_t* child,
+                        const double* leaf_v, const double* finer, double* out64, float* out32, cudaStream_t s);
+cudaError_t cells_gather(int32_t n, const double* in, const int32_t* slot, double* out, cudaStream_t s);
 // multigrid (mg_host.cpp)
 std::string mg_alloc(pff_mg& mg);
 std::string mg_setup(pff_mg& mg, cudaStream_t s);

@@ -113,9 +113,14 @@ def max_over_ranks(ws, v):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device="cpu" if dist.get_backend() == "gloo" else "cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(ws, units_per_rank, t_max):
+    """Units processed by all ranks per second (replicas: every rank does the same work)."""
+    return ws * units_per_rank / t_max
 
 
 def build_sets(mesh, n_sets, dtype, seed=0):
@@ -372,7 +377,7 @@ def main():
     t = time_applies(sets, args.steps, args.warmup, ws)
     clocks = sampler.stop() if sampler else None
     t = max_over_ranks(ws, t)
-    value = ws * dofs * args.steps / t / 1e9
+    value = whole_job_rate(ws, dofs * args.steps, t) / 1e9
     ms = 1e3 * t / args.steps
     del sets
 
@@ -384,7 +389,7 @@ def main():
     del sets64
 
     te, bi, bo = time_e2e(mesh, torch.float32, max(10, args.steps // 4), 3)
-    e2e = ws * dofs * max(10, args.steps // 4) / max_over_ranks(ws, te) / 1e9
+    e2e = whole_job_rate(ws, dofs * max(10, args.steps // 4), max_over_ranks(ws, te)) / 1e9
 
     if rank != 0:
         return

@@ -1,0 +1,63 @@
+"""Host logic of the multi-GPU bench path (replicas only), on CPU with two gloo
+ranks: rendezvous, barrier, max-over-ranks timing, the whole-job rate, and the
+reference arm printing on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE="2", RANK=str(rank),
+                      LOCAL_RANK=str(rank), PFF_BENCH_GLOO="1")
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    ws, r, local = bench.dist_init()
+    bench.barrier(ws)
+    t = bench.max_over_ranks(ws, 1.0 + r)        # rank 1 is the slower one
+    q.put((r, ws, t, bench.whole_job_rate(ws, 100.0, t)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time_and_rate():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, ws, t, rate in out:
+        assert ws == 2 and t == 2.0            # max over ranks
+        assert rate == 2 * 100.0 / 2.0         # all ranks' units / the slowest rank's time
+
+
+def test_reference_arm_prints_on_rank0_only():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+    env["RANK"] = "0"
+    env["LOCAL_RANK"] = "0"
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] == line["cpu_baseline"]["value"]

@@ -24,6 +24,7 @@
 // (x_full = C x on input, C^T y on output).  No atomics.
 #include "kernels.cuh"
 
+#include <cmath>
 #include <mutex>
 #include <unordered_map>
 
@@ -921,9 +922,33 @@ int resident_blocks(const void* fn, int threads, size_t smem) {
   return n;
 }
 
+namespace {
+#include "apply_q2.cuh"
+}  // namespace
+
+template <typename T>
+void fill_q2(Q2Tab<T>& t) {
+  // 3-point Gauss rule on [0, 1]
+  const double g[3] = {0.5 - 0.1 * std::sqrt(15.0), 0.5, 0.5 + 0.1 * std::sqrt(15.0)};
+  const double w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  for (int q = 0; q < 3; ++q) {
+    const double x = g[q];
+    // Lagrange basis on the nodes 0, 1/2, 1 and its derivative
+    const double L[3] = {2.0 * (x - 0.5) * (x - 1.0), -4.0 * x * (x - 1.0), 2.0 * x * (x - 0.5)};
+    const double D[3] = {4.0 * x - 3.0, 4.0 - 8.0 * x, 4.0 * x - 1.0};
+    for (int a = 0; a < 3; ++a) {
+      t.L[a][q] = T(L[a]);
+      t.D[a][q] = T(D[a]);
+    }
+    t.w[q] = T(w[q]);
+  }
+}
+
 void fill_cell_constants(ApplyArgs& a, int nlevels) {
   fill_mat(a.mf, a);
   fill_mat(a.md, a);
+  fill_q2(a.q2f);
+  fill_q2(a.q2d);
   for (int l = 0; l < nlevels && l < kMaxLevels; ++l) {
     fill_geom(a.gf[l], a, a.hx[l], a.hy[l]);
     fill_geom(a.gd[l], a, a.hx[l], a.hy[l]);
@@ -933,6 +958,7 @@ void fill_cell_constants(ApplyArgs& a, int nlevels) {
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
+  if (a.fe_degree == 2) return launch_apply_q2<T>(a, op, s);
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
   const int units = (a.lay.nbricks * NSEG + 1) / 2;  // two strips per warp
   const unsigned blk = 32 * WARPS;

@@ -68,6 +68,15 @@ struct LevGeom {
   T wpx, wpy;          // 2 G_c l JxW / hx^2, 2 G_c l JxW / hy^2
 };
 
+// Q2 tables: 1D Lagrange basis on the nodes 0, 1/2, 1 of [0, 1] at the 3-point
+// Gauss points, its derivative, and the Gauss weights (precision of the kernel).
+template <typename T>
+struct Q2Tab {
+  T L[3][3];   // L[a][q] = l_a(g_q)
+  T D[3][3];   // D[a][q] = l_a'(g_q)
+  T w[3];
+};
+
 struct ApplyArgs {
   DevLayout lay;
   const DevHanging* hang;
@@ -89,6 +98,8 @@ struct ApplyArgs {
   MatConst<double> md;
   LevGeom<float> gf[kMaxLevels];
   LevGeom<double> gd[kMaxLevels];
+  Q2Tab<float> q2f;
+  Q2Tab<double> q2d;
   int mode;
   int fe_degree;
 };

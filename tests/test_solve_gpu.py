@@ -94,7 +94,11 @@ def test_gmres_solves_constrained_system(prec):
     xg = unblocks(P, x.cpu().numpy())
     xg = np.concatenate([xg[:, 0], xg[:, 1], xg[:, 2]])
     err = np.linalg.norm(xg - xs) / np.linalg.norm(xs)
-    assert err < 1e-7, err
+    # With the FP32 V-cycle the Arnoldi relation of left-preconditioned GMRES holds
+    # only to the FP32 rounding of the preconditioner, which leaves an error floor
+    # near 1e-7 whatever the tolerance (the Newton loop re-evaluates residuals in
+    # FP64); the FP64 V-cycle has no such floor.
+    assert err < (1e-6 if prec == "f32" else 1e-7), err
 
 
 @pytest.mark.parametrize("name", ["small", "band4_3_3"])

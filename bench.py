@@ -388,6 +388,25 @@ def main():
     g64 = dofs * k64 / t64 / 1e9
     del sets64
 
+    # Q2 u and phi on the same mesh (16,368,207 DoFs): FP32 and FP64 applies
+    mesh2 = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(2)
+    info2 = mesh2.info
+    dofs2 = 3 * info2["n_nodes"]
+    per_set2 = info2["n_slots"] * (16 + 12 + 12)
+    sets2 = build_sets(mesh2, max(2, int(np.ceil(2.2 * L2_BYTES / per_set2))), torch.float32, seed=0)
+    k2 = max(20, args.steps // 10)
+    t2 = time_applies(sets2, k2, 3, 1)
+    del sets2
+    sets2 = build_sets(mesh2, 2, torch.float64, seed=0)
+    k2d = max(5, args.steps // 100)
+    t2d = time_applies(sets2, k2d, 3, 1)
+    del sets2
+    q2 = {"dofs": dofs2, "nodes": info2["n_nodes"],
+          "f32": {"value": dofs2 * k2 / t2 / 1e9, "unit": "GDoF/s", "steps": k2,
+                  "us_per_apply": 1e6 * t2 / k2},
+          "f64": {"value": dofs2 * k2d / t2d / 1e9, "unit": "GDoF/s", "steps": k2d,
+                  "us_per_apply": 1e6 * t2d / k2d}}
+
     te, bi, bo = time_e2e(mesh, torch.float32, max(10, args.steps // 4), 3)
     e2e = whole_job_rate(ws, dofs * max(10, args.steps // 4), max_over_ranks(ws, te)) / 1e9
 
@@ -396,6 +415,8 @@ def main():
     hbm, peak_kind = load_peaks()
     alg_bytes = info["n_nodes"] * 10 * 4  # x (3), y (3), linearisation (4) per node, FP32
     achieved = alg_bytes / (t / args.steps) / 1e9
+    q2["f32"]["hbm_frac"] = info2["n_nodes"] * 40 / (t2 / k2) / 1e9 / hbm
+    q2["f64"]["hbm_frac"] = info2["n_nodes"] * 80 / (t2d / k2d) / 1e9 / hbm
     traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
@@ -412,6 +433,7 @@ def main():
                              "interface fix-up kernel)"},
         "f64_apply": {"value": g64, "unit": "GDoF/s", "steps": k64,
                       "hbm_frac": info["n_nodes"] * 80 / (t64 / k64) / 1e9 / hbm},
+        "q2_apply": q2,
         "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,

@@ -23,11 +23,17 @@ A (Problem 2, sigma^+ read as sigma):
     dA_u/dE_K = (g(phi~) sigma_1(u), e(psi))_K
     dA_phi/dE_K = (1 - kappa)(phi sigma_1(u) : e(u), psi)_K
 
+Several load steps (``tcv_adjoint_steps``): phi^(n-1) is phi_tilde and the
+obstacle of step n, so the adjoint of step n passes a phi-sensitivity to step
+n - 1 through (dA/dphi_tilde)^T (``phit_vjp``) and through the active rows.
+
 Pinned by tests/test_oracle_adjoint.py: the TCV gradient and the parameter
 derivatives against central differences of ``operators.tcv`` and
 ``operators.residual_form`` (both exact: J is bilinear in (u, phi), A is linear
-in p, G_c and E_K), and the adjoint gradient against central differences of
-converged load steps (relative step 1e-6).
+in p, G_c and E_K), phit_vjp against central differences of the residual form
+in phi_tilde (quadratic: exact), and the one- and several-step adjoint
+gradients against central differences of converged load steps (relative step
+1e-6).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -117,3 +123,75 @@ def param_vjp(mesh, mat, st, w):
     d_p, d_gc, d_e = residual_param_derivatives(mesh, mat, st)
     wf = C @ w
     return -float(wf @ d_p), -float(wf @ d_gc), -np.asarray(d_e.T @ wf).ravel()
+
+
+def phit_vjp(mesh, mat, st, w):
+    """C^T (dA/dphi_tilde)^T (C w): phi-vector (nn).  A depends on phi_tilde through
+    g(phi~) = (1-kappa) phi~^2 + kappa and phi~^2 p in the u-equation (Problem 2):
+        (dA_u/dphi~ [psi], w_u) = (psi, 2 phi~ [(1-kappa) sigma(u) : e(w_u) + p div w_u])."""
+    nn = mesh.nn
+    C = ops.C3(mesh)
+    wf = C @ w
+    wu = np.stack([wf[:nn], wf[nn:2 * nn]], 1)
+    out = np.zeros(nn)
+    for level, idx in ops.level_groups(mesh):
+        d = ops._CellData(mesh, mat, st, level, idx)
+        T = d.T
+        gw = np.einsum('qad,cai->cqid', T.dN, wu[d.cn])        # grad w_u: [i][d]
+        ew = 0.5 * (gw + np.swapaxes(gw, -1, -2))
+        sw = np.einsum('cqmn,cqmn->cq', d.sig_u, ew)
+        divw = gw[:, :, 0, 0] + gw[:, :, 1, 1]
+        val = 2.0 * d.phitq * ((1.0 - mat.kappa) * sw + mat.p * divw)
+        np.add.at(out, d.cn, np.einsum('q,cq,qa->ca', T.JxW, val, T.N))
+    return mesh.C.T @ out
+
+
+def tcv_adjoint_steps(mesh, mats, us, phis, actives, E_cells=None):
+    """Gradient of J = TCV(U^N) after N load steps (Algorithm 2, phi_tilde and the
+    obstacle of step n are phi^(n-1)) with respect to each step's pressure p_n,
+    G_c and E_K.
+
+    mats[n-1]: Material of step n; us[n], phis[n]: converged state of step n
+    (n = 0: the initial state, u = 0 and phi = phi^0, independent of the
+    parameters); actives[n-1]: final active set of step n.
+
+    Step n: free rows [C^T A(U^n; phi~ = phi^(n-1))]_F = 0, active rows
+    phi^n - phi^(n-1) = 0.  Its Jacobian in U^n is [[K_FF, K_FA], [0, I]] with
+    K = C^T G C (the free rows still see the active values).  Backwards:
+        K_FF^T mu_F = gbar_F,  mu_A = gbar_A - K_FA^T mu_F,
+        gbar^N = C^T dJ/dU^N (Dirichlet rows 0),
+        gbar^(n-1) = (0, 0, -C^T (dA/dphi~)^T C M_f mu^n + mu^n on the active rows of step n),
+        dJ/dtheta = sum_n (C M_f mu^n) . dR_n/dtheta,  R = -A.
+    """
+    nn = mesh.nn
+    N = len(mats)
+    C = ops.C3(mesh)
+    st = ops.State(mesh, us[N], phis[N], phis[N - 1], E_cells)
+    gbar = C.T @ tcv_gradient(mesh, st)
+    gbar[:nn][mesh.dirichlet] = 0.0
+    gbar[nn:2 * nn][mesh.dirichlet] = 0.0
+    g_p = np.zeros(N)
+    g_gc = 0.0
+    g_e = np.zeros(len(mesh.cells))
+    for n in range(N, 0, -1):
+        mat = mats[n - 1]
+        act = np.asarray(actives[n - 1], bool)
+        st = ops.State(mesh, us[n], phis[n], phis[n - 1], E_cells)
+        K = (C.T @ ops.assemble_jacobian(mesh, mat, st) @ C).tocsc()
+        free = ops.free_dofs(mesh, act)
+        fixed = ops.fixed_dofs(mesh, act)
+        f = np.nonzero(free)[0]
+        mu = np.zeros(3 * nn)
+        mu[f] = spla.spsolve(K[f][:, f].T.tocsc(), gbar[f])
+        fx = np.nonzero(fixed)[0]
+        mu[fx] = gbar[fx] - K[f][:, fx].T @ mu[f]
+        wf = mu * free
+        a, b, c = param_vjp(mesh, mat, st, wf)
+        g_p[n - 1] = a
+        g_gc += b
+        g_e += c
+        if n > 1:
+            gbar = np.zeros(3 * nn)
+            gbar[2 * nn:] = -phit_vjp(mesh, mat, st, wf)
+            gbar[2 * nn:][act] += mu[2 * nn:][act]
+    return dict(p=g_p, Gc=g_gc, E=g_e)

@@ -142,3 +142,83 @@ def test_adjoint_gradient_central_difference(name, p):
         Em[c] -= hh
         fd = (J(base, Ep) - J(base, Em)) / (2 * hh)
         assert abs(fd - g["E"][c]) <= 1e-5 * abs(fd), (c, fd, g["E"][c])
+
+
+@pytest.mark.parametrize("name,k", [("tiny", 1), ("small", 1), ("tiny", 2)])
+def test_phit_vjp_central_difference(name, k):
+    """A is quadratic in phi_tilde, so a central difference of w . A in direction v is exact."""
+    om = mesh(name, k)
+    u, phi, phit = random_state(om, seed=3)
+    E = cell_E(om)
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.3, eps=2.0 * om.h_min_diag(), kappa=1e-3, p=0.2)
+    rng = np.random.Generator(np.random.PCG64(8))
+    w = rng.normal(size=3 * om.nn)
+    v = rng.normal(size=om.nn)
+    got = v @ adj.phit_vjp(om, mat, ops.State(om, u, phi, phit, E), w)
+    wf = ops.C3(om) @ w
+    eps = 1e-3
+    Ap = ops.residual_form(om, mat, ops.State(om, u, phi, phit + eps * v, E))
+    Am = ops.residual_form(om, mat, ops.State(om, u, phi, phit - eps * v, E))
+    fd = wf @ (Ap - Am) / (2 * eps)
+    assert abs(got - fd) <= 1e-10 * max(abs(fd), 1e-12), (got, fd)
+
+
+def sneddon_steps(om, base, E, ps, tol=1e-13):
+    """Load steps at pressures ps from the initial crack; returns mats, us, phis, actives."""
+    h = om.h_min_diag()
+    u0, po = solvers.sneddon_initial(om, h)
+    mats, us, phis, acts = [], [u0], [po], []
+    u, phi, act = u0, po.copy(), None
+    for p in ps:
+        kw = dict(base, p=p)
+        mat = ops.Material(**kw)
+        u, phi_new, act, info = solvers.load_step(om, mat, 1e4, u, phi.copy(), phi, active_prev=act, E_cells=E,
+                                                  tol=tol, atol=1e-15, gmres_rtol=1e-12)
+        assert info.converged
+        phi = phi_new
+        mats.append(mat)
+        us.append(u)
+        phis.append(phi)
+        acts.append(act)
+    return mats, us, phis, acts
+
+
+def test_multi_step_adjoint_central_difference():
+    """Three load steps: dJ/dp_n, dJ/dG_c and dJ/dE_K of the final TCV from one
+    backward sweep against central differences of three-step solves (relative
+    step 1e-6, bound 1e-5)."""
+    om = mesh("tiny")
+    E = cell_E(om)
+    base = dict(E=1.0, nu=0.2, Gc=1.0, eps=2.0 * om.h_min_diag(), kappa=1e-10)
+    ps = [0.1, 0.15, 0.2]
+    mats, us, phis, acts = sneddon_steps(om, base, E, ps)
+    g = adj.tcv_adjoint_steps(om, mats, us, phis, acts, E)
+    # the single-step formula agrees for one step
+    g1 = adj.tcv_adjoint_steps(om, mats[:1], us[:2], phis[:2], acts[:1], E)
+    r1 = adj.tcv_adjoint(om, mats[0], ops.State(om, us[1], phis[1], phis[0], E), acts[0])
+    assert abs(g1["p"][0] - r1["p"]) <= 1e-12 * abs(r1["p"]) and abs(g1["Gc"] - r1["Gc"]) <= 1e-10 * abs(r1["Gc"])
+
+    def J(bkw, pss, Ec):
+        _, uu, pp, aa = sneddon_steps(om, bkw, Ec, pss)
+        for a0, a1 in zip(aa, acts):
+            assert np.array_equal(a0, a1), "active set changed under the perturbation"
+        return ops.tcv(om, ops.State(om, uu[-1], pp[-1], pp[-1]))
+
+    rel = 1e-6
+    for n in range(len(ps)):
+        hh = rel * ps[n]
+        pp_, pm_ = list(ps), list(ps)
+        pp_[n] += hh
+        pm_[n] -= hh
+        fd = (J(base, pp_, E) - J(base, pm_, E)) / (2 * hh)
+        assert abs(fd - g["p"][n]) <= 1e-5 * abs(fd), (n, fd, g["p"][n])
+    hh = rel * base["Gc"]
+    fd = (J(dict(base, Gc=base["Gc"] + hh), ps, E) - J(dict(base, Gc=base["Gc"] - hh), ps, E)) / (2 * hh)
+    assert abs(fd - g["Gc"]) <= 1e-5 * abs(fd), (fd, g["Gc"])
+    for c in np.argsort(-np.abs(g["E"]))[:2]:
+        hh = rel * E[c]
+        Ep, Em = E.copy(), E.copy()
+        Ep[c] += hh
+        Em[c] -= hh
+        fd = (J(base, ps, Ep) - J(base, ps, Em)) / (2 * hh)
+        assert abs(fd - g["E"][c]) <= 1e-5 * abs(fd), (c, fd, g["E"][c])

@@ -282,6 +282,25 @@ pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const d
                            const uint8_t* active, double rtol, int32_t restart, int32_t maxiter, double* gE_cells,
                            double* g_host, pff_solve_info* info, void* stream);
 
+/* Checkpointed adjoint of J = TCV(U^N) over n_steps load steps of Algorithm 2,
+ * step k (1..N) solved from phi_old = phi_tilde = phi[k-1] at pressure
+ * p_host[k-1] with final active set active[k-1]:
+ *   u[k], phi[k] (k = 0..N): host arrays of device pointers to the converged
+ *   states (u: 2*n_slots, phi: n_slots doubles; k = 0 is the initial state);
+ *   active[k] (k = 0..N-1): host array of device pointers (n_slots bytes).
+ * Backwards from G~_N^T mu = C^T dJ/dU^N, each step passes its phi-sensitivity
+ * to the previous one through phi_tilde (the degradation and pressure terms of
+ * the u-equation) and through its active rows (obstacle phi[k-1]); the free rows
+ * of a step still see the active values, which the active-row adjoint accounts
+ * for.  Outputs: gp_host[k-1] = dJ/dp_k (host, n_steps), *gGc_host = dJ/dG_c,
+ * gE_cells (device, n_leaf_cells, may be NULL) = dJ/dE_K.  Leaves the problem's
+ * state, active set and multigrid at step 1; restores the pressure.
+ * Synchronises.  Errors as pff_tcv_adjoint.                                  */
+pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t n_steps, const double* const* u,
+                                 const double* const* phi, const uint8_t* const* active, const double* p_host,
+                                 double rtol, int32_t restart, int32_t maxiter, double* gE_cells, double* gp_host,
+                                 double* gGc_host, pff_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

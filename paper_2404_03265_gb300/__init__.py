@@ -219,3 +219,29 @@ def tcv_adjoint(problem, mg, u, phi, phi_old, active, gE=None, rtol=1e-10, resta
         _lib.check(st)
     return dict(p=float(out[0]), Gc=float(out[1]), iterations=info.gmres_total, converged=bool(info.converged),
                 status=st)
+
+
+def tcv_adjoint_steps(problem, mg, us, phis, actives, ps, gE=None, rtol=1e-10, restart=50, maxiter=2000,
+                      stream=None, check=True):
+    """dJ/dp_k (k = 1..N), dJ/dG_c (and dJ/dE_K into gE) of J = TCV after N load steps.
+
+    us, phis: N + 1 converged states (index 0 the initial state) as device tensors
+    (u (2, n_slots), phi (n_slots,) float64); actives: N uint8 device tensors;
+    ps: the N pressures."""
+    N = len(ps)
+    assert len(us) == N + 1 and len(phis) == N + 1 and len(actives) == N
+    VP = _lib.ctypes.c_void_p
+    ua = (VP * (N + 1))(*[_lib.ptr(t) for t in us])
+    pa = (VP * (N + 1))(*[_lib.ptr(t) for t in phis])
+    aa = (VP * N)(*[_lib.ptr(t) for t in actives])
+    p_host = np.ascontiguousarray(ps, dtype=np.float64)
+    gp = np.zeros(N)
+    ggc = np.zeros(1)
+    info = _lib.SolveInfo()
+    st = _lib.lib().pff_tcv_adjoint_steps(problem._h, mg._h, N, ua, pa, aa, _lib.ptr(p_host), rtol, restart, maxiter,
+                                          None if gE is None else _lib.ptr(gE), _lib.ptr(gp), _lib.ptr(ggc),
+                                          _lib.ctypes.byref(info), _lib.stream_ptr(stream))
+    if check:
+        _lib.check(st)
+    return dict(p=gp, Gc=float(ggc[0]), gmres_total=info.gmres_total, gmres_max=info.gmres_max,
+                converged=bool(info.converged), status=st)

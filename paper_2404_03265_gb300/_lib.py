@@ -100,6 +100,9 @@ _SIGS = [
     ("pff_param_vjp", ctypes.c_int32, [_P, _P, _P, _P, _P]),
     ("pff_tcv_adjoint", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    ("pff_tcv_adjoint_steps", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
+                                               ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                               ctypes.POINTER(SolveInfo), _P]),
 ]
 
 

@@ -7,6 +7,7 @@
 // With G~ the constrained Jacobian of Sec. 3.1:
 //     G~^T lambda = M_f C^T dJ/dU,        dJ/dtheta = (C M_f lambda) . dR/dtheta,  R = -A.
 // The transposed solve reuses the block V-cycle (its blocks are symmetric).
+#include <algorithm>
 #include <cstring>
 
 #include "solve.cuh"
@@ -52,14 +53,15 @@ std::string set_cell_modulus(pff_problem& pb, const double* E, cudaStream_t s) {
   return "";
 }
 
-cudaError_t tcv_gradient(pff_problem& pb, const double* u, const double* phi, double* g, cudaStream_t s) {
+cudaError_t tcv_gradient(pff_problem& pb, const double* u, const double* phi, double* g, cudaStream_t s,
+                         const uint8_t* rows) {
   const Mesh& M = pb.mesh->m;
   const DevMesh& D = pb.mesh->dev;
   SolverWS& W = pb.ws;
   const int64_t n = M.lay.n_slots;
   RET(make_state(n, u, phi, phi, D.slot_flags, D.hang, D.nhang, M.k, W.st, s));
-  // mode 0: fixed rows (Dirichlet u, active phi) 0, hanging rows 0, C^T applied
-  return leaf_op(pb, OP_TCV_GRAD, 0, W.st, pb.cmask, W.tmp, W.tmp + 2 * n, g, g + 2 * n, s);
+  // mode 0: rows fixed in `rows` (default: Dirichlet u and active phi) 0, hanging rows 0, C^T applied
+  return leaf_op(pb, OP_TCV_GRAD, 0, W.st, rows ? rows : pb.cmask, W.tmp, W.tmp + 2 * n, g, g + 2 * n, s);
 }
 
 cudaError_t param_vjp(pff_problem& pb, const double* w, double* gE, double* g_host, cudaStream_t s) {
@@ -102,6 +104,68 @@ cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const doub
   RET(gmres_solve(pb, mg, 1, W.rhs, W.dU, rtol, restart, maxiter, gr, s));
   if (gr.breakdown || !gr.converged) return cudaSuccess;  // caller reports
   return param_vjp(pb, W.dU, gE, g_host, s);
+}
+
+}  // namespace pff
+
+namespace pff {
+
+// Checkpointed adjoint over n_steps load steps (see the header of this file):
+// step k (1..N) has state (u[k], phi[k]), phi_tilde = obstacle = phi[k-1],
+// active set active[k-1] and pressure p[k-1].  Backwards from
+// gbar^N = C^T dJ/dU^N (Dirichlet rows 0):
+//   G~_k^T mu = gbar^k (GMRES; the fixed rows of mu equal gbar there),
+//   dJ/dtheta += (C M_f mu) . dR_k/dtheta,
+//   gbar^(k-1) = (0, 0, -(dA/dphi~)^T C M_f mu + [mu - K^T C M_f mu] on the active rows),
+// the bracket being the active-row adjoint of the full step Jacobian, whose free
+// rows still see the active values (K = C^T G C).
+cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* const* u, const double* const* phi,
+                              const uint8_t* const* active, const double* p, double rtol, int restart, int maxiter,
+                              double* gE, double* gp_host, double* ggc_host, AdjointStats& st, std::string& err,
+                              cudaStream_t s) {
+  const Mesh& M = pb.mesh->m;
+  const DevMesh& D = pb.mesh->dev;
+  SolverWS& W = pb.ws;
+  const int64_t n = M.lay.n_slots;
+  if (gE && !pb.adj_cell) {
+    pb.adj_cell = pb.bufs.alloc<double>(D.n_leaf_cells);
+    if (!pb.adj_cell) return cudaErrorMemoryAllocation;
+  }
+  const double p_saved = pb.prm.p;
+  struct Restore {
+    pff_problem& pb; double p;
+    ~Restore() { pb.prm.p = p; }
+  } restore{pb, p_saved};
+  RET(tcv_gradient(pb, u[N], phi[N], W.rhs, s, pb.cmask_dir));
+  if (gE) RET(cudaMemsetAsync(gE, 0, D.n_leaf_cells * sizeof(double), s));
+  *ggc_host = 0.0;
+  for (int k = N; k >= 1; --k) {
+    RET(launch_set_lin(n, u[k], phi[k], phi[k - 1], D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
+    pb.has_state = true;
+    RET(launch_leaf_cmask(n, D.slot_flags, active[k - 1], pb.cmask, s));
+    pb.prm.p = p[k - 1];
+    err = mg_setup(mg, s);
+    if (!err.empty()) return cudaErrorUnknown;
+    GmresResult gr;
+    RET(gmres_solve(pb, mg, 1, W.rhs, W.dU, rtol, restart, maxiter, gr, s));
+    st.gmres_total += gr.iterations;
+    st.gmres_max = std::max(st.gmres_max, gr.iterations);
+    st.last = gr;
+    if (gr.breakdown || !gr.converged) { st.failed_step = k; return cudaSuccess; }
+    double g2[2];
+    RET(param_vjp(pb, W.dU, gE ? pb.adj_cell : nullptr, g2, s));
+    gp_host[k - 1] = g2[0];
+    *ggc_host += g2[1];
+    if (gE) RET(axpby(D.n_leaf_cells, gE, gE, 1.0, pb.adj_cell, 1.0, s));
+    if (k > 1) {
+      RET(mask_fixed(n, pb.cmask, W.dU, W.tmp, s));
+      // t1 = C^T G^T C (M_f mu) on every row but Dirichlet u; t2 = (dA/dphi~)^T (M_f mu)
+      RET(leaf_op(pb, OP_FULL_T, MODE_MASK_INPUT, pb.lin64, pb.cmask_dir, W.tmp, W.tmp + 2 * n, W.R, W.R + 2 * n, s));
+      RET(leaf_op(pb, OP_PHIT_VJP, MODE_MASK_INPUT, pb.lin64, pb.cmask_dir, W.tmp, W.tmp + 2 * n, W.du0, W.res, s));
+      RET(adj_carry(n, active[k - 1], W.dU, W.R, W.res, W.rhs, s));
+    }
+  }
+  return cudaStreamSynchronize(s);
 }
 
 }  // namespace pff

@@ -516,3 +516,43 @@ extern "C" pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double*
     return PFF_OK;
   })
 }
+
+extern "C" pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t n_steps, const double* const* u,
+                                            const double* const* phi, const uint8_t* const* active,
+                                            const double* p_host, double rtol, int32_t restart, int32_t maxiter,
+                                            double* gE_cells, double* gp_host, double* gGc_host,
+                                            pff_solve_info* info, void* stream) {
+  PFF_TRY({
+    if (!pb || !mg || !u || !phi || !active || !p_host || !gp_host || !gGc_host)
+      return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (n_steps < 1) return fail(PFF_ERR_INVALID_ARG, "n_steps must be >= 1");
+    for (int k = 0; k <= n_steps; ++k)
+      if (!u[k] || !phi[k]) return fail(PFF_ERR_INVALID_ARG, "NULL state pointer");
+    for (int k = 0; k < n_steps; ++k)
+      if (!active[k]) return fail(PFF_ERR_INVALID_ARG, "NULL active-set pointer");
+    if (mg->pb != pb) return fail(PFF_ERR_INVALID_ARG, "multigrid object of another problem");
+    if (restart < 1 || restart > 500 || maxiter < 1 || !(rtol > 0)) return fail(PFF_ERR_INVALID_ARG, "bad options");
+    std::string e = ensure_workspace(*pb, restart);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    AdjointStats st;
+    std::string err;
+    const cudaError_t ce = tcv_adjoint_steps(*pb, *mg, n_steps, u, phi, active, p_host, rtol, restart, maxiter,
+                                             gE_cells, gp_host, gGc_host, st, err, cudaStream_t(stream));
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->gmres_total = st.gmres_total;
+      info->gmres_max = st.gmres_max;
+      info->converged = st.failed_step == 0 ? 1 : 0;
+      info->residual0 = st.last.initial;
+      info->residual = st.last.estimate;
+    }
+    if (!err.empty()) return fail(PFF_ERR_CUDA, "pff_mg_setup: " + err);
+    PFF_CUDA(ce);
+    if (st.failed_step) {
+      if (st.last.breakdown) return fail(PFF_ERR_GMRES_BREAKDOWN, "GMRES breakdown in the adjoint of a load step");
+      return fail(PFF_ERR_NOT_CONVERGED, "adjoint GMRES did not reach the tolerance at load step " +
+                                             std::to_string(st.failed_step));
+    }
+    return PFF_OK;
+  })
+}

@@ -92,14 +92,15 @@ __device__ __forceinline__ P psub(P a, P b) { return pfma(b, pbc(decltype(a.x)(-
 
 // Which node fields an operator reads.
 template <int OP> struct Needs {
-  static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_VJP);
+  static constexpr bool xu = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_VJP || OP == OP_PHIT_VJP);
   static constexpr bool xp = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_VJP);
   static constexpr bool linU = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_PP || OP == OP_PP_DIAG ||
-                                OP == OP_RESID || OP == OP_TCV || OP == OP_TCV_GRAD || OP == OP_VJP);
+                                OP == OP_RESID || OP == OP_TCV || OP == OP_TCV_GRAD || OP == OP_VJP ||
+                                OP == OP_PHIT_VJP);
   static constexpr bool phi = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_RESID || OP == OP_TCV ||
                                OP == OP_TCV_GRAD || OP == OP_VJP);
   static constexpr bool phit = (OP == OP_FULL || OP == OP_FULL_T || OP == OP_UU || OP == OP_UU_DIAG ||
-                                OP == OP_RESID || OP == OP_VJP);
+                                OP == OP_RESID || OP == OP_VJP || OP == OP_PHIT_VJP);
 };
 
 // Node data of a column pair (A, B) of one window row, in registers.
@@ -326,6 +327,22 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
     rux[0] = pmul(njxw, sE);
     ruy[0] = pmul(njxw, sP);
     rp[0] = pmul(njxw, sG);
+  } else if (OP == OP_PHIT_VJP) {
+    // (dA/dphi~)^T x: value test of 2 phi~ [(1-kappa) sigma(u):e(x_u) + p div x_u]
+    P fv[2][2];
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+      for (int q2 = 0; q2 < 2; ++q2) {
+        const P ge12 = padd(uxy[q1], uyx[q2]);
+        const P s11 = pfma(c2ml, e11[q2], pmul(cl, e22[q1]));
+        const P s22 = pfma(cl, e11[q2], pmul(c2ml, e22[q1]));
+        const P s12 = pmul(cm, ge12);
+        const P sw = pfma(s11, ax[q2], pfma(s22, dy[q1], pmul(s12, padd(bxy[q1], cyx[q2]))));
+        const P pt = phitq[q1][q2];
+        fv[q1][q2] = pmul(padd(pt, pt), pfma(omk, sw, pmul(pbc(m.p), padd(ax[q2], dy[q1]))));
+      }
+    ptest_value(fv, pbc(g.jxw), rp);
   } else if (OP == OP_UU_DIAG || OP == OP_PP_DIAG) {
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
@@ -607,7 +624,7 @@ __device__ __forceinline__ void read_row(const Stage<T>& st, int hl, int right_l
 template <typename T, int OP>
 __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_base, int n, int c, uint8_t cm,
                                            T y0, T y1, T y2) {
-  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV);
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   T* yu = reinterpret_cast<T*>(a.yu);
@@ -647,7 +664,7 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 template <typename T, int OP>
 __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MINB64) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
   using P = typename VT<T>::T2;
-  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV);
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const unsigned FULL = 0xffffffffu;
@@ -986,6 +1003,7 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
     PFF_LAUNCH(OP_TCV)
     PFF_LAUNCH(OP_TCV_GRAD)
     PFF_LAUNCH(OP_VJP)
+    PFF_LAUNCH(OP_PHIT_VJP)
 #undef PFF_LAUNCH
     default: return cudaErrorInvalidValue;
   }

@@ -115,6 +115,9 @@ __device__ __forceinline__ void q2_point(const Q2Point<T>& q, const MatConst<T>&
     c.f0[1] = q.phiy;
     c.fx[2] = q.ux;
     c.fy[2] = q.uy;
+  } else if constexpr (OP == OP_PHIT_VJP) {
+    const T sw = s11 * q.ax + s22 * q.dy + s12 * (q.bxy + q.cyx);
+    c.f0[2] = T(2) * q.phit * (m.omk * sw + m.p * (q.ax + q.dy));
   } else if constexpr (OP == OP_VJP) {
     // per cell: E_K, p and G_c derivatives of x . R (unit-modulus constants in m)
     const T u11 = m.c2ml * q.uxx + m.cl * q.uyy, u22 = m.cl * q.uxx + m.c2ml * q.uyy, u12 = m.cm * ge12;
@@ -376,6 +379,7 @@ cudaError_t launch_apply_q2(const ApplyArgs& a, int op, cudaStream_t s) {
     PFF_LAUNCH2(OP_TCV)
     PFF_LAUNCH2(OP_TCV_GRAD)
     PFF_LAUNCH2(OP_VJP)
+    PFF_LAUNCH2(OP_PHIT_VJP)
 #undef PFF_LAUNCH2
     default: return cudaErrorInvalidValue;
   }

@@ -28,6 +28,7 @@ enum OpKind : int {
   OP_TCV = 8,      // (u . grad phi, psi) per basis function (summed: total crack volume)
   OP_TCV_GRAD = 9, // dJ/dU of J = TCV: (psi_u . grad phi) and (u . grad psi_phi) per basis function
   OP_VJP = 10,     // per cell: x . dR/dtheta for theta = E_K, p, G_c (R = -A, x taken through C)
+  OP_PHIT_VJP = 11,// phi rows: (dA/dphi_tilde)^T x = (psi, 2 phi~ [(1-kappa) sigma(u):e(x_u) + p div x_u])
 };
 
 // mode bits

@@ -107,6 +107,27 @@ __global__ void k_du0(int64_t n, const uint8_t* __restrict__ act, const double* 
   }
 }
 
+// out = x with the fixed components (constraint-mask bits 0, 1, 2) zeroed; 3 blocks
+__global__ void k_mask_fixed(int64_t n, const uint8_t* __restrict__ cmask, const double* __restrict__ x,
+                             double* out) {
+  GRID_STRIDE(s, n) {
+    const uint8_t cm = cmask[s];
+    out[s] = (cm & 1) ? 0.0 : x[s];
+    out[n + s] = (cm & 2) ? 0.0 : x[n + s];
+    out[2 * n + s] = (cm & 4) ? 0.0 : x[2 * n + s];
+  }
+}
+
+// adjoint carry to the previous load step: g = (0, 0, -t2 + act (mu_phi - t1_phi))
+__global__ void k_adj_carry(int64_t n, const uint8_t* __restrict__ act, const double* __restrict__ mu,
+                            const double* __restrict__ t1, const double* __restrict__ t2, double* g) {
+  GRID_STRIDE(s, n) {
+    g[s] = 0.0;
+    g[n + s] = 0.0;
+    g[2 * n + s] = -t2[s] + (act[s] ? mu[2 * n + s] - t1[2 * n + s] : 0.0);
+  }
+}
+
 __global__ void k_axpby(int64_t n, double* out, const double* __restrict__ x, double a, const double* __restrict__ y,
                         double b) {
   GRID_STRIDE(i, n) out[i] = a * x[i] + b * y[i];
@@ -212,6 +233,17 @@ cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_
 cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
                        cudaStream_t s) {
   if (n > 0) k_du0<<<blocks_for(n), TPB, 0, s>>>(n, act, phi, phi_old, du0);
+  return cudaGetLastError();
+}
+
+cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s) {
+  if (n > 0) k_mask_fixed<<<blocks_for(n), TPB, 0, s>>>(n, cmask, x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
+                      cudaStream_t s) {
+  if (n > 0) k_adj_carry<<<blocks_for(n), TPB, 0, s>>>(n, act, mu, t1, t2, g);
   return cudaGetLastError();
 }
 

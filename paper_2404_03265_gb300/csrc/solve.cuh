@@ -25,6 +25,11 @@ cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_
                        const double* phi_old, const uint8_t* flags, double* rhs, cudaStream_t s);
 cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
                        cudaStream_t s);
+// out = x with fixed components (constraint mask) zeroed, 3 blocks of n
+cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
+// g = (0, 0, -t2 + act * (mu_phi - t1_phi)): adjoint right-hand side of the previous load step
+cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
+                      cudaStream_t s);
 cudaError_t axpby(int64_t n, double* out, const double* x, double a, const double* y, double b, cudaStream_t s);
 cudaError_t scale(int64_t n, double* out, const double* x, double a, cudaStream_t s);
 int reduction_partials();

@@ -141,6 +141,7 @@ struct pff_problem {
   double* lev_ecell64 = nullptr;  // lev_total
   float* lev_ecell32 = nullptr;
   double* cell_out = nullptr;     // 3 * n_slots: per-cell VJP values
+  double* adj_cell = nullptr;     // n_leaf_cells: per-step modulus gradient of the multi-step adjoint
 };
 
 namespace pff {
@@ -210,7 +211,16 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
                              uint8_t* active, const NewtonOpts& o, NewtonInfo& info, cudaStream_t s);
 // per-cell modulus and the adjoint TCV gradient (adjoint.cpp)
 std::string set_cell_modulus(pff_problem& pb, const double* E_cells, cudaStream_t s);
-cudaError_t tcv_gradient(pff_problem& pb, const double* u, const double* phi, double* g, cudaStream_t s);
+cudaError_t tcv_gradient(pff_problem& pb, const double* u, const double* phi, double* g, cudaStream_t s,
+                         const uint8_t* rows = nullptr);
+struct AdjointStats {
+  int gmres_total = 0, gmres_max = 0, failed_step = 0;
+  GmresResult last;
+};
+cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* const* u, const double* const* phi,
+                              const uint8_t* const* active, const double* p, double rtol, int restart, int maxiter,
+                              double* gE, double* gp_host, double* ggc_host, AdjointStats& st, std::string& err,
+                              cudaStream_t s);
 cudaError_t param_vjp(pff_problem& pb, const double* w, double* gE_cells, double* g_host, cudaStream_t s);
 cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const double* phi, const double* phi_old,
                         const uint8_t* active, double rtol, int restart, int maxiter, double* gE, double* g_host,

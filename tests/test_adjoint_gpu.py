@@ -332,3 +332,93 @@ def test_autograd_load_step_65k():
         Em[c] -= hh
         fd = (Jfd({}, Ep) - Jfd({}, Em)) / (2 * hh)
         assert abs(fd - gE[c]) <= 1e-5 * abs(fd), (c, fd, gE[c])
+
+
+def gpu_steps(P, pb, mg, po, ps, tol=1e-12):
+    """Load steps at pressures ps from the initial crack on the GPU; checkpoints per step."""
+    import torch
+    from paper_2404_03265_gb300 import newton_step
+    us = [torch.zeros((2, P.n_slots), dtype=torch.float64, device="cuda")]
+    phis = [dev(P.to_slots(po))]
+    acts = []
+    act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
+    for p in ps:
+        pb.set_pressure(p)
+        u = us[-1].clone()
+        phi = phis[-1].clone()
+        info = newton_step(pb, mg, u, phi, phis[-1], act, tol=tol, atol=1e-15)
+        assert info["converged"], info
+        us.append(u)
+        phis.append(phi)
+        acts.append(act.clone())
+    return us, phis, acts
+
+
+def test_multi_step_adjoint_vs_oracle_and_differences():
+    """Three load steps (p = 0.1, 0.15, 0.2) on the 4,293-DoF mesh with lognormal E_K:
+    the checkpointed GPU adjoint against the oracle's (1e-6; states agree to about
+    1e-7) and against central differences of three-step GPU solves (1e-5)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Problem, tcv_adjoint_steps
+    P = pair("small")
+    om = P.om
+    E = cell_E(P)
+    ps = [0.1, 0.15, 0.2]
+    base = P.material()
+    # oracle
+    _, po = solvers.sneddon_initial(om, om.h_min_diag())
+    mats, ous, ophis, oacts = [], [np.zeros((om.nn, 2))], [po], []
+    u, phi, act = ous[0], po.copy(), None
+    for p in ps:
+        mat = ops.Material(**dict(base, p=p))
+        u, phi_n, act, info = solvers.load_step(om, mat, 1e4, u, phi.copy(), phi, active_prev=act, E_cells=E,
+                                                tol=1e-12, atol=1e-15)
+        assert info.converged
+        phi = phi_n
+        mats.append(mat)
+        ous.append(u)
+        ophis.append(phi)
+        oacts.append(act)
+    go = adj.tcv_adjoint_steps(om, mats, ous, ophis, oacts, E)
+    # GPU
+    pb = Problem(P.lm, **base)
+    pb.set_cell_modulus(dev(E))
+    mg = MG(pb, PFF_F32)
+    us, phis, acts = gpu_steps(P, pb, mg, po, ps)
+    for a_g, a_o in zip(acts, oacts):
+        assert np.array_equal(P.from_slots(a_g.cpu().numpy()).astype(bool), a_o)
+    gE = torch.full((len(E),), float("nan"), dtype=torch.float64, device="cuda")
+    r = tcv_adjoint_steps(pb, mg, us, phis, acts, ps, gE=gE, rtol=1e-12)
+    assert r["converged"]
+    J = ops.tcv(om, ops.State(om, ous[-1], ophis[-1], ophis[-1]))
+    for n in range(len(ps)):
+        assert close(r["p"][n], go["p"][n], 1e-6, 0.0), (n, r["p"][n], go["p"][n])
+    assert close(r["Gc"], go["Gc"], 1e-6, 1e-10 * J / base["Gc"]), (r["Gc"], go["Gc"])
+    inf, two = rel_err(gE.cpu().numpy(), go["E"])
+    assert inf < 1e-6 and two < 1e-6, (inf, two)
+
+    # central differences of three-step GPU solves
+    def Jfd(kw, pss, Ec):
+        pb.set_params(**kw)
+        pb.set_cell_modulus(dev(Ec))
+        u2, p2, a2 = gpu_steps(P, pb, mg, po, pss)
+        for x0, x1 in zip(a2, acts):
+            assert torch.equal(x0, x1), "active set changed under the perturbation"
+        return pb.tcv(u2[-1], p2[-1])
+
+    rel = 1e-6
+    hh = rel * ps[0]
+    fd = (Jfd({}, [ps[0] + hh] + ps[1:], E) - Jfd({}, [ps[0] - hh] + ps[1:], E)) / (2 * hh)
+    assert abs(fd - r["p"][0]) <= 1e-5 * abs(fd), (fd, r["p"][0])
+    hh = rel * base["Gc"]
+    fd = (Jfd({"Gc": base["Gc"] + hh}, ps, E) - Jfd({"Gc": base["Gc"] - hh}, ps, E)) / (2 * hh)
+    pb.set_params(Gc=base["Gc"])
+    assert abs(fd - r["Gc"]) <= 1e-5 * abs(fd), (fd, r["Gc"])
+    gEn = gE.cpu().numpy()
+    c = int(np.argmax(np.abs(gEn)))
+    hh = rel * E[c]
+    Ep, Em = E.copy(), E.copy()
+    Ep[c] += hh
+    Em[c] -= hh
+    fd = (Jfd({}, ps, Ep) - Jfd({}, ps, Em)) / (2 * hh)
+    assert abs(fd - gEn[c]) <= 1e-5 * abs(fd), (c, fd, gEn[c])

@@ -216,7 +216,7 @@ def time_e2e(mesh, dtype, steps, warmup):
 SOLVE_LOADS = (1e-3, 1.5e-3, 2e-3)
 
 
-def time_solve(precision, loads=SOLVE_LOADS):
+def time_solve(precision, loads=SOLVE_LOADS, matvec=None):
     """Load steps of Algorithm 2 on the 1,043,811-DoF band-refined crack mesh
     (16x16 coarse, 5 global, 7 band steps; Q1): line-search Newton / PDAS with
     FP64 GMRES preconditioned by the block V-cycle in the given precision.
@@ -250,7 +250,7 @@ def time_solve(precision, loads=SOLVE_LOADS):
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(s)
-        r = newton_step(pb, mg, u, phi, phi_old, act, check=False)
+        r = newton_step(pb, mg, u, phi, phi_old, act, check=False, matvec=precision if matvec is None else matvec)
         e1.record(s)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
@@ -260,6 +260,7 @@ def time_solve(precision, loads=SOLVE_LOADS):
         k = max(r["newton"], 1)
         steps.append({"p": p, "s": t, "newton": r["newton"], "gmres_mean": r["gmres_total"] / k,
                       "gmres_max": r["gmres_max"], "gmres": r["gmres"], "linesearch_failures": r["linesearch_failures"],
+                      "s_mg_setup": r["time_mg_setup"], "s_gmres": r["time_gmres"],
                       "active": r["active_size"], "converged": bool(r["converged"]), "status": r["status"],
                       "residual": r["residual"], "tcv": tcv, "tcv_rel_err": abs(tcv - tcv_ref) / tcv_ref})
         phi_old.copy_(phi)
@@ -267,6 +268,87 @@ def time_solve(precision, loads=SOLVE_LOADS):
     ph = phi.cpu().numpy()[valid]
     return {"dofs": 3 * info["n_nodes"], "steps": steps,
             "s_per_load_step": float(np.mean([st["s"] for st in steps]))}, uh, ph
+
+
+LARGE_LOADS = (1e-3, 1.5e-3, 2e-3, 2.5e-3, 3e-3)
+
+
+def time_large(loads=LARGE_LOADS):
+    """The largest workload: Q2 u and phi on the band-refined crack mesh (14x14
+    coarse, 6 global, 9 band steps; 16,515,855 DoFs), five load steps of
+    Algorithm 2 with the FP32 V-cycle, then the checkpointed adjoint gradient of
+    the final TCV with respect to every step's pressure and G_c.  Reports seconds
+    per load step, the adjoint's seconds, and the device memory in use."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Mesh, Problem, newton_step, tcv_adjoint_steps
+    import synthetic as synth
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    mesh = Mesh.from_recipe(synth.recipe("large")).finalize(2)
+    info = mesh.info
+    ns = info["n_slots"]
+    X, Y, F = mesh.slots()
+    valid = (F & 1) == 1
+    x, y = synth.node_xy(X[valid], Y[valid], info["x_max"], info["y_max"])
+    h = info["h_min"]
+    po_h = np.ones(ns)
+    po_h[valid] = synth.crack_phi_old(x, y, h)
+    m = synth.material(h_min=h)
+    pb = Problem(mesh, E=m["E"], nu=m["nu"], Gc=m["Gc"], eps=m["eps"], kappa=m["kappa"], p=loads[0], c=m["c"])
+    mg = MG(pb, PFF_F32)
+    dev = torch.device("cuda")
+    us = [torch.zeros((2, ns), dtype=torch.float64, device=dev)]
+    phis = [torch.tensor(po_h, device=dev)]
+    acts = []
+    act = torch.zeros(ns, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    steps = []
+    eprime = m["E"] / (1.0 - m["nu"] ** 2)
+    for p in loads:
+        pb.set_pressure(p)
+        u = us[-1].clone()
+        phi = phis[-1].clone()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r = newton_step(pb, mg, u, phi, phis[-1], act, check=False, matvec=PFF_F32)
+        e1.record(s)
+        torch.cuda.synchronize()
+        tcv = pb.tcv(u, phi)
+        k = max(r["newton"], 1)
+        steps.append({"p": p, "s": e0.elapsed_time(e1) / 1e3, "newton": r["newton"],
+                      "gmres_mean": r["gmres_total"] / k, "gmres_max": r["gmres_max"], "active": r["active_size"],
+                      "s_mg_setup": r["time_mg_setup"], "s_gmres": r["time_gmres"],
+                      "converged": bool(r["converged"]), "status": r["status"], "tcv": tcv,
+                      "tcv_rel_err": abs(tcv - 2.0 * np.pi * p / eprime) / (2.0 * np.pi * p / eprime)})
+        us.append(u)
+        phis.append(phi)
+        acts.append(act.clone())
+        if not r["converged"]:
+            break
+    out = {"workload": "large: Q2 u and phi, 14x14 coarse on (-10,10)^2, 6 global + 9 band refinements toward "
+                       "the crack, %d DoFs, %d levels; Sneddon crack, l = 2 h_min; p = %s; FP32 V-cycle, FP64 "
+                       "Newton/GMRES (Jacobian applies inside GMRES in FP32)" % (3 * info["n_nodes"], info["finest_level"] + 1,
+                                          ", ".join("%g" % p for p in loads)),
+           "dofs": 3 * info["n_nodes"], "steps": steps,
+           "s_per_load_step": float(np.mean([st["s"] for st in steps]))}
+    if len(acts) == len(loads):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        g = tcv_adjoint_steps(pb, mg, us, phis, acts, list(loads), rtol=1e-8, check=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        out["adjoint"] = {"s": e0.elapsed_time(e1) / 1e3, "dJ_dp": [float(v) for v in g["p"]], "dJ_dGc": g["Gc"],
+                          "gmres_total": g["gmres_total"], "gmres_max": g["gmres_max"],
+                          "converged": g["converged"], "status": g["status"]}
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    out["device_bytes_in_use"] = int(free0 - free1)
+    out["device_bytes_total"] = int(total)
+    return out
 
 
 def cpu_baseline(budget_s=12.0):
@@ -350,6 +432,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the load-step timing leg")
+    ap.add_argument("--large", action="store_true",
+                    help="add the 16.5M-DoF Q2 five-load-step solve and its checkpointed adjoint")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -441,17 +525,25 @@ def main():
     if not args.no_solve:
         from paper_2404_03265_gb300 import PFF_F32, PFF_F64
         r32, u32, p32 = time_solve(PFF_F32)
+        r32d, u32d, p32d = time_solve(PFF_F32, matvec=PFF_F64)
         r64, u64, p64 = time_solve(PFF_F64)
         line["solve"] = {
             "workload": "solve: 16x16 coarse on (-10,10)^2, 5 global + 7 band refinements toward the crack "
                         "(|x|<=1+2h_min, |y|<=2h_min), Q1, %d DoFs; Sneddon crack, E=1, nu=0.2, G_c=1, "
                         "l=2h_min, kappa=1e-10, c=1e4; p = %s" % (r32["dofs"], ", ".join("%g" % p for p in SOLVE_LOADS)),
             "unit": "s/load step", "newton_tol": 1e-8, "gmres_rtol": 1e-6,
-            "fp32_mg": r32, "fp64_mg": r64,
+            "fp32_mg": r32, "fp32_mg_fp64_matvec": r32d, "fp64_mg": r64,
+            "note": "fp32_mg: V-cycle and the Jacobian applies inside GMRES in FP32 (Krylov basis, "
+                    "orthogonalisation, Givens, residual, line search, active set, lambda_max and coarse solve in "
+                    "FP64); fp32_mg_fp64_matvec: FP32 V-cycle only; fp64_mg: everything in FP64",
             "speedup_fp32_mg": r64["s_per_load_step"] / r32["s_per_load_step"],
             "fp32_vs_fp64_rel_l2": {"u": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
                                     "phi": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))},
+            "fp32_fp64_matvec_vs_fp64_rel_l2": {"u": float(np.linalg.norm(u32d - u64) / np.linalg.norm(u64)),
+                                                "phi": float(np.linalg.norm(p32d - p64) / np.linalg.norm(p64))},
         }
+    if args.large:
+        line["large"] = time_large()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -174,6 +174,9 @@ typedef struct pff_solve_info {
   double margin;               /* min |R_i / B_ii + c (phi_i - phi_i^old)| over DoFs */
   int32_t gmres_per_newton[128];
   double residual_history[129];
+  double time_mg_setup;        /* seconds in multigrid set-up (Newton step)      */
+  double time_gmres;           /* seconds in GMRES (Newton step); the rest of the
+                                  step is residuals, active sets, line search     */
 } pff_solve_info;
 
 typedef struct pff_newton_opts {
@@ -185,6 +188,11 @@ typedef struct pff_newton_opts {
   int32_t gmres_maxiter;
   int32_t max_newton; /* Newton iteration cap (100)                           */
   int32_t ls_max;     /* line-search trials (10)                              */
+  int32_t matvec_precision; /* Jacobian applies inside GMRES: PFF_F64 (default,
+                               0) or PFF_F32 (FP64 Krylov vectors rounded in
+                               and out; the residual, line search, active set,
+                               orthogonalisation and Givens rotations stay FP64) */
+  int32_t reserved;   /* 0                                                    */
 } pff_newton_opts;
 
 /* ---- allocation-free variant of pff_apply (no counterpart in the paper) ----

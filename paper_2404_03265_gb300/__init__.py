@@ -192,9 +192,10 @@ def gmres(problem, mg, rhs, x, rtol=1e-6, restart=50, maxiter=500, transpose=Fal
 
 
 def newton_step(problem, mg, u, phi, phi_old, active, tol=1e-8, atol=1e-13, gmres_rtol=1e-6, omega=0.5,
-                restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, stream=None, check=True):
-    """One load step of Algorithm 2 (u (2, n_slots), phi, phi_old (n_slots,) float64; active uint8)."""
-    o = _lib.NewtonOpts(tol, atol, gmres_rtol, omega, restart, gmres_maxiter, max_newton, ls_max)
+                restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, matvec=PFF_F64, stream=None, check=True):
+    """One load step of Algorithm 2 (u (2, n_slots), phi, phi_old (n_slots,) float64; active uint8).
+    matvec: precision of the Jacobian applies inside GMRES (PFF_F64 or PFF_F32)."""
+    o = _lib.NewtonOpts(tol, atol, gmres_rtol, omega, restart, gmres_maxiter, max_newton, ls_max, matvec, 0)
     info = _lib.SolveInfo()
     st = _lib.lib().pff_newton_pdas_step(problem._h, mg._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phi_old),
                                          _lib.ptr(active), _lib.ctypes.byref(o), _lib.ctypes.byref(info),

@@ -42,7 +42,8 @@ class SolveInfo(ctypes.Structure):
                 ("linesearch_failures", ctypes.c_int32), ("gmres_total", ctypes.c_int32),
                 ("gmres_max", ctypes.c_int32), ("pad", ctypes.c_int32), ("active_size", ctypes.c_int64),
                 ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("margin", ctypes.c_double),
-                ("gmres_per_newton", ctypes.c_int32 * 128), ("residual_history", ctypes.c_double * 129)]
+                ("gmres_per_newton", ctypes.c_int32 * 128), ("residual_history", ctypes.c_double * 129),
+                ("time_mg_setup", ctypes.c_double), ("time_gmres", ctypes.c_double)]
 
     def to_dict(self):
         n = self.newton_iterations
@@ -50,13 +51,15 @@ class SolveInfo(ctypes.Structure):
                     gmres_total=self.gmres_total, gmres_max=self.gmres_max, active_size=self.active_size,
                     residual0=self.residual0, residual=self.residual, margin=self.margin,
                     gmres=list(self.gmres_per_newton[:min(n, 128)]),
-                    residual_history=list(self.residual_history[:min(n + 1, 129)]))
+                    residual_history=list(self.residual_history[:min(n + 1, 129)]),
+                    time_mg_setup=self.time_mg_setup, time_gmres=self.time_gmres)
 
 
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
                 ("omega", ctypes.c_double), ("restart", ctypes.c_int32), ("gmres_maxiter", ctypes.c_int32),
-                ("max_newton", ctypes.c_int32), ("ls_max", ctypes.c_int32)]
+                ("max_newton", ctypes.c_int32), ("ls_max", ctypes.c_int32), ("matvec_precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None

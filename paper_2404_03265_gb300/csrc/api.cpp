@@ -326,6 +326,8 @@ extern "C" pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam
 
 extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (!mg) return;
+  mg_release_graphs(*mg);
+  if (mg->cap_stream) cudaStreamDestroy(mg->cap_stream);
   mg->mem.release();
   delete mg;
 }
@@ -388,6 +390,8 @@ static void fill_info(const NewtonInfo& in, pff_solve_info* out) {
   out->residual = in.residual.empty() ? 0.0 : in.residual.back();
   out->margin = in.margin;
   for (size_t i = 0; i < in.residual.size() && i < 129; ++i) out->residual_history[i] = in.residual[i];
+  out->time_mg_setup = in.t_setup;
+  out->time_gmres = in.t_gmres;
 }
 
 extern "C" pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
@@ -426,7 +430,9 @@ extern "C" pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* 
       o.tol = opts->tol; o.atol = opts->atol; o.gmres_rtol = opts->gmres_rtol; o.omega = opts->omega;
       o.restart = opts->restart; o.gmres_maxiter = opts->gmres_maxiter; o.max_newton = opts->max_newton;
       o.ls_max = opts->ls_max;
+      o.matvec = opts->matvec_precision;
     }
+    if (o.matvec != PFF_F64 && o.matvec != PFF_F32) return fail(PFF_ERR_INVALID_ARG, "bad matvec precision");
     if (o.restart < 1 || o.restart > 500 || o.max_newton < 0 || o.ls_max < 1 || !(o.omega > 0 && o.omega <= 1))
       return fail(PFF_ERR_INVALID_ARG, "bad Newton options");
     std::string e = ensure_workspace(*pb, o.restart);

@@ -125,6 +125,8 @@ std::string mg_alloc(pff_mg& mg) {
   const int64_t N = D.lev_total;
   int64_t nmax = 0;
   for (const auto& L : D.levels) nmax = std::max<int64_t>(nmax, L.lv.n_slots);
+  mg.vc_in = mg.mem.alloc<double>(3 * mg.pb->mesh->m.lay.n_slots);
+  mg.vc_out = mg.mem.alloc<double>(3 * mg.pb->mesh->m.lay.n_slots);
   mg.lin64 = mg.mem.alloc<double>(4 * N);
   mg.lin32 = mg.mem.alloc<float>(4 * N);
   mg.cmask = mg.mem.alloc<uint8_t>(N);
@@ -154,7 +156,13 @@ std::string mg_alloc(pff_mg& mg) {
 
 // Per Newton step: level linearisation, level constraint masks, inverse
 // diagonals, eigenvalue estimates and the coarse inverse of both blocks.
+void mg_release_graphs(pff_mg& mg) {
+  for (auto& g : mg.vc_exec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
 std::string mg_setup(pff_mg& mg, cudaStream_t s) {
+  mg_release_graphs(mg);   // the V-cycle graphs hold this set-up's coefficients
   pff_problem& pb = *mg.pb;
   const Mesh& M = pb.mesh->m;
   const DevMesh& D = pb.mesh->dev;
@@ -323,24 +331,32 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     if (!(lam > 0)) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
     const double a = mg.lo * lam, bb = mg.hi * lam;
     const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
-    T* v = out;
-    T* vp = yp + o;
-    T* tmp = y + o;
-    cudaError_t ee = mg_chebyshev_first<T>(n, v, vp, dinv + o, rhs, T(1.0 / theta), s);
+    // three iterates (current, previous, next) rotate roles each step; the start is
+    // chosen so that the last step writes `out`
+    const int steps = mg.degree - 1;
+    T* w0 = out;
+    T* w1 = yp + o;
+    T* w2 = y + o;
+    T *cur, *prev, *nxt;   // each step maps (cur, prev, nxt) to (nxt, cur, prev)
+    switch (steps % 3) {
+      case 0: cur = w0; prev = w1; nxt = w2; break;
+      case 1: cur = w1; prev = w2; nxt = w0; break;
+      default: cur = w1; prev = w0; nxt = w2; break;
+    }
+    cudaError_t ee = mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s);
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
     for (int j = 1; j < mg.degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
-      ee = level_apply<T>(mg, l, block_op(b), v, t + o, s);
+      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s);
       if (ee != cudaSuccess) return ee;
-      // tmp = v + rho_n rho (v - vp) + 2 rho_n / delta D^-1 (rhs - A v)
-      ee = mg_chebyshev_step<T>(n, tmp, v, vp, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
+      // next = cur + rho_n rho (cur - prev) + 2 rho_n / delta D^-1 (rhs - A cur)
+      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
       if (ee != cudaSuccess) return ee;
-      // rotate: vp <- v, v <- tmp (copies keep the buffer roles fixed)
-      ee = cudaMemcpyAsync(vp, v, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-      if (ee != cudaSuccess) return ee;
-      ee = cudaMemcpyAsync(v, tmp, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-      if (ee != cudaSuccess) return ee;
+      T* old_prev = prev;
+      prev = cur;
+      cur = nxt;
+      nxt = old_prev;
       rho = rho_n;
     }
     return cudaSuccess;
@@ -382,9 +398,45 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
 
 }  // namespace
 
-cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s) {
+static cudaError_t vcycle_direct(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s) {
   if (mg.precision == PFF_F64) return vcycle_t<double>(mg, block, r, z, s);
   return vcycle_t<float>(mg, block, r, z, s);
+}
+
+// Capture the V-cycle of one block, reading vc_in and writing vc_out at the
+// block's offset; false if the graph could not be made (the direct path is used).
+static bool vcycle_capture(pff_mg& mg, int block) {
+  const int64_t n = mg.pb->mesh->m.lay.n_slots;
+  const int64_t off = block == 0 ? 0 : 2 * n;
+  if (!mg.cap_stream && cudaStreamCreateWithFlags(&mg.cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaStreamBeginCapture(mg.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  const cudaError_t e = vcycle_direct(mg, block, mg.vc_in + off, mg.vc_out + off, mg.cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(mg.cap_stream, &g);
+  bool ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+  if (ok) ok = cudaGraphInstantiate(&mg.vc_exec[block], g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    mg.vc_exec[block] = nullptr;
+    cudaGetLastError();   // clear a capture error; the direct path follows
+  }
+  return ok;
+}
+
+cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s) {
+  if (mg.graphs_ok && mg.vc_in && mg.vc_out) {
+    if (!mg.vc_exec[block] && !vcycle_capture(mg, block)) mg.graphs_ok = false;
+    if (mg.vc_exec[block]) {
+      const int64_t n = mg.pb->mesh->m.lay.n_slots;
+      const int64_t off = block == 0 ? 0 : 2 * n;
+      const size_t bytes = size_t(block == 0 ? 2 * n : n) * sizeof(double);
+      cudaError_t e = cudaMemcpyAsync(mg.vc_in + off, r, bytes, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaGraphLaunch(mg.vc_exec[block], s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(z, mg.vc_out + off, bytes, cudaMemcpyDeviceToDevice, s);
+      return e;
+    }
+  }
+  return vcycle_direct(mg, block, r, z, s);
 }
 
 template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t);

@@ -107,6 +107,13 @@ __global__ void k_du0(int64_t n, const uint8_t* __restrict__ act, const double* 
   }
 }
 
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* b) {
+  GRID_STRIDE(s, n) b[s] = float(a[s]);
+}
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* b) {
+  GRID_STRIDE(s, n) b[s] = double(a[s]);
+}
+
 // out = x with the fixed components (constraint-mask bits 0, 1, 2) zeroed; 3 blocks
 __global__ void k_mask_fixed(int64_t n, const uint8_t* __restrict__ cmask, const double* __restrict__ x,
                              double* out) {
@@ -233,6 +240,15 @@ cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_
 cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
                        cudaStream_t s) {
   if (n > 0) k_du0<<<blocks_for(n), TPB, 0, s>>>(n, act, phi, phi_old, du0);
+  return cudaGetLastError();
+}
+
+cudaError_t f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
+  if (n > 0) k_f64_to_f32<<<blocks_for(n), TPB, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+cudaError_t f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t s) {
+  if (n > 0) k_f32_to_f64<<<blocks_for(n), TPB, 0, s>>>(n, a, b);
   return cudaGetLastError();
 }
 

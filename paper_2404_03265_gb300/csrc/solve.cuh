@@ -25,6 +25,8 @@ cudaError_t newton_rhs(int64_t n, const double* R, const double* t, const uint8_
                        const double* phi_old, const uint8_t* flags, double* rhs, cudaStream_t s);
 cudaError_t newton_du0(int64_t n, const uint8_t* act, const double* phi, const double* phi_old, double* du0,
                        cudaStream_t s);
+cudaError_t f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
+cudaError_t f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t s);
 // out = x with fixed components (constraint mask) zeroed, 3 blocks of n
 cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
 // g = (0, 0, -t2 + act * (mu_phi - t1_phi)): adjoint right-hand side of the previous load step

@@ -10,6 +10,7 @@
 //    of the update from their constraint, and a line search U + omega^(l-1) dU
 //    accepting the first decrease of the Newton residual.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -79,6 +80,8 @@ std::string ensure_workspace(pff_problem& pb, int restart) {
   W.h = W.mem.alloc<double>(restart + 2);
   W.scal = W.mem.alloc<double>(8);
   W.bad = W.mem.alloc<int>(1);
+  W.x32 = W.mem.alloc<float>(n3);
+  W.y32 = W.mem.alloc<float>(n3);
   if (!W.mem.err.empty()) return W.mem.err;
   W.ready = true;
   return "";
@@ -101,11 +104,18 @@ static cudaError_t precond(pff_mg& mg, const double* v, double* z, cudaStream_t 
 }
 
 cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double* b, double* x, double rtol,
-                        int restart, int maxiter, GmresResult& res, cudaStream_t s) {
+                        int restart, int maxiter, GmresResult& res, cudaStream_t s, int matvec) {
   SolverWS& W = pb.ws;
   const int64_t n = pb.mesh->m.lay.n_slots, n3 = 3 * n;
   const int op = transpose ? OP_FULL_T : OP_FULL;
-  auto A = [&](const double* v, double* y) {
+  // y = G~ v (or G~^T v); in FP32 the FP64 Krylov vectors are rounded in and out
+  auto A = [&](const double* v, double* y) -> cudaError_t {
+    if (matvec == PFF_F32) {
+      RET(f64_to_f32(n3, v, W.x32, s));
+      RET(leaf_apply(pb, PFF_F32, transpose ? PFF_OP_TRANSPOSE : PFF_OP_JACOBIAN, W.x32, W.x32 + 2 * n, W.y32,
+                     W.y32 + 2 * n, s));
+      return f32_to_f64(n3, W.y32, y, s);
+    }
     return leaf_op(pb, op, MODE_MASK_INPUT | MODE_IDENTITY, pb.lin64, pb.cmask, v, v + 2 * n, y, y + 2 * n, s);
   };
   RET(cudaMemsetAsync(x, 0, n3 * sizeof(double), s));
@@ -269,10 +279,14 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     RET(newton_du0(n, W.act, phi, phi_old, W.du0, s));
     RET(leaf_op(pb, OP_FULL, 0, pb.lin64, pb.cmask, W.du0, W.du0 + 2 * n, W.tmp, W.tmp + 2 * n, s));
     RET(newton_rhs(n, W.R, W.tmp, W.act, phi, phi_old, D.slot_flags, W.rhs, s));
+    const auto t_setup0 = std::chrono::steady_clock::now();
     std::string e = mg_setup(mg, s);
+    const auto t_setup1 = std::chrono::steady_clock::now();
+    info.t_setup += std::chrono::duration<double>(t_setup1 - t_setup0).count();
     if (!e.empty()) { info.error = e; return cudaErrorUnknown; }
     GmresResult gr;
-    RET(gmres_solve(pb, mg, 0, W.rhs, W.dU, o.gmres_rtol, o.restart, o.gmres_maxiter, gr, s));
+    RET(gmres_solve(pb, mg, 0, W.rhs, W.dU, o.gmres_rtol, o.restart, o.gmres_maxiter, gr, s, o.matvec));
+    info.t_gmres += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup1).count();
     info.gmres.push_back(gr.iterations);
     if (gr.breakdown) info.gmres_breakdown = true;
     RET(distribute_hanging(n, D.hang, D.nhang, M.k, 3, W.dU, s));

@@ -90,6 +90,7 @@ struct SolverWS {
   unsigned long long* stats = nullptr;
   double *partial = nullptr, *h = nullptr, *scal = nullptr;
   int* bad = nullptr;
+  float *x32 = nullptr, *y32 = nullptr;   // FP32 operator applies inside GMRES (3 blocks each)
 };
 
 struct GmresResult {
@@ -102,6 +103,7 @@ struct GmresResult {
 struct NewtonOpts {
   double tol = 1e-8, atol = 1e-13, gmres_rtol = 1e-6, omega = 0.5;
   int restart = 50, gmres_maxiter = 500, max_newton = 100, ls_max = 10;
+  int matvec = PFF_F64;   // precision of the Jacobian applies inside GMRES
 };
 
 struct NewtonInfo {
@@ -113,6 +115,7 @@ struct NewtonInfo {
   std::vector<int> gmres;
   std::vector<int64_t> active_size, changes;
   std::string error;
+  double t_setup = 0.0, t_gmres = 0.0;   // host wall seconds in multigrid set-up and in GMRES
 };
 
 }  // namespace pff
@@ -181,6 +184,12 @@ struct pff_mg {
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *diag = nullptr;
   double *partial = nullptr, *sc = nullptr, *hist = nullptr;
   bool ready = false;
+  // V-cycles replayed as CUDA graphs (one per block, captured after each set-up;
+  // inputs and outputs pass through fixed staging vectors of 3 * n_slots doubles)
+  bool graphs_ok = true;
+  cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
+  double *vc_in = nullptr, *vc_out = nullptr;
 };
 
 namespace pff {
@@ -202,7 +211,7 @@ cudaError_t leaf_op(pff_problem& pb, int kop, int mode, const double* lin, const
                     const double* xp, double* yu, double* yp, cudaStream_t s);
 std::string ensure_workspace(pff_problem& pb, int restart);
 cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double* b, double* x, double rtol,
-                        int restart, int maxiter, GmresResult& res, cudaStream_t s);
+                        int restart, int maxiter, GmresResult& res, cudaStream_t s, int matvec = PFF_F64);
 cudaError_t leaf_residual(pff_problem& pb, const double* u, const double* phi, const double* phit, double* R,
                           cudaStream_t s);
 cudaError_t lumped_mass(pff_problem& pb, double* B, cudaStream_t s);
@@ -233,6 +242,7 @@ cudaError_t cells_level(int32_t n, const int32_t* dst, const int32_t* src, const
 cudaError_t cells_gather(int32_t n, const double* in, const int32_t* slot, double* out, cudaStream_t s);
 // multigrid (mg_host.cpp)
 std::string mg_alloc(pff_mg& mg);
+void mg_release_graphs(pff_mg& mg);
 std::string mg_setup(pff_mg& mg, cudaStream_t s);
 cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s);
 // level operator y = A_l x of one block (op OP_UU / OP_PP / *_DIAG), precision of T

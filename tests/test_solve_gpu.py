@@ -102,9 +102,10 @@ def test_gmres_solves_constrained_system(prec):
 
 
 @pytest.mark.parametrize("name", ["small", "band4_3_3"])
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "f32mv"])
 def test_newton_pdas_load_step(name, prec):
-    """Sneddon load step on the GPU against the oracle load step (Algorithm 2)."""
+    """Sneddon load step on the GPU against the oracle load step (Algorithm 2).
+    f32mv: FP32 V-cycle and FP32 Jacobian applies inside GMRES."""
     import torch
     from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, newton_step
     P = Pair(name, 1)
@@ -116,11 +117,12 @@ def test_newton_pdas_load_step(name, prec):
     assert io.converged
     pb = problem(P, mat)
     mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
+    mv = PFF_F32 if prec == "f32mv" else PFF_F64
     us = dev(P.to_slots(u0).T)
     ps = dev(P.to_slots(phi_old))
     pos = dev(P.to_slots(phi_old))
     act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
-    info = newton_step(pb, mg, us, ps, pos, act)
+    info = newton_step(pb, mg, us, ps, pos, act, matvec=mv)
     assert info["converged"], info
     ug = P.from_slots(us.cpu().numpy().T)
     pg = P.from_slots(ps.cpu().numpy())

@@ -414,7 +414,7 @@ def profiled_traffic():
     with open(prof) as f:
         text = f.read()
     h = hashlib.sha256()
-    for name in ("apply.cu", "kernels.cuh"):
+    for name in ("apply.cu", "apply_q2.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2404_03265_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     m_hash = re.search(r"first 16 hex\): `([0-9a-f]{16})`", text)

@@ -80,7 +80,8 @@ typedef struct pff_params {
   double eps;     /* length scale l                                          */
   double kappa;   /* regularisation in g(phi) = (1-kappa) phi^2 + kappa      */
   double p;       /* pressure                                                */
-  double c;       /* primal-dual active set constant                        */
+  double c;       /* primal-dual active set constant; c <= 0 selects the
+                     per-DoF c_i = 2 |lambda_i / (phi_i - phi_old_i)| of Sec. 2 */
 } pff_params;
 
 const char* pff_last_error(void);
@@ -155,6 +156,15 @@ pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void*
 pff_status pff_mg_create(pff_problem* pb, int32_t precision, pff_mg** out);
 pff_status pff_mg_setup(pff_mg* mg, void* stream);
 pff_status pff_vcycle(pff_mg* mg, int32_t block, const double* r, double* z, void* stream);
+/* Inverse diagonal of block `block` on `level` (Sec. 3.2 Chebyshev-Jacobi):
+ * 1/diag(A_l) on interior rows, 0 on refinement-edge, Dirichlet and active
+ * rows and holes, FP64, as set up by the last pff_mg_setup.  Written to out
+ * (device, ncomp * n_slots_l doubles, components in blocks; ncomp = 2 for block
+ * 0, 1 for block 1) if out is not NULL and capacity suffices; *n_out (may be
+ * NULL) receives that count.  X_host, Y_host (may be NULL): n_slots_l finest-grid
+ * integer coordinates of the level's slots (-1 for holes).                     */
+pff_status pff_inverse_diagonal(const pff_mg* mg, int32_t level, int32_t block, double* out, int32_t* X_host,
+                                int32_t* Y_host, int64_t capacity, int64_t* n_out, void* stream);
 /* lambda_max estimates per level (host array of finest_level + 1 doubles; entry 0 unused) */
 pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam_host, int32_t n);
 void pff_mg_destroy(pff_mg* mg);
@@ -193,6 +203,8 @@ typedef struct pff_newton_opts {
                                and out; the residual, line search, active set,
                                orthogonalisation and Givens rotations stay FP64) */
   int32_t reserved;   /* 0                                                    */
+  const double* phi_tilde; /* device, n_slots: phi_tilde of the u-equation (Sec. 2,
+                              "old step or extrapolation"); NULL: phi_old      */
 } pff_newton_opts;
 
 /* ---- allocation-free variant of pff_apply (no counterpart in the paper) ----
@@ -221,6 +233,16 @@ typedef struct pff_newton_opts {
 #define PFF_NOALLOC_MAX_PARTIALS 65536
 pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
                              void* yu, void* yp, void* stream);
+
+/* Active set of Algorithm 2 at (R, phi, phi_old): A = { i : R_i / B_ii +
+ * c (phi_i - phi_old_i) > 0 } with R the condensed residual (3 blocks of
+ * n_slots doubles, as from pff_residual; its phi block is used), B the lumped
+ * phi mass and c from pff_params; never on hanging nodes or holes.  active
+ * (device, n_slots bytes): the previous set on input, the new one on output.
+ * n_changed, n_active, margin (host, may be NULL): entries that changed, size of
+ * the set, min |indicator| over nodes.  Synchronises.                         */
+pff_status pff_active_set(pff_problem* pb, const double* R, const double* phi, const double* phi_old,
+                          uint8_t* active, int64_t* n_changed, int64_t* n_active, double* margin, void* stream);
 
 /* Pressure p of the current load step (Problem 1).                           */
 pff_status pff_set_pressure(pff_problem* pb, double p);

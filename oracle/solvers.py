@@ -98,12 +98,19 @@ def newton_residual(mesh, R, active, phi, phi_old):
 
 
 def active_set(mesh, R, B, phi, phi_old, c):
-    """A = { i : R_phi,i / B_ii + c (phi_i - phi_old_i) > 0 }, never on hanging nodes."""
+    """A = { i : R_phi,i / B_ii + c (phi_i - phi_old_i) > 0 }, never on hanging nodes.
+
+    c <= 0 selects the per-DoF constant of Sec. 2, c_i = 2 |lambda_i / (phi_i - phi_old_i)|,
+    for which c_i (phi_i - phi_old_i) = 2 |lambda_i| sign(phi_i - phi_old_i) (0 where phi_i = phi_old_i)."""
     nn = mesh.nn
     ok = ~mesh.is_hanging
     lam = np.zeros(nn)
     lam[ok] = R[2 * nn:][ok] / B[ok]
-    ind = lam + c * (phi - phi_old)
+    d = phi - phi_old
+    if c > 0:
+        ind = lam + c * d
+    else:
+        ind = lam + np.where(d > 0, 2.0 * np.abs(lam), np.where(d < 0, -2.0 * np.abs(lam), 0.0))
     return (ind > 0) & ok, ind
 
 
@@ -119,11 +126,13 @@ class StepInfo:
 
 
 def load_step(mesh, mat, c, u, phi, phi_old, active_prev=None, E_cells=None, tol=1e-8, gmres_rtol=1e-6,
-              restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, omega=0.5, mg_kw=None, atol=1e-13):
-    """One load step of Algorithm 2; returns (u, phi, active, info)."""
+              restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, omega=0.5, mg_kw=None, atol=1e-13,
+              phi_tilde=None):
+    """One load step of Algorithm 2; returns (u, phi, active, info).  phi_tilde: the
+    linearised phase field of the u-equation (Sec. 2), phi_old when None."""
     nn = mesh.nn
     mg_kw = mg_kw or {}
-    phit = phi_old.copy()
+    phit = phi_old.copy() if phi_tilde is None else np.asarray(phi_tilde, dtype=np.float64).copy()
     B = ops.lumped_mass(mesh)
     C = mesh.C
     u = np.stack([C @ u[:, 0], C @ u[:, 1]], 1)

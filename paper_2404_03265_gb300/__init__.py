@@ -101,6 +101,15 @@ class Problem:
         _lib.check(_lib.lib().pff_apply(self._h, prec, op, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(yu),
                                         _lib.ptr(yp), _lib.stream_ptr(stream)))
 
+    def active_set(self, R, phi, phi_old, active, stream=None):
+        """Algorithm 2's active set from the condensed residual R (3, n_slots); active updated in place.
+        Returns (n_changed, n_active, margin)."""
+        nc, na, mg_ = _lib.ctypes.c_int64(), _lib.ctypes.c_int64(), _lib.ctypes.c_double()
+        _lib.check(_lib.lib().pff_active_set(self._h, _lib.ptr(R), _lib.ptr(phi), _lib.ptr(phi_old), _lib.ptr(active),
+                                             _lib.ctypes.byref(nc), _lib.ctypes.byref(na), _lib.ctypes.byref(mg_),
+                                             _lib.stream_ptr(stream)))
+        return nc.value, na.value, mg_.value
+
     def set_pressure(self, p):
         _lib.check(_lib.lib().pff_set_pressure(self._h, p))
         self.params["p"] = p
@@ -167,6 +176,20 @@ class MG:
         """z = MG(r); block 0: r, z float64 (2, n_slots); block 1: (n_slots,)."""
         _lib.check(_lib.lib().pff_vcycle(self._h, block, _lib.ptr(r), _lib.ptr(z), _lib.stream_ptr(stream)))
 
+    def inverse_diagonal(self, level, block, stream=None):
+        """(dinv (ncomp * n_slots_l,) float64 device tensor, X, Y level-slot coordinates)."""
+        import torch
+        n = _lib.ctypes.c_int64()
+        _lib.check(_lib.lib().pff_inverse_diagonal(self._h, level, block, None, None, None, 0,
+                                                   _lib.ctypes.byref(n), _lib.stream_ptr(stream)))
+        ns = n.value // (2 if block == 0 else 1)
+        out = torch.empty(n.value, dtype=torch.float64, device="cuda")
+        X = np.empty(ns, np.int32)
+        Y = np.empty(ns, np.int32)
+        _lib.check(_lib.lib().pff_inverse_diagonal(self._h, level, block, _lib.ptr(out), _lib.ptr(X), _lib.ptr(Y),
+                                                   n.value, None, _lib.stream_ptr(stream)))
+        return out, X, Y
+
     def lam(self, block):
         out = np.zeros(self.n_levels)
         _lib.check(_lib.lib().pff_mg_lambda(self._h, block, _lib.ptr(out), self.n_levels))
@@ -192,10 +215,13 @@ def gmres(problem, mg, rhs, x, rtol=1e-6, restart=50, maxiter=500, transpose=Fal
 
 
 def newton_step(problem, mg, u, phi, phi_old, active, tol=1e-8, atol=1e-13, gmres_rtol=1e-6, omega=0.5,
-                restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, matvec=PFF_F64, stream=None, check=True):
+                restart=50, gmres_maxiter=500, max_newton=100, ls_max=10, matvec=PFF_F64, phi_tilde=None,
+                stream=None, check=True):
     """One load step of Algorithm 2 (u (2, n_slots), phi, phi_old (n_slots,) float64; active uint8).
-    matvec: precision of the Jacobian applies inside GMRES (PFF_F64 or PFF_F32)."""
-    o = _lib.NewtonOpts(tol, atol, gmres_rtol, omega, restart, gmres_maxiter, max_newton, ls_max, matvec, 0)
+    matvec: precision of the Jacobian applies inside GMRES (PFF_F64 or PFF_F32); phi_tilde: the
+    linearised phase field of the u-equation (device tensor), phi_old when None."""
+    o = _lib.NewtonOpts(tol, atol, gmres_rtol, omega, restart, gmres_maxiter, max_newton, ls_max, matvec, 0,
+                        None if phi_tilde is None else _lib.ptr(phi_tilde))
     info = _lib.SolveInfo()
     st = _lib.lib().pff_newton_pdas_step(problem._h, mg._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(phi_old),
                                          _lib.ptr(active), _lib.ctypes.byref(o), _lib.ctypes.byref(info),

@@ -59,7 +59,7 @@ class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
                 ("omega", ctypes.c_double), ("restart", ctypes.c_int32), ("gmres_maxiter", ctypes.c_int32),
                 ("max_newton", ctypes.c_int32), ("ls_max", ctypes.c_int32), ("matvec_precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("phi_tilde", ctypes.c_void_p)]
 
 
 _lib = None
@@ -103,6 +103,10 @@ _SIGS = [
     ("pff_param_vjp", ctypes.c_int32, [_P, _P, _P, _P, _P]),
     ("pff_tcv_adjoint", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    ("pff_active_set", ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), _P]),
+    ("pff_inverse_diagonal", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64), _P]),
     ("pff_tcv_adjoint_steps", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                                ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                                ctypes.POINTER(SolveInfo), _P]),

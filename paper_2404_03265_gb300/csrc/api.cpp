@@ -11,6 +11,7 @@
 #include "../../include/pff.h"
 #include "kernels.cuh"
 #include "mesh.h"
+#include "solve.cuh"
 #include "state.h"
 
 using namespace pff;
@@ -431,6 +432,7 @@ extern "C" pff_status pff_newton_pdas_step(pff_problem* pb, pff_mg* mg, double* 
       o.restart = opts->restart; o.gmres_maxiter = opts->gmres_maxiter; o.max_newton = opts->max_newton;
       o.ls_max = opts->ls_max;
       o.matvec = opts->matvec_precision;
+      o.phi_tilde = opts->phi_tilde;
     }
     if (o.matvec != PFF_F64 && o.matvec != PFF_F32) return fail(PFF_ERR_INVALID_ARG, "bad matvec precision");
     if (o.restart < 1 || o.restart > 500 || o.max_newton < 0 || o.ls_max < 1 || !(o.omega > 0 && o.omega <= 1))
@@ -559,6 +561,64 @@ extern "C" pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t
       return fail(PFF_ERR_NOT_CONVERGED, "adjoint GMRES did not reach the tolerance at load step " +
                                              std::to_string(st.failed_step));
     }
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_active_set(pff_problem* pb, const double* R, const double* phi, const double* phi_old,
+                                     uint8_t* active, int64_t* n_changed, int64_t* n_active, double* margin,
+                                     void* stream) {
+  PFF_TRY({
+    if (!pb || !R || !phi || !phi_old || !active) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    const cudaStream_t s = cudaStream_t(stream);
+    SolverWS& W = pb->ws;
+    const int64_t n = pb->mesh->m.lay.n_slots;
+    PFF_CUDA(lumped_mass(*pb, W.B + 2 * n, s));
+    PFF_CUDA(cudaMemcpyAsync(W.act_prev, active, n, cudaMemcpyDeviceToDevice, s));
+    PFF_CUDA(cudaMemsetAsync(W.stats, 0, 2 * sizeof(unsigned long long), s));
+    const unsigned long long big = 0x7ff0000000000000ull;
+    PFF_CUDA(cudaMemcpyAsync(W.stats + 2, &big, sizeof(big), cudaMemcpyHostToDevice, s));
+    PFF_CUDA(active_set(n, R, W.B + 2 * n, phi, phi_old, pb->mesh->dev.slot_flags, pb->prm.c, W.act_prev, W.act,
+                        W.stats, s));
+    PFF_CUDA(cudaMemcpyAsync(active, W.act, n, cudaMemcpyDeviceToDevice, s));
+    unsigned long long st[3];
+    PFF_CUDA(cudaMemcpyAsync(st, W.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaStreamSynchronize(s));
+    if (n_changed) *n_changed = int64_t(st[0]);
+    if (n_active) *n_active = int64_t(st[1]);
+    if (margin) {
+      double m;
+      std::memcpy(&m, &st[2], sizeof(m));
+      *margin = m;
+    }
+    return PFF_OK;
+  })
+}
+
+extern "C" pff_status pff_inverse_diagonal(const pff_mg* mg, int32_t level, int32_t block, double* out,
+                                           int32_t* X_host, int32_t* Y_host, int64_t capacity, int64_t* n_out,
+                                           void* stream) {
+  PFF_TRY({
+    if (!mg) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (!mg->ready) return fail(PFF_ERR_STATE, "pff_mg_setup has not been called");
+    const Mesh& M = mg->pb->mesh->m;
+    const DevMesh& D = mg->pb->mesh->dev;
+    if (level < 0 || level >= int32_t(D.levels.size())) return fail(PFF_ERR_INVALID_ARG, "bad level");
+    if (block != 0 && block != 1) return fail(PFF_ERR_INVALID_ARG, "bad block");
+    const MGBlock& B = mg->blk[block];
+    const DevLevel& lv = D.levels[level].lv;
+    const int64_t n = int64_t(B.ncomp) * lv.n_slots;
+    if (n_out) *n_out = n;
+    if (out) {
+      if (capacity < n) return fail(PFF_ERR_INVALID_ARG, "output capacity too small");
+      PFF_CUDA(cudaMemcpyAsync(out, B.dinv64 + B.ncomp * lv.off, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                               cudaStream_t(stream)));
+    }
+    const LevelMesh& lm = M.levels[level];
+    if (X_host) std::memcpy(X_host, lm.slot_X.data(), lm.slot_X.size() * sizeof(int32_t));
+    if (Y_host) std::memcpy(Y_host, lm.slot_Y.data(), lm.slot_Y.size() * sizeof(int32_t));
     return PFF_OK;
   })
 }

@@ -57,7 +57,13 @@ __global__ void k_active(int64_t n, const double* __restrict__ R, const double* 
     const uint8_t f = flags[s];
     uint8_t a = 0;
     if ((f & 1) && !(f & 4)) {
-      const double ind = R[2 * n + s] / B[s] + c * (phi[s] - phio[s]);
+      // c > 0: constant c; c <= 0: c_i = 2 |lambda_i / (phi_i - phi_old_i)| (Sec. 2), so that
+      // c_i (phi_i - phi_old_i) = 2 |lambda_i| sign(phi_i - phi_old_i).  Products and sums are
+      // rounded separately (no contraction), as in the reference evaluation of the rule.
+      const double lam = __ddiv_rn(R[2 * n + s], B[s]);
+      const double d = __dsub_rn(phi[s], phio[s]);
+      const double ind = c > 0.0 ? __dadd_rn(lam, __dmul_rn(c, d))
+                                 : __dadd_rn(lam, d > 0.0 ? 2.0 * fabs(lam) : (d < 0.0 ? -2.0 * fabs(lam) : 0.0));
       a = ind > 0.0 ? 1 : 0;
       // |ind| as its IEEE bit pattern: ordered like the value for non-negative doubles
       const double ai = fabs(ind);

@@ -235,6 +235,8 @@ cudaError_t total_crack_volume(pff_problem& pb, const double* u, const double* p
 // One load step of Algorithm 2.  u (2 n), phi (n) are updated in place; active (n) in/out.
 cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi, const double* phi_old,
                              uint8_t* active, const NewtonOpts& o, NewtonInfo& info, cudaStream_t s) {
+  // phi_tilde of the u-equation: the old step unless an extrapolation is given (Sec. 2)
+  const double* phit = o.phi_tilde ? o.phi_tilde : phi_old;
   const Mesh& M = pb.mesh->m;
   const DevMesh& D = pb.mesh->dev;
   SolverWS& W = pb.ws;
@@ -245,8 +247,8 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
   RET(cudaMemcpyAsync(W.act_prev, active, n, cudaMemcpyDeviceToDevice, s));
   double r0 = -1.0;
   for (int k = 0; k <= o.max_newton; ++k) {
-    // residual and active set at U^k (phi_tilde = phi_old for the load step)
-    RET(leaf_residual(pb, u, phi, phi_old, W.R, s));
+    // residual and active set at U^k
+    RET(leaf_residual(pb, u, phi, phit, W.R, s));
     RET(cudaMemsetAsync(W.stats, 0, 2 * sizeof(unsigned long long), s));
     const unsigned long long big = 0x7ff0000000000000ull;
     RET(cudaMemcpyAsync(W.stats + 2, &big, sizeof(big), cudaMemcpyHostToDevice, s));
@@ -273,7 +275,7 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     }
     if (k == o.max_newton) break;
     // linearisation, constraints, right-hand side with the inhomogeneous constraint on A
-    RET(launch_set_lin(n, u, phi, phi_old, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
+    RET(launch_set_lin(n, u, phi, phit, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
     pb.has_state = true;
     RET(launch_leaf_cmask(n, D.slot_flags, W.act, pb.cmask, s));
     RET(newton_du0(n, W.act, phi, phi_old, W.du0, s));
@@ -296,7 +298,7 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     for (int l = 1; l <= o.ls_max; ++l) {
       RET(axpby(2 * n, W.ut, u, 1.0, W.dU, w, s));
       RET(axpby(n, W.ut + 2 * n, phi, 1.0, W.dU + 2 * n, w, s));
-      RET(leaf_residual(pb, W.ut, W.ut + 2 * n, phi_old, W.R, s));
+      RET(leaf_residual(pb, W.ut, W.ut + 2 * n, phit, W.R, s));
       RET(newton_residual(n, W.R, W.act, W.ut + 2 * n, phi_old, D.slot_flags, W.res, s));
       double nt = 0.0;
       RET(norm2(pb, n3, W.res, &nt, s));

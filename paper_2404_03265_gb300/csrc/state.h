@@ -104,6 +104,7 @@ struct NewtonOpts {
   double tol = 1e-8, atol = 1e-13, gmres_rtol = 1e-6, omega = 0.5;
   int restart = 50, gmres_maxiter = 500, max_newton = 100, ls_max = 10;
   int matvec = PFF_F64;   // precision of the Jacobian applies inside GMRES
+  const double* phi_tilde = nullptr;   // linearised phase field of the u-equation (phi_old when null)
 };
 
 struct NewtonInfo {

@@ -75,3 +75,24 @@ def test_vcycle_parity(name, frac, prec, tol):
         assert np.all(z[om.is_hanging] == 0.0)
         inf, two = rel_err(z, zref)
         assert inf < tol and two < tol, (blk, prec, inf, two)
+
+
+@pytest.mark.parametrize("name,frac", [("small", 0.0), ("small", 0.05), ("band4_2_4", 0.0)])
+def test_inverse_diagonal(name, frac):
+    """pff_inverse_diagonal against the oracle's 1/diag(A_l) on interior rows, 0 elsewhere (1e-12)."""
+    P, mat, u, phi, phit, active, M = setup_pair(name, frac)
+    pb, mg = lib_mg(P, mat, u, phi, phit, active, "f64")
+    for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
+        for l, lm in enumerate(M.levels):
+            d, X, Y = mg.inverse_diagonal(l, b)
+            d = d.cpu().numpy().reshape(nc, -1)
+            valid = X >= 0
+            assert np.all(d[:, ~valid] == 0.0)
+            key = Y[valid].astype(np.int64) * (lm.Xmax + 1) + X[valid]
+            node = np.searchsorted(lm.key, key)
+            assert np.array_equal(lm.key[node], key)
+            ref = M.B[blk][l].dinv.reshape(nc, -1)[:, node]
+            got = d[:, valid]
+            assert np.array_equal(got == 0.0, ref == 0.0), (blk, l)
+            scale = np.abs(ref).max() if np.abs(ref).max() > 0 else 1.0
+            assert np.abs(got - ref).max() <= 1e-12 * scale, (blk, l)

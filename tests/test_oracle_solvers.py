@@ -93,3 +93,43 @@ def test_tcv_converges_under_refinement():
     assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1]
     # h = 0.110 lies between Table 2's 0.1768 and 0.0884 rows, h = 0.055 between 0.0884 and 0.0442
     assert errs[0][1] < t2[2, 2] and errs[1][1] < t2[3, 2]
+
+
+def test_adaptive_pdas_constant_rule():
+    """c <= 0 applies c_i = 2 |lambda_i / (phi_i - phi_old_i)| per DoF (Sec. 2): the indicator's
+    sign equals that of lambda_i + c_i (phi_i - phi_old_i) written out, and lambda_i where phi_i = phi_old_i."""
+    om = LeafMesh(build_recipe(synth.recipe("tiny")), 1)
+    rng = np.random.Generator(np.random.PCG64(3))
+    nn = om.nn
+    R = rng.normal(size=3 * nn)
+    B = rng.uniform(0.5, 2.0, nn)
+    phi_old = rng.uniform(size=nn)
+    d = rng.choice([-1.0, 0.0, 1.0], size=nn) * rng.uniform(0.1, 1.0, nn)
+    phi = phi_old + d
+    act, ind = solvers.active_set(om, R, B, phi, phi_old, 0.0)
+    lam = R[2 * nn:] / B
+    ok = ~om.is_hanging
+    for i in np.nonzero(ok)[0]:
+        if d[i] != 0.0:
+            ci = 2.0 * abs(lam[i] / (phi[i] - phi_old[i]))
+            ref = lam[i] + ci * (phi[i] - phi_old[i])
+        else:
+            ref = lam[i]
+        assert (ref > 0) == act[i]
+        assert abs(ind[i] - ref) <= 1e-12 * max(1.0, abs(ref))
+    assert not act[~ok].any()
+
+
+def test_adaptive_pdas_constant_same_solution():
+    """The discrete variational inequality has one solution: the load step with the adaptive
+    constant reaches the one of the constant c = 1e4 (same active set, u and phi to 1e-7)."""
+    om = LeafMesh(build_recipe(synth.recipe("small")), 1)
+    h = om.h_min_diag()
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.0, eps=2.0 * h, kappa=1e-10, p=1e-3)
+    u0, po = solvers.sneddon_initial(om, h)
+    u1, p1, a1, i1 = solvers.load_step(om, mat, 1e4, u0, po.copy(), po)
+    u2, p2, a2, i2 = solvers.load_step(om, mat, 0.0, u0, po.copy(), po)
+    assert i1.converged and i2.converged
+    assert np.array_equal(a1, a2)
+    assert np.linalg.norm(u1 - u2) <= 1e-7 * np.linalg.norm(u1)
+    assert np.linalg.norm(p1 - p2) <= 1e-7 * np.linalg.norm(p1)

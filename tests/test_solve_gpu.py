@@ -138,3 +138,63 @@ def test_newton_pdas_load_step(name, prec):
     tcv = pb.tcv(us, ps)
     tref = ops.tcv(om, ops.State(om, uo, po, po))
     assert abs(tcv - tref) < 1e-7 * abs(tref)
+
+
+@pytest.mark.parametrize("name", ["small", "band4_2_4"])
+def test_active_set_call(name):
+    """pff_active_set on the GPU residual against the oracle's active set of its own
+    residual (bit-identical set; changes counted against the previous set)."""
+    import torch
+    P = Pair(name, 1)
+    om = P.om
+    mat = P.material(kappa=1e-3, p=0.2)
+    u, phi, phit = random_linearisation(P, seed=2, u_std=0.05)
+    rng = np.random.Generator(np.random.PCG64(12))
+    phi_old = np.clip(phi + rng.normal(0.0, 1e-4, om.nn), 0.0, 1.0)
+    pb = problem(P, mat)
+    us, ps, pts, pos = dev(P.to_slots(u).T), dev(P.to_slots(phi)), dev(P.to_slots(phit)), dev(P.to_slots(phi_old))
+    R = torch.zeros((3, P.n_slots), dtype=torch.float64, device="cuda")
+    pb.residual(us, ps, pts, R)
+    prev = random_active(P, seed=4, frac=0.3)
+    act = dev(P.to_slots(prev.astype(np.uint8)))
+    changed, n_act, margin = pb.active_set(R, ps, pos, act)
+    st = ops.State(om, u, phi, phit)
+    Rref = ops.condense(om, -ops.residual_form(om, ops.Material(**mat), st))
+    aref, ind = solvers.active_set(om, Rref, ops.lumped_mass(om), phi, phi_old, 1e4)
+    got = P.from_slots(act.cpu().numpy()).astype(bool)
+    assert np.array_equal(got, aref)
+    assert n_act == int(aref.sum()) and changed == int((aref != prev).sum())
+    assert 0 < aref.sum() < om.nn
+    assert abs(margin - np.abs(ind[~om.is_hanging]).min()) <= 1e-9 * np.abs(ind).max()
+
+
+@pytest.mark.parametrize("variant", ["adaptive_c", "phi_tilde"])
+def test_newton_variants(variant):
+    """Load step with the adaptive PDAS constant (c <= 0) or with a phi_tilde other than
+    phi_old, against the oracle's load step with the same setting (same active set,
+    u and phi within 1e-7)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, newton_step
+    P = Pair("small", 1)
+    om = P.om
+    h = om.h_min_diag()
+    mat = P.material()
+    u0, phi_old = solvers.sneddon_initial(om, h)
+    c = 0.0 if variant == "adaptive_c" else 1e4
+    pt = 0.9 * phi_old + 0.1 if variant == "phi_tilde" else None
+    uo, po, ao, io = solvers.load_step(om, ops.Material(**mat), c, u0, phi_old.copy(), phi_old, phi_tilde=pt)
+    assert io.converged
+    from paper_2404_03265_gb300 import Problem
+    pb = Problem(P.lm, **mat, c=c)
+    mg = MG(pb, PFF_F32)
+    us = dev(P.to_slots(u0).T)
+    ps = dev(P.to_slots(phi_old))
+    pos = dev(P.to_slots(phi_old))
+    act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
+    info = newton_step(pb, mg, us, ps, pos, act, phi_tilde=None if pt is None else dev(P.to_slots(pt)))
+    assert info["converged"], info
+    assert np.array_equal(P.from_slots(act.cpu().numpy()).astype(bool), ao)
+    ug = P.from_slots(us.cpu().numpy().T)
+    pg = P.from_slots(ps.cpu().numpy())
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-7
+    assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-7

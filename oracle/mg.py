@@ -188,6 +188,49 @@ def chebyshev(apply_A, dinv, d, lam, degree, lo=0.08, hi=1.2, x0=None):
     return x
 
 
+def ritz_extremes_cg(apply_A, dinv, b, steps=12):
+    """(smallest, largest) Ritz value of `steps` Jacobi-preconditioned CG steps from residual b."""
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    alphas, betas = [], []
+    if rz <= 0:
+        return 0.0, 0.0
+    for _ in range(steps):
+        q = apply_A(p)
+        pq = float(p @ q)
+        if pq <= 0:
+            break
+        alpha = rz / pq
+        r = r - alpha * q
+        z = dinv * r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        if rz_new <= 1e-300:
+            break
+        p = z + beta * p
+        rz = rz_new
+    m = len(alphas)
+    if m == 0:
+        return 0.0, 0.0
+    diag = np.array([1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0) for j in range(m)])
+    off = np.array([np.sqrt(betas[j]) / alphas[j] for j in range(m - 1)])
+    ev = sla.eigh_tridiagonal(diag, off, eigvals_only=True)
+    return float(ev.min()), float(ev.max())
+
+
+def coarse_chebyshev_degree(a, b, tol=1e-3, cap=64):
+    """Smallest degree m with 1 / T_m((b + a) / (b - a)) <= tol (Chebyshev error bound on [a, b])."""
+    sigma = (b + a) / (b - a)
+    for m in range(1, cap + 1):
+        if 1.0 / np.cosh(m * np.arccosh(sigma)) <= tol:
+            return m
+    return cap
+
+
 def lambda_max_cg(apply_A, dinv, b, steps=12):
     """Largest Ritz value of `steps` Jacobi-preconditioned CG steps from residual b."""
     r = b.copy()
@@ -246,8 +289,12 @@ class MG:
     """Block-diagonal local-smoothing V-cycles at a linearisation point."""
 
     def __init__(self, leaf, mat, u, phi, phit, active, E_cells=None, degree=3, lanczos_steps=12,
-                 smooth=(0.08, 1.2), blocks=("uu", "pp")):
+                 smooth=(0.08, 1.2), blocks=("uu", "pp"), coarse="direct"):
+        """coarse: "direct" (dense Cholesky of the level-0 block) or "chebyshev" (Sec. 3.2:
+        Chebyshev-Jacobi on level 0 over [0.9 lambda_min, 1.2 lambda_max] of the Ritz values of the
+        same CG run, degree from coarse_chebyshev_degree)."""
         self.leaf, self.mat, self.degree, self.smooth = leaf, mat, degree, smooth
+        self.coarse = coarse
         Lf = leaf.Lf
         C = leaf.C
         uf = np.stack([C @ u[:, 0], C @ u[:, 1]], 1)
@@ -312,6 +359,13 @@ class MG:
                 blk.lam = lambda_max_cg(blk.apply, blk.dinv, start, lanczos_steps) if blk.interior.any() else 0.0
             # coarse solve on interior DoFs of level 0 (E_0 is empty)
             b0 = bl[0]
+            if coarse == "chebyshev":
+                lm = b0.lm
+                start = np.array([lanczos_start(gx, gy) for gx, gy in zip(lm.gx // 1, lm.gy // 1)])
+                start = np.tile(start, b0.ncomp) * b0.interior
+                lo, hi = ritz_extremes_cg(b0.apply, b0.dinv, start, lanczos_steps) if b0.interior.any() \
+                    else (0.0, 0.0)
+                b0.cheb = (0.9 * lo, 1.2 * hi, coarse_chebyshev_degree(0.9 * lo, 1.2 * hi) if hi > 0 else 0)
             I0 = np.nonzero(b0.interior)[0]
             b0.I0 = I0
             b0.A0 = b0.A[I0][:, I0].toarray() if len(I0) else np.zeros((0, 0))
@@ -355,7 +409,11 @@ class MG:
             d[l - 1][bl[l - 1].fixed] = 0.0
         b0 = bl[0]
         x0 = np.zeros(nc * b0.lm.nn)
-        if len(b0.I0):
+        if self.coarse == "chebyshev":
+            a, b, m = b0.cheb
+            if m > 0:
+                x0 = chebyshev(b0.apply, b0.dinv, d[0], 1.0, m, a, b)
+        elif len(b0.I0):
             x0[b0.I0] = sla.cho_solve(b0.cho, d[0][b0.I0])
         x[0] = x0
         for l in range(1, L + 1):

@@ -137,3 +137,45 @@ def test_preconditioner_reaches_every_free_dof(k):
     PA = np.column_stack([M.vcycle("pp", A[:, j]) for j in free])[free]
     sv = np.linalg.svd(PA, compute_uv=False)
     assert sv.min() > 1e-3 * sv.max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("frac", [0.0, 0.05])
+def test_coarse_chebyshev(k, frac):
+    """The Chebyshev coarse solver of Sec. 3.2: its level-0 error obeys the exact
+    Chebyshev bound over the true spectrum of D^-1 A_0, its interval brackets the
+    Ritz values, and the V-cycle with it stays symmetric."""
+    leaf, mat, u, phi, phit, active = build("small", k, active_frac=frac, u_std=1e-3, phit_one=False)
+    M = mg.MG(leaf, mat, u, phi, phit, active, coarse="chebyshev")
+    rng = np.random.default_rng(5)
+    for blk in ("uu", "pp"):
+        b0 = M.B[blk][0]
+        a, b, m = b0.cheb
+        if not b0.interior.any():   # every level-0 DoF fixed: nothing to solve
+            assert m == 0
+            continue
+        assert 0 < a < b and m >= 1
+        I = np.nonzero(b0.interior)[0]
+        A0 = b0.A[I][:, I].toarray()
+        Dh = np.sqrt(b0.dinv[I])
+        lam = np.linalg.eigvalsh(Dh[:, None] * A0 * Dh[None, :])    # spectrum of D^-1 A_0
+        d = np.zeros(b0.A.shape[0])
+        d[I] = rng.normal(size=len(I))
+        x_direct = np.zeros_like(d)
+        x_direct[I] = np.linalg.solve(A0, d[I])
+        x_cheb = mg.chebyshev(b0.apply, b0.dinv, d, 1.0, m, a, b)
+        e = x_cheb - x_direct
+        theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+        Tm = lambda t: np.cosh(m * np.arccosh(t)) if t >= 1 else (np.cos(m * np.arccos(t)) if t > -1 else
+                                                                   (-1) ** m * np.cosh(m * np.arccosh(-t)))
+        factor = max(abs(Tm((theta - l) / delta)) for l in lam) / Tm(theta / delta)
+        eA = np.sqrt(e[I] @ A0 @ e[I])
+        xA = np.sqrt(x_direct[I] @ A0 @ x_direct[I])
+        assert eA <= factor * xA * (1 + 1e-9), (blk, eA / xA, factor)
+    nn = leaf.nn
+    for blk, n, free in (("uu", 2 * nn, np.tile(~leaf.dirichlet & ~leaf.is_hanging, 2)),
+                         ("pp", nn, ~active & ~leaf.is_hanging)):
+        x = rng.normal(size=n) * free
+        y = rng.normal(size=n) * free
+        zx, zy = M.vcycle(blk, x) * free, M.vcycle(blk, y) * free
+        assert abs(x @ zy - y @ zx) < 1e-10 * abs(x @ zy)

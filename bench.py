@@ -216,7 +216,7 @@ def time_e2e(mesh, dtype, steps, warmup):
 SOLVE_LOADS = (1e-3, 1.5e-3, 2e-3)
 
 
-def time_solve(precision, loads=SOLVE_LOADS, matvec=None):
+def time_solve(precision, loads=SOLVE_LOADS, matvec=None, coarse="direct"):
     """Load steps of Algorithm 2 on the 1,043,811-DoF band-refined crack mesh
     (16x16 coarse, 5 global, 7 band steps; Q1): line-search Newton / PDAS with
     FP64 GMRES preconditioned by the block V-cycle in the given precision.
@@ -236,7 +236,7 @@ def time_solve(precision, loads=SOLVE_LOADS, matvec=None):
     po_h[valid] = synth.crack_phi_old(x, y, h)
     m = synth.material(h_min=h)
     pb = Problem(mesh, E=m["E"], nu=m["nu"], Gc=m["Gc"], eps=m["eps"], kappa=m["kappa"], p=loads[0], c=m["c"])
-    mg = MG(pb, precision)
+    mg = MG(pb, precision, coarse=coarse)
     dev = torch.device("cuda")
     u = torch.zeros((2, ns), dtype=torch.float64, device=dev)
     phi = torch.tensor(po_h, device=dev)
@@ -526,16 +526,18 @@ def main():
         from paper_2404_03265_gb300 import PFF_F32, PFF_F64
         r32, u32, p32 = time_solve(PFF_F32)
         r32d, u32d, p32d = time_solve(PFF_F32, matvec=PFF_F64)
+        r32c, u32c, p32c = time_solve(PFF_F32, matvec=PFF_F64, coarse="chebyshev")
         r64, u64, p64 = time_solve(PFF_F64)
         line["solve"] = {
             "workload": "solve: 16x16 coarse on (-10,10)^2, 5 global + 7 band refinements toward the crack "
                         "(|x|<=1+2h_min, |y|<=2h_min), Q1, %d DoFs; Sneddon crack, E=1, nu=0.2, G_c=1, "
                         "l=2h_min, kappa=1e-10, c=1e4; p = %s" % (r32["dofs"], ", ".join("%g" % p for p in SOLVE_LOADS)),
             "unit": "s/load step", "newton_tol": 1e-8, "gmres_rtol": 1e-6,
-            "fp32_mg": r32, "fp32_mg_fp64_matvec": r32d, "fp64_mg": r64,
+            "fp32_mg": r32, "fp32_mg_fp64_matvec": r32d, "fp32_mg_chebyshev_coarse": r32c, "fp64_mg": r64,
             "note": "fp32_mg: V-cycle and the Jacobian applies inside GMRES in FP32 (Krylov basis, "
                     "orthogonalisation, Givens, residual, line search, active set, lambda_max and coarse solve in "
-                    "FP64); fp32_mg_fp64_matvec: FP32 V-cycle only; fp64_mg: everything in FP64",
+                    "FP64); fp32_mg_fp64_matvec: FP32 V-cycle only; fp32_mg_chebyshev_coarse: the same with the "
+                    "Chebyshev-Jacobi coarse solver instead of the direct one; fp64_mg: everything in FP64",
             "speedup_fp32_mg": r64["s_per_load_step"] / r32["s_per_load_step"],
             "fp32_vs_fp64_rel_l2": {"u": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
                                     "phi": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))},

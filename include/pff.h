@@ -167,6 +167,12 @@ pff_status pff_inverse_diagonal(const pff_mg* mg, int32_t level, int32_t block, 
                                 int32_t* Y_host, int64_t capacity, int64_t* n_out, void* stream);
 /* lambda_max estimates per level (host array of finest_level + 1 doubles; entry 0 unused) */
 pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam_host, int32_t n);
+/* Coarse-level solver of the V-cycle: mode 0 (default) a direct FP64 solve of the
+ * level-0 block; mode 1 Chebyshev-Jacobi on level 0 (Sec. 3.2: the extreme
+ * eigenvalues of the same CG run give the interval [0.9 lambda_min, 1.2
+ * lambda_max]; the degree is the smallest with a Chebyshev error bound of 1e-3,
+ * at most 64).  Takes effect at the next pff_mg_setup.                         */
+pff_status pff_mg_set_coarse(pff_mg* mg, int32_t mode);
 void pff_mg_destroy(pff_mg* mg);
 
 /* ---- residual, GMRES, Newton / primal-dual active set ---------------------

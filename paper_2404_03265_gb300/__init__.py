@@ -162,11 +162,14 @@ class Problem:
 class MG:
     """Block-diagonal GMG preconditioner (u-u block 0, phi-phi block 1) of a Problem."""
 
-    def __init__(self, problem, precision=PFF_F32):
+    def __init__(self, problem, precision=PFF_F32, coarse="direct"):
+        """coarse: "direct" (FP64 solve of the level-0 block) or "chebyshev" (Sec. 3.2)."""
         self.problem = problem
         h = _lib.ctypes.c_void_p()
         _lib.check(_lib.lib().pff_mg_create(problem._h, precision, _lib.ctypes.byref(h)))
         self._h = h
+        if coarse != "direct":
+            _lib.check(_lib.lib().pff_mg_set_coarse(self._h, {"chebyshev": 1}[coarse]))
         self.n_levels = problem.mesh.info["finest_level"] + 1
 
     def setup(self, stream=None):

@@ -622,3 +622,14 @@ extern "C" pff_status pff_inverse_diagonal(const pff_mg* mg, int32_t level, int3
     return PFF_OK;
   })
 }
+
+extern "C" pff_status pff_mg_set_coarse(pff_mg* mg, int32_t mode) {
+  PFF_TRY({
+    if (!mg) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (mode != 0 && mode != 1) return fail(PFF_ERR_INVALID_ARG, "bad coarse mode");
+    mg->coarse_mode = mode;
+    mg->ready = false;
+    mg_release_graphs(*mg);
+    return PFF_OK;
+  })
+}

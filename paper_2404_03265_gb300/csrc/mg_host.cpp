@@ -55,6 +55,42 @@ double tridiag_max_eig(const std::vector<double>& d, const std::vector<double>& 
   return 0.5 * (lo + hi);
 }
 
+// Smallest eigenvalue of the same symmetric tridiagonal matrix (bisection on the Sturm count).
+double tridiag_min_eig(const std::vector<double>& d, const std::vector<double>& e) {
+  const int m = int(d.size());
+  if (m == 0) return 0.0;
+  double lo = d[0], hi = d[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < m - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      const double qq = (q == 0.0) ? 1e-300 : q;
+      q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), 1e-300); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Smallest degree m with 1 / T_m((b + a) / (b - a)) <= tol (Chebyshev error bound on [a, b]).
+int chebyshev_degree(double a, double b, double tol = 1e-3, int cap = 64) {
+  const double sigma = (b + a) / (b - a);
+  for (int m = 1; m <= cap; ++m)
+    if (1.0 / std::cosh(m * std::acosh(sigma)) <= tol) return m;
+  return cap;
+}
+
 // Dense Cholesky A = L L^T in place (lower), then A^{-1} via two triangular solves per column.
 bool dense_spd_inverse(int n, std::vector<double>& A, std::vector<double>& inv) {
   for (int j = 0; j < n; ++j) {
@@ -187,7 +223,8 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
       CK(mg_invert_diag(lv.n_slots, B.ncomp, mg.diag, lv.flags, mg.cmask + lv.off, B.fixbits,
                         B.dinv64 + B.ncomp * lv.off, B.dinv32 + B.ncomp * lv.off, s));
       B.lam[l] = 0.0;
-      if (l == 0) continue;
+      if (l == 0) { B.c0_a = B.c0_b = 0.0; B.c0_deg = 0; }
+      if (l == 0 && mg.coarse_mode == 0) continue;
       // lambda_max of D^-1 A on the interior: Jacobi-preconditioned CG from a fixed start vector
       const int64_t nn = B.ncomp * n;
       const double* dinv = B.dinv64 + B.ncomp * lv.off;
@@ -222,7 +259,14 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
       for (int j = 0; j < m; ++j) dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
       for (int j = 0; j + 1 < m; ++j) ee[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
       B.lam[l] = tridiag_max_eig(dd, ee);
+      if (l == 0 && B.lam[0] > 0.0) {
+        // Chebyshev coarse solver: both Ritz extremes of the same CG run
+        B.c0_a = 0.9 * tridiag_min_eig(dd, ee);
+        B.c0_b = 1.2 * B.lam[0];
+        B.c0_deg = B.c0_a > 0.0 ? chebyshev_degree(B.c0_a, B.c0_b) : 0;
+      }
     }
+    if (mg.coarse_mode != 0) continue;
     // coarse level: dense FP64 block by probing with (2k+1)^2 colours per component
     const DevMesh::Level& L0 = D.levels[0];
     const LevelMesh& lm0 = M.levels[0];
@@ -324,16 +368,16 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
                      pb.cmask, B.fixbits, s));
   }
   // Chebyshev on level l: solve A v = rhs from v = 0 into out (buffers v, vp, t)
-  auto cheb = [&](int l, const T* rhs, T* out) -> cudaError_t {
+  // Chebyshev on level l over [a, bb], `degree` applications of D^-1: solve A v = rhs
+  // from v = 0 into out (buffers yp, y, t)
+  auto cheb_ab = [&](int l, const T* rhs, T* out, double a, double bb, int degree) -> cudaError_t {
     const DevLevel& lv = D.levels[l].lv;
     const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
-    const double lam = B.lam[l];
-    if (!(lam > 0)) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
-    const double a = mg.lo * lam, bb = mg.hi * lam;
+    if (!(bb > 0) || degree < 1) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
     const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
     // three iterates (current, previous, next) rotate roles each step; the start is
     // chosen so that the last step writes `out`
-    const int steps = mg.degree - 1;
+    const int steps = degree - 1;
     T* w0 = out;
     T* w1 = yp + o;
     T* w2 = y + o;
@@ -346,7 +390,7 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     cudaError_t ee = mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s);
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
-    for (int j = 1; j < mg.degree; ++j) {
+    for (int j = 1; j < degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
       ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s);
       if (ee != cudaSuccess) return ee;
@@ -361,6 +405,11 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     }
     return cudaSuccess;
   };
+  // smoothing on level l >= 1: degree mg.degree on [lo, hi] * lambda_max
+  auto cheb = [&](int l, const T* rhs, T* out) -> cudaError_t {
+    const double lam = B.lam[l];
+    return cheb_ab(l, rhs, out, mg.lo * lam, mg.hi * lam, lam > 0 ? mg.degree : 0);
+  };
   // down sweep
   for (int l = nl - 1; l >= 1; --l) {
     const DevLevel& lv = D.levels[l].lv;
@@ -372,7 +421,8 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
                       d + nc * lc.off, mg.cmask + lc.off, B.fixbits, s));
   }
   // coarse
-  VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s));
+  if (mg.coarse_mode == 1) VC(cheb_ab(0, d, x, B.c0_a, B.c0_b, B.c0_deg));
+  else VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s));
   // up sweep
   for (int l = 1; l < nl; ++l) {
     const DevLevel& lv = D.levels[l].lv;

@@ -161,7 +161,9 @@ struct MGBlock {
   void* y = nullptr;
   void* yp = nullptr;
   void* t = nullptr;
-  std::vector<double> lam;         // lambda_max estimate per level (level 0 unused)
+  std::vector<double> lam;         // lambda_max estimate per level (level 0: only with the Chebyshev coarse solver)
+  double c0_a = 0.0, c0_b = 0.0;   // Chebyshev coarse solver: interval [0.9 lambda_min, 1.2 lambda_max] on level 0
+  int c0_deg = 0;                  // and its degree
   int32_t n_coarse = 0;
   int32_t* coarse_idx = nullptr;   // level-0 entries (comp * n_0 + slot) of the coarse interior
   double* coarse_inv = nullptr;    // dense FP64 inverse, n_coarse^2
@@ -175,6 +177,7 @@ struct pff_mg {
   int precision = PFF_F32;         // arithmetic of the V-cycle
   int degree = 3;                  // Chebyshev degree
   int lanczos_steps = 12;
+  int coarse_mode = 0;             // 0: direct FP64 solve on level 0, 1: Chebyshev-Jacobi (Sec. 3.2)
   double lo = 0.08, hi = 1.2;      // smoothing range [lo, hi] * lambda_max
   pff::DevAllocs mem;
   double* lin64 = nullptr;         // 4 * lev_total (level linearisation)

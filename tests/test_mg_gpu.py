@@ -96,3 +96,39 @@ def test_inverse_diagonal(name, frac):
             assert np.array_equal(got == 0.0, ref == 0.0), (blk, l)
             scale = np.abs(ref).max() if np.abs(ref).max() > 0 else 1.0
             assert np.abs(got - ref).max() <= 1e-12 * scale, (blk, l)
+
+
+@pytest.mark.parametrize("name,frac", [("small", 0.0), ("small", 0.05), ("band4_2_4", 0.0)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_vcycle_chebyshev_coarse(name, frac, prec, tol):
+    """V-cycle with the Chebyshev coarse solver of Sec. 3.2 against the oracle's (same
+    reading of interval and degree), and the level-0 lambda_max (1e-9)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, Problem
+    P, mat, u, phi, phit, active, _ = setup_pair(name, frac)
+    om = P.om
+    nn = om.nn
+    M = omg.MG(om, ops.Material(**mat), u, phi, phit, active, coarse="chebyshev")
+    pb = Problem(P.lm, **mat)
+    pb.set_state(torch.tensor(P.to_slots(u).T.copy(), device="cuda"), torch.tensor(P.to_slots(phi), device="cuda"),
+                 torch.tensor(P.to_slots(phit), device="cuda"))
+    pb.set_active(torch.tensor(P.to_slots(active.astype(np.uint8)), device="cuda"))
+    mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32, coarse="chebyshev")
+    mg.setup()
+    rng = np.random.default_rng(3)
+    for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
+        lam = mg.lam(b)
+        ref = M.B[blk][0].cheb[1] / 1.2
+        assert abs(lam[0] - ref) <= 1e-9 * max(abs(ref), 1e-300), (blk, lam[0], ref)
+        r = rng.normal(size=(nn, nc))
+        zref = M.vcycle(blk, np.concatenate([r[:, c] for c in range(nc)]))
+        zref = np.stack([zref[c * nn:(c + 1) * nn] for c in range(nc)], 1)
+        rs = P.to_slots(r)
+        rt = torch.tensor(rs.T.copy() if nc == 2 else rs[:, 0].copy(), device="cuda")
+        zt = torch.full_like(rt, float("nan"))
+        mg.vcycle(b, rt, zt)
+        torch.cuda.synchronize()
+        zs = zt.cpu().numpy()
+        z = P.from_slots(zs.T if nc == 2 else zs[:, None])
+        inf, two = rel_err(z, zref)
+        assert inf < tol and two < tol, (blk, prec, inf, two)

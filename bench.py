@@ -266,8 +266,17 @@ def time_solve(precision, loads=SOLVE_LOADS, matvec=None, coarse="direct"):
         phi_old.copy_(phi)
     uh = u.cpu().numpy()[:, valid]
     ph = phi.cpu().numpy()[valid]
+    # COD profile of the last step (Sec. 4) beside the closed forms: the paper prints
+    # 2 p l0 / E' sqrt(1 - x^2 / l0^2); the one consistent with TCV_ref is twice that
+    xs = np.linspace(-0.9, 0.9, 19)
+    cod = pb.cod(u, phi, xs)
+    p_last = loads[-1]
+    base = p_last / (m["E"] / (1.0 - m["nu"] ** 2)) * np.sqrt(1.0 - xs ** 2)
     return {"dofs": 3 * info["n_nodes"], "steps": steps,
-            "s_per_load_step": float(np.mean([st["s"] for st in steps]))}, uh, ph
+            "s_per_load_step": float(np.mean([st["s"] for st in steps])),
+            "cod": {"x": [float(v) for v in xs], "cod": [float(v) for v in cod],
+                    "rel_err_vs_4pl0_over_Eprime": float(np.max(np.abs(cod - 4.0 * base) / (4.0 * base))),
+                    "rel_err_vs_2pl0_over_Eprime": float(np.max(np.abs(cod - 2.0 * base) / (2.0 * base)))}}, uh, ph
 
 
 LARGE_LOADS = (1e-3, 1.5e-3, 2e-3, 2.5e-3, 3e-3)

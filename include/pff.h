@@ -261,6 +261,13 @@ pff_status pff_residual(pff_problem* pb, const double* u, const double* phi, con
 pff_status pff_lumped_mass(pff_problem* pb, double* B, void* stream);
 /* Total crack volume integral of u . grad phi (Sec. 4) into *out_host (synchronises). */
 pff_status pff_tcv(pff_problem* pb, const double* u, const double* phi, double* out_host, void* stream);
+/* Crack opening displacement (Sec. 4): COD(x) = integral over y of u . grad phi
+ * along the vertical line at each x_host[i] (host, n_x values), by the
+ * (k+1)-point Gauss rule in y on every leaf cell the line crosses (a cell
+ * [x0, x0 + hx) contains x when x0 <= x < x0 + hx).  u: 2*n_slots, phi: n_slots
+ * (device).  cod_host: n_x doubles (host).  Synchronises.                    */
+pff_status pff_cod(pff_problem* pb, const double* u, const double* phi, const double* x_host, int32_t n_x,
+                   double* cod_host, void* stream);
 /* Left-preconditioned GMRES on G~ x = rhs (transpose != 0: G~^T) with the block
  * V-cycle preconditioner of mg, x0 = 0; synchronises.  Errors:
  * PFF_ERR_NOT_CONVERGED, PFF_ERR_GMRES_BREAKDOWN, PFF_ERR_NONFINITE (info filled). */

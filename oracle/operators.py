@@ -269,3 +269,36 @@ def condense(mesh, r):
 def distribute(mesh, x):
     """x_full = C x: hanging entries from their parents."""
     return C3(mesh) @ x
+
+
+def cod(mesh, st, xs):
+    """COD(x) = integral over y of u . grad phi along the vertical line at x (Sec. 4)
+    for every x in xs: the (k+1)-point Gauss rule in y on each leaf cell the line
+    crosses.  A cell [x0, x0 + hx) contains x when x0 <= x < x0 + hx, with
+    x0 = domain x0 + i hx in FP64; a line on a vertical cell edge takes the cells
+    to its right."""
+    from .fe import gauss01, lagrange1d
+    tr = mesh.tree
+    k = mesh.k
+    eta, w = gauss01(k + 1)
+    Le, dLe = lagrange1d(k, eta)            # (k+1, nq) in y
+    xs = np.asarray(xs, dtype=np.float64)
+    out = np.zeros(len(xs))
+    for level, idx in level_groups(mesh):
+        hx, hy = tr.hx(level), tr.hy(level)
+        x0 = tr.x0 + mesh.cells[idx, 1] * hx
+        for n, x in enumerate(xs):
+            sel = np.nonzero((x0 <= x) & (x < x0 + hx))[0]
+            for c in sel:
+                t = (x - x0[c]) / hx
+                Lx, dLx = lagrange1d(k, [t])
+                cn = mesh.cell_nodes[idx[c]].reshape(k + 1, k + 1)   # [b][a]
+                ux, uy, ph = st.u[cn, 0], st.u[cn, 1], st.phi[cn]
+                tot = 0.0
+                for q in range(k + 1):
+                    Nab = Le[:, q][:, None] * Lx[:, 0][None, :]          # [b][a]
+                    dxab = Le[:, q][:, None] * dLx[:, 0][None, :] / hx
+                    dyab = dLe[:, q][:, None] * Lx[:, 0][None, :] / hy
+                    tot += w[q] * ((Nab * ux).sum() * (dxab * ph).sum() + (Nab * uy).sum() * (dyab * ph).sum())
+                out[n] += hy * tot
+    return out

@@ -152,6 +152,14 @@ class Problem:
                                       _lib.stream_ptr(stream)))
         return out.value
 
+    def cod(self, u, phi, xs, stream=None):
+        """COD(x) = integral over y of u . grad phi along the vertical lines x = xs (Sec. 4)."""
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        out = np.zeros(len(xs))
+        _lib.check(_lib.lib().pff_cod(self._h, _lib.ptr(u), _lib.ptr(phi), _lib.ptr(xs), len(xs), _lib.ptr(out),
+                                      _lib.stream_ptr(stream)))
+        return out
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:

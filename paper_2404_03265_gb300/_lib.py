@@ -94,6 +94,7 @@ _SIGS = [
     ("pff_residual", ctypes.c_int32, [_P, _P, _P, _P, _P, _P]),
     ("pff_lumped_mass", ctypes.c_int32, [_P, _P, _P]),
     ("pff_tcv", ctypes.c_int32, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("pff_cod", ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32, _P, _P]),
     ("pff_gmres_solve", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.POINTER(SolveInfo), _P]),
     ("pff_newton_pdas_step", ctypes.c_int32, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(NewtonOpts),

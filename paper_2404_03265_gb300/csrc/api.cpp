@@ -633,3 +633,16 @@ extern "C" pff_status pff_mg_set_coarse(pff_mg* mg, int32_t mode) {
     return PFF_OK;
   })
 }
+
+extern "C" pff_status pff_cod(pff_problem* pb, const double* u, const double* phi, const double* x_host, int32_t n_x,
+                              double* cod_host, void* stream) {
+  PFF_TRY({
+    if (!pb || !u || !phi || (n_x > 0 && (!x_host || !cod_host))) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (n_x < 0) return fail(PFF_ERR_INVALID_ARG, "n_x < 0");
+    std::string e = ensure_workspace(*pb, 50);
+    if (!e.empty()) return fail(PFF_ERR_OOM, e);
+    e = cod_profile(*pb, u, phi, x_host, n_x, cod_host, cudaStream_t(stream));
+    if (!e.empty()) return fail(PFF_ERR_CUDA, "pff_cod: " + e);
+    return PFF_OK;
+  })
+}

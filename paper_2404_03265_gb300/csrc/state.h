@@ -238,6 +238,9 @@ cudaError_t param_vjp(pff_problem& pb, const double* w, double* gE_cells, double
 cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const double* phi, const double* phi_old,
                         const uint8_t* active, double rtol, int restart, int maxiter, double* gE, double* g_host,
                         GmresResult& gr, std::string& err, cudaStream_t s);
+// COD(x) profile (qoi.cu): x host array of nx line positions, result to out_host; synchronises
+std::string cod_profile(pff_problem& pb, const double* u, const double* phi, const double* x, int nx, double* out_host,
+                        cudaStream_t s);
 // cell kernels (cells.cu)
 cudaError_t cells_scatter(int32_t n, const double* v, const int32_t* slot, double* out64, float* out32,
                           cudaStream_t s);

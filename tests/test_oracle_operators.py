@@ -153,3 +153,23 @@ def test_lumped_mass_and_tcv():
     assert abs(ops.tcv(m, st) - 4000.0) < 1e-9
     st = ops.State(m, np.stack([0 * x, y], 1), y.copy(), np.ones(m.nn))
     assert abs(ops.tcv(m, st)) < 1e-9
+
+
+@pytest.mark.parametrize("name,k", [("tiny", 1), ("small", 1), ("small", 2)])
+def test_cod_linear_fields_closed_form(name, k):
+    """For linear u and phi (exactly represented, also across hanging nodes) u . grad phi is
+    linear in y, so COD(x) = int_{-10}^{10} (u_x phi_x + u_y phi_y) dy has a closed form."""
+    om = LeafMesh(build_recipe(synth.recipe(name)), k)
+    x, y = om.node_xy()
+    a, b, c, d, e, f, g, hh, q = 0.3, -0.2, 0.5, 0.1, 0.4, -0.3, 0.7, 0.25, -0.15
+    u = np.stack([a + b * x + c * y, d + e * x + f * y], 1)
+    phi = g + hh * x + q * y
+    st = ops.State(om, u, phi, phi)
+    xs = np.array([-9.37, -3.1, -0.4, 0.0, 1.234, 7.77])
+    got = ops.cod(om, st, xs)
+    # integral over y in (-10, 10) of (a + b x + c y) hh + (d + e x + f y) q
+    ref = 20.0 * ((a + b * xs) * hh + (d + e * xs) * q)   # the odd terms in y integrate to 0
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12), (got, ref)
+    # the same field's TCV, integral of u . grad phi over the domain
+    tcv = ops.tcv(om, st)
+    assert abs(tcv - 20.0 * 20.0 * (a * hh + d * q)) <= 1e-10 * max(1.0, abs(tcv))

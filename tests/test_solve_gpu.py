@@ -198,3 +198,25 @@ def test_newton_variants(variant):
     pg = P.from_slots(ps.cpu().numpy())
     assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-7
     assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-7
+
+
+@pytest.mark.parametrize("name,k", [("small", 1), ("band4_2_4", 1), ("small", 2)])
+def test_cod_profile(name, k):
+    """pff_cod against the oracle's COD(x) on a random state (1e-12) and against the
+    closed form for linear fields."""
+    from paper_2404_03265_gb300 import Problem
+    P = Pair(name, k)
+    om = P.om
+    mat = P.material()
+    u, phi, phit = random_linearisation(P, seed=6, u_std=0.1)
+    pb = Problem(P.lm, **mat)
+    xs = np.array([-9.9, -2.5, -1.0 + 1e-3, -0.3, 0.0, 0.77, 3.3, 9.999])
+    got = pb.cod(dev(P.to_slots(u).T), dev(P.to_slots(phi)), xs)
+    ref = ops.cod(om, ops.State(om, u, phi, phi), xs)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (got, ref)
+    x, y = om.node_xy()
+    ul = np.stack([0.3 - 0.2 * x + 0.5 * y, 0.1 + 0.4 * x - 0.3 * y], 1)
+    pl = 0.7 + 0.25 * x - 0.15 * y
+    got = pb.cod(dev(P.to_slots(ul).T), dev(P.to_slots(pl)), xs)
+    ref = 20.0 * ((0.3 - 0.2 * xs) * 0.25 + (0.1 + 0.4 * xs) * -0.15)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12), (got, ref)

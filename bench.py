@@ -255,6 +255,8 @@ def time_solve(precision, loads=SOLVE_LOADS, matvec=None, coarse="direct"):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         tcv = pb.tcv(u, phi)
+        ph_h = phi.cpu().numpy()[valid]
+        half = float(np.abs(x[ph_h < 0.5]).max()) if (ph_h < 0.5).any() else 0.0
         eprime = m["E"] / (1.0 - m["nu"] ** 2)
         tcv_ref = 2.0 * np.pi * p * 1.0 ** 2 / eprime
         k = max(r["newton"], 1)
@@ -262,7 +264,8 @@ def time_solve(precision, loads=SOLVE_LOADS, matvec=None, coarse="direct"):
                       "gmres_max": r["gmres_max"], "gmres": r["gmres"], "linesearch_failures": r["linesearch_failures"],
                       "s_mg_setup": r["time_mg_setup"], "s_gmres": r["time_gmres"],
                       "active": r["active_size"], "converged": bool(r["converged"]), "status": r["status"],
-                      "residual": r["residual"], "tcv": tcv, "tcv_rel_err": abs(tcv - tcv_ref) / tcv_ref})
+                      "residual": r["residual"], "tcv": tcv, "tcv_rel_err": abs(tcv - tcv_ref) / tcv_ref,
+                      "crack_half_length": half})
         phi_old.copy_(phi)
     uh = u.cpu().numpy()[:, valid]
     ph = phi.cpu().numpy()[valid]

@@ -220,3 +220,43 @@ def test_cod_profile(name, k):
     got = pb.cod(dev(P.to_slots(ul).T), dev(P.to_slots(pl)), xs)
     ref = 20.0 * ((0.3 - 0.2 * xs) * 0.25 + (0.1 + 0.4 * xs) * -0.15)
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-12), (got, ref)
+
+
+def test_propagating_crack_sequence():
+    """Load steps p = 0.2 .. 0.65 across the critical pressure (about 0.57 for the continuum):
+    the crack grows, the active set changes from step to step; each GPU step against the
+    oracle step from the same history (same active set, u and phi within 1e-7), phi never
+    above phi_old, and the crack longer at the end."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Problem, newton_step
+    P = Pair("small", 1)
+    om = P.om
+    h = om.h_min_diag()
+    x, _ = om.node_xy()
+    uo, po = solvers.sneddon_initial(om, h)
+    phio = po.copy()
+    act_o = None
+    base = P.material()
+    pb = Problem(P.lm, **base)
+    mg = MG(pb, PFF_F32)
+    us = dev(P.to_slots(uo).T)
+    ps = dev(P.to_slots(po))
+    act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
+    lengths = []
+    for p in (0.2, 0.4, 0.5, 0.55, 0.6, 0.65):
+        mat = ops.Material(**dict(base, p=p))
+        uo, phin, act_o, io = solvers.load_step(om, mat, 1e4, uo, phio.copy(), phio, active_prev=act_o, max_newton=60)
+        assert io.converged
+        pb.set_pressure(p)
+        pold = ps.clone()
+        info = newton_step(pb, mg, us, ps, pold, act, max_newton=60)
+        assert info["converged"], (p, info)
+        assert np.array_equal(P.from_slots(act.cpu().numpy()).astype(bool), act_o), p
+        ug = P.from_slots(us.cpu().numpy().T)
+        pg = P.from_slots(ps.cpu().numpy())
+        assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-7, p
+        assert np.linalg.norm(pg - phin) / np.linalg.norm(phin) < 1e-7, p
+        assert np.all(pg <= P.from_slots(pold.cpu().numpy()) + 1e-12)
+        lengths.append(np.abs(x[pg < 0.5]).max())
+        phio = phin
+    assert lengths[-1] > lengths[0] + 0.3, lengths

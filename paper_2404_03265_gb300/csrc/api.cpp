@@ -329,6 +329,9 @@ extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (!mg) return;
   mg_release_graphs(*mg);
   if (mg->cap_stream) cudaStreamDestroy(mg->cap_stream);
+  if (mg->cap_stream2) cudaStreamDestroy(mg->cap_stream2);
+  if (mg->ev_fork) cudaEventDestroy(mg->ev_fork);
+  if (mg->ev_join) cudaEventDestroy(mg->ev_join);
   mg->mem.release();
   delete mg;
 }

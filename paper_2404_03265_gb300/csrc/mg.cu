@@ -125,6 +125,35 @@ __global__ void k_coarse_gather(int32_t n, const int32_t* idx, const T* d, doubl
   GRID_STRIDE(i, n) tmp[i] = double(d[idx[i]]);
 }
 
+// Gauss-Jordan sweep k: row[] and col[] are row k and column k before the sweep;
+// the sweep writes row k+1 and column k+1 after it into row_n[] and col_n[], so
+// no thread reads an entry another thread of the same sweep writes.
+__global__ void k_gj_init(int32_t n, const double* __restrict__ A, double* rc) {
+  GRID_STRIDE(i, n) {
+    rc[i] = A[i];
+    rc[n + i] = A[i * n];
+  }
+}
+
+__global__ void k_gj_sweep(int32_t n, int32_t k, double* A, const double* __restrict__ rc, double* __restrict__ rcn,
+                           int32_t* bad) {
+  const double* row = rc;
+  const double* col = rc + n;
+  const double p = row[k];
+  if (!(p > 0.0) && blockIdx.x == 0 && threadIdx.x == 0) *bad = 1;
+  const double ip = 1.0 / p;
+  GRID_STRIDE(e, int64_t(n) * n) {
+    const int32_t i = int32_t(e / n), j = int32_t(e - int64_t(i) * n);
+    double v;
+    if (i == k) v = j == k ? ip : row[j] * ip;
+    else if (j == k) v = -col[i] * ip;
+    else v = A[e] - col[i] * row[j] * ip;
+    A[e] = v;
+    if (i == k + 1) rcn[j] = v;
+    if (j == k + 1) rcn[n + i] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_coarse_matvec(int32_t n, const int32_t* idx, const double* __restrict__ A,
                                 const double* __restrict__ tmp, T* x) {
@@ -331,6 +360,17 @@ cudaError_t mg_leaf_init(int64_t ns_leaf, int ncomp, const double* r, double* z,
                                                                    fixbits);
   return cudaGetLastError();
 }
+cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  k_gj_init<<<blocks_for(n), TPB, 0, s>>>(n, A, rc);
+  const unsigned nb = blocks_for(int64_t(n) * n);
+  for (int32_t k = 0; k < n; ++k) {
+    k_gj_sweep<<<nb, TPB, 0, s>>>(n, k, A, rc + (k & 1) * 2 * int64_t(n), rc + ((k + 1) & 1) * 2 * int64_t(n), bad);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t mg_coarse(int32_t n, const int32_t* idx, const double* Ainv, const T* d, T* x, double* tmp,
                       cudaStream_t s) {

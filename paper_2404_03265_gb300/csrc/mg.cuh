@@ -57,6 +57,13 @@ cudaError_t mg_copy_out(int32_t n, int ncomp, const int32_t* leaf_slot, const in
 // z = r on fixed leaf DoFs, 0 elsewhere (hanging nodes and holes included)
 cudaError_t mg_leaf_init(int64_t ns_leaf, int ncomp, const double* r, double* z, const uint8_t* leaf_cmask,
                          const uint8_t* leaf_flags, int fixbits, cudaStream_t s);
+// In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by Gauss-Jordan
+// sweeps without pivoting: the pivots are the diagonals of successive Schur
+// complements, positive for an SPD matrix.  rc: scratch of 4 n doubles.  *bad is
+// set to 1 when a pivot is not positive (the matrix is then not SPD and A holds
+// no inverse); it is cleared first.
+cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s);
+
 // coarse solve x[idx] = Ainv (d[idx]) (dense FP64 inverse over the interior entries)
 template <typename T>
 cudaError_t mg_coarse(int32_t n, const int32_t* idx, const double* Ainv, const T* d, T* x, double* tmp,

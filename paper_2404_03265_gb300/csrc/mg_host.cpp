@@ -91,37 +91,6 @@ int chebyshev_degree(double a, double b, double tol = 1e-3, int cap = 64) {
   return cap;
 }
 
-// Dense Cholesky A = L L^T in place (lower), then A^{-1} via two triangular solves per column.
-bool dense_spd_inverse(int n, std::vector<double>& A, std::vector<double>& inv) {
-  for (int j = 0; j < n; ++j) {
-    double s = A[size_t(j) * n + j];
-    for (int k = 0; k < j; ++k) s -= A[size_t(j) * n + k] * A[size_t(j) * n + k];
-    if (!(s > 0)) return false;
-    const double ljj = std::sqrt(s);
-    A[size_t(j) * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      double t = A[size_t(i) * n + j];
-      for (int k = 0; k < j; ++k) t -= A[size_t(i) * n + k] * A[size_t(j) * n + k];
-      A[size_t(i) * n + j] = t / ljj;
-    }
-  }
-  inv.assign(size_t(n) * n, 0.0);
-  std::vector<double> y(n);
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) {
-      double t = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= A[size_t(i) * n + k] * y[k];
-      y[i] = t / A[size_t(i) * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int k = i + 1; k < n; ++k) t -= A[size_t(k) * n + i] * inv[size_t(k) * n + c];
-      inv[size_t(i) * n + c] = t / A[size_t(i) * n + i];
-    }
-  }
-  return true;
-}
-
 #define CK(call)                                              \
   do {                                                        \
     cudaError_t e_ = (call);                                  \
@@ -186,6 +155,7 @@ std::string mg_alloc(pff_mg& mg) {
   mg.partial = mg.mem.alloc<double>(1024);
   mg.sc = mg.mem.alloc<double>(8);
   mg.hist = mg.mem.alloc<double>(2 * 64);
+  mg.spd_bad = mg.mem.alloc<int32_t>(1);
   if (!mg.mem.err.empty()) return mg.mem.err;
   return "";
 }
@@ -195,6 +165,7 @@ std::string mg_alloc(pff_mg& mg) {
 void mg_release_graphs(pff_mg& mg) {
   for (auto& g : mg.vc_exec)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  if (mg.vc_both) { cudaGraphExecDestroy(mg.vc_both); mg.vc_both = nullptr; }
 }
 
 std::string mg_setup(pff_mg& mg, cudaStream_t s) {
@@ -321,18 +292,25 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
             }
           }
         }
-    std::vector<double> inv;
-    if (nI > 0 && !dense_spd_inverse(nI, A, inv)) return "coarse level block is not positive definite";
-    if (B.n_coarse != nI || !B.coarse_idx) {
-      B.coarse_idx = mg.mem.alloc<int32_t>(std::max(nI, 1));
-      B.coarse_inv = mg.mem.alloc<double>(std::max<int64_t>(int64_t(nI) * nI, 1));
-      B.coarse_tmp = mg.mem.alloc<double>(std::max(nI, 1));
+    if (!B.coarse_idx || nI > B.coarse_cap) {
+      const int32_t cap = std::max(nI, 1);
+      B.coarse_idx = mg.mem.alloc<int32_t>(cap);
+      B.coarse_inv = mg.mem.alloc<double>(int64_t(cap) * cap);
+      B.coarse_tmp = mg.mem.alloc<double>(cap);
+      B.coarse_rc = mg.mem.alloc<double>(4 * int64_t(cap));
       if (!mg.mem.err.empty()) return mg.mem.err;
-      B.n_coarse = nI;
+      B.coarse_cap = cap;
     }
+    B.n_coarse = nI;
     if (nI > 0) {
+      // the assembled block goes to the device and is inverted there in place
       CK(cudaMemcpyAsync(B.coarse_idx, eidx.data(), nI * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(B.coarse_inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(B.coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(mg_spd_invert(nI, B.coarse_inv, B.coarse_rc, mg.spd_bad, s));
+      int32_t bad = 0;
+      CK(cudaMemcpyAsync(&bad, mg.spd_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (bad) return "coarse level block is not positive definite";
     }
     CK(cudaStreamSynchronize(s));
   }
@@ -487,6 +465,52 @@ cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStr
     }
   }
   return vcycle_direct(mg, block, r, z, s);
+}
+
+// Capture both blocks' V-cycles as one graph.  They share no buffer (each block
+// has its own level vectors, inverse diagonals and coarse data; the staging
+// vectors are split at 2 n_slots), so the phi block runs on a second branch
+// forked from and joined back into the capture stream.
+static bool precond_capture(pff_mg& mg) {
+  const int64_t n = mg.pb->mesh->m.lay.n_slots;
+  if (!mg.cap_stream && cudaStreamCreateWithFlags(&mg.cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!mg.cap_stream2 && cudaStreamCreateWithFlags(&mg.cap_stream2, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!mg.ev_fork && cudaEventCreateWithFlags(&mg.ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
+  if (!mg.ev_join && cudaEventCreateWithFlags(&mg.ev_join, cudaEventDisableTiming) != cudaSuccess) return false;
+  if (cudaStreamBeginCapture(mg.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  cudaError_t e = cudaEventRecord(mg.ev_fork, mg.cap_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(mg.cap_stream2, mg.ev_fork, 0);
+  if (e == cudaSuccess) e = vcycle_direct(mg, 1, mg.vc_in + 2 * n, mg.vc_out + 2 * n, mg.cap_stream2);
+  if (e == cudaSuccess) e = vcycle_direct(mg, 0, mg.vc_in, mg.vc_out, mg.cap_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(mg.ev_join, mg.cap_stream2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(mg.cap_stream, mg.ev_join, 0);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(mg.cap_stream, &g);
+  bool ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+  if (ok) ok = cudaGraphInstantiate(&mg.vc_both, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    mg.vc_both = nullptr;
+    cudaGetLastError();
+  }
+  return ok;
+}
+
+cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s) {
+  const int64_t n = mg.pb->mesh->m.lay.n_slots;
+  if (mg.graphs_ok && mg.vc_in && mg.vc_out) {
+    if (!mg.vc_both && !precond_capture(mg)) mg.graphs_ok = false;
+    if (mg.vc_both) {
+      const size_t bytes = size_t(3 * n) * sizeof(double);
+      cudaError_t e = cudaMemcpyAsync(mg.vc_in, v, bytes, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaGraphLaunch(mg.vc_both, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(z, mg.vc_out, bytes, cudaMemcpyDeviceToDevice, s);
+      return e;
+    }
+  }
+  cudaError_t e = vcycle_direct(mg, 0, v, z, s);
+  if (e == cudaSuccess) e = vcycle_direct(mg, 1, v + 2 * n, z + 2 * n, s);
+  return e;
 }
 
 template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t);

@@ -131,6 +131,17 @@ __global__ void k_mask_fixed(int64_t n, const uint8_t* __restrict__ cmask, const
   }
 }
 
+// out = x on the fixed rows of cmask (bit 1, 2: u_x, u_y; bit 4: phi), out unchanged elsewhere
+__global__ void k_copy_fixed(int64_t n, const uint8_t* __restrict__ cmask, const double* __restrict__ x,
+                             double* out) {
+  GRID_STRIDE(s, n) {
+    const uint8_t cm = cmask[s];
+    if (cm & 1) out[s] = x[s];
+    if (cm & 2) out[n + s] = x[n + s];
+    if (cm & 4) out[2 * n + s] = x[2 * n + s];
+  }
+}
+
 // adjoint carry to the previous load step: g = (0, 0, -t2 + act (mu_phi - t1_phi))
 __global__ void k_adj_carry(int64_t n, const uint8_t* __restrict__ act, const double* __restrict__ mu,
                             const double* __restrict__ t1, const double* __restrict__ t2, double* g) {
@@ -260,6 +271,11 @@ cudaError_t f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t s) {
 
 cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s) {
   if (n > 0) k_mask_fixed<<<blocks_for(n), TPB, 0, s>>>(n, cmask, x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s) {
+  if (n > 0) k_copy_fixed<<<blocks_for(n), TPB, 0, s>>>(n, cmask, x, out);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ cudaError_t f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
 cudaError_t f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t s);
 // out = x with fixed components (constraint mask) zeroed, 3 blocks of n
 cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
+// out = x on the rows cmask marks fixed; the other rows of out are left as they are
+cudaError_t copy_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
 // g = (0, 0, -t2 + act * (mu_phi - t1_phi)): adjoint right-hand side of the previous load step
 cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
                       cudaStream_t s);

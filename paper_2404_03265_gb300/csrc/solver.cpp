@@ -98,9 +98,7 @@ static cudaError_t norm2(pff_problem& pb, int64_t n, const double* a, double* ou
 
 // P^-1 v for the full vector (u block, phi block)
 static cudaError_t precond(pff_mg& mg, const double* v, double* z, cudaStream_t s) {
-  const int64_t n = mg.pb->mesh->m.lay.n_slots;
-  RET(mg_vcycle(mg, 0, v, z, s));
-  return mg_vcycle(mg, 1, v + 2 * n, z + 2 * n, s);
+  return mg_precond(mg, v, z, s);
 }
 
 cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double* b, double* x, double rtol,
@@ -291,6 +289,10 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     info.t_gmres += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup1).count();
     info.gmres.push_back(gr.iterations);
     if (gr.breakdown) info.gmres_breakdown = true;
+    // G~ is the identity on the fixed rows and couples them to no free row, so the
+    // fixed part of the solution is the right-hand side there, taken exactly
+    // (phi_old - phi on the active set: the step lands on phi_old)
+    RET(copy_fixed(n, pb.cmask, W.rhs, W.dU, s));
     RET(distribute_hanging(n, D.hang, D.nhang, M.k, 3, W.dU, s));
     // line search on the Newton residual under the current active set
     bool accepted = false;

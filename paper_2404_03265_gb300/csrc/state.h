@@ -164,10 +164,11 @@ struct MGBlock {
   std::vector<double> lam;         // lambda_max estimate per level (level 0: only with the Chebyshev coarse solver)
   double c0_a = 0.0, c0_b = 0.0;   // Chebyshev coarse solver: interval [0.9 lambda_min, 1.2 lambda_max] on level 0
   int c0_deg = 0;                  // and its degree
-  int32_t n_coarse = 0;
+  int32_t n_coarse = 0, coarse_cap = 0;
   int32_t* coarse_idx = nullptr;   // level-0 entries (comp * n_0 + slot) of the coarse interior
   double* coarse_inv = nullptr;    // dense FP64 inverse, n_coarse^2
   double* coarse_tmp = nullptr;
+  double* coarse_rc = nullptr;     // 4 n_coarse: pivot rows and columns of the inversion
 };
 
 }  // namespace pff
@@ -192,8 +193,12 @@ struct pff_mg {
   // inputs and outputs pass through fixed staging vectors of 3 * n_slots doubles)
   bool graphs_ok = true;
   cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
-  cudaStream_t cap_stream = nullptr;
+  // both blocks in one graph: the phi block runs on a forked branch beside the u block
+  cudaGraphExec_t vc_both = nullptr;
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double *vc_in = nullptr, *vc_out = nullptr;
+  int32_t* spd_bad = nullptr;      // set by the coarse inversion when a pivot is not positive
 };
 
 namespace pff {
@@ -252,6 +257,8 @@ std::string mg_alloc(pff_mg& mg);
 void mg_release_graphs(pff_mg& mg);
 std::string mg_setup(pff_mg& mg, cudaStream_t s);
 cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s);
+// both blocks of the preconditioner on the full vector (u_x | u_y | phi)
+cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s);
 // level operator y = A_l x of one block (op OP_UU / OP_PP / *_DIAG), precision of T
 template <typename T>
 cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s);

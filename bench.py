@@ -263,6 +263,8 @@ def time_solve(precision, loads=SOLVE_LOADS, matvec=None, coarse="direct"):
         steps.append({"p": p, "s": t, "newton": r["newton"], "gmres_mean": r["gmres_total"] / k,
                       "gmres_max": r["gmres_max"], "gmres": r["gmres"], "linesearch_failures": r["linesearch_failures"],
                       "s_mg_setup": r["time_mg_setup"], "s_gmres": r["time_gmres"],
+                      "s_gmres_apply": r["time_gmres_apply"], "s_gmres_vcycle": r["time_gmres_vcycle"],
+                      "s_gmres_orth": r["time_gmres_orth"],
                       "active": r["active_size"], "converged": bool(r["converged"]), "status": r["status"],
                       "residual": r["residual"], "tcv": tcv, "tcv_rel_err": abs(tcv - tcv_ref) / tcv_ref,
                       "crack_half_length": half})
@@ -332,6 +334,8 @@ def time_large(loads=LARGE_LOADS):
         steps.append({"p": p, "s": e0.elapsed_time(e1) / 1e3, "newton": r["newton"],
                       "gmres_mean": r["gmres_total"] / k, "gmres_max": r["gmres_max"], "active": r["active_size"],
                       "s_mg_setup": r["time_mg_setup"], "s_gmres": r["time_gmres"],
+                      "s_gmres_apply": r["time_gmres_apply"], "s_gmres_vcycle": r["time_gmres_vcycle"],
+                      "s_gmres_orth": r["time_gmres_orth"],
                       "converged": bool(r["converged"]), "status": r["status"], "tcv": tcv,
                       "tcv_rel_err": abs(tcv - 2.0 * np.pi * p / eprime) / (2.0 * np.pi * p / eprime)})
         us.append(u)
@@ -549,7 +553,11 @@ def main():
             "note": "fp32_mg: V-cycle and the Jacobian applies inside GMRES in FP32 (Krylov basis, "
                     "orthogonalisation, Givens, residual, line search, active set, lambda_max and coarse solve in "
                     "FP64); fp32_mg_fp64_matvec: FP32 V-cycle only; fp32_mg_chebyshev_coarse: the same with the "
-                    "Chebyshev-Jacobi coarse solver instead of the direct one; fp64_mg: everything in FP64",
+                    "Chebyshev-Jacobi coarse solver instead of the direct one; fp64_mg: everything in FP64. "
+                    "Per step: s_mg_setup and s_gmres are host wall seconds; s_gmres_apply, s_gmres_vcycle and "
+                    "s_gmres_orth are device seconds (CUDA events) of the operator applies, block V-cycles and "
+                    "Gram-Schmidt inside the GMRES iterations; s - s_mg_setup - s_gmres is residuals, active "
+                    "sets and line search",
             "speedup_fp32_mg": r64["s_per_load_step"] / r32["s_per_load_step"],
             "fp32_vs_fp64_rel_l2": {"u": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
                                     "phi": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))},

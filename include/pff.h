@@ -193,6 +193,13 @@ typedef struct pff_solve_info {
   double time_mg_setup;        /* seconds in multigrid set-up (Newton step)      */
   double time_gmres;           /* seconds in GMRES (Newton step); the rest of the
                                   step is residuals, active sets, line search     */
+  /* device seconds inside the GMRES iterations (CUDA events on the solve stream):
+     operator applies (with their precision conversions), block V-cycles (with
+     their staging copies), and Gram-Schmidt orthogonalisation plus the norm of
+     the new basis vector.  time_gmres minus their sum is host work and waits. */
+  double time_gmres_apply;
+  double time_gmres_vcycle;
+  double time_gmres_orth;
 } pff_solve_info;
 
 typedef struct pff_newton_opts {

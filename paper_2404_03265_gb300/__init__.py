@@ -219,7 +219,8 @@ def gmres(problem, mg, rhs, x, rtol=1e-6, restart=50, maxiter=500, transpose=Fal
     st = _lib.lib().pff_gmres_solve(problem._h, mg._h, int(transpose), _lib.ptr(rhs), _lib.ptr(x), rtol, restart,
                                     maxiter, _lib.ctypes.byref(info), _lib.stream_ptr(stream))
     d = dict(iterations=info.gmres_total, converged=bool(info.converged), initial=info.residual0,
-             estimate=info.residual, status=st)
+             estimate=info.residual, status=st, time_apply=info.time_gmres_apply,
+             time_vcycle=info.time_gmres_vcycle, time_orth=info.time_gmres_orth)
     if check:
         _lib.check(st)
     return d

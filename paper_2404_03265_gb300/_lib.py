@@ -43,7 +43,9 @@ class SolveInfo(ctypes.Structure):
                 ("gmres_max", ctypes.c_int32), ("pad", ctypes.c_int32), ("active_size", ctypes.c_int64),
                 ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("margin", ctypes.c_double),
                 ("gmres_per_newton", ctypes.c_int32 * 128), ("residual_history", ctypes.c_double * 129),
-                ("time_mg_setup", ctypes.c_double), ("time_gmres", ctypes.c_double)]
+                ("time_mg_setup", ctypes.c_double), ("time_gmres", ctypes.c_double),
+                ("time_gmres_apply", ctypes.c_double), ("time_gmres_vcycle", ctypes.c_double),
+                ("time_gmres_orth", ctypes.c_double)]
 
     def to_dict(self):
         n = self.newton_iterations
@@ -52,7 +54,9 @@ class SolveInfo(ctypes.Structure):
                     residual0=self.residual0, residual=self.residual, margin=self.margin,
                     gmres=list(self.gmres_per_newton[:min(n, 128)]),
                     residual_history=list(self.residual_history[:min(n + 1, 129)]),
-                    time_mg_setup=self.time_mg_setup, time_gmres=self.time_gmres)
+                    time_mg_setup=self.time_mg_setup, time_gmres=self.time_gmres,
+                    time_gmres_apply=self.time_gmres_apply, time_gmres_vcycle=self.time_gmres_vcycle,
+                    time_gmres_orth=self.time_gmres_orth)
 
 
 class NewtonOpts(ctypes.Structure):

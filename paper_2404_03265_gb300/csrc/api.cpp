@@ -232,6 +232,8 @@ extern "C" pff_status pff_problem_create(pff_mesh* m, const pff_params* prm, pff
 
 extern "C" void pff_problem_destroy(pff_problem* pb) {
   if (!pb) return;
+  for (auto& e : pb->gm_ev)
+    if (e) cudaEventDestroy(e);
   pb->ws.mem.release();
   pb->bufs.release();
   delete pb;
@@ -332,6 +334,11 @@ extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (mg->cap_stream2) cudaStreamDestroy(mg->cap_stream2);
   if (mg->ev_fork) cudaEventDestroy(mg->ev_fork);
   if (mg->ev_join) cudaEventDestroy(mg->ev_join);
+  for (int i = 0; i <= pff_mg::kSetupStreams; ++i) {
+    if (mg->su_stream[i]) cudaStreamDestroy(mg->su_stream[i]);
+    if (mg->su_done[i]) cudaEventDestroy(mg->su_done[i]);
+  }
+  if (mg->su_start) cudaEventDestroy(mg->su_start);
   mg->mem.release();
   delete mg;
 }
@@ -396,6 +403,9 @@ static void fill_info(const NewtonInfo& in, pff_solve_info* out) {
   for (size_t i = 0; i < in.residual.size() && i < 129; ++i) out->residual_history[i] = in.residual[i];
   out->time_mg_setup = in.t_setup;
   out->time_gmres = in.t_gmres;
+  out->time_gmres_apply = in.t_apply;
+  out->time_gmres_vcycle = in.t_vcycle;
+  out->time_gmres_orth = in.t_orth;
 }
 
 extern "C" pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
@@ -416,6 +426,9 @@ extern "C" pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t trans
       info->converged = gr.converged ? 1 : 0;
       info->residual0 = gr.initial;
       info->residual = gr.estimate;
+      info->time_gmres_apply = gr.t_apply;
+      info->time_gmres_vcycle = gr.t_vcycle;
+      info->time_gmres_orth = gr.t_orth;
     }
     if (gr.breakdown) return fail(PFF_ERR_GMRES_BREAKDOWN, "GMRES breakdown");
     if (!std::isfinite(gr.estimate)) return fail(PFF_ERR_NONFINITE, "non-finite residual in GMRES");

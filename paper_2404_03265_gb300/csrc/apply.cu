@@ -494,10 +494,10 @@ struct __align__(16) Stage {
   uint32_t cm[32];   // constraint-mask words (4 slots per word) of the columns' slots
 };
 
-template <typename T>
+template <typename T, int NR>
 struct HalfSmem {
   Stage<T> st[DEPTH];
-  int32_t code[2][NROWS][32];   // storage codes of the lane columns per strip row (two strips)
+  int32_t code[2][NR][32];   // storage codes of the lane columns per strip row (two strips)
 };
 
 template <typename T>
@@ -661,8 +661,13 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
   }
 }
 
-template <typename T, int OP>
+// RS: node rows per strip (RSEG by default; 1 for latency-bound small level meshes)
+template <typename T, int OP, int RS = RSEG>
 __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MINB64) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
+  static_assert(NB % RS == 0, "strip height must divide the brick");
+  constexpr int SROWS = RS;          // node rows per strip
+  constexpr int SSEG = NB / RS;      // strips per brick
+  constexpr int SREAD = RS + 2;      // node rows a strip reads
   using P = typename VT<T>::T2;
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int half = lane >> 4, hl = lane & 15;
-  HalfSmem<T>& sm = reinterpret_cast<HalfSmem<T>*>(smem_raw)[(threadIdx.x >> 5) * 2 + half];
+  HalfSmem<T, SREAD>& sm = reinterpret_cast<HalfSmem<T, SREAD>*>(smem_raw)[(threadIdx.x >> 5) * 2 + half];
   const int right_lane = (half << 4) | ((hl + 1) & 15);
   const int left_lane = (half << 4) | ((hl + 15) & 15);
   const MatConst<T>& mc = matc<T>(a);
@@ -680,27 +685,27 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   T* yu = reinterpret_cast<T*>(a.yu);
   T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
-  const int nunits = a.lay.nbricks * NSEG;
+  const int nunits = a.lay.nbricks * SSEG;
   // Persistent warps.  Half-warp h of warp w sweeps the strips (units)
   // 2w + h + k * stride, k = 0, 1, ...; their node rows form one continuous
-  // stream j = k * NROWS + i, kept DEPTH-1 rows ahead in the cp.async ring
+  // stream j = k * SREAD + i, kept DEPTH-1 rows ahead in the cp.async ring
   // across strip boundaries.
   const int stride = gridDim.x * WARPS * 2;
   const int ubase0 = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2;
   if (ubase0 >= nunits) return;  // warp-uniform
   const int nrounds = (nunits - ubase0 + stride - 1) / stride;
-  const int nstream = nrounds * NROWS;
+  const int nstream = nrounds * SREAD;
   // codes of strip k into table k & 1 (all 32 lanes: shuffles); returns its pairwise flag
   auto build_codes = [&](int k) -> bool {
     const int unit = ubase0 + k * stride + half;
     const bool valid = unit < nunits;
-    const int b = valid ? unit / NSEG : 0;
-    const int r0 = valid ? (unit % NSEG) * RSEG : 0;
+    const int b = valid ? unit / SSEG : 0;
+    const int r0 = valid ? (unit % SSEG) * SROWS : 0;
     const BrickDesc* bd = a.lay.bricks + b;
     const int nbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
     const int irr = __ldg(&bd->irr);
 #pragma unroll
-    for (int i = 0; i < NROWS; ++i) {
+    for (int i = 0; i < SREAD; ++i) {
       const int r = r0 - 1 + i;
       int32_t cA = regular_code(nbase, nA, r);
       int32_t cB = regular_code(nbase, nB, r);
@@ -719,7 +724,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   int k_issue = 0;
   auto issue_stream = [&](int j) {
     if (j < nstream) {
-      const int k = j / NROWS, i = j - k * NROWS;
+      const int k = j / SREAD, i = j - k * SREAD;
       if (k != k_issue) { pw_issue = build_codes(k); k_issue = k; }
       issue_row<T, OP>(a, pw_issue, sm.code[k & 1][i][2 * hl], sm.code[k & 1][i][2 * hl + 1], sm.st[j % DEPTH], hl);
     }
@@ -736,12 +741,12 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MI
   P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
 #pragma unroll 1
   for (int j = 0; j < nstream; ++j) {
-    const int k = j / NROWS, i = j - k * NROWS;
+    const int k = j / SREAD, i = j - k * SREAD;
     if (i == 0) {
       const int unit = ubase0 + k * stride + half;
       valid = unit < nunits;
-      const int b = valid ? unit / NSEG : 0;
-      r0 = valid ? (unit % NSEG) * RSEG : 0;
+      const int b = valid ? unit / SSEG : 0;
+      r0 = valid ? (unit % SSEG) * SROWS : 0;
       const BrickDesc* bd = a.lay.bricks + b;
       irr = __ldg(&bd->irr);
       own_base = __ldg(bd->nbr_base + 4);
@@ -977,19 +982,34 @@ cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree == 2) return launch_apply_q2<T>(a, op, s);
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
-  const int units = (a.lay.nbricks * NSEG + 1) / 2;  // two strips per warp
   const unsigned blk = 32 * WARPS;
-  const size_t smem = sizeof(HalfSmem<T>) * 2 * WARPS;
-  auto grid_of = [&](const void* fn) -> unsigned {
+  auto grid_of = [&](const void* fn, int strips_per_brick, size_t smem) -> unsigned {
+    const int units = (a.lay.nbricks * strips_per_brick + 1) / 2;  // two strips per warp
     const int full = resident_blocks(fn, int(blk), smem);
     const int need = (units + WARPS - 1) / WARPS;
     return unsigned(need < full ? need : full);
   };
+  const size_t smem = sizeof(HalfSmem<T, NROWS>) * 2 * WARPS;
+  // The level block operators of the V-cycle mostly run on small level meshes,
+  // where one wave of single-row strips covers the mesh: there the shorter
+  // per-strip chain (3 node rows read, 2 cell rows) gives the lower latency.
+  if (op == OP_UU || op == OP_PP) {
+    const size_t smem1 = sizeof(HalfSmem<T, 3>) * 2 * WARPS;
+    const void* fn = op == OP_UU ? reinterpret_cast<const void*>(&apply_q1_kernel<T, OP_UU, 1>)
+                                 : reinterpret_cast<const void*>(&apply_q1_kernel<T, OP_PP, 1>);
+    const int need = ((a.lay.nbricks * NB + 1) / 2 + WARPS - 1) / WARPS;
+    if (need <= resident_blocks(fn, int(blk), smem1)) {
+      const unsigned g = grid_of(fn, NB, smem1);
+      if (op == OP_UU) apply_q1_kernel<T, OP_UU, 1><<<g, blk, smem1, s>>>(a);
+      else apply_q1_kernel<T, OP_PP, 1><<<g, blk, smem1, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   switch (op) {
 #define PFF_LAUNCH(OPV)                                                                        \
     case OPV: {                                                                                \
       const void* fn = reinterpret_cast<const void*>(&apply_q1_kernel<T, OPV>);               \
-      apply_q1_kernel<T, OPV><<<grid_of(fn), blk, smem, s>>>(a);                               \
+      apply_q1_kernel<T, OPV><<<grid_of(fn, NSEG, smem), blk, smem, s>>>(a);                   \
       break;                                                                                   \
     }
     PFF_LAUNCH(OP_FULL)

@@ -37,16 +37,6 @@ __global__ void k_cheb_step(int64_t n, T* xnew, const T* x, const T* xprev, cons
 }
 
 template <typename T>
-__global__ void k_residual(int64_t n, T* r, const T* d, const T* ax) {
-  GRID_STRIDE(i, n) r[i] = d[i] - ax[i];
-}
-
-template <typename T>
-__global__ void k_axpy(int64_t n, T* y, const T* x, T a) {
-  GRID_STRIDE(i, n) y[i] += a * x[i];
-}
-
-template <typename T>
 __global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* __restrict__ ptr,
                            const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ df,
                            const T* __restrict__ axf, T* dc, const uint8_t* __restrict__ cmask_c, int fixbits) {
@@ -80,42 +70,63 @@ __global__ void k_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const
 }
 
 template <typename T>
-__global__ void k_copy_in(int32_t n, int ncomp, const int32_t* __restrict__ ls, const int32_t* __restrict__ vs,
-                          const double* __restrict__ r, int64_t nsl, T* d, int64_t nsv,
+__global__ void k_copy_in(int64_t nsl, int ncomp, DevHome home, const double* __restrict__ r, T* d,
                           const uint8_t* __restrict__ lcm, int fixbits) {
-  GRID_STRIDE(i, n) {
-    const int a = ls[i], b = vs[i];
-    const uint8_t cm = lcm[a];
+  GRID_STRIDE(s, nsl) {
+    const int32_t b = home.slot[s];
+    if (b < 0) continue;
+    const int64_t base = int64_t(ncomp) * home.off[s] + b, nl = home.nsl[s];
+    const uint8_t cm = lcm[s];
     for (int c = 0; c < ncomp; ++c) {
       const int bit = (fixbits == 4) ? 4 : (1 << c);
-      if (!(cm & bit)) d[c * nsv + b] = T(r[c * nsl + a]);
+      if (!(cm & bit)) d[base + c * nl] = T(r[c * nsl + s]);
     }
   }
 }
 
 template <typename T>
-__global__ void k_copy_out(int32_t n, int ncomp, const int32_t* __restrict__ ls, const int32_t* __restrict__ vs,
-                           const T* __restrict__ x, int64_t nsv, double* z, int64_t nsl,
-                           const uint8_t* __restrict__ lcm, int fixbits) {
-  GRID_STRIDE(i, n) {
-    const int a = ls[i], b = vs[i];
-    const uint8_t cm = lcm[a];
+__global__ void k_copy_out(int64_t nsl, int ncomp, DevHome home, const T* __restrict__ x,
+                           const double* __restrict__ r, double* z, const uint8_t* __restrict__ lcm,
+                           const uint8_t* __restrict__ lflags, int fixbits) {
+  GRID_STRIDE(s, nsl) {
+    const uint8_t cm = lcm[s];
+    const bool node = (lflags[s] & 1) && !(lflags[s] & 4);
+    const int32_t b = home.slot[s];
+    const int64_t base = b >= 0 ? int64_t(ncomp) * home.off[s] + b : 0, nl = b >= 0 ? home.nsl[s] : 0;
     for (int c = 0; c < ncomp; ++c) {
       const int bit = (fixbits == 4) ? 4 : (1 << c);
-      if (!(cm & bit)) z[c * nsl + a] = double(x[c * nsv + b]);
+      double v = 0.0;
+      if (cm & bit) v = node ? r[c * nsl + s] : 0.0;
+      else if (b >= 0) v = double(x[base + c * nl]);
+      z[c * nsl + s] = v;
     }
   }
 }
 
-__global__ void k_leaf_init(int64_t ns, int ncomp, const double* __restrict__ r, double* z,
-                            const uint8_t* __restrict__ lcm, const uint8_t* __restrict__ lflags, int fixbits) {
-  GRID_STRIDE(s, ns) {
-    const uint8_t cm = lcm[s];
-    const bool node = (lflags[s] & 1) && !(lflags[s] & 4);
-    for (int c = 0; c < ncomp; ++c) {
-      const int bit = (fixbits == 4) ? 4 : (1 << c);
-      z[c * ns + s] = (node && (cm & bit)) ? r[c * ns + s] : 0.0;
+template <typename T>
+__global__ void k_cheb_first_res(int64_t n, T* x, T* xprev, T* r, const T* __restrict__ dinv,
+                                 const T* __restrict__ d, const T* __restrict__ ax, T c0, T* xadd) {
+  GRID_STRIDE(i, n) {
+    const T ri = d[i] - ax[i];
+    const T v = c0 * dinv[i] * ri;
+    if (xadd != nullptr) {
+      xadd[i] += v;
+    } else {
+      r[i] = ri;
+      x[i] = v;
+      xprev[i] = T(0);
     }
+  }
+}
+
+template <typename T>
+__global__ void k_cheb_step_add(int64_t n, T* xadd, const T* __restrict__ x, const T* __restrict__ xprev,
+                                const T* __restrict__ dinv, const T* __restrict__ d, const T* __restrict__ ax, T a,
+                                T b) {
+  GRID_STRIDE(i, n) {
+    const T xi = x[i];
+    const T v = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
+    xadd[i] += v;
   }
 }
 
@@ -266,30 +277,62 @@ __global__ void k_dot_final(int nb, const double* __restrict__ part, double* out
 }
 
 // sc: 0 rz, 1 pq, 2 rz_new, 3 alpha, 4 beta, 5 ok (1 while the iteration is healthy)
-__global__ void k_cg_alpha(double* sc) {
-  const double pq = sc[1];
-  const bool ok = sc[5] > 0.5 && pq > 0.0 && sc[0] > 0.0;
-  sc[3] = ok ? sc[0] / pq : 0.0;
-  if (!ok) sc[5] = 0.0;
+__global__ void k_cg_init(double* sc) {
+  if (threadIdx.x < 8) sc[threadIdx.x] = threadIdx.x == 5 ? 1.0 : 0.0;
 }
 
-__global__ void k_cg_beta(double* sc, double* hist, int step) {
-  const bool ok = sc[5] > 0.5;
-  const double beta = ok ? sc[2] / sc[0] : 0.0;
-  sc[4] = beta;
-  hist[2 * step + 0] = ok ? sc[3] : 0.0;   // alpha_j (0 marks a stop)
-  hist[2 * step + 1] = beta;
-  if (!(ok && sc[2] > 1e-300)) sc[5] = 0.0;
-  sc[0] = sc[2];
-}
-
-__global__ void k_cg_r(int64_t n, double* r, double* z, const double* __restrict__ q, const double* __restrict__ dinv,
-                       const double* __restrict__ sc) {
+// r -= alpha q, z = D^-1 r and the block partial sums of r.z (the grid and the
+// summation order of k_dot_partial, so the dot is the same as a separate one)
+__global__ void k_cg_r_dot(int64_t n, double* r, double* z, const double* __restrict__ q,
+                           const double* __restrict__ dinv, const double* __restrict__ sc, double* part) {
+  __shared__ double sh[TPB];
   const double alpha = sc[3];
+  double acc = 0.0;
   GRID_STRIDE(i, n) {
     const double ri = r[i] - alpha * q[i];
+    const double zi = dinv[i] * ri;
     r[i] = ri;
-    z[i] = dinv[i] * ri;
+    z[i] = zi;
+    acc += ri * zi;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// sc[slot] = sum of the partials (the order of k_dot_final), then slot 1: alpha =
+// rz / pq; slot 2: beta = rz_new / rz, the coefficient history (alpha_j, beta_j;
+// alpha_j = 0 marks a stop) and rz = rz_new.  sc[5] drops to 0 on a breakdown.
+__global__ void k_dot_final_cg(int nb, const double* __restrict__ part, double* sc, int slot, double* hist,
+                               int step) {
+  __shared__ double sh[TPB];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += TPB) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  sc[slot] = sh[0];
+  if (slot == 1) {
+    const double pq = sc[1];
+    const bool ok = sc[5] > 0.5 && pq > 0.0 && sc[0] > 0.0;
+    sc[3] = ok ? sc[0] / pq : 0.0;
+    if (!ok) sc[5] = 0.0;
+  } else if (slot == 2) {
+    const bool ok = sc[5] > 0.5;
+    const double beta = ok ? sc[2] / sc[0] : 0.0;
+    sc[4] = beta;
+    hist[2 * step + 0] = ok ? sc[3] : 0.0;
+    hist[2 * step + 1] = beta;
+    if (!(ok && sc[2] > 1e-300)) sc[5] = 0.0;
+    sc[0] = sc[2];
   }
 }
 
@@ -315,16 +358,6 @@ cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, co
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t mg_residual(int64_t n, T* r, const T* d, const T* ax, cudaStream_t s) {
-  if (n > 0) k_residual<T><<<blocks_for(n), TPB, 0, s>>>(n, r, d, ax);
-  return cudaGetLastError();
-}
-template <typename T>
-cudaError_t mg_axpy(int64_t n, T* y, const T* x, T a, cudaStream_t s) {
-  if (n > 0) k_axpy<T><<<blocks_for(n), TPB, 0, s>>>(n, y, x, a);
-  return cudaGetLastError();
-}
-template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* ptr, const int32_t* col,
                         const float* val, const T* d_f, const T* ax_f, T* d_c, const uint8_t* cmask_c, int fixbits,
                         cudaStream_t s) {
@@ -340,24 +373,28 @@ cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const in
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t mg_copy_in(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const double* r,
-                       int64_t ns_leaf, T* d, int64_t ns_l, const uint8_t* leaf_cmask, int fixbits, cudaStream_t s) {
-  if (n > 0) k_copy_in<T><<<blocks_for(n), TPB, 0, s>>>(n, ncomp, leaf_slot, lev_slot, r, ns_leaf, d, ns_l,
-                                                        leaf_cmask, fixbits);
+cudaError_t mg_copy_in(int64_t ns_leaf, int ncomp, DevHome home, const double* r, T* d, const uint8_t* leaf_cmask,
+                       int fixbits, cudaStream_t s) {
+  if (ns_leaf > 0) k_copy_in<T><<<blocks_for(ns_leaf), TPB, 0, s>>>(ns_leaf, ncomp, home, r, d, leaf_cmask, fixbits);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t mg_copy_out(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const T* x,
-                        int64_t ns_l, double* z, int64_t ns_leaf, const uint8_t* leaf_cmask, int fixbits,
-                        cudaStream_t s) {
-  if (n > 0) k_copy_out<T><<<blocks_for(n), TPB, 0, s>>>(n, ncomp, leaf_slot, lev_slot, x, ns_l, z, ns_leaf,
-                                                         leaf_cmask, fixbits);
+cudaError_t mg_copy_out(int64_t ns_leaf, int ncomp, DevHome home, const T* x, const double* r, double* z,
+                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s) {
+  if (ns_leaf > 0)
+    k_copy_out<T><<<blocks_for(ns_leaf), TPB, 0, s>>>(ns_leaf, ncomp, home, x, r, z, leaf_cmask, leaf_flags, fixbits);
   return cudaGetLastError();
 }
-cudaError_t mg_leaf_init(int64_t ns_leaf, int ncomp, const double* r, double* z, const uint8_t* leaf_cmask,
-                         const uint8_t* leaf_flags, int fixbits, cudaStream_t s) {
-  if (ns_leaf > 0) k_leaf_init<<<blocks_for(ns_leaf), TPB, 0, s>>>(ns_leaf, ncomp, r, z, leaf_cmask, leaf_flags,
-                                                                   fixbits);
+template <typename T>
+cudaError_t mg_chebyshev_first_res(int64_t n, T* x, T* xprev, T* r, const T* dinv, const T* d, const T* ax, T c0,
+                                   T* xadd, cudaStream_t s) {
+  if (n > 0) k_cheb_first_res<T><<<blocks_for(n), TPB, 0, s>>>(n, x, xprev, r, dinv, d, ax, c0, xadd);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
+                                  const T* ax, T a, T b, cudaStream_t s) {
+  if (n > 0) k_cheb_step_add<T><<<blocks_for(n), TPB, 0, s>>>(n, xadd, x, xprev, dinv, d, ax, a, b);
   return cudaGetLastError();
 }
 cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s) {
@@ -409,23 +446,28 @@ cudaError_t dot64(int64_t n, const double* a, const double* b, double* partial, 
   k_dot_final<<<1, TPB, 0, s>>>(DOT_BLOCKS, partial, out);
   return cudaGetLastError();
 }
-cudaError_t cg_update_r(int64_t n, double* r, double* z, const double* q, const double* dinv, const double* sc,
-                        cudaStream_t s) {
-  if (n > 0) k_cg_r<<<blocks_for(n), TPB, 0, s>>>(n, r, z, q, dinv, sc);
-  return cudaGetLastError();
-}
 cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* sc, cudaStream_t s) {
   if (n > 0) k_cg_p<<<blocks_for(n), TPB, 0, s>>>(n, p, z, sc);
   return cudaGetLastError();
 }
-cudaError_t cg_scalars_alpha(double* sc, cudaStream_t s) {
-  k_cg_alpha<<<1, 1, 0, s>>>(sc);
+cudaError_t dot_partial64(int64_t n, const double* a, const double* b, double* partial, cudaStream_t s) {
+  k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, a, b, partial);
   return cudaGetLastError();
 }
-cudaError_t cg_scalars_beta(double* sc, double* hist, int step, cudaStream_t s) {
-  k_cg_beta<<<1, 1, 0, s>>>(sc, hist, step);
+cudaError_t cg_dot_final(const double* partial, double* sc, int slot, double* hist, int step, cudaStream_t s) {
+  k_dot_final_cg<<<1, TPB, 0, s>>>(DOT_BLOCKS, partial, sc, slot, hist, step);
   return cudaGetLastError();
 }
+cudaError_t cg_update_r_dot(int64_t n, double* r, double* z, const double* q, const double* dinv, const double* sc,
+                            double* partial, cudaStream_t s) {
+  k_cg_r_dot<<<DOT_BLOCKS, TPB, 0, s>>>(n, r, z, q, dinv, sc, partial);
+  return cudaGetLastError();
+}
+cudaError_t cg_init_scalars(double* sc, cudaStream_t s) {
+  k_cg_init<<<1, 32, 0, s>>>(sc);
+  return cudaGetLastError();
+}
+int mg_dot_partials() { return DOT_BLOCKS; }
 cudaError_t fill64(int64_t n, double* x, double v, cudaStream_t s) {
   if (n > 0) k_fill64<<<blocks_for(n), TPB, 0, s>>>(n, x, v);
   return cudaGetLastError();
@@ -439,16 +481,17 @@ cudaError_t copy64(int64_t n, double* dst, const double* src, cudaStream_t s) {
   template cudaError_t mg_chebyshev_first<T>(int64_t, T*, T*, const T*, const T*, T, cudaStream_t);           \
   template cudaError_t mg_chebyshev_step<T>(int64_t, T*, const T*, const T*, const T*, const T*, const T*, T,  \
                                             T, cudaStream_t);                                                  \
-  template cudaError_t mg_residual<T>(int64_t, T*, const T*, const T*, cudaStream_t);                         \
-  template cudaError_t mg_axpy<T>(int64_t, T*, const T*, T, cudaStream_t);                                    \
   template cudaError_t mg_restrict<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,          \
                                       const float*, const T*, const T*, T*, const uint8_t*, int, cudaStream_t); \
   template cudaError_t mg_prolong<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,           \
                                      const float*, const T*, T*, const uint8_t*, int, cudaStream_t);           \
-  template cudaError_t mg_copy_in<T>(int32_t, int, const int32_t*, const int32_t*, const double*, int64_t, T*, \
-                                     int64_t, const uint8_t*, int, cudaStream_t);                              \
-  template cudaError_t mg_copy_out<T>(int32_t, int, const int32_t*, const int32_t*, const T*, int64_t, double*,\
-                                      int64_t, const uint8_t*, int, cudaStream_t);                             \
+  template cudaError_t mg_copy_in<T>(int64_t, int, DevHome, const double*, T*, const uint8_t*, int, cudaStream_t); \
+  template cudaError_t mg_copy_out<T>(int64_t, int, DevHome, const T*, const double*, double*, const uint8_t*,     \
+                                      const uint8_t*, int, cudaStream_t);                                          \
+  template cudaError_t mg_chebyshev_first_res<T>(int64_t, T*, T*, T*, const T*, const T*, const T*, T, T*,        \
+                                                 cudaStream_t);                                                    \
+  template cudaError_t mg_chebyshev_step_add<T>(int64_t, T*, const T*, const T*, const T*, const T*, const T*, T, \
+                                                T, cudaStream_t);                                                  \
   template cudaError_t mg_coarse<T>(int32_t, const int32_t*, const double*, const T*, T*, double*, cudaStream_t);
 INST(float)
 INST(double)

@@ -20,9 +20,16 @@ struct DevLevel {
   const int32_t* R_ptr = nullptr;  // restriction rows (level-1 slots) -> this level's slots
   const int32_t* R_col = nullptr;
   const float* R_val = nullptr;
-  int32_t n_copy = 0;              // leaf nodes whose home level is this one
-  const int32_t* copy_leaf = nullptr;
-  const int32_t* copy_level = nullptr;
+};
+
+// Home level of each leaf slot: a free leaf node's defect enters, and its
+// correction leaves, the coarsest level among its leaf cells.  Per leaf slot:
+// that level's slot offset in the concatenated level storage, its slot on that
+// level (-1: hanging node or hole) and that level's slot count.
+struct DevHome {
+  const int32_t* off = nullptr;
+  const int32_t* slot = nullptr;
+  const int32_t* nsl = nullptr;
 };
 
 // ---- elementwise / sparse kernels (T = float or double for the level vectors)
@@ -31,10 +38,6 @@ cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T
 template <typename T>
 cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d,
                               const T* ax, T a, T b, cudaStream_t s);
-template <typename T>
-cudaError_t mg_residual(int64_t n, T* r, const T* d, const T* ax, cudaStream_t s);
-template <typename T>
-cudaError_t mg_axpy(int64_t n, T* y, const T* x, T a, cudaStream_t s);
 // d_c[y] += sum_z R[y,z] (d_f[z] - ax_f[z]) over coarse slots; zero on coarse fixed rows
 template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t nc_stride, int64_t nf_stride, const int32_t* ptr,
@@ -45,18 +48,25 @@ template <typename T>
 cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nf_stride, int64_t nc_stride, const int32_t* ptr,
                        const int32_t* col, const float* val, const T* x_c, T* x_f, const uint8_t* cmask_f,
                        int fixbits, cudaStream_t s);
-// level d (ncomp blocks of stride ns_l) <- leaf r (double, ncomp blocks of stride ns_leaf) on free leaf nodes
+// Level vectors of a block: level l at ncomp * off_l, component c at + c * n_slots_l.
+// copy_in: d on each free leaf node's home level <- leaf r (double, ncomp blocks of
+// stride ns_leaf).  copy_out: z = r on fixed leaf node DoFs, the home-level value
+// of x on free ones, 0 on hanging nodes and holes.
 template <typename T>
-cudaError_t mg_copy_in(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const double* r,
-                       int64_t ns_leaf, T* d, int64_t ns_l, const uint8_t* leaf_cmask, int fixbits,
-                       cudaStream_t s);
+cudaError_t mg_copy_in(int64_t ns_leaf, int ncomp, DevHome home, const double* r, T* d, const uint8_t* leaf_cmask,
+                       int fixbits, cudaStream_t s);
 template <typename T>
-cudaError_t mg_copy_out(int32_t n, int ncomp, const int32_t* leaf_slot, const int32_t* lev_slot, const T* x,
-                        int64_t ns_l, double* z, int64_t ns_leaf, const uint8_t* leaf_cmask, int fixbits,
-                        cudaStream_t s);
-// z = r on fixed leaf DoFs, 0 elsewhere (hanging nodes and holes included)
-cudaError_t mg_leaf_init(int64_t ns_leaf, int ncomp, const double* r, double* z, const uint8_t* leaf_cmask,
-                         const uint8_t* leaf_flags, int fixbits, cudaStream_t s);
+cudaError_t mg_copy_out(int64_t ns_leaf, int ncomp, DevHome home, const T* x, const double* r, double* z,
+                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s);
+// Post-smoothing pieces.  first_res: r = d - ax, x = c0 D^-1 r, xprev = 0; with
+// xadd != NULL (degree 1) instead xadd += c0 D^-1 (d - ax), nothing stored.
+// step_add: xadd += the Chebyshev step of mg_chebyshev_step (not stored).
+template <typename T>
+cudaError_t mg_chebyshev_first_res(int64_t n, T* x, T* xprev, T* r, const T* dinv, const T* d, const T* ax, T c0,
+                                   T* xadd, cudaStream_t s);
+template <typename T>
+cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
+                                  const T* ax, T a, T b, cudaStream_t s);
 // In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by Gauss-Jordan
 // sweeps without pivoting: the pivots are the diagonals of successive Schur
 // complements, positive for an SPD matrix.  rc: scratch of 4 n doubles.  *bad is
@@ -86,12 +96,21 @@ cudaError_t mg_start_vector(int32_t ns_l, int ncomp, const int32_t* gx, const in
                             double* r, cudaStream_t s);
 // deterministic dot product: partial sums per block, then one ordered sum -> out[0]
 cudaError_t dot64(int64_t n, const double* a, const double* b, double* partial, double* out, cudaStream_t s);
-// CG step pieces on device scalars sc[] = {rz, pq, rz_new, alpha, beta, ok}
-cudaError_t cg_update_r(int64_t n, double* r, double* z, const double* q, const double* dinv, const double* sc,
-                        cudaStream_t s);
+// Jacobi-preconditioned CG on device scalars sc[] = {rz, pq, rz_new, alpha, beta, ok}.
+// dot_partial64: the block partial sums of a.b (the grid and order of dot64);
+// cg_dot_final: sc[slot] = their sum, then slot 1 sets alpha, slot 2 beta and
+// hist[2 step], hist[2 step + 1]; cg_update_r_dot: r -= alpha q, z = D^-1 r with
+// the partial sums of r.z; cg_update_p: p = z + beta p.  partial holds
+// mg_dot_partials() doubles.
 cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* sc, cudaStream_t s);
-cudaError_t cg_scalars_alpha(double* sc, cudaStream_t s);
-cudaError_t cg_scalars_beta(double* sc, double* hist, int step, cudaStream_t s);
+cudaError_t dot_partial64(int64_t n, const double* a, const double* b, double* partial, cudaStream_t s);
+cudaError_t cg_dot_final(const double* partial, double* sc, int slot, double* hist, int step, cudaStream_t s);
+cudaError_t cg_update_r_dot(int64_t n, double* r, double* z, const double* q, const double* dinv, const double* sc,
+                            double* partial, cudaStream_t s);
+// CG scalars {rz, pq, rz_new, alpha, beta, ok, -, -} = {0, 0, 0, 0, 0, 1, 0, 0}
+cudaError_t cg_init_scalars(double* sc, cudaStream_t s);
+// number of per-block partial sums dot64 writes (its partial buffer holds this many doubles)
+int mg_dot_partials();
 cudaError_t fill64(int64_t n, double* x, double v, cudaStream_t s);
 cudaError_t copy64(int64_t n, double* dst, const double* src, cudaStream_t s);
 

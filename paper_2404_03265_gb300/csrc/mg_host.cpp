@@ -24,6 +24,8 @@ namespace pff {
 
 namespace {
 
+constexpr int kMaxLanczos = 64;   // CG coefficient pairs stored per set-up chain
+
 inline int block_op(int b) { return b == 0 ? OP_UU : OP_PP; }
 inline int block_diag_op(int b) { return b == 0 ? OP_UU_DIAG : OP_PP_DIAG; }
 
@@ -128,8 +130,6 @@ cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStr
 std::string mg_alloc(pff_mg& mg) {
   const DevMesh& D = mg.pb->mesh->dev;
   const int64_t N = D.lev_total;
-  int64_t nmax = 0;
-  for (const auto& L : D.levels) nmax = std::max<int64_t>(nmax, L.lv.n_slots);
   mg.vc_in = mg.mem.alloc<double>(3 * mg.pb->mesh->m.lay.n_slots);
   mg.vc_out = mg.mem.alloc<double>(3 * mg.pb->mesh->m.lay.n_slots);
   mg.lin64 = mg.mem.alloc<double>(4 * N);
@@ -147,15 +147,17 @@ std::string mg_alloc(pff_mg& mg) {
     for (auto* p : bufs) *p = mg.mem.alloc<unsigned char>(n * esz);
     B.lam.assign(D.levels.size(), 0.0);
   }
-  mg.cg_r = mg.mem.alloc<double>(2 * nmax);
-  mg.cg_z = mg.mem.alloc<double>(2 * nmax);
-  mg.cg_p = mg.mem.alloc<double>(2 * nmax);
-  mg.cg_q = mg.mem.alloc<double>(2 * nmax);
-  mg.diag = mg.mem.alloc<double>(2 * nmax);
-  mg.partial = mg.mem.alloc<double>(1024);
-  mg.sc = mg.mem.alloc<double>(8);
-  mg.hist = mg.mem.alloc<double>(2 * 64);
-  mg.spd_bad = mg.mem.alloc<int32_t>(1);
+  const int nchain = 2 * int(D.levels.size());
+  for (int b = 0; b < 2; ++b) mg.su_vec[b] = mg.mem.alloc<double>(5 * mg.blk[b].ncomp * N);
+  mg.su_partial = mg.mem.alloc<double>(int64_t(nchain) * mg_dot_partials());
+  mg.su_sc = mg.mem.alloc<double>(8 * nchain);
+  mg.su_hist = mg.mem.alloc<double>(2 * kMaxLanczos * nchain);
+  const int Mc = 2 * mg.pb->mesh->m.k + 1;
+  const int64_t n0 = D.levels.empty() ? 0 : D.levels[0].lv.n_slots;
+  mg.probe_len = (2 * 2 + 1 * 1) * Mc * Mc * n0;   // sum over blocks of ncomp^2 Mc^2 n_0
+  mg.probe_in = mg.mem.alloc<double>(std::max<int64_t>(mg.probe_len, 1));
+  mg.probe_out = mg.mem.alloc<double>(std::max<int64_t>(mg.probe_len, 1));
+  mg.spd_bad = mg.mem.alloc<int32_t>(2);
   if (!mg.mem.err.empty()) return mg.mem.err;
   return "";
 }
@@ -168,6 +170,29 @@ void mg_release_graphs(pff_mg& mg) {
   if (mg.vc_both) { cudaGraphExecDestroy(mg.vc_both); mg.vc_both = nullptr; }
 }
 
+// Lambda_max (and on level 0 the Chebyshev interval) of one (block, level) from
+// the CG coefficients alpha_j, beta_j of its chain: the Lanczos tridiagonal
+// d_j = 1/alpha_j + beta_{j-1}/alpha_{j-1}, e_j = sqrt(beta_j)/alpha_j.
+static void eigen_from_cg(pff_mg& mg, MGBlock& B, int l, const double* hist) {
+  std::vector<double> al, be;
+  for (int j = 0; j < mg.lanczos_steps; ++j) {
+    if (!(hist[2 * j] > 0)) break;
+    al.push_back(hist[2 * j]);
+    be.push_back(hist[2 * j + 1]);
+  }
+  const int m = int(al.size());
+  std::vector<double> dd(m), ee(m > 0 ? m - 1 : 0);
+  for (int j = 0; j < m; ++j) dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+  for (int j = 0; j + 1 < m; ++j) ee[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
+  B.lam[l] = tridiag_max_eig(dd, ee);
+  if (l == 0 && B.lam[0] > 0.0) {
+    // Chebyshev coarse solver: both Ritz extremes of the same CG run
+    B.c0_a = 0.9 * tridiag_min_eig(dd, ee);
+    B.c0_b = 1.2 * B.lam[0];
+    B.c0_deg = B.c0_a > 0.0 ? chebyshev_degree(B.c0_a, B.c0_b) : 0;
+  }
+}
+
 std::string mg_setup(pff_mg& mg, cudaStream_t s) {
   mg_release_graphs(mg);   // the V-cycle graphs hold this set-up's coefficients
   pff_problem& pb = *mg.pb;
@@ -175,6 +200,8 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
   const DevMesh& D = pb.mesh->dev;
   const int nl = int(D.levels.size());
   const int64_t nsleaf = M.lay.n_slots;
+  const int64_t N = D.lev_total;
+  if (mg.lanczos_steps > kMaxLanczos) return "too many Lanczos steps";
   for (int l = 0; l < nl; ++l) {
     const DevLevel& lv = D.levels[l].lv;
     CK(mg_inject_lin(lv.n_slots, lv.slot_leaf, pb.lin64, nsleaf, mg.lin64 + 4 * lv.off, mg.lin32 + 4 * lv.off, s));
@@ -185,60 +212,63 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
     CK(mg_level_cmask(lv.n_slots, lv.flags, lv.slot_leaf, pb.cmask, fine ? fine->R_ptr : nullptr,
                       fine ? fine->R_col : nullptr, fine ? mg.cmask + fine->off : nullptr, mg.cmask + lv.off, s));
   }
-  for (int b = 0; b < 2; ++b) {
-    MGBlock& B = mg.blk[b];
-    for (int l = 0; l < nl; ++l) {
+  // 1. One chain per (block, level), finest levels first, spread over the stream
+  //    pool: inverse diagonal, then the Jacobi-preconditioned CG run whose
+  //    coefficients give lambda_max of D^-1 A on the interior (level 0: only for
+  //    the Chebyshev coarse solver).  The chains share no buffer.
+  constexpr int K = pff_mg::kSetupStreams;
+  if (!mg.su_start) CK(cudaEventCreateWithFlags(&mg.su_start, cudaEventDisableTiming));
+  for (int i = 0; i <= K; ++i) {
+    if (!mg.su_stream[i]) CK(cudaStreamCreateWithFlags(&mg.su_stream[i], cudaStreamNonBlocking));
+    if (!mg.su_done[i]) CK(cudaEventCreateWithFlags(&mg.su_done[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(mg.su_start, s));
+  for (int i = 0; i <= K; ++i) CK(cudaStreamWaitEvent(mg.su_stream[i], mg.su_start, 0));
+  const int np = mg_dot_partials();
+  int chain = 0;
+  for (int l = nl - 1; l >= 0; --l)
+    for (int b = 0; b < 2; ++b, ++chain) {
+      cudaStream_t t = mg.su_stream[chain % K];
+      MGBlock& B = mg.blk[b];
       const DevLevel& lv = D.levels[l].lv;
-      const int64_t n = lv.n_slots;
-      CK(level_apply<double>(mg, l, block_diag_op(b), mg.diag, mg.diag, s));
-      CK(mg_invert_diag(lv.n_slots, B.ncomp, mg.diag, lv.flags, mg.cmask + lv.off, B.fixbits,
-                        B.dinv64 + B.ncomp * lv.off, B.dinv32 + B.ncomp * lv.off, s));
+      const int64_t nn = B.ncomp * int64_t(lv.n_slots), o = B.ncomp * lv.off, vs = B.ncomp * N;
+      double* diag = mg.su_vec[b] + o;
+      double* r = mg.su_vec[b] + vs + o;
+      double* z = mg.su_vec[b] + 2 * vs + o;
+      double* p = mg.su_vec[b] + 3 * vs + o;
+      double* q = mg.su_vec[b] + 4 * vs + o;
+      const int c = b * nl + l;
+      double* part = mg.su_partial + int64_t(c) * np;
+      double* sc = mg.su_sc + 8 * c;
+      double* hist = mg.su_hist + 2 * kMaxLanczos * c;
+      CK(level_apply<double>(mg, l, block_diag_op(b), diag, diag, t));
+      CK(mg_invert_diag(lv.n_slots, B.ncomp, diag, lv.flags, mg.cmask + lv.off, B.fixbits, B.dinv64 + o,
+                        B.dinv32 + o, t));
       B.lam[l] = 0.0;
       if (l == 0) { B.c0_a = B.c0_b = 0.0; B.c0_deg = 0; }
       if (l == 0 && mg.coarse_mode == 0) continue;
-      // lambda_max of D^-1 A on the interior: Jacobi-preconditioned CG from a fixed start vector
-      const int64_t nn = B.ncomp * n;
-      const double* dinv = B.dinv64 + B.ncomp * lv.off;
-      CK(mg_start_vector(lv.n_slots, B.ncomp, D.levels[l].gx, D.levels[l].gy, dinv, mg.cg_r, s));
-      CK(fill64(nn, mg.cg_q, 0.0, s));
-      // scalars {rz, pq, rz_new, alpha = 0, beta, ok = 1}; z = D^-1 r, p = z, rz = r.z
-      const double sc0[8] = {0, 0, 0, 0, 0, 1, 0, 0};
-      CK(cudaMemcpyAsync(mg.sc, sc0, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(cg_update_r(nn, mg.cg_r, mg.cg_z, mg.cg_q, dinv, mg.sc, s));
-      CK(copy64(nn, mg.cg_p, mg.cg_z, s));
-      CK(dot64(nn, mg.cg_r, mg.cg_z, mg.partial, mg.sc + 0, s));
+      const double* dinv = B.dinv64 + o;
+      CK(mg_start_vector(lv.n_slots, B.ncomp, D.levels[l].gx, D.levels[l].gy, dinv, r, t));
+      CK(fill64(nn, q, 0.0, t));
+      // z = D^-1 r, rz = r.z, p = z
+      CK(cg_init_scalars(sc, t));
+      CK(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
+      CK(cg_dot_final(part, sc, 0, hist, 0, t));
+      CK(copy64(nn, p, z, t));
       for (int j = 0; j < mg.lanczos_steps; ++j) {
-        CK(level_apply<double>(mg, l, block_op(b), mg.cg_p, mg.cg_q, s));
-        CK(dot64(nn, mg.cg_p, mg.cg_q, mg.partial, mg.sc + 1, s));
-        CK(cg_scalars_alpha(mg.sc, s));
-        CK(cg_update_r(nn, mg.cg_r, mg.cg_z, mg.cg_q, dinv, mg.sc, s));
-        CK(dot64(nn, mg.cg_r, mg.cg_z, mg.partial, mg.sc + 2, s));
-        CK(cg_scalars_beta(mg.sc, mg.hist, j, s));
-        CK(cg_update_p(nn, mg.cg_p, mg.cg_z, mg.sc, s));
-      }
-      std::vector<double> hist(2 * mg.lanczos_steps);
-      CK(cudaMemcpyAsync(hist.data(), mg.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      std::vector<double> al, be;
-      for (int j = 0; j < mg.lanczos_steps; ++j) {
-        if (!(hist[2 * j] > 0)) break;
-        al.push_back(hist[2 * j]);
-        be.push_back(hist[2 * j + 1]);
-      }
-      const int m = int(al.size());
-      std::vector<double> dd(m), ee(m > 0 ? m - 1 : 0);
-      for (int j = 0; j < m; ++j) dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-      for (int j = 0; j + 1 < m; ++j) ee[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
-      B.lam[l] = tridiag_max_eig(dd, ee);
-      if (l == 0 && B.lam[0] > 0.0) {
-        // Chebyshev coarse solver: both Ritz extremes of the same CG run
-        B.c0_a = 0.9 * tridiag_min_eig(dd, ee);
-        B.c0_b = 1.2 * B.lam[0];
-        B.c0_deg = B.c0_a > 0.0 ? chebyshev_degree(B.c0_a, B.c0_b) : 0;
+        // q = A p; pq, alpha; r -= alpha q, z = D^-1 r, rz_new, beta; p = z + beta p
+        CK(level_apply<double>(mg, l, block_op(b), p, q, t));
+        CK(dot_partial64(nn, p, q, part, t));
+        CK(cg_dot_final(part, sc, 1, hist, j, t));
+        CK(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
+        CK(cg_dot_final(part, sc, 2, hist, j, t));
+        CK(cg_update_p(nn, p, z, sc, t));
       }
     }
-    if (mg.coarse_mode != 0) continue;
-    // coarse level: dense FP64 block by probing with (2k+1)^2 colours per component
+  // 2. Direct coarse solve: the dense level-0 block of each block by probing with
+  //    (2k+1)^2 colours per component (all probes applied in one batch on s, beside
+  //    the chains), assembled on the host and inverted on the device.
+  if (mg.coarse_mode == 0) {
     const DevMesh::Level& L0 = D.levels[0];
     const LevelMesh& lm0 = M.levels[0];
     const int n0 = L0.lv.n_slots;
@@ -254,66 +284,107 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
         gy[q] = lm0.slot_Y[q] >> M.Lf;
         pos[(int64_t(gx[q]) << 32) | gy[q]] = q;
       }
-    std::vector<int32_t> eidx;            // interior entries (comp * n0 + slot)
-    std::vector<int32_t> ent_of(size_t(B.ncomp) * n0, -1);
-    for (int q = 0; q < n0; ++q)
-      for (int c = 0; c < B.ncomp; ++c) {
-        const int bit = B.fixbits == 4 ? 4 : (1 << c);
-        if (gx[q] >= 0 && !(cm0[q] & bit)) {
-          ent_of[size_t(c) * n0 + q] = int32_t(eidx.size());
-          eidx.push_back(c * n0 + q);
-        }
+    // probe (b, c, cy, cx) at probe_base[b] + ((c * Mc + cy) * Mc + cx) * ncomp_b * n0
+    int64_t probe_base[2];
+    probe_base[0] = 0;
+    probe_base[1] = int64_t(mg.blk[0].ncomp) * mg.blk[0].ncomp * Mc * Mc * n0;
+    if (probe_base[1] + int64_t(mg.blk[1].ncomp) * mg.blk[1].ncomp * Mc * Mc * n0 > mg.probe_len)
+      return "coarse probe buffer too small";
+    std::vector<double> probes(size_t(mg.probe_len), 0.0), resp(size_t(mg.probe_len));
+    for (int b = 0; b < 2; ++b) {
+      const int nc = mg.blk[b].ncomp;
+      for (int c = 0; c < nc; ++c)
+        for (int cy = 0; cy < Mc; ++cy)
+          for (int cx = 0; cx < Mc; ++cx) {
+            double* pr = probes.data() + probe_base[b] + ((c * Mc + cy) * Mc + cx) * int64_t(nc) * n0;
+            for (int q = 0; q < n0; ++q)
+              if (gx[q] >= 0 && gx[q] % Mc == cx && gy[q] % Mc == cy) pr[size_t(c) * n0 + q] = 1.0;
+          }
+    }
+    CK(cudaMemcpyAsync(mg.probe_in, probes.data(), probes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < 2; ++b) {
+      const int nc = mg.blk[b].ncomp;
+      for (int pi = 0; pi < nc * Mc * Mc; ++pi) {
+        const int64_t off = probe_base[b] + pi * int64_t(nc) * n0;
+        CK(level_apply<double>(mg, 0, block_op(b), mg.probe_in + off, mg.probe_out + off, s));
       }
-    const int nI = int(eidx.size());
-    std::vector<double> A(size_t(nI) * nI, 0.0), probe(size_t(B.ncomp) * n0), yv(size_t(B.ncomp) * n0);
-    for (int c = 0; c < B.ncomp; ++c)
-      for (int cy = 0; cy < Mc; ++cy)
-        for (int cx = 0; cx < Mc; ++cx) {
-          std::fill(probe.begin(), probe.end(), 0.0);
-          for (int q = 0; q < n0; ++q)
-            if (gx[q] >= 0 && gx[q] % Mc == cx && gy[q] % Mc == cy) probe[size_t(c) * n0 + q] = 1.0;
-          CK(cudaMemcpyAsync(mg.cg_p, probe.data(), probe.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-          CK(level_apply<double>(mg, 0, block_op(b), mg.cg_p, mg.cg_q, s));
-          CK(cudaMemcpyAsync(yv.data(), mg.cg_q, yv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-          for (int q = 0; q < n0; ++q) {
-            if (gx[q] < 0) continue;
-            // the probed node within distance k of q in each direction
-            const int jx = gx[q] - k + ((cx - (gx[q] - k)) % Mc + Mc) % Mc;
-            const int jy = gy[q] - k + ((cy - (gy[q] - k)) % Mc + Mc) % Mc;
-            auto it = pos.find((int64_t(jx) << 32) | jy);
-            if (it == pos.end()) continue;
-            const int32_t col = ent_of[size_t(c) * n0 + it->second];
-            if (col < 0) continue;
-            for (int cr = 0; cr < B.ncomp; ++cr) {
-              const int32_t row = ent_of[size_t(cr) * n0 + q];
-              if (row < 0) continue;
-              A[size_t(row) * nI + col] = yv[size_t(cr) * n0 + q];
-            }
+    }
+    CK(cudaMemcpyAsync(resp.data(), mg.probe_out, resp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> A[2];
+    std::vector<int32_t> eidx[2];
+    for (int b = 0; b < 2; ++b) {
+      MGBlock& B = mg.blk[b];
+      const int nc = B.ncomp;
+      std::vector<int32_t> ent_of(size_t(nc) * n0, -1);   // interior entries (comp * n0 + slot)
+      for (int q = 0; q < n0; ++q)
+        for (int c = 0; c < nc; ++c) {
+          const int bit = B.fixbits == 4 ? 4 : (1 << c);
+          if (gx[q] >= 0 && !(cm0[q] & bit)) {
+            ent_of[size_t(c) * n0 + q] = int32_t(eidx[b].size());
+            eidx[b].push_back(c * n0 + q);
           }
         }
-    if (!B.coarse_idx || nI > B.coarse_cap) {
-      const int32_t cap = std::max(nI, 1);
-      B.coarse_idx = mg.mem.alloc<int32_t>(cap);
-      B.coarse_inv = mg.mem.alloc<double>(int64_t(cap) * cap);
-      B.coarse_tmp = mg.mem.alloc<double>(cap);
-      B.coarse_rc = mg.mem.alloc<double>(4 * int64_t(cap));
-      if (!mg.mem.err.empty()) return mg.mem.err;
-      B.coarse_cap = cap;
+      const int nI = int(eidx[b].size());
+      A[b].assign(size_t(nI) * nI, 0.0);
+      for (int c = 0; c < nc; ++c)
+        for (int cy = 0; cy < Mc; ++cy)
+          for (int cx = 0; cx < Mc; ++cx) {
+            const double* yv = resp.data() + probe_base[b] + ((c * Mc + cy) * Mc + cx) * int64_t(nc) * n0;
+            for (int q = 0; q < n0; ++q) {
+              if (gx[q] < 0) continue;
+              // the probed node within distance k of q in each direction
+              const int jx = gx[q] - k + ((cx - (gx[q] - k)) % Mc + Mc) % Mc;
+              const int jy = gy[q] - k + ((cy - (gy[q] - k)) % Mc + Mc) % Mc;
+              auto it = pos.find((int64_t(jx) << 32) | jy);
+              if (it == pos.end()) continue;
+              const int32_t col = ent_of[size_t(c) * n0 + it->second];
+              if (col < 0) continue;
+              for (int cr = 0; cr < nc; ++cr) {
+                const int32_t row = ent_of[size_t(cr) * n0 + q];
+                if (row < 0) continue;
+                A[b][size_t(row) * nI + col] = yv[size_t(cr) * n0 + q];
+              }
+            }
+          }
+      if (!B.coarse_idx || nI > B.coarse_cap) {
+        const int32_t cap = std::max(nI, 1);
+        B.coarse_idx = mg.mem.alloc<int32_t>(cap);
+        B.coarse_inv = mg.mem.alloc<double>(int64_t(cap) * cap);
+        B.coarse_tmp = mg.mem.alloc<double>(cap);
+        B.coarse_rc = mg.mem.alloc<double>(4 * int64_t(cap));
+        if (!mg.mem.err.empty()) return mg.mem.err;
+        B.coarse_cap = cap;
+      }
+      B.n_coarse = nI;
     }
-    B.n_coarse = nI;
-    if (nI > 0) {
-      // the assembled block goes to the device and is inverted there in place
-      CK(cudaMemcpyAsync(B.coarse_idx, eidx.data(), nI * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(B.coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(mg_spd_invert(nI, B.coarse_inv, B.coarse_rc, mg.spd_bad, s));
-      int32_t bad = 0;
-      CK(cudaMemcpyAsync(&bad, mg.spd_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (bad) return "coarse level block is not positive definite";
+    // the two inversions run side by side (block 1 on the extra pool stream)
+    for (int b = 0; b < 2; ++b) {
+      MGBlock& B = mg.blk[b];
+      cudaStream_t t = b == 0 ? s : mg.su_stream[K];
+      CK(cudaMemsetAsync(mg.spd_bad + b, 0, sizeof(int32_t), t));
+      if (B.n_coarse == 0) continue;
+      CK(cudaMemcpyAsync(B.coarse_idx, eidx[b].data(), B.n_coarse * sizeof(int32_t), cudaMemcpyHostToDevice, t));
+      CK(cudaMemcpyAsync(B.coarse_inv, A[b].data(), A[b].size() * sizeof(double), cudaMemcpyHostToDevice, t));
+      CK(mg_spd_invert(B.n_coarse, B.coarse_inv, B.coarse_rc, mg.spd_bad + b, t));
     }
-    CK(cudaStreamSynchronize(s));
   }
+  // 3. join the pool, read the CG coefficients (and coarse status) once
+  for (int i = 0; i <= K; ++i) {
+    CK(cudaEventRecord(mg.su_done[i], mg.su_stream[i]));
+    CK(cudaStreamWaitEvent(s, mg.su_done[i], 0));
+  }
+  std::vector<double> hist(size_t(2) * nl * 2 * kMaxLanczos);
+  int32_t bad[2] = {0, 0};
+  CK(cudaMemcpyAsync(hist.data(), mg.su_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (mg.coarse_mode == 0) CK(cudaMemcpyAsync(bad, mg.spd_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad[0] || bad[1]) return "coarse level block is not positive definite";
+  for (int b = 0; b < 2; ++b)
+    for (int l = 0; l < nl; ++l) {
+      if (l == 0 && mg.coarse_mode == 0) continue;
+      eigen_from_cg(mg, mg.blk[b], l, hist.data() + size_t(b * nl + l) * 2 * kMaxLanczos);
+    }
   mg.ready = true;
   return "";
 }
@@ -340,12 +411,7 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
 #define VC(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
   VC(cudaMemsetAsync(d, 0, nc * N * sizeof(T), s));
   VC(cudaMemsetAsync(x, 0, nc * N * sizeof(T), s));
-  for (int l = 0; l < nl; ++l) {
-    const DevLevel& lv = D.levels[l].lv;
-    VC(mg_copy_in<T>(lv.n_copy, nc, lv.copy_leaf, lv.copy_level, r, nsleaf, d + nc * lv.off, lv.n_slots,
-                     pb.cmask, B.fixbits, s));
-  }
-  // Chebyshev on level l: solve A v = rhs from v = 0 into out (buffers v, vp, t)
+  VC(mg_copy_in<T>(nsleaf, nc, D.home, r, d, pb.cmask, B.fixbits, s));
   // Chebyshev on level l over [a, bb], `degree` applications of D^-1: solve A v = rhs
   // from v = 0 into out (buffers yp, y, t)
   auto cheb_ab = [&](int l, const T* rhs, T* out, double a, double bb, int degree) -> cudaError_t {
@@ -401,25 +467,54 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
   // coarse
   if (mg.coarse_mode == 1) VC(cheb_ab(0, d, x, B.c0_a, B.c0_b, B.c0_deg));
   else VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s));
+  // Post-smoothing on level l of the defect d - A x (t holds A x), from zero,
+  // added to x: the first step forms the defect, the last adds instead of storing.
+  // The level defect d is free once the first step has read it.
+  auto cheb_post = [&](int l) -> cudaError_t {
+    const DevLevel& lv = D.levels[l].lv;
+    const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
+    const double lam = B.lam[l];
+    const int degree = mg.degree;
+    if (!(lam > 0) || degree < 1) return cudaSuccess;   // a zero correction
+    const double a = mg.lo * lam, bb = mg.hi * lam;
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    if (degree == 1)
+      return mg_chebyshev_first_res<T>(n, nullptr, nullptr, nullptr, dinv + o, d + o, t + o, T(1.0 / theta), x + o, s);
+    T* cur = yp + o;
+    T* prev = y + o;
+    T* nxt = d + o;
+    cudaError_t ee = mg_chebyshev_first_res<T>(n, cur, prev, rr + o, dinv + o, d + o, t + o, T(1.0 / theta),
+                                               nullptr, s);
+    if (ee != cudaSuccess) return ee;
+    double rho = 1.0 / sigma;
+    for (int j = 1; j < degree; ++j) {
+      const double rho_n = 1.0 / (2.0 * sigma - rho);
+      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s);
+      if (ee != cudaSuccess) return ee;
+      if (j == degree - 1)
+        return mg_chebyshev_step_add<T>(n, x + o, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho),
+                                        T(2.0 * rho_n / delta), s);
+      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
+      if (ee != cudaSuccess) return ee;
+      T* old_prev = prev;
+      prev = cur;
+      cur = nxt;
+      nxt = old_prev;
+      rho = rho_n;
+    }
+    return cudaSuccess;
+  };
   // up sweep
   for (int l = 1; l < nl; ++l) {
     const DevLevel& lv = D.levels[l].lv;
     const DevLevel& lc = D.levels[l - 1].lv;
-    const int64_t o = nc * lv.off, n = nc * int64_t(lv.n_slots);
+    const int64_t o = nc * lv.off;
     VC(mg_prolong<T>(lv.n_slots, nc, lv.n_slots, lc.n_slots, lv.P_ptr, lv.P_col, lv.P_val, x + nc * lc.off, x + o,
                      mg.cmask + lv.off, B.fixbits, s));
     VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s));
-    VC(mg_residual<T>(n, rr + o, d + o, t + o, s));
-    // post-smoothing correction; the level defect d is not needed any more and holds it
-    VC(cheb(l, rr + o, d + o));
-    VC(mg_axpy<T>(n, x + o, d + o, T(1), s));
+    VC(cheb_post(l));
   }
-  VC(mg_leaf_init(nsleaf, nc, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s));
-  for (int l = 0; l < nl; ++l) {
-    const DevLevel& lv = D.levels[l].lv;
-    VC(mg_copy_out<T>(lv.n_copy, nc, lv.copy_leaf, lv.copy_level, x + nc * lv.off, lv.n_slots, z, nsleaf,
-                      pb.cmask, B.fixbits, s));
-  }
+  VC(mg_copy_out<T>(nsleaf, nc, D.home, x, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s));
 #undef VC
   return cudaSuccess;
 }

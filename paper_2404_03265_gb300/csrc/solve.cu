@@ -161,20 +161,52 @@ __global__ void k_scale(int64_t n, double* out, const double* __restrict__ x, do
   GRID_STRIDE(i, n) out[i] = a * x[i];
 }
 
-// partial[b * k + j] = sum over this block's rows of V_j . w
+// partial[b * k + j] = sum over this block's rows of V_j . w.  The basis vectors
+// go in chunks of MD_J; a thread visits its rows i = t, t + S, t + 2 S, ...
+// (S = the grid's thread count) in that order, as a plain grid-stride dot does,
+// but issues the loads of MD_R consecutive visits (w and MD_J basis entries each)
+// together.  It keeps MD_J sums, and the block reduces all of them in one
+// shared-memory tree (fixed order).
+constexpr int MD_J = 8;
+constexpr int MD_R = 4;
 __global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ V, int64_t ld,
                                    const double* __restrict__ w, double* partial) {
-  __shared__ double sh[TPB];
-  for (int j = 0; j < k; ++j) {
-    double acc = 0.0;
-    GRID_STRIDE(i, n) acc += V[j * ld + i] * w[i];
-    sh[threadIdx.x] = acc;
+  __shared__ double sh[MD_J][TPB];
+  const int64_t S = int64_t(gridDim.x) * TPB;
+  for (int j0 = 0; j0 < k; j0 += MD_J) {
+    const int jn = k - j0 < MD_J ? k - j0 : MD_J;
+    double acc[MD_J];
+#pragma unroll
+    for (int q = 0; q < MD_J; ++q) acc[q] = 0.0;
+    const double* Vc = V + int64_t(j0) * ld;
+    for (int64_t i0 = int64_t(blockIdx.x) * TPB + threadIdx.x; i0 < n; i0 += MD_R * S) {
+      double wv[MD_R], vv[MD_J][MD_R];
+#pragma unroll
+      for (int e = 0; e < MD_R; ++e) {
+        const int64_t i = i0 + e * S;
+        wv[e] = i < n ? w[i] : 0.0;
+#pragma unroll
+        for (int q = 0; q < MD_J; ++q) vv[q][e] = (q < jn && i < n) ? Vc[q * ld + i] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < MD_R; ++e) {
+        if (i0 + e * S < n) {
+#pragma unroll
+          for (int q = 0; q < MD_J; ++q) acc[q] += vv[q][e] * wv[e];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MD_J; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
     for (int o = TPB / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      if (threadIdx.x < o) {
+#pragma unroll
+        for (int q = 0; q < MD_J; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+      }
       __syncthreads();
     }
-    if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * k + j] = sh[0];
+    if (threadIdx.x < jn) partial[int64_t(blockIdx.x) * k + j0 + threadIdx.x] = sh[threadIdx.x][0];
     __syncthreads();
   }
 }
@@ -193,12 +225,25 @@ __global__ void k_multidot_final(int nb, int k, const double* __restrict__ parti
   if (threadIdx.x == 0) out[j] = sh[0];
 }
 
-// w += sign * sum_j h_j V_j
+// w += sign * sum_j h_j V_j (the sum in the order j = 0, 1, ...; loads of four
+// basis entries are issued together; h staged in shared memory)
+constexpr int MAX_BASIS = 512;
 __global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
                              double sign, double* w) {
+  __shared__ double hs[MAX_BASIS];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
   GRID_STRIDE(i, n) {
     double acc = 0.0;
-    for (int j = 0; j < k; ++j) acc += h[j] * V[j * ld + i];
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      const double v0 = V[j * ld + i], v1 = V[(j + 1) * ld + i], v2 = V[(j + 2) * ld + i], v3 = V[(j + 3) * ld + i];
+      acc += hs[j] * v0;
+      acc += hs[j + 1] * v1;
+      acc += hs[j + 2] * v2;
+      acc += hs[j + 3] * v3;
+    }
+    for (; j < k; ++j) acc += hs[j] * V[j * ld + i];
     w[i] += sign * acc;
   }
 }
@@ -307,6 +352,7 @@ cudaError_t multidot(int64_t n, int k, const double* V, int64_t ld, const double
 
 cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ld, const double* h, double sign, double* w,
                        cudaStream_t s) {
+  if (k > MAX_BASIS) return cudaErrorInvalidValue;
   if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ld, h, sign, w);
   return cudaGetLastError();
 }

@@ -78,6 +78,7 @@ std::string ensure_workspace(pff_problem& pb, int restart) {
   W.stats = W.mem.alloc<unsigned long long>(4);
   W.partial = W.mem.alloc<double>(size_t(reduction_partials()) * (restart + 2));
   W.h = W.mem.alloc<double>(restart + 2);
+  W.hh = W.mem.alloc<double>(2 * (restart + 1) + 1);
   W.scal = W.mem.alloc<double>(8);
   W.bad = W.mem.alloc<int>(1);
   W.x32 = W.mem.alloc<float>(n3);
@@ -116,6 +117,9 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     }
     return leaf_op(pb, op, MODE_MASK_INPUT | MODE_IDENTITY, pb.lin64, pb.cmask, v, v + 2 * n, y, y + 2 * n, s);
   };
+  for (auto& e : pb.gm_ev)
+    if (!e) RET(cudaEventCreate(&e));
+  cudaEvent_t* ev = pb.gm_ev;
   RET(cudaMemsetAsync(x, 0, n3 * sizeof(double), s));
   RET(precond(mg, b, W.V, s));
   double beta = 0.0;
@@ -129,8 +133,11 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
   }
   const double target = rtol * beta;
   int it = 0;
-  std::vector<double> H(size_t(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), h(restart + 1),
-      h2(restart + 1);
+  std::vector<double> H(size_t(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1),
+      hh(2 * (restart + 1) + 1);
+  double* h1d = W.hh;                     // first pass coefficients
+  double* h2d = W.hh + (restart + 1);     // second pass
+  double* nwd = W.hh + 2 * (restart + 1); // |w|^2
   while (it < maxiter) {
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
@@ -140,17 +147,29 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     bool conv = false;
     for (int j = 0; j < restart; ++j) {
       double* Vj = W.V + size_t(j) * n3;
+      RET(cudaEventRecord(ev[0], s));
       RET(A(Vj, W.tmp));
+      RET(cudaEventRecord(ev[1], s));
       RET(precond(mg, W.tmp, W.w, s));
-      // classical Gram-Schmidt, twice
-      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, W.h, s));
-      RET(cudaMemcpyAsync(h.data(), W.h, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      RET(multi_axpy(n3, j + 1, W.V, n3, W.h, -1.0, W.w, s));
-      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, W.h, s));
-      RET(cudaMemcpyAsync(h2.data(), W.h, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      RET(multi_axpy(n3, j + 1, W.V, n3, W.h, -1.0, W.w, s));
-      double hn = 0.0;
-      RET(norm2(pb, n3, W.w, &hn, s));  // synchronises: h, h2 are on the host
+      RET(cudaEventRecord(ev[2], s));
+      // classical Gram-Schmidt, twice; the coefficients stay on the device until
+      // one copy brings both passes and |w|^2 to the host
+      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, h1d, s));
+      RET(multi_axpy(n3, j + 1, W.V, n3, h1d, -1.0, W.w, s));
+      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, h2d, s));
+      RET(multi_axpy(n3, j + 1, W.V, n3, h2d, -1.0, W.w, s));
+      RET(dot64(n3, W.w, W.w, W.partial, nwd, s));
+      RET(cudaEventRecord(ev[3], s));
+      RET(cudaMemcpyAsync(hh.data(), W.hh, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RET(cudaStreamSynchronize(s));
+      const double* h = hh.data();
+      const double* h2 = hh.data() + (restart + 1);
+      const double hn = std::sqrt(hh[2 * (restart + 1)]);
+      float ms[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < 3; ++q) RET(cudaEventElapsedTime(&ms[q], ev[q], ev[q + 1]));
+      res.t_apply += 1e-3 * ms[0];
+      res.t_vcycle += 1e-3 * ms[1];
+      res.t_orth += 1e-3 * ms[2];
       for (int i = 0; i <= j; ++i) H[size_t(i) * restart + j] = h[i] + h2[i];
       H[size_t(j + 1) * restart + j] = hn;
       for (int i = 0; i < j; ++i) {
@@ -288,6 +307,9 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     RET(gmres_solve(pb, mg, 0, W.rhs, W.dU, o.gmres_rtol, o.restart, o.gmres_maxiter, gr, s, o.matvec));
     info.t_gmres += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup1).count();
     info.gmres.push_back(gr.iterations);
+    info.t_apply += gr.t_apply;
+    info.t_vcycle += gr.t_vcycle;
+    info.t_orth += gr.t_orth;
     if (gr.breakdown) info.gmres_breakdown = true;
     // G~ is the identity on the fixed rows and couples them to no free row, so the
     // fixed part of the solution is the right-hand side there, taken exactly

@@ -65,9 +65,6 @@ std::string upload_mesh(pff_mesh& pm) {
       L.lv.R_col = D.mem.upload(lm.R_col);
       L.lv.R_val = D.mem.upload(rv);
     }
-    L.lv.n_copy = int32_t(lm.copy_leaf.size());
-    L.lv.copy_leaf = D.mem.upload(lm.copy_leaf);
-    L.lv.copy_level = D.mem.upload(lm.copy_level);
     std::vector<int32_t> gx(lm.slot_X.size()), gy(lm.slot_Y.size());
     for (size_t q = 0; q < gx.size(); ++q) {
       gx[q] = lm.slot_X[q] < 0 ? -1 : (lm.slot_X[q] >> (M.Lf - int(l)));
@@ -81,6 +78,27 @@ std::string upload_mesh(pff_mesh& pm) {
     L.cell_child = D.mem.upload(lm.cell_child);
   }
   D.lev_total = off;
+  {
+    // each free leaf node is on the copy list of exactly one level (its home)
+    std::vector<int32_t> hoff(size_t(M.lay.n_slots), 0), hslot(size_t(M.lay.n_slots), -1),
+        hnsl(size_t(M.lay.n_slots), 0);
+    for (size_t l = 0; l < M.levels.size(); ++l) {
+      const LevelMesh& lm = M.levels[l];
+      for (size_t i = 0; i < lm.copy_leaf.size(); ++i) {
+        const int32_t s = lm.copy_leaf[i];
+        if (hslot[s] >= 0) {
+          D.release();
+          return "leaf slot on two copy lists";
+        }
+        hoff[s] = int32_t(D.levels[l].lv.off);
+        hslot[s] = lm.copy_level[i];
+        hnsl[s] = D.levels[l].lv.n_slots;
+      }
+    }
+    D.home.off = D.mem.upload(hoff);
+    D.home.slot = D.mem.upload(hslot);
+    D.home.nsl = D.mem.upload(hnsl);
+  }
   if (!D.mem.err.empty()) {
     std::string err = D.mem.err;
     D.release();

@@ -72,6 +72,7 @@ struct DevMesh {
   };
   std::vector<Level> levels;
   int64_t lev_total = 0;     // sum of level slot counts
+  DevHome home;              // per leaf slot: its home level (copy in and out of the V-cycle)
   void release() {
     mem.release();
     levels.clear();
@@ -89,6 +90,7 @@ struct SolverWS {
   uint8_t *act = nullptr, *act_prev = nullptr;
   unsigned long long* stats = nullptr;
   double *partial = nullptr, *h = nullptr, *scal = nullptr;
+  double* hh = nullptr;   // one Arnoldi step on the device: both Gram-Schmidt passes and |w|^2 (2 (restart + 1) + 1)
   int* bad = nullptr;
   float *x32 = nullptr, *y32 = nullptr;   // FP32 operator applies inside GMRES (3 blocks each)
 };
@@ -98,6 +100,7 @@ struct GmresResult {
   bool converged = false;
   bool breakdown = false;
   double initial = 0.0, estimate = 0.0;
+  double t_apply = 0.0, t_vcycle = 0.0, t_orth = 0.0;   // device seconds per phase of the iterations
 };
 
 struct NewtonOpts {
@@ -117,6 +120,7 @@ struct NewtonInfo {
   std::vector<int64_t> active_size, changes;
   std::string error;
   double t_setup = 0.0, t_gmres = 0.0;   // host wall seconds in multigrid set-up and in GMRES
+  double t_apply = 0.0, t_vcycle = 0.0, t_orth = 0.0;   // device seconds inside GMRES (GmresResult)
 };
 
 }  // namespace pff
@@ -146,6 +150,7 @@ struct pff_problem {
   float* lev_ecell32 = nullptr;
   double* cell_out = nullptr;     // 3 * n_slots: per-cell VJP values
   double* adj_cell = nullptr;     // n_leaf_cells: per-step modulus gradient of the multi-step adjoint
+  cudaEvent_t gm_ev[4] = {};      // GMRES phase timing (created on first use)
 };
 
 namespace pff {
@@ -185,9 +190,19 @@ struct pff_mg {
   float* lin32 = nullptr;
   uint8_t* cmask = nullptr;        // lev_total
   pff::MGBlock blk[2];             // 0: u-u block, 1: phi-phi block
-  // FP64 scratch for the eigenvalue estimate and set-up
-  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *diag = nullptr;
-  double *partial = nullptr, *sc = nullptr, *hist = nullptr;
+  // Set-up: the inverse diagonal and CG eigenvalue estimate of each (block, level)
+  // form an independent chain; the chains run on a pool of streams.  FP64 scratch:
+  // per block 5 level vectors (diag, r, z, p, q) of ncomp * lev_total, per chain
+  // the dot partials, 8 CG scalars and 2 * 64 CG coefficients.
+  static constexpr int kSetupStreams = 8;   // the extra stream inverts the second coarse block
+  cudaStream_t su_stream[kSetupStreams + 1] = {};
+  cudaEvent_t su_done[kSetupStreams + 1] = {};
+  cudaEvent_t su_start = nullptr;
+  double* su_vec[2] = {nullptr, nullptr};
+  double *su_partial = nullptr, *su_sc = nullptr, *su_hist = nullptr;
+  // coarse probing: all colours of both blocks at once (in and out, probe_len doubles each)
+  double *probe_in = nullptr, *probe_out = nullptr;
+  int64_t probe_len = 0;
   bool ready = false;
   // V-cycles replayed as CUDA graphs (one per block, captured after each set-up;
   // inputs and outputs pass through fixed staging vectors of 3 * n_slots doubles)
@@ -198,7 +213,7 @@ struct pff_mg {
   cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double *vc_in = nullptr, *vc_out = nullptr;
-  int32_t* spd_bad = nullptr;      // set by the coarse inversion when a pivot is not positive
+  int32_t* spd_bad = nullptr;      // per block: set by the coarse inversion when a pivot is not positive
 };
 
 namespace pff {

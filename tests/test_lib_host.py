@@ -67,3 +67,30 @@ def test_refine_marked_and_errors():
         m.refine_global(1)
     with pytest.raises(PffError):
         Mesh(1, -1, 0, 1, 1, 1)
+
+
+@pytest.mark.parametrize("py_name,c_name", [("MeshInfo", "pff_mesh_info"), ("Params", "pff_params"),
+                                            ("SolveInfo", "pff_solve_info"), ("NewtonOpts", "pff_newton_opts")])
+def test_binding_struct_layouts_match_header(py_name, c_name, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that
+    a C compiler gives the struct of the same name in include/pff.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2404_03265_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cls = getattr(_lib, py_name)
+    fields = [f[0] for f in cls._fields_]
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "pff.h"', "int main(void) {",
+           '  printf("%%zu\\n", sizeof(%s));' % c_name]
+    src += ['  printf("%%zu\\n", offsetof(%s, %s));' % (c_name, f) for f in fields]
+    src += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(tmp_path / "layout.c"), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(cls), (c_name, got[0], ctypes.sizeof(cls))
+    for f, off in zip(fields, got[1:]):
+        assert getattr(cls, f).offset == off, (c_name, f, off, getattr(cls, f).offset)

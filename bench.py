@@ -450,9 +450,17 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the load-step timing leg")
     ap.add_argument("--large", action="store_true",
                     help="add the 16.5M-DoF Q2 five-load-step solve and its checkpointed adjoint")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="run only the first load step of the solve leg (FP32 V-cycle, FP32 GMRES applies) and "
+                         "print its record: a small case for profiling the set-up, V-cycle and GMRES kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.solve_only:
+        from paper_2404_03265_gb300 import PFF_F32
+        r, _, _ = time_solve(PFF_F32, loads=SOLVE_LOADS[:1])
+        print(json.dumps({"solve_only": r}))
         return
     args.warmup = max(args.warmup, 3)
 

@@ -157,8 +157,11 @@ __global__ void k_axpby(int64_t n, double* out, const double* __restrict__ x, do
   GRID_STRIDE(i, n) out[i] = a * x[i] + b * y[i];
 }
 
-__global__ void k_scale(int64_t n, double* out, const double* __restrict__ x, double a) {
-  GRID_STRIDE(i, n) out[i] = a * x[i];
+
+// Krylov basis storage: rows in blocks of kBasisBlock; block r holds the rows
+// r kBasisBlock .. of every basis vector j contiguously, at r ldb + j kBasisBlock.
+__device__ __forceinline__ int64_t basis_row(int64_t i, int64_t ldb) {
+  return (i / kBasisBlock) * ldb + (i % kBasisBlock);
 }
 
 // partial[b * k + j] = sum over this block's rows of V_j . w.  The basis vectors
@@ -169,7 +172,7 @@ __global__ void k_scale(int64_t n, double* out, const double* __restrict__ x, do
 // shared-memory tree (fixed order).
 constexpr int MD_J = 8;
 constexpr int MD_R = 4;
-__global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ V, int64_t ld,
+__global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ V, int64_t ldb,
                                    const double* __restrict__ w, double* partial) {
   __shared__ double sh[MD_J][TPB];
   const int64_t S = int64_t(gridDim.x) * TPB;
@@ -178,15 +181,16 @@ __global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ 
     double acc[MD_J];
 #pragma unroll
     for (int q = 0; q < MD_J; ++q) acc[q] = 0.0;
-    const double* Vc = V + int64_t(j0) * ld;
+    const double* Vc = V + int64_t(j0) * kBasisBlock;
     for (int64_t i0 = int64_t(blockIdx.x) * TPB + threadIdx.x; i0 < n; i0 += MD_R * S) {
       double wv[MD_R], vv[MD_J][MD_R];
 #pragma unroll
       for (int e = 0; e < MD_R; ++e) {
         const int64_t i = i0 + e * S;
+        const int64_t bi = basis_row(i, ldb);
         wv[e] = i < n ? w[i] : 0.0;
 #pragma unroll
-        for (int q = 0; q < MD_J; ++q) vv[q][e] = (q < jn && i < n) ? Vc[q * ld + i] : 0.0;
+        for (int q = 0; q < MD_J; ++q) vv[q][e] = (q < jn && i < n) ? Vc[bi + q * kBasisBlock] : 0.0;
       }
 #pragma unroll
       for (int e = 0; e < MD_R; ++e) {
@@ -228,23 +232,34 @@ __global__ void k_multidot_final(int nb, int k, const double* __restrict__ parti
 // w += sign * sum_j h_j V_j (the sum in the order j = 0, 1, ...; loads of four
 // basis entries are issued together; h staged in shared memory)
 constexpr int MAX_BASIS = 512;
-__global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
+__global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int64_t ldb, const double* __restrict__ h,
                              double sign, double* w) {
   __shared__ double hs[MAX_BASIS];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
   GRID_STRIDE(i, n) {
+    const double* Vi = V + basis_row(i, ldb);
     double acc = 0.0;
     int j = 0;
     for (; j + 4 <= k; j += 4) {
-      const double v0 = V[j * ld + i], v1 = V[(j + 1) * ld + i], v2 = V[(j + 2) * ld + i], v3 = V[(j + 3) * ld + i];
+      const double v0 = Vi[j * kBasisBlock], v1 = Vi[(j + 1) * kBasisBlock], v2 = Vi[(j + 2) * kBasisBlock],
+                   v3 = Vi[(j + 3) * kBasisBlock];
       acc += hs[j] * v0;
       acc += hs[j + 1] * v1;
       acc += hs[j + 2] * v2;
       acc += hs[j + 3] * v3;
     }
-    for (; j < k; ++j) acc += hs[j] * V[j * ld + i];
+    for (; j < k; ++j) acc += hs[j] * Vi[j * kBasisBlock];
     w[i] += sign * acc;
+  }
+}
+
+// basis vector j = a x, also written contiguously to vc (x may be vc)
+__global__ void k_store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc) {
+  GRID_STRIDE(i, n) {
+    const double v = a * x[i];
+    V[basis_row(i, ldb) + int64_t(j) * kBasisBlock] = v;
+    vc[i] = v;
   }
 }
 
@@ -335,25 +350,27 @@ cudaError_t axpby(int64_t n, double* out, const double* x, double a, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t scale(int64_t n, double* out, const double* x, double a, cudaStream_t s) {
-  if (n > 0) k_scale<<<blocks_for(n), TPB, 0, s>>>(n, out, x, a);
-  return cudaGetLastError();
-}
 
 int reduction_partials() { return RED_BLOCKS; }
 
-cudaError_t multidot(int64_t n, int k, const double* V, int64_t ld, const double* w, double* partial, double* out,
+cudaError_t multidot(int64_t n, int k, const double* V, int64_t ldb, const double* w, double* partial, double* out,
                      cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  k_multidot_partial<<<RED_BLOCKS, TPB, 0, s>>>(n, k, V, ld, w, partial);
+  k_multidot_partial<<<RED_BLOCKS, TPB, 0, s>>>(n, k, V, ldb, w, partial);
   k_multidot_final<<<k, TPB, 0, s>>>(RED_BLOCKS, k, partial, out);
   return cudaGetLastError();
 }
 
-cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ld, const double* h, double sign, double* w,
+cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const double* h, double sign, double* w,
                        cudaStream_t s) {
   if (k > MAX_BASIS) return cudaErrorInvalidValue;
-  if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ld, h, sign, w);
+  if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ldb, h, sign, w);
+  return cudaGetLastError();
+}
+
+cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
+                        cudaStream_t s) {
+  if (n > 0) k_store_basis<<<blocks_for(n), TPB, 0, s>>>(n, V, ldb, j, x, a, vc);
   return cudaGetLastError();
 }
 

@@ -35,14 +35,21 @@ cudaError_t copy_fixed(int64_t n, const uint8_t* cmask, const double* x, double*
 cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
                       cudaStream_t s);
 cudaError_t axpby(int64_t n, double* out, const double* x, double a, const double* y, double b, cudaStream_t s);
-cudaError_t scale(int64_t n, double* out, const double* x, double a, cudaStream_t s);
 int reduction_partials();
-// out[j] = V_j . w, j < k (V_j = V + j * ld)
-cudaError_t multidot(int64_t n, int k, const double* V, int64_t ld, const double* w, double* partial, double* out,
+// Krylov basis V in row blocks: entry i of basis vector j at
+// (i / kBasisBlock) ldb + j kBasisBlock + i % kBasisBlock, ldb = (vectors held) kBasisBlock,
+// so the rows of one block of all vectors are adjacent in memory.
+constexpr int64_t kBasisBlock = 2048;
+inline int64_t basis_blocks(int64_t n) { return (n + kBasisBlock - 1) / kBasisBlock; }
+// out[j] = V_j . w, j < k
+cudaError_t multidot(int64_t n, int k, const double* V, int64_t ldb, const double* w, double* partial, double* out,
                      cudaStream_t s);
 // w += sign * sum_j h[j] V_j  (h on the device)
-cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ld, const double* h, double sign, double* w,
+cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const double* h, double sign, double* w,
                        cudaStream_t s);
+// V_j = a x, and vc = a x contiguously (x may be vc)
+cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
+                        cudaStream_t s);
 cudaError_t vsum(int64_t n, const double* a, double* partial, double* out, cudaStream_t s);
 cudaError_t all_finite(int64_t n, const double* a, int* bad, cudaStream_t s);
 

@@ -62,7 +62,8 @@ std::string ensure_workspace(pff_problem& pb, int restart) {
   W = SolverWS();
   W.restart = restart;
   const int64_t n3 = 3 * n;
-  W.V = W.mem.alloc<double>(size_t(restart + 1) * n3);
+  W.V = W.mem.alloc<double>(size_t(basis_blocks(n3)) * size_t(restart + 1) * kBasisBlock);
+  W.vc = W.mem.alloc<double>(n3);
   W.w = W.mem.alloc<double>(n3);
   W.tmp = W.mem.alloc<double>(n3);
   W.rhs = W.mem.alloc<double>(n3);
@@ -121,9 +122,10 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     if (!e) RET(cudaEventCreate(&e));
   cudaEvent_t* ev = pb.gm_ev;
   RET(cudaMemsetAsync(x, 0, n3 * sizeof(double), s));
-  RET(precond(mg, b, W.V, s));
+  const int64_t ldb = int64_t(restart + 1) * kBasisBlock;   // row-block stride of the basis
+  RET(precond(mg, b, W.vc, s));
   double beta = 0.0;
-  RET(norm2(pb, n3, W.V, &beta, s));
+  RET(norm2(pb, n3, W.vc, &beta, s));
   res = GmresResult();
   res.initial = beta;
   if (!(beta > 0.0)) {
@@ -142,22 +144,22 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
-    RET(scale(n3, W.V, W.V, 1.0 / beta, s));
+    RET(store_basis(n3, W.V, ldb, 0, W.vc, 1.0 / beta, W.vc, s));
     int jd = 0;
     bool conv = false;
     for (int j = 0; j < restart; ++j) {
-      double* Vj = W.V + size_t(j) * n3;
+      // W.vc holds V_j contiguously
       RET(cudaEventRecord(ev[0], s));
-      RET(A(Vj, W.tmp));
+      RET(A(W.vc, W.tmp));
       RET(cudaEventRecord(ev[1], s));
       RET(precond(mg, W.tmp, W.w, s));
       RET(cudaEventRecord(ev[2], s));
       // classical Gram-Schmidt, twice; the coefficients stay on the device until
       // one copy brings both passes and |w|^2 to the host
-      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, h1d, s));
-      RET(multi_axpy(n3, j + 1, W.V, n3, h1d, -1.0, W.w, s));
-      RET(multidot(n3, j + 1, W.V, n3, W.w, W.partial, h2d, s));
-      RET(multi_axpy(n3, j + 1, W.V, n3, h2d, -1.0, W.w, s));
+      RET(multidot(n3, j + 1, W.V, ldb, W.w, W.partial, h1d, s));
+      RET(multi_axpy(n3, j + 1, W.V, ldb, h1d, -1.0, W.w, s));
+      RET(multidot(n3, j + 1, W.V, ldb, W.w, W.partial, h2d, s));
+      RET(multi_axpy(n3, j + 1, W.V, ldb, h2d, -1.0, W.w, s));
       RET(dot64(n3, W.w, W.w, W.partial, nwd, s));
       RET(cudaEventRecord(ev[3], s));
       RET(cudaMemcpyAsync(hh.data(), W.hh, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -192,7 +194,7 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
         conv = std::fabs(g[j + 1]) <= target || hn == 0.0;
         break;
       }
-      RET(scale(n3, W.V + size_t(j + 1) * n3, W.w, 1.0 / hn, s));
+      RET(store_basis(n3, W.V, ldb, j + 1, W.w, 1.0 / hn, W.vc, s));
     }
     // y = H^-1 g (upper triangular), x += V y
     std::vector<double> y(jd, 0.0);
@@ -203,7 +205,7 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     }
     if (jd > 0) {
       RET(cudaMemcpyAsync(W.h, y.data(), jd * sizeof(double), cudaMemcpyHostToDevice, s));
-      RET(multi_axpy(n3, jd, W.V, n3, W.h, 1.0, x, s));
+      RET(multi_axpy(n3, jd, W.V, ldb, W.h, 1.0, x, s));
     }
     res.iterations = it;
     res.estimate = std::fabs(g[jd]);
@@ -212,8 +214,8 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     // restart from the true preconditioned residual
     RET(A(x, W.tmp));
     RET(axpby(n3, W.tmp, b, 1.0, W.tmp, -1.0, s));
-    RET(precond(mg, W.tmp, W.V, s));
-    RET(norm2(pb, n3, W.V, &beta, s));
+    RET(precond(mg, W.tmp, W.vc, s));
+    RET(norm2(pb, n3, W.vc, &beta, s));
     res.estimate = beta;
     if (beta <= target) { res.converged = true; return cudaSuccess; }
   }

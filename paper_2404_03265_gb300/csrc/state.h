@@ -86,6 +86,7 @@ struct SolverWS {
   bool ready = false;
   int restart = 0;
   double *V = nullptr, *w = nullptr, *tmp = nullptr, *rhs = nullptr, *R = nullptr, *res = nullptr;
+  double* vc = nullptr;   // the newest basis vector, contiguous (V is stored in row blocks)
   double *dU = nullptr, *du0 = nullptr, *st = nullptr, *ut = nullptr, *B = nullptr;
   uint8_t *act = nullptr, *act_prev = nullptr;
   unsigned long long* stats = nullptr;

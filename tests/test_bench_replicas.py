@@ -51,12 +51,12 @@ def test_two_gloo_ranks_max_time_and_rate():
 def test_reference_arm_prints_on_rank0_only():
     env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+                        "--warmup", "0", "--ref-seconds", "2"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
     env["RANK"] = "0"
     env["LOCAL_RANK"] = "0"
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+                        "--warmup", "0", "--ref-seconds", "2"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"

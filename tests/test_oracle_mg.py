@@ -179,3 +179,38 @@ def test_coarse_chebyshev(k, frac):
         y = rng.normal(size=n) * free
         zx, zy = M.vcycle(blk, x) * free, M.vcycle(blk, y) * free
         assert abs(x @ zy - y @ zx) < 1e-10 * abs(x @ zy)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_global_level_operators_are_uniform_mesh_jacobians(k):
+    """On each globally refined level l the level blocks (the cells of level l with
+    the linearisation injected from the leaf nodes) equal the u-u and phi-phi
+    Jacobian blocks of the uniform mesh with l global refinements, built on its own
+    (own node numbering and coordinates) with the same nodal values at the same
+    points: variable-coefficient rediscretisation on each level, as the V-cycle of
+    Sec. 3.2 uses, and not a Galerkin product."""
+    rec = dict(domain=synth.DOMAIN, ncx=2, ncy=2, n_global=2, steps=[("box", -2.0, 2.0, -1.0, 1.0)] * 2)
+    leaf = LeafMesh(build_recipe(rec), k)
+    u, phi, phit = synth.linearisation(leaf.X, leaf.Y, leaf.Xmax, leaf.Ymax, seed=3, u_std=0.2)
+    mat = ops.Material(E=1.0, nu=0.2, Gc=1.3, eps=0.5, kappa=1e-3, p=0.3)
+    M = mg.MG(leaf, mat, u, phi, phit, np.zeros(leaf.nn, bool))
+    uf = np.stack([leaf.C @ u[:, 0], leaf.C @ u[:, 1]], 1)
+    pf, ptf = leaf.C @ phi, leaf.C @ phit
+    for l in range(rec["n_global"] + 1):
+        uni = LeafMesh(build_recipe(dict(rec, n_global=l, steps=[])), k)
+        assert not uni.is_hanging.any()
+        s = 1 << (leaf.Lf - l)
+        key = (uni.Y * s) * (leaf.Xmax + 1) + uni.X * s
+        ln = np.searchsorted(leaf.key, key)
+        assert np.array_equal(leaf.key[ln], key)
+        G = ops.assemble_jacobian(uni, mat, ops.State(uni, uf[ln], pf[ln], ptf[ln])).toarray()
+        lm = M.levels[l]
+        li = lm.find(uni.X * s, uni.Y * s)
+        assert lm.nn == uni.nn and np.array_equal(np.sort(li), np.arange(lm.nn))
+        n = uni.nn
+        pu = np.concatenate([li, lm.nn + li])
+        Auu = M.B["uu"][l].A.toarray()[np.ix_(pu, pu)]
+        App = M.B["pp"][l].A.toarray()[np.ix_(li, li)]
+        for got, ref in ((Auu, G[:2 * n, :2 * n]), (App, G[2 * n:, 2 * n:])):
+            assert np.abs(ref).max() > 0
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()

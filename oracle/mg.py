@@ -35,10 +35,10 @@ Readings where the paper is silent:
 
 Pinned: Chebyshev error polynomial on a diagonal operator; Ritz value bounds;
 V-cycle == multiplicative subspace correction (constant coefficients);
-symmetry of the V-cycle; on globally refined levels, the variable-coefficient
-level blocks == the Jacobian blocks of the uniform mesh of that level built on
-its own.  Parity unpinned beyond these for the variable-coefficient operators
-of the locally refined levels (no V-cycle output is printed in the paper).
+symmetry of the V-cycle; the variable-coefficient level blocks == the Jacobian
+blocks of a uniform mesh built on its own (own numbering and coordinates) with
+the same nodal values: of the whole level on globally refined levels, and of
+the level's cells within their bounding rectangle on locally refined ones.
 """
 import numpy as np
 import scipy.linalg as sla

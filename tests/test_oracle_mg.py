@@ -214,3 +214,59 @@ def test_global_level_operators_are_uniform_mesh_jacobians(k):
         for got, ref in ((Auu, G[:2 * n, :2 * n]), (App, G[2 * n:, 2 * n:])):
             assert np.abs(ref).max() > 0
             assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_local_level_operators_are_submesh_jacobians(k):
+    """Each locally refined level's blocks equal the Jacobian blocks of a uniform mesh
+    built on its own over the level's bounding rectangle (cells of the same size, no
+    hanging nodes, own node numbering), assembled over the cells of that level only,
+    with the same nodal values: the level operator of local smoothing is the
+    rediscretisation on the level's own cells, with the refinement edge left open."""
+    rec = dict(domain=synth.DOMAIN, ncx=4, ncy=4, n_global=2, steps=[("box", -2.0, 2.0, -1.0, 1.0)] * 3)
+    leaf = LeafMesh(build_recipe(rec), k)
+    assert leaf.Lf == 5
+    u, phi, phit = synth.linearisation(leaf.X, leaf.Y, leaf.Xmax, leaf.Ymax, seed=4, u_std=0.2)
+    mat = ops.Material(E=1.0, nu=0.3, Gc=0.7, eps=0.4, kappa=1e-2, p=0.2)
+    M = mg.MG(leaf, mat, u, phi, phit, np.zeros(leaf.nn, bool))
+    uf = np.stack([leaf.C @ u[:, 0], leaf.C @ u[:, 1]], 1)
+    pf, ptf = leaf.C @ phi, leaf.C @ phit
+    x0, x1, y0, y1 = synth.DOMAIN
+    not_rect = 0
+    for l in range(rec["n_global"] + 1, leaf.Lf + 1):
+        lm = M.levels[l]
+        i, j = lm.cells[:, 1], lm.cells[:, 2]
+        i0, i1, j0, j1 = i.min(), i.max(), j.min(), j.max()
+        not_rect += len(lm.cells) < (i1 - i0 + 1) * (j1 - j0 + 1)
+        hx = (x1 - x0) / (rec["ncx"] << l)
+        hy = (y1 - y0) / (rec["ncy"] << l)
+        sub = (x0 + i0 * hx, x0 + (i1 + 1) * hx, y0 + j0 * hy, y0 + (j1 + 1) * hy)
+        uni = LeafMesh(build_recipe(dict(domain=sub, ncx=int(i1 - i0 + 1), ncy=int(j1 - j0 + 1), n_global=0,
+                                         steps=[])), k)
+        assert not uni.is_hanging.any()
+        ucell = {(int(a), int(b)): c for c, (_, a, b) in enumerate(uni.cells)}
+        idx = np.array(sorted(ucell[(int(a - i0), int(b - j0))] for a, b in zip(i, j)))
+        s = 1 << (leaf.Lf - l)
+        X, Y = (uni.X + i0 * k) * s, (uni.Y + j0 * k) * s
+        key = Y * (leaf.Xmax + 1) + X
+        ln = np.minimum(np.searchsorted(leaf.key, key), leaf.nn - 1)
+        there = leaf.key[ln] == key              # uniform nodes that are leaf nodes
+        li = lm.find(X, Y)                       # uniform nodes that are level nodes
+        assert np.all(there[li >= 0])
+        assert np.array_equal(np.sort(li[li >= 0]), np.arange(lm.nn))
+        z = lambda a: np.where(there.reshape((-1,) + (1,) * (a.ndim - 1)), a[ln], 0.0)
+        st = ops.State(uni, z(uf), z(pf), z(ptf))
+        G = ops.assemble_jacobian(uni, mat, st, cell_idx=idx).toarray()
+        keep = np.nonzero(li >= 0)[0]            # in level order below
+        keep = keep[np.argsort(li[keep])]
+        n = uni.nn
+        gu = np.concatenate([keep, n + keep])
+        ref_uu = G[np.ix_(gu, gu)]
+        ref_pp = G[np.ix_(2 * n + keep, 2 * n + keep)]
+        for got, ref in ((M.B["uu"][l].A.toarray(), ref_uu), (M.B["pp"][l].A.toarray(), ref_pp)):
+            assert np.abs(ref).max() > 0
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        # no entries of the uniform assembly outside the level's nodes
+        outside = np.setdiff1d(np.arange(3 * n), np.concatenate([gu, 2 * n + keep]))
+        assert not np.any(G[outside]) and not np.any(G[:, outside])
+    assert not_rect >= 1   # the 2:1 balance closure makes some level non-rectangular

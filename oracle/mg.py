@@ -10,7 +10,7 @@ on the levels above 0; local smoothing acts only on the cells refined to the
 current level (no hanging nodes on a level); Dirichlet conditions go to the
 levels canonically; a DoF is inactive on a level only if all its neighbours are.
 
-Readings where the paper is silent (see DESIGN.md):
+Readings where the paper is silent:
 * level mesh l = all cells of refinement level l (leaf or refined); its
   refinement edge E_l = level nodes that touch a leaf cell of level < l;
 * level linearisation = injection of the (constraint-resolved) leaf nodal

@@ -659,7 +659,7 @@ def main():
         }
     if args.large:
         line["large"] = time_large()
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
 

@@ -42,9 +42,11 @@ Quadrature: (k+1)^2 Gauss points per leaf cell on every term.
 
 Pinned by tests/test_oracle_operators.py: closed-form elastic energy of linear
 fields, rigid modes, patch test with hanging nodes, pure-elasticity limit
-(R == 0 at u = 0, phi = 1), central-difference Jacobian of the residual
-(cubic in U, Richardson-extrapolated), block triangular / symmetric diagonal
-blocks, TCV of an exactly represented field.
+(R == 0 at u = 0, phi = 1), closed-form sum rules of every term of A for
+linear fields (exact domain integrals of the weak form at linear test fields),
+Table 1's Lame constants, central-difference Jacobian of the residual (cubic
+in U, Richardson-extrapolated), block triangular / symmetric diagonal blocks,
+TCV of an exactly represented field.
 """
 import numpy as np
 import scipy.sparse as sp

@@ -173,3 +173,73 @@ def test_cod_linear_fields_closed_form(name, k):
     # the same field's TCV, integral of u . grad phi over the domain
     tcv = ops.tcv(om, st)
     assert abs(tcv - 20.0 * 20.0 * (a * hh + d * q)) <= 1e-10 * max(1.0, abs(tcv))
+
+
+def test_table1_lame_constants():
+    """Table 1 lists mu = 0.42 and lambda = 0.28 for E = 1, nu = 0.2 (two digits):
+    the plane-strain Lame constants E / (2 (1 + nu)) and E nu / ((1 + nu)(1 - 2 nu))."""
+    m = ops.Material(E=1.0, nu=0.2)
+    assert round(m.mu, 2) == 0.42 and round(m.lam, 2) == 0.28
+
+
+@pytest.mark.parametrize("name,k", [("small", 1), ("tiny", 2)])
+def test_residual_sum_rules_closed_form(name, k):
+    """Problem 2 for fields linear in x and y, on a mesh with hanging nodes.  Every
+    integrand then has degree <= 3 in each variable, so the (k+1)^2 Gauss rule is
+    exact, and contracting the assembled form with the nodal values of a linear
+    test field w (reproduced exactly on every cell) gives the domain integral of
+    the weak form at w, computed here in closed form by exact polynomial
+    integration over the square:
+        A_u(w)   = (g(phi~) sigma(u), e(w)) + (phi~^2 p, div w),  g = (1 - kappa) phi~^2 + kappa
+        A_phi(w) = ((1 - kappa) phi sigma(u):e(u), w) + 2 p (phi div u, w)
+                   - G_c / l (1 - phi, w) + G_c l (grad phi, grad w),
+    with the plane-strain sigma(u) = 2 mu e(u) + lambda tr e(u) I.  Every term,
+    sign and factor enters one of the checked integrals."""
+    sp = pytest.importorskip("sympy")
+    om = mesh(name, k)
+    x0, x1, y0, y1 = synth.DOMAIN
+    R = sp.Rational
+    E, nu, Gc, ell, kappa, p = R(3, 2), R(1, 5), R(7, 10), R(3, 4), R(1, 20), R(3, 10)
+    mu, lam = E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+    x, y = sp.symbols("x y")
+    ux = R(1, 40) + R(3, 200) * x - R(1, 100) * y
+    uy = -R(1, 50) + R(1, 80) * x + R(1, 160) * y
+    phi = R(1, 2) + R(1, 40) * x + R(1, 60) * y
+    phit = R(3, 5) - R(1, 50) * x + R(1, 30) * y
+    exx, eyy, exy = sp.diff(ux, x), sp.diff(uy, y), (sp.diff(ux, y) + sp.diff(uy, x)) / 2
+    sxx, syy, sxy = 2 * mu * exx + lam * (exx + eyy), 2 * mu * eyy + lam * (exx + eyy), 2 * mu * exy
+    g = (1 - kappa) * phit ** 2 + kappa
+    integ = lambda f: sp.integrate(sp.integrate(sp.expand(f), (x, x0, x1)), (y, y0, y1))
+
+    def a_u(wx, wy):
+        wxx, wyy, wxy = sp.diff(wx, x), sp.diff(wy, y), (sp.diff(wx, y) + sp.diff(wy, x)) / 2
+        return integ(g * (sxx * wxx + syy * wyy + 2 * sxy * wxy) + phit ** 2 * p * (wxx + wyy))
+
+    def a_phi(w):
+        se = sxx * exx + syy * eyy + 2 * sxy * exy
+        return integ((1 - kappa) * phi * se * w + 2 * p * phi * (exx + eyy) * w - Gc / ell * (1 - phi) * w
+                     + Gc * ell * (sp.diff(phi, x) * sp.diff(w, x) + sp.diff(phi, y) * sp.diff(w, y)))
+
+    # the oracle on the same fields
+    X = x0 + om.X * (x1 - x0) / om.Xmax
+    Y = y0 + om.Y * (y1 - y0) / om.Ymax
+    ev = lambda f: sp.lambdify((x, y), f, "numpy")(X, Y) * np.ones(om.nn)
+    st = ops.State(om, np.stack([ev(ux), ev(uy)], 1), ev(phi), ev(phit))
+    mat = ops.Material(E=float(E), nu=float(nu), Gc=float(Gc), eps=float(ell), kappa=float(kappa), p=float(p))
+    A = ops.residual_form(om, mat, st)
+    nn = om.nn
+    Au = (A[:nn], A[nn:2 * nn])
+    Ap = A[2 * nn:]
+    checks = []
+    for wx, wy in ((1, 0), (0, 1), (x, 0), (y, 0), (0, x), (0, y), (x + 2 * y, y - 3 * x)):
+        ref = float(a_u(sp.sympify(wx), sp.sympify(wy)))
+        got = float(Au[0] @ ev(sp.sympify(wx)) + Au[1] @ ev(sp.sympify(wy)))
+        checks.append((got, ref))
+    for w in (1, x, y, 2 * x - y):
+        ref = float(a_phi(sp.sympify(w)))
+        got = float(Ap @ ev(sp.sympify(w)))
+        checks.append((got, ref))
+    scale = max(abs(r) for _, r in checks)
+    for got, ref in checks:
+        assert abs(got - ref) <= 1e-12 * scale, (got, ref)
+    assert sum(abs(r) > 1e-6 * scale for _, r in checks) >= 8   # the checks are not trivially zero

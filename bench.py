@@ -473,12 +473,15 @@ def run_reference(args):
     if rank != 0:
         return
     o = OracleApplySample()
+    o.step(1000)   # first call: one-time costs stay out of the calibration
     probes = []
     for m in (1000, 10000):
         t0 = time.perf_counter()
         o.step(m)
         probes.append((m, time.perf_counter() - t0))
-    b = max((probes[1][1] - probes[0][1]) / (probes[1][0] - probes[0][0]), 1e-9)
+    # t(m) = a + b m; b is kept at least half the mean cost per cell of the larger
+    # probe, so that a noisy fit cannot inflate the step size
+    b = max((probes[1][1] - probes[0][1]) / (probes[1][0] - probes[0][0]), 0.5 * probes[1][1] / probes[1][0])
     a = max(probes[0][1] - b * probes[0][0], 0.0)
     k, w = max(args.steps, 1), max(args.warmup, 0)
     tau = max(args.ref_seconds, 0.0) / (k + w)

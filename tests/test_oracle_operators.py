@@ -182,8 +182,8 @@ def test_table1_lame_constants():
     assert round(m.mu, 2) == 0.42 and round(m.lam, 2) == 0.28
 
 
-@pytest.mark.parametrize("name,k", [("small", 1), ("tiny", 2)])
-def test_residual_sum_rules_closed_form(name, k):
+@pytest.mark.parametrize("name,k,deg", [("small", 1, 1), ("tiny", 2, 1), ("tiny", 2, 2), ("small", 2, 2)])
+def test_residual_sum_rules_closed_form(name, k, deg):
     """Problem 2 for fields linear in x and y, on a mesh with hanging nodes.  Every
     integrand then has degree <= 3 in each variable, so the (k+1)^2 Gauss rule is
     exact, and contracting the assembled form with the nodal values of a linear
@@ -194,7 +194,10 @@ def test_residual_sum_rules_closed_form(name, k):
         A_phi(w) = ((1 - kappa) phi sigma(u):e(u), w) + 2 p (phi div u, w)
                    - G_c / l (1 - phi, w) + G_c l (grad phi, grad w),
     with the plane-strain sigma(u) = 2 mu e(u) + lambda tr e(u) I.  Every term,
-    sign and factor enters one of the checked integrals."""
+    sign and factor enters one of the checked integrals.  For Q2 (3 x 3 Gauss,
+    exact to degree 5) the fields may also be quadratic (deg = 2): the integrands
+    then have degree <= 5 in each variable, and Q2 reproduces the fields exactly,
+    hanging edges included."""
     sp = pytest.importorskip("sympy")
     om = mesh(name, k)
     x0, x1, y0, y1 = synth.DOMAIN
@@ -206,6 +209,11 @@ def test_residual_sum_rules_closed_form(name, k):
     uy = -R(1, 50) + R(1, 80) * x + R(1, 160) * y
     phi = R(1, 2) + R(1, 40) * x + R(1, 60) * y
     phit = R(3, 5) - R(1, 50) * x + R(1, 30) * y
+    if deg == 2:
+        ux += R(1, 2000) * x * x - R(1, 3000) * x * y
+        uy += R(1, 1500) * y * y + R(1, 4000) * x * x
+        phi += R(1, 800) * x * y - R(1, 1000) * y * y
+        phit += R(1, 900) * x * x + R(1, 700) * x * y
     exx, eyy, exy = sp.diff(ux, x), sp.diff(uy, y), (sp.diff(ux, y) + sp.diff(uy, x)) / 2
     sxx, syy, sxy = 2 * mu * exx + lam * (exx + eyy), 2 * mu * eyy + lam * (exx + eyy), 2 * mu * exy
     g = (1 - kappa) * phit ** 2 + kappa

@@ -38,7 +38,8 @@ V-cycle == multiplicative subspace correction (constant coefficients);
 symmetry of the V-cycle; the variable-coefficient level blocks == the Jacobian
 blocks of a uniform mesh built on its own (own numbering and coordinates) with
 the same nodal values: of the whole level on globally refined levels, and of
-the level's cells within their bounding rectangle on locally refined ones.
+the level's cells within their bounding rectangle on locally refined ones; the
+prolongation reproduces every x^a y^b with a, b <= k exactly.
 """
 import numpy as np
 import scipy.linalg as sla

@@ -270,3 +270,30 @@ def test_local_level_operators_are_submesh_jacobians(k):
         outside = np.setdiff1d(np.arange(3 * n), np.concatenate([gu, 2 * n + keep]))
         assert not np.any(G[outside]) and not np.any(G[:, outside])
     assert not_rect >= 1   # the 2:1 balance closure makes some level non-rectangular
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_prolongation_reproduces_qk_polynomials(k):
+    """The level prolongation is nodal interpolation of the coarse Q_k field: it maps
+    the coarse nodal values of every polynomial x^a y^b with a, b <= k to its fine
+    nodal values exactly, on every level of a locally refined mesh; and a monomial
+    of degree k + 1 in x is not reproduced (the test would pass a degree-blind P)."""
+    rec = dict(domain=synth.DOMAIN, ncx=4, ncy=4, n_global=1, steps=[("box", -2.0, 2.0, -1.0, 1.0)] * 3)
+    leaf = LeafMesh(build_recipe(rec), k)
+    M = mg.MG(leaf, ops.Material(), np.zeros((leaf.nn, 2)), np.ones(leaf.nn), np.ones(leaf.nn),
+              np.zeros(leaf.nn, bool), blocks=("pp",))
+    x0, x1, y0, y1 = synth.DOMAIN
+    xy = lambda lm: (x0 + lm.X * (x1 - x0) / lm.Xmax, y0 + lm.Y * (y1 - y0) / lm.Ymax)
+    missed = 0
+    for l in range(1, leaf.Lf + 1):
+        fine, coarse, P = M.levels[l], M.levels[l - 1], M.P[l]
+        xf, yf = xy(fine)
+        xc, yc = xy(coarse)
+        for a in range(k + 1):
+            for b in range(k + 1):
+                got = P @ (xc ** a * yc ** b)
+                ref = xf ** a * yf ** b
+                assert np.abs(got - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0), (l, a, b)
+        got = P @ xc ** (k + 1)
+        missed += np.abs(got - xf ** (k + 1)).max() > 1e-6 * np.abs(xf ** (k + 1)).max()
+    assert missed == leaf.Lf

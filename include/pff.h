@@ -150,7 +150,10 @@ pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void*
  * direct FP64 solve on level 0.  precision selects the V-cycle arithmetic
  * (PFF_F32: applies, smoothing and transfers in FP32).
  * pff_mg_setup uses the problem's current state and active set (call it after
- * pff_set_state / pff_set_active); it synchronises the stream.
+ * pff_set_state / pff_set_active); it synchronises the stream.  Its per-level
+ * work (inverse diagonals, eigenvalue estimates) runs on an internal pool of
+ * streams that is joined back into `stream` before it returns; the level-0
+ * blocks are assembled by probing and inverted on the device.
  * pff_vcycle: z = MG(r) for one block; fixed leaf DoFs (Dirichlet u, active phi)
  * get z = r, hanging entries and holes 0.  r and z are device vectors.          */
 pff_status pff_mg_create(pff_problem* pb, int32_t precision, pff_mg** out);

@@ -181,36 +181,57 @@ def time_applies(sets, steps, warmup, ws):
 
 
 def time_e2e(mesh, dtype, steps, warmup):
-    """Same metric through the C-ABI with HOST buffers: H2D of x, apply, D2H of y per step."""
+    """Same metric through the C-ABI with HOST buffers.  Every step copies x in
+    from pinned host memory, applies, and copies y out to pinned host memory.
+    Steps are double-buffered over two device buffer sets and three streams
+    (copy in, apply, copy out), so one step's copies overlap its neighbours'
+    apply; events order the reuse of each set."""
     import torch
     from paper_2404_03265_gb300 import PFF_OP_JACOBIAN
-    pb, xu, xp, yu, yp = build_sets(mesh, 1, dtype, seed=0)[0]
-    hxu = xu.cpu().pin_memory()
-    hxp = xp.cpu().pin_memory()
-    hyu = torch.empty_like(hxu).pin_memory()
-    hyp = torch.empty_like(hxp).pin_memory()
-    s = torch.cuda.current_stream()
+    sets = build_sets(mesh, 2, dtype, seed=0)
+    hxu = sets[0][1].cpu().pin_memory()
+    hxp = sets[0][2].cpu().pin_memory()
+    hy = [(torch.empty_like(hxu).pin_memory(), torch.empty_like(hxp).pin_memory()) for _ in range(2)]
+    s_in, s_ap, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_ap = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    torch.cuda.synchronize()
+    for i in range(2):
+        for ev in (ev_in[i], ev_ap[i], ev_out[i]):
+            ev.record(s_in)
 
-    def step():
-        xu.copy_(hxu, non_blocking=True)
-        xp.copy_(hxp, non_blocking=True)
-        pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
-        hyu.copy_(yu, non_blocking=True)
-        hyp.copy_(yp, non_blocking=True)
+    def step(k):
+        i = k % 2
+        pb, xu, xp, yu, yp = sets[i]
+        s_in.wait_event(ev_ap[i])            # the apply of step k - 2 has read x_i
+        with torch.cuda.stream(s_in):
+            xu.copy_(hxu, non_blocking=True)
+            xp.copy_(hxp, non_blocking=True)
+        ev_in[i].record(s_in)
+        s_ap.wait_event(ev_in[i])
+        s_ap.wait_event(ev_out[i])           # the copy out of step k - 2 has read y_i
+        pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN, stream=s_ap)
+        ev_ap[i].record(s_ap)
+        s_out.wait_event(ev_ap[i])
+        with torch.cuda.stream(s_out):
+            hy[i][0].copy_(yu, non_blocking=True)
+            hy[i][1].copy_(yp, non_blocking=True)
+        ev_out[i].record(s_out)
 
-    for _ in range(warmup):
-        step()
+    for k in range(warmup):
+        step(k)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(steps):
-        step()
-    e1.record(s)
+    e0.record(s_in)
+    for k in range(steps):
+        step(k)
+    e1.record(s_out)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     nb = hxu.numel() * hxu.element_size() + hxp.numel() * hxp.element_size()
-    return t, nb, hyu.numel() * hyu.element_size() + hyp.numel() * hyp.element_size()
+    return t, nb, hy[0][0].numel() * hy[0][0].element_size() + hy[0][1].numel() * hy[0][1].element_size()
 
 
 SOLVE_LOADS = (1e-3, 1.5e-3, 2e-3)

@@ -141,6 +141,19 @@ pff_status pff_set_active(pff_problem* pb, const uint8_t* active, void* stream);
 pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
                      void* yu, void* yp, void* stream);
 
+/* Shape of the Q1 cell loop (Sec. 3.3's matrix-free cell-by-cell evaluation;
+ * the shape changes the schedule, not the arithmetic: every cell and every nodal
+ * sum is evaluated in the same order, so results are bitwise the same).  A warp
+ * sweeps a strip of 2 * strip_half_rows node rows of a 30 x 30 brick, its lower
+ * and upper halves side by side.  strip_half_rows: 15 (one strip per brick), 5
+ * or 1 (3 or 15 shorter strips: more warps for small level meshes of the
+ * V-cycle), or 0 (default: chosen per call from the number of bricks).  It acts
+ * on the Jacobian (pff_apply) and the multigrid level block operators; the other
+ * Q1 operators always use 15; Q2 meshes ignore it.  V-cycles captured by an
+ * earlier pff_mg_setup keep their shape until the next one.
+ * Errors: PFF_ERR_INVALID_ARG for other values.                               */
+pff_status pff_set_cell_loop(pff_problem* pb, int32_t strip_half_rows);
+
 /* ---- multigrid preconditioner (Sec. 3.2) -----------------------------------
  * One V-cycle per diagonal block of G~: block 0 = u-u (2 components, vectors of
  * 2*n_slots doubles), block 1 = phi-phi (n_slots doubles).  Levels are all cells
@@ -225,23 +238,28 @@ typedef struct pff_newton_opts {
 
 /* ---- allocation-free variant of pff_apply (no counterpart in the paper) ----
  * Same operators, arguments, layout and results as pff_apply.  The difference is
- * where the apply keeps its interface partial sums (one triple per interface
- * node of an irregular brick, condensed by a second kernel): pff_apply uses
- * buffers made by pff_problem_create, this call uses one fixed device array of
- * PFF_NOALLOC_MAX_PARTIALS triples (1.5 MiB) that is part of the library image.
- * No device or pinned memory is allocated by the call, directly or through a
- * library.  It serves callers that must not allocate while they run: a host
- * whose caching allocator has reserved nearly all device memory (a library
+ * where the apply keeps its scratch: the interface partial sums (one triple per
+ * interface node of an irregular brick, condensed by a second kernel) and, on Q1
+ * meshes, the input resolved on each hanging node (one triple each).  pff_apply
+ * uses buffers made by pff_problem_create; this call uses one fixed device array
+ * of PFF_NOALLOC_MAX_PARTIALS triples (1.5 MiB) that is part of the library
+ * image.  No device or pinned memory is allocated by the call, directly or
+ * through a library.  It serves callers that must not allocate while they run: a
+ * host whose caching allocator has reserved nearly all device memory (a library
  * cudaMalloc could fail at any time there), or a latency-bound loop that cannot
  * afford cudaFree's implicit device synchronisation.
- * Set-up: the first call on a device (that device current) looks up the array's
- * address (cudaGetSymbolAddress) and caches it; make that first call outside any
- * stream capture.
+ * Set-up: pff_problem_create loads the module holding the array on the current
+ * device and caches the array's address (cudaGetSymbolAddress), so that loading
+ * the module, which reserves the array, does not happen inside this call.  On a
+ * device where no problem was created the first call does that look-up itself;
+ * make it outside any stream capture there.  The cached address does not
+ * survive cudaDeviceReset (which invalidates every problem as well).
  * Limits and hazards:
- *  - a mesh with pff_mesh_info.n_partials > PFF_NOALLOC_MAX_PARTIALS is rejected
- *    with PFF_ERR_INVALID_ARG (use pff_apply);
+ *  - a mesh with pff_mesh_info.n_partials, plus n_hanging for fe_degree 1, above
+ *    PFF_NOALLOC_MAX_PARTIALS is rejected with PFF_ERR_INVALID_ARG (use
+ *    pff_apply);
  *  - the array is shared by all problems and streams of a device and keeps the
- *    previous call's contents (nothing in it has to start at zero: every partial
+ *    previous call's contents (nothing in it has to start at zero: every value
  *    that is read is written earlier in the same call); calls that may execute
  *    at the same time on one device race on it, so order them on one stream or
  *    with events;

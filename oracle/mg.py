@@ -16,10 +16,10 @@ Readings where the paper is silent:
 * level linearisation = injection of the (constraint-resolved) leaf nodal
   values; per-cell modulus of a refined cell = mean of its four children;
 * level active set: level-l nodes that coincide with an active leaf node, or
-  that lie below their home level (the coarsest level among the node's leaf
-  cells) and interpolate onto an active node of level l+1 (pessimistic
-  coarsening); on its home level a DoF keeps its leaf state, since it is
-  smoothed on no other level;
+  that are not on their home level (the coarsest level among the node's leaf
+  cells; hanging positions have none) and interpolate onto an active node of
+  level l+1 (pessimistic coarsening); on its home level a DoF keeps its leaf
+  state, since it is smoothed on no other level;
 * Chebyshev: textbook three-term recurrence for D^-1 A on [a, b];
   lambda_max: largest Ritz value of 12 steps of Jacobi-preconditioned CG from a
   fixed start vector 1 + 0.01 * (splitmix64(key) mod 1000) / 1000;
@@ -34,7 +34,11 @@ Readings where the paper is silent:
   tests/test_oracle_mg.py against that definition computed independently).
 
 Pinned: Chebyshev error polynomial on a diagonal operator; Ritz value bounds;
-V-cycle == multiplicative subspace correction (constant coefficients);
+V-cycle == multiplicative subspace correction (constant coefficients), also
+with an active set inside a single-level region; the level active sets ==
+their construction from level basis functions evaluated geometrically, every
+free leaf DoF interior on its home level, and every level-interior function
+zero on the active leaf nodes in that setting;
 symmetry of the V-cycle; the variable-coefficient level blocks == the Jacobian
 blocks of a uniform mesh built on its own (own numbering and coordinates) with
 the same nodal values: of the whole level on globally refined levels, and of
@@ -318,23 +322,7 @@ class MG:
         for c, (l, i, j) in enumerate(leaf.cells):
             lmin[leaf.cell_nodes[c]] = np.minimum(lmin[leaf.cell_nodes[c]], l)
         self.lmin = lmin
-        # level active sets (phi block), finest to coarsest: a level node is
-        # active if the leaf node at its position is active, or if it lies below
-        # its home level and interpolates onto an active node of the next finer
-        # level (pessimistic coarsening).  On its home level a DoF keeps its own
-        # leaf state, else it would be smoothed on no level at all.
-        act = [None] * (Lf + 1)
-        for l in range(Lf, -1, -1):
-            lm = self.levels[l]
-            ln = lm.leaf_node
-            a = self.active_leaf[ln] & ~leaf.is_hanging[ln]
-            if l < Lf:
-                Pf = self.P[l + 1]   # fine(l+1) x coarse(l)
-                child_active = (abs(Pf).T @ act[l + 1].astype(np.float64)) > 0
-                home = (lmin[ln] == l) & ~leaf.is_hanging[ln]
-                a = a | (child_active & ~home)
-            act[l] = a
-        self.act = act
+        self.act = self.level_active()
         self.copy_idx = {}
         for l, lm in enumerate(self.levels):
             nodes = np.nonzero((lmin == l) & ~leaf.is_hanging)[0]
@@ -350,7 +338,7 @@ class MG:
                 if name == "uu":
                     bl.append(Block(lm, Auu, lm.dirichlet, 2))
                 else:
-                    bl.append(Block(lm, App, act[l], 1))
+                    bl.append(Block(lm, App, self.act[l], 1))
             for l, blk in enumerate(bl):
                 if l == 0:
                     blk.lam = None
@@ -374,6 +362,28 @@ class MG:
             b0.A0 = b0.A[I0][:, I0].toarray() if len(I0) else np.zeros((0, 0))
             b0.cho = sla.cho_factor(b0.A0) if len(I0) else None
             self.B[name] = bl
+
+    def level_active(self):
+        """Level active sets of the phi block (Sec. 3.2, last paragraph), finest to
+        coarsest: a level node is active if the leaf node at its position is
+        active, or -- unless this level is the node's home level -- if it
+        interpolates onto an active node of the next finer level (pessimistic
+        coarsening).  On its home level a DoF keeps its own leaf state, else it
+        would be smoothed on no level at all.  Hanging positions have no home."""
+        leaf = self.leaf
+        Lf = leaf.Lf
+        act = [None] * (Lf + 1)
+        for l in range(Lf, -1, -1):
+            lm = self.levels[l]
+            ln = lm.leaf_node
+            a = self.active_leaf[ln] & ~leaf.is_hanging[ln]
+            if l < Lf:
+                Pf = self.P[l + 1]   # fine(l+1) x coarse(l)
+                child_active = (abs(Pf).T @ act[l + 1].astype(np.float64)) > 0
+                home = (self.lmin[ln] == l) & ~leaf.is_hanging[ln]
+                a = a | (child_active & ~home)
+            act[l] = a
+        return act
 
     # ---- level helpers
     def _P(self, l, ncomp):

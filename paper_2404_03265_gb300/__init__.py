@@ -110,6 +110,10 @@ class Problem:
                                              _lib.stream_ptr(stream)))
         return nc.value, na.value, mg_.value
 
+    def set_cell_loop(self, strip_half_rows):
+        """Q1 cell-loop strip half-height: 15, 5, 1, or 0 (by mesh size)."""
+        _lib.check(_lib.lib().pff_set_cell_loop(self._h, strip_half_rows))
+
     def set_pressure(self, p):
         _lib.check(_lib.lib().pff_set_pressure(self._h, p))
         self.params["p"] = p

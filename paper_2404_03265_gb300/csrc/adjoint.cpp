@@ -95,7 +95,7 @@ cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const doub
   SolverWS& W = pb.ws;
   const int64_t n = M.lay.n_slots;
   // the converged state, phi_tilde = phi_old, and its active set
-  RET(launch_set_lin(n, u, phi, phi_old, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
+  RET(launch_set_lin(n, u, phi, phi_old, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, pb.hlin64, pb.hlin32, s));
   pb.has_state = true;
   RET(launch_leaf_cmask(n, D.slot_flags, active, pb.cmask, s));
   err = mg_setup(mg, s);
@@ -140,7 +140,7 @@ cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* 
   if (gE) RET(cudaMemsetAsync(gE, 0, D.n_leaf_cells * sizeof(double), s));
   *ggc_host = 0.0;
   for (int k = N; k >= 1; --k) {
-    RET(launch_set_lin(n, u[k], phi[k], phi[k - 1], D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
+    RET(launch_set_lin(n, u[k], phi[k], phi[k - 1], D.hang, D.nhang, M.k, pb.lin64, pb.lin32, pb.hlin64, pb.hlin32, s));
     pb.has_state = true;
     RET(launch_leaf_cmask(n, D.slot_flags, active[k - 1], pb.cmask, s));
     pb.prm.p = p[k - 1];

@@ -225,6 +225,13 @@ extern "C" pff_status pff_problem_create(pff_mesh* m, const pff_params* prm, pff
       delete pb;
       return fail(PFF_ERR_OOM, e);
     }
+    const cudaError_t ce = noalloc_prepare();
+    if (ce != cudaSuccess) {
+      pb->bufs.release();
+      delete pb;
+      return fail(PFF_ERR_CUDA, std::string("pff_problem_create: fixed scratch of pff_apply_noalloc: ") +
+                                    cudaGetErrorString(ce));
+    }
     *out = pb;
     return PFF_OK;
   })
@@ -246,7 +253,7 @@ extern "C" pff_status pff_set_state(pff_problem* pb, const double* u, const doub
     const Mesh& M = pb->mesh->m;
     const DevMesh& D = pb->mesh->dev;
     PFF_CUDA(launch_set_lin(M.lay.n_slots, u, phi, phit, D.hang, D.nhang, M.k, pb->lin64, pb->lin32,
-                            cudaStream_t(stream)));
+                            pb->hlin64, pb->hlin32, cudaStream_t(stream)));
     pb->has_state = true;
     return PFF_OK;
   })
@@ -341,6 +348,16 @@ extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (mg->su_start) cudaEventDestroy(mg->su_start);
   mg->mem.release();
   delete mg;
+}
+
+extern "C" pff_status pff_set_cell_loop(pff_problem* pb, int32_t strip_half_rows) {
+  PFF_TRY({
+    if (!pb) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (strip_half_rows != 0 && strip_half_rows != 15 && strip_half_rows != 5 && strip_half_rows != 1)
+      return fail(PFF_ERR_INVALID_ARG, "strip_half_rows must be 0, 15, 5 or 1");
+    pb->sweep_sh = strip_half_rows;
+    return PFF_OK;
+  })
 }
 
 // ------------------------------------------------------------------ solvers

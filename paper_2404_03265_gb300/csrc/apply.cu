@@ -9,24 +9,25 @@
 // The u-rows do not see dphi (block lower triangular, Sec. 3.2); the diagonal
 // blocks are the multigrid level operators (Sec. 3.2).
 //
-// Execution: "row sweeps" over strips of RSEG node rows of a brick of 30x30
-// owned node slots.  A half-warp (16 lanes) covers the 32 window columns
-// -1..30; lane l holds columns 2l-1 and 2l and evaluates the two cells to
-// their right as one packed pair: every sum-factorised 2x2 Gauss operation of
-// the two cells is one paired FP32 instruction (FFMA2 / FADD2 / FMUL2).
-// Node rows stream HBM -> shared memory through a per-half-warp cp.async ring
-// several rows ahead of the arithmetic.  Neighbouring lanes exchange node
-// values and nodal contributions with shuffles; there is no block barrier.
-// Input x has its hanging-node constraints resolved on the fly and fixed
-// components masked.  Each owned node is written once, by one lane, in a
-// fixed summation order.  Nodes shared with another level, hanging nodes and
-// their parents write partial sums; a small fix-up kernel condenses them
-// (x_full = C x on input, C^T y on output).  No atomics.
+// Execution: a column sweep over the brick layout (see sweep_q1_kernel).  A
+// warp takes a strip of a brick of 30x30 owned node slots; lane L holds window
+// node column L-1 (-1..30) and evaluates the cell to its right; the strip's
+// lower and upper halves advance one cell row per step side by side, so every
+// sum-factorised 2x2 Gauss operation of the two cells is one paired FP32
+// instruction (FFMA2 / FADD2 / FMUL2) with no per-member index arithmetic.
+// Neighbouring lanes exchange node values and nodal contributions with
+// shuffles; there is no block barrier and no shared memory.  Input x has its
+// hanging-node constraints resolved on the fly and fixed components masked.
+// Each owned node is written once, by one lane, in a fixed summation order.
+// Nodes shared with another level, hanging nodes and their parents write
+// partial sums; a small fix-up kernel condenses them (x_full = C x on input,
+// C^T y on output).  No atomics.
 #include "kernels.cuh"
 
 #include <cmath>
 #include <mutex>
 #include <unordered_map>
+#include <utility>
 
 namespace pff {
 
@@ -39,27 +40,6 @@ template <> struct VT<double> { using T2 = double2; using T4 = dbl4; };
 constexpr int NB = 30;          // owned node slots per brick side
 constexpr int WN = 32;          // window nodes per side (columns -1..30)
 constexpr int NCW = 31;         // window cells per side (cells -1..29)
-#ifndef PFF_RSEG
-#define PFF_RSEG 3
-#endif
-#ifndef PFF_WARPS
-#define PFF_WARPS 4
-#endif
-#ifndef PFF_MINB
-#define PFF_MINB 4
-#endif
-#ifndef PFF_MINB64
-#define PFF_MINB64 2
-#endif
-#ifndef PFF_DEPTH
-#define PFF_DEPTH 4
-#endif
-constexpr int RSEG = PFF_RSEG;    // node rows per half-warp strip
-constexpr int NSEG = NB / RSEG;   // strips per brick
-constexpr int WARPS = PFF_WARPS;  // warps per CTA; a half-warp sweeps one strip per round
-constexpr int DEPTH = PFF_DEPTH;  // ring stages (rows in flight: DEPTH-1)
-constexpr int NROWS = RSEG + 2;   // node rows a strip reads
-static_assert(NB % RSEG == 0, "strip height must divide the brick");
 
 // 2-point Gauss rule on [0, 1]
 constexpr double GA = 0.21132486540518711775;
@@ -76,7 +56,7 @@ __device__ __forceinline__ dbl4 ldg4(const dbl4* p) {
 }
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
-// ---- packed pairs (cell A, cell B).  FP32: Blackwell paired instructions.
+// ---- packed pairs (two cells).  FP32: Blackwell paired instructions.
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -115,11 +95,13 @@ template <typename P>
 struct PField {
   P dxi[2], deta[2];
   P dx0, dy0, X;
-  __device__ __forceinline__ void init(P v0, P v1, P v2, P v3) {
-    using T = decltype(v0.x);
-    dx0 = psub(v1, v0);
-    dy0 = psub(v2, v0);
-    X = psub(psub(v3, v2), dx0);
+  // b, t: values at the cell's lower-left and upper-left nodes; hb, ht: the
+  // right node minus the left node along the lower and upper edge
+  __device__ __forceinline__ void init(P b, P hb, P t, P ht) {
+    using T = decltype(b.x);
+    dx0 = hb;
+    dy0 = psub(t, b);
+    X = psub(ht, hb);
     dxi[0] = pfma(pbc(T(GA)), X, dx0);
     dxi[1] = pfma(pbc(T(GB)), X, dx0);
     deta[0] = pfma(pbc(T(GA)), X, dy0);
@@ -169,13 +151,16 @@ __device__ __forceinline__ void ptest_value(const P fv[2][2], P jxw, P r[4]) {
   r[3] = pfma(jxw, pt, r[3]);
 }
 
-// Two Q1 cells at once.  v[0] = nodes (0,0) of cells A and B, v[1] = (1,0),
-// v[2] = (0,1), v[3] = (1,1).  out[3*N + c]: contribution to node N of
+// Two Q1 cells at once (the members of every pair).  b: fields at the cells'
+// lower-left nodes (0,0), hb: node (1,0) minus node (0,0); t: fields at the
+// upper-left nodes (0,1), ht: node (1,1) minus node (0,1).  out[3*N + c]:
+// contribution to node N (0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1)) of
 // component c (0 u_x, 1 u_y, 2 phi), as a pair over the two cells.  ec: the
 // cells' moduli E_K (the elastic constants in m are then those of unit E), or 1.
 // OP_VJP returns its three per-cell values in out[0..2].
 template <typename T, int OP>
-__device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatConst<T>& m, const LevGeom<T>& g,
+__device__ __forceinline__ void q1_cell_pair(const NodePair<T>& b, const NodePair<T>& hb, const NodePair<T>& t,
+                                             const NodePair<T>& ht, const MatConst<T>& m, const LevGeom<T>& g,
                                              typename VT<T>::T2 ec, typename VT<T>::T2 out[12]) {
   using N = Needs<OP>;
   using P = typename VT<T>::T2;
@@ -187,8 +172,8 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
   PField<P> fux, fuy, fphi, fphit;
   P e11[2], e22[2], uyx[2], uxy[2];
   if (N::linU) {
-    fux.init(v[0].lx, v[1].lx, v[2].lx, v[3].lx);
-    fuy.init(v[0].ly, v[1].ly, v[2].ly, v[3].ly);
+    fux.init(b.lx, hb.lx, t.lx, ht.lx);
+    fuy.init(b.ly, hb.ly, t.ly, ht.ly);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       e11[q] = pmul(fux.dxi[q], ihx);    // du_x/dx at eta_q
@@ -198,14 +183,14 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
     }
   }
   P phiq[2][2], phitq[2][2];
-  if (N::phi) { fphi.init(v[0].lz, v[1].lz, v[2].lz, v[3].lz); fphi.values(v[0].lz, phiq); }
-  if (N::phit) { fphit.init(v[0].lw, v[1].lw, v[2].lw, v[3].lw); fphit.values(v[0].lw, phitq); }
+  if (N::phi) { fphi.init(b.lz, hb.lz, t.lz, ht.lz); fphi.values(b.lz, phiq); }
+  if (N::phit) { fphit.init(b.lw, hb.lw, t.lw, ht.lw); fphit.values(b.lw, phitq); }
   // ---- input
   PField<P> fxu, fxv, fxp;
   P ax[2], dy[2], bxy[2], cyx[2], xpq[2][2];
   if (N::xu) {
-    fxu.init(v[0].x0, v[1].x0, v[2].x0, v[3].x0);
-    fxv.init(v[0].x1, v[1].x1, v[2].x1, v[3].x1);
+    fxu.init(b.x0, hb.x0, t.x0, ht.x0);
+    fxv.init(b.x1, hb.x1, t.x1, ht.x1);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       ax[q] = pmul(fxu.dxi[q], ihx);     // d du_x/dx at eta_q
@@ -214,7 +199,7 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
       bxy[q] = pmul(fxu.deta[q], ihy);   // d du_x/dy at xi_q
     }
   }
-  if (N::xp) { fxp.init(v[0].xp, v[1].xp, v[2].xp, v[3].xp); fxp.values(v[0].xp, xpq); }
+  if (N::xp) { fxp.init(b.xp, hb.xp, t.xp, ht.xp); fxp.values(b.xp, xpq); }
   if (OP == OP_RESID || OP == OP_MASS || OP == OP_TCV) {
     // R = -A(U)(psi), Problem 2 with sigma^+ read as sigma:
     //   A_u(psi)   = (g(phi~) sigma(u), e(psi)) + (phi~^2 p, div psi)
@@ -223,7 +208,7 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
     // MASS: (1, psi);  TCV: (u . grad phi, psi)
     P S11[2][2], S12[2][2], S22[2][2], fv[2][2];
     P uxq[2][2], uyq[2][2];
-    if (OP == OP_TCV) { fux.values(v[0].lx, uxq); fuy.values(v[0].ly, uyq); }
+    if (OP == OP_TCV) { fux.values(b.lx, uxq); fuy.values(b.ly, uyq); }
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
@@ -280,8 +265,8 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T> v[4], const MatCo
   } else if (OP == OP_TCV_GRAD) {
     // J = integral of u . grad phi:  dJ/du_(A,i) = (dphi/dx_i, N_A),  dJ/dphi_A = (u, grad N_A)
     P uxq[2][2], uyq[2][2], gpx[2][2], gpy[2][2];
-    fux.values(v[0].lx, uxq);
-    fuy.values(v[0].ly, uyq);
+    fux.values(b.lx, uxq);
+    fuy.values(b.ly, uyq);
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
@@ -454,31 +439,7 @@ template <typename T> __device__ __forceinline__ LevGeom<T> geom(const ApplyArgs
 template <> __device__ __forceinline__ LevGeom<float> geom<float>(const ApplyArgs& a, int level) { return a.gf[level]; }
 template <> __device__ __forceinline__ LevGeom<double> geom<double>(const ApplyArgs& a, int level) { return a.gd[level]; }
 
-// ---- asynchronous global -> shared copies (cp.async), per lane
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
-}
-// copies of one value / one adjacent pair of values of type T
-template <typename T>
-__device__ __forceinline__ void cp_one(T* dst, const T* src) {
-  if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
-}
-template <typename T>
-__device__ __forceinline__ void cp_pair(T* dst, const T* src) {
-  if constexpr (sizeof(T) == 4) cp_async8(dst, src); else cp_async16(dst, src);
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
-
-// Node fields in a ring stage (structure of arrays over the 32 columns of a
-// half-warp; lane l holds columns 2l, 2l+1, so its pair is one aligned load).
+// Node fields of the cell loops.
 enum Field : int { F_XU = 0, F_XV = 1, F_XP = 2, F_LU = 3, F_LV = 4, F_LP = 5, F_LT = 6, NF = 7 };
 
 template <int OP>
@@ -489,18 +450,6 @@ __device__ __forceinline__ constexpr bool field_used(int f) {
 }
 
 template <typename T>
-struct __align__(16) Stage {
-  T f[NF][32];
-  uint32_t cm[32];   // constraint-mask words (4 slots per word) of the columns' slots
-};
-
-template <typename T, int NR>
-struct HalfSmem {
-  Stage<T> st[DEPTH];
-  int32_t code[2][NR][32];   // storage codes of the lane columns per strip row (two strips)
-};
-
-template <typename T>
 __device__ __forceinline__ const T* field_ptr(const ApplyArgs& a, int f) {
   const T* xu = reinterpret_cast<const T*>(a.xu);
   const T* lin = reinterpret_cast<const T*>(a.lin);
@@ -509,113 +458,6 @@ __device__ __forceinline__ const T* field_ptr(const ApplyArgs& a, int f) {
     case F_XV: return xu + a.n_slots;
     case F_XP: return reinterpret_cast<const T*>(a.xp);
     default: return lin + (f - F_LU) * a.n_slots;
-  }
-}
-
-// Storage code of node (n, r) (brick-relative, -1..30) of a regular brick; the
-// 3x3 neighbour bases are held by lanes 0..8 of each half-warp.  All 32 lanes
-// call it (the two half-warps may hold different bricks).
-__device__ __forceinline__ int32_t regular_code(int nbase, int n, int r) {
-  const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
-  const int dy = r < 0 ? -1 : (r >= NB ? 1 : 0);
-  const int base = __shfl_sync(0xffffffffu, nbase, (dy + 1) * 3 + dx + 1, 16);
-  return base + (n - dx * NB) + NB * (r - dy * NB);
-}
-
-// Issue the copies of the lane's two columns of one strip row.
-template <typename T, int OP>
-__device__ __forceinline__ void issue_row(const ApplyArgs& a, bool pairwise, int32_t cA, int32_t cB, Stage<T>& st,
-                                          int hl) {
-  const int jA = 2 * hl, jB = 2 * hl + 1;
-  if (pairwise) {  // both slots present, adjacent and 2-aligned
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-      if (field_used<OP>(f)) cp_pair(&st.f[f][jA], field_ptr<T>(a, f) + cA);
-    cp_async4(&st.cm[jA], reinterpret_cast<const uint32_t*>(a.cmask + (cA & ~3)));
-  } else {
-    if (cA >= 0) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if (field_used<OP>(f)) cp_one(&st.f[f][jA], field_ptr<T>(a, f) + cA);
-      cp_async4(&st.cm[jA], reinterpret_cast<const uint32_t*>(a.cmask + (cA & ~3)));
-    }
-    if (cB >= 0) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if (field_used<OP>(f)) cp_one(&st.f[f][jB], field_ptr<T>(a, f) + cB);
-      cp_async4(&st.cm[jB], reinterpret_cast<const uint32_t*>(a.cmask + (cB & ~3)));
-    }
-  }
-}
-
-// Make the landed row usable: masked components zeroed, absent slots zeroed,
-// hanging slots filled from their constraint x_h = sum w x_parent.  Returns
-// the constraint-mask byte of the column.
-template <typename T, int OP>
-__device__ __forceinline__ uint8_t settle_slot(const ApplyArgs& a, int32_t code, Stage<T>& st, int j, uint32_t cmw,
-                                               int byte) {
-  using N = Needs<OP>;
-  const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
-  if (code >= 0) {
-    const uint8_t cm = uint8_t(cmw >> (8 * byte));
-    if (mask && cm) {
-      if (N::xu && (cm & 1)) st.f[F_XU][j] = T(0);
-      if (N::xu && (cm & 2)) st.f[F_XV][j] = T(0);
-      if (N::xp && (cm & 4)) st.f[F_XP][j] = T(0);
-    }
-    return cm;
-  }
-  if (code == kAbsent) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-      if (field_used<OP>(f)) st.f[f][j] = T(0);
-    return 0;
-  }
-  const DevHanging& h = a.hang[-2 - code];
-#pragma unroll
-  for (int f = F_LU; f < NF; ++f)
-    if (field_used<OP>(f)) st.f[f][j] = ldg(field_ptr<T>(a, f) + h.slot);
-  T v0 = 0, v1 = 0, vp = 0;
-  const int np = a.fe_degree + 1;
-  for (int b = 0; b < np; ++b) {
-    const int ps = h.parent[b];
-    const T w = T(h.weight[b]);
-    T p0 = 0, p1 = 0, pp = 0;
-    if (N::xu) { p0 = ldg(field_ptr<T>(a, F_XU) + ps); p1 = ldg(field_ptr<T>(a, F_XV) + ps); }
-    if (N::xp) pp = ldg(field_ptr<T>(a, F_XP) + ps);
-    if (mask) {
-      const uint8_t cm = ldg(a.cmask + ps);
-      if (cm & 1) p0 = 0;
-      if (cm & 2) p1 = 0;
-      if (cm & 4) pp = 0;
-    }
-    v0 += w * p0; v1 += w * p1; vp += w * pp;
-  }
-  if (N::xu) { st.f[F_XU][j] = v0; st.f[F_XV][j] = v1; }
-  if (N::xp) st.f[F_XP][j] = vp;
-  return 0;
-}
-
-// The lane's node pair of a settled row, and the right-hand pair (own B, next lane's A).
-template <typename T, int OP>
-__device__ __forceinline__ void read_row(const Stage<T>& st, int hl, int right_lane, NodePair<T>& v, NodePair<T>& r) {
-  using P = typename VT<T>::T2;
-  const unsigned FULL = 0xffffffffu;
-  P* dst[NF] = {&v.x0, &v.x1, &v.xp, &v.lx, &v.ly, &v.lz, &v.lw};
-  P* dsr[NF] = {&r.x0, &r.x1, &r.xp, &r.lx, &r.ly, &r.lz, &r.lw};
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    if (field_used<OP>(f)) {
-      const P q = *reinterpret_cast<const P*>(&st.f[f][2 * hl]);
-      *dst[f] = q;
-      P o;
-      o.x = q.y;
-      o.y = __shfl_sync(FULL, q.x, right_lane);
-      *dsr[f] = o;
-    } else {
-      *dst[f] = pbc(T(0));
-      *dsr[f] = pbc(T(0));
-    }
   }
 }
 
@@ -661,218 +503,480 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
   }
 }
 
-// RS: node rows per strip (RSEG by default; 1 for latency-bound small level meshes)
-template <typename T, int OP, int RS = RSEG>
-__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? PFF_MINB : PFF_MINB64) apply_q1_kernel(const __grid_constant__ ApplyArgs a) {
-  static_assert(NB % RS == 0, "strip height must divide the brick");
-  constexpr int SROWS = RS;          // node rows per strip
-  constexpr int SSEG = NB / RS;      // strips per brick
-  constexpr int SREAD = RS + 2;      // node rows a strip reads
+// ---- column sweep (the Q1 cell loop) ---------------------------------------
+//
+// One warp takes a strip of 2 SH owned node rows r0 .. r0 + 2 SH - 1 of a brick.
+// Lane L holds window node column n = L - 1 (-1..30) and evaluates the cell to
+// its right.  The strip's two halves (owned rows r0 .. r0+SH-1 and r0+SH ..
+// r0+2SH-1) are swept upwards side by side, one cell row each per step: they are
+// the two members of every packed operation.  A half needs SH + 1 cell rows (its
+// own and the one below), so a step reads one new node row per half.  The right
+// neighbour's node values come by shuffle; the contributions of the left
+// neighbour's cell by shuffle, those of the cell row below as a carry in
+// registers.  Each owned node is completed once, by its own lane, in the fixed
+// order ((carry + left lower-right) + own lower-left); the carry is (own
+// upper-left + left upper-right).
+// Node rows stream HBM -> shared memory through a per-warp cp.async ring,
+// SW_DEPTH - 1 rows ahead of the arithmetic; each lane copies and reads only its
+// own column, so the ring needs no barrier.
+
+#ifndef PFF_SW_WARPS
+#define PFF_SW_WARPS 4
+#endif
+#ifndef PFF_SW_MINB
+#define PFF_SW_MINB 3
+#endif
+#ifndef PFF_SW_MINB64
+#define PFF_SW_MINB64 2
+#endif
+#ifndef PFF_SW_DEPTH
+#define PFF_SW_DEPTH 4
+#endif
+constexpr int SW_WARPS = PFF_SW_WARPS;   // warps (strips) per block
+constexpr int SW_DEPTH = PFF_SW_DEPTH;   // ring stages per warp
+
+// ---- asynchronous global -> shared copies (cp.async), per lane
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+template <typename T>
+__device__ __forceinline__ void cp_one(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
+
+// ---- programmatic dependent launch (PTX griddepcontrol)
+// wait: until the grid this launch depends on has completed and its writes are
+// visible (no-op for a launch without the dependency); trigger: let the next
+// launch, if it is programmatically dependent, start scheduling.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// One node row of both halves in flight (per lane): node fields, the aligned
+// constraint-mask word holding each node's byte, the storage code, the modulus
+// of the cell whose lower-left node this is, and (irregular bricks) the owned
+// node's partial-sum slot and the word holding its storage action.
+template <typename T>
+struct __align__(16) SweepStage {
+  T f[NF][2][32];
+  T e[2][32];
+  uint32_t cm[2][32];
+  int32_t code[2][32];
+  int32_t part[2][32];
+  uint32_t actw[2][32];
+};
+
+// One node of one half: its fields and constraint-mask byte.
+template <typename T>
+struct NodeRaw {
+  T f[NF];
+  uint32_t cm;
+};
+
+// Issue the copies of the lane's node of half h.  A stored node (code >= 0)
+// copies its fields and constraint word from its slot.  A hanging node (code
+// <= -2, table entry -2 - code) copies its linearisation from a.hlin and its
+// input C x from a.hang_x (written by hang_x_kernel, the launch this one may
+// depend on), both indexed by the entry; without a.hlin the linearisation comes
+// from the node's own slot (resolved there by set_lin).
+template <typename T, int OP>
+__device__ __forceinline__ void issue_node(const ApplyArgs& a, int32_t code, SweepStage<T>& st, int h, int lane) {
+  using N = Needs<OP>;
+  st.code[h][lane] = code;
+  if (code >= 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], field_ptr<T>(a, f) + code);
+    cp_async4(&st.cm[h][lane], reinterpret_cast<const uint32_t*>(a.cmask + (code & ~3)));
+  } else if (code != kAbsent) {
+    const int hi = -2 - code;
+    if (a.hlin != nullptr) {
+      const T* hl = reinterpret_cast<const T*>(a.hlin);
+#pragma unroll
+      for (int f = F_LU; f < NF; ++f)
+        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], hl + (f - F_LU) * int64_t(a.nhang) + hi);
+    } else {
+      const int slot = __ldg(&a.hang[hi].slot);
+#pragma unroll
+      for (int f = F_LU; f < NF; ++f)
+        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], field_ptr<T>(a, f) + slot);
+    }
+    if (N::xu || N::xp) {
+      pdl_wait();
+      const T* hx = reinterpret_cast<const T*>(a.hang_x);
+#pragma unroll
+      for (int f = F_XU; f <= F_XP; ++f)
+        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], hx + f * int64_t(a.nhang) + hi);
+    }
+  }
+}
+
+// Read the lane's landed node of half h: fixed input components zeroed
+// (MODE_MASK_INPUT) on stored nodes; absent nodes are zero; hanging nodes carry
+// no constraint of their own.
+template <typename T, int OP>
+__device__ __forceinline__ void read_node(const ApplyArgs& a, const SweepStage<T>& st, int h, int lane,
+                                          NodeRaw<T>& r) {
+  using N = Needs<OP>;
+  const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
+  const int32_t code = st.code[h][lane];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) r.f[f] = T(0);
+  r.cm = 0;
+  if (code != kAbsent) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (field_used<OP>(f)) r.f[f] = st.f[f][h][lane];
+  }
+  if (code >= 0) {
+    r.cm = (st.cm[h][lane] >> (8 * (code & 3))) & 0xffu;
+    if (mask && r.cm) {
+      if (N::xu && (r.cm & 1)) r.f[F_XU] = T(0);
+      if (N::xu && (r.cm & 2)) r.f[F_XV] = T(0);
+      if (N::xp && (r.cm & 4)) r.f[F_XP] = T(0);
+    }
+  }
+}
+
+// A node row of both halves as pairs: own values o and (right neighbour - own) h.
+template <typename T, int OP>
+__device__ __forceinline__ void make_row(const NodeRaw<T>& r0, const NodeRaw<T>& r1, NodePair<T>& o,
+                                         NodePair<T>& h) {
   using P = typename VT<T>::T2;
+  const unsigned FULL = 0xffffffffu;
+  P* po[NF] = {&o.x0, &o.x1, &o.xp, &o.lx, &o.ly, &o.lz, &o.lw};
+  P* ph[NF] = {&h.x0, &h.x1, &h.xp, &h.lx, &h.ly, &h.lz, &h.lw};
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (field_used<OP>(f)) {
+      P v;
+      v.x = r0.f[f];
+      v.y = r1.f[f];
+      P rt;
+      rt.x = __shfl_down_sync(FULL, v.x, 1);
+      rt.y = __shfl_down_sync(FULL, v.y, 1);
+      *po[f] = v;
+      *ph[f] = psub(rt, v);
+    } else {
+      *po[f] = pbc(T(0));
+      *ph[f] = pbc(T(0));
+    }
+  }
+}
+
+// The stored value of an owned node of an irregular brick after the cell loop:
+// storage action (final value, zero, or none: another level's or the fix-up's),
+// partial sum, constraint rows.
+template <typename T, int OP>
+__device__ __forceinline__ void write_owned(const ApplyArgs& a, int slot, int act_s, int part, uint8_t cm, T y0,
+                                            T y1, T y2) {
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
-  const unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31;
-  const int half = lane >> 4, hl = lane & 15;
-  HalfSmem<T, SREAD>& sm = reinterpret_cast<HalfSmem<T, SREAD>*>(smem_raw)[(threadIdx.x >> 5) * 2 + half];
-  const int right_lane = (half << 4) | ((hl + 1) & 15);
-  const int left_lane = (half << 4) | ((hl + 15) & 15);
-  const MatConst<T>& mc = matc<T>(a);
-  // lane columns: nodes (2hl, 2hl+1) for hl < 15; lane 15 holds the halo nodes (30, -1)
-  const int nA = hl < 15 ? 2 * hl : NB, nB = hl < 15 ? 2 * hl + 1 : -1;
   T* yu = reinterpret_cast<T*>(a.yu);
   T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
-  const int nunits = a.lay.nbricks * SSEG;
-  // Persistent warps.  Half-warp h of warp w sweeps the strips (units)
-  // 2w + h + k * stride, k = 0, 1, ...; their node rows form one continuous
-  // stream j = k * SREAD + i, kept DEPTH-1 rows ahead in the cp.async ring
-  // across strip boundaries.
-  const int stride = gridDim.x * WARPS * 2;
-  const int ubase0 = (blockIdx.x * WARPS + (threadIdx.x >> 5)) * 2;
-  if (ubase0 >= nunits) return;  // warp-uniform
-  const int nrounds = (nunits - ubase0 + stride - 1) / stride;
-  const int nstream = nrounds * SREAD;
-  // codes of strip k into table k & 1 (all 32 lanes: shuffles); returns its pairwise flag
-  auto build_codes = [&](int k) -> bool {
-    const int unit = ubase0 + k * stride + half;
-    const bool valid = unit < nunits;
-    const int b = valid ? unit / SSEG : 0;
-    const int r0 = valid ? (unit % SSEG) * SROWS : 0;
-    const BrickDesc* bd = a.lay.bricks + b;
-    const int nbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
-    const int irr = __ldg(&bd->irr);
-#pragma unroll
-    for (int i = 0; i < SREAD; ++i) {
-      const int r = r0 - 1 + i;
-      int32_t cA = regular_code(nbase, nA, r);
-      int32_t cB = regular_code(nbase, nB, r);
-      if (irr >= 0) {
-        const int32_t* w = a.lay.win + irr * (WN * WN) + WN * (r + 1);
-        cA = __ldg(w + nA + 1);
-        cB = __ldg(w + nB + 1);
-      }
-      if (!valid) { cA = kAbsent; cB = kAbsent; }
-      sm.code[k & 1][i][2 * hl] = cA;
-      sm.code[k & 1][i][2 * hl + 1] = cB;
+  if (part >= 0) {
+    T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
+    ib[0] = y0; ib[1] = y1; ib[2] = y2;
+  }
+  if (act_s == kActFinal) {
+    if (isDiag) {
+      if (cm & 1) y0 = T(0);
+      if (cm & 2) y1 = T(0);
+      if (cm & 4) y2 = T(0);
+    } else if (cm) {
+      const bool ident = (a.mode & MODE_IDENTITY) != 0;
+      const T* xu = reinterpret_cast<const T*>(a.xu);
+      if (cm & 1) y0 = ident ? ldg(xu + slot) : T(0);
+      if (cm & 2) y1 = ident ? ldg(xu + a.n_slots + slot) : T(0);
+      if (cm & 4) y2 = ident ? ldg(reinterpret_cast<const T*>(a.xp) + slot) : T(0);
     }
-    return valid && irr < 0 && hl < 15;
+    if (outU) { yu[slot] = y0; yv[slot] = y1; }
+    if (outP) yp[slot] = y2;
+  } else if (act_s == kActZero) {
+    if (outU) { yu[slot] = T(0); yv[slot] = T(0); }
+    if (outP) yp[slot] = T(0);
+  }
+}
+
+template <typename T, int OP, int SH>
+__global__ void __launch_bounds__(32 * SW_WARPS, sizeof(T) == 4 ? PFF_SW_MINB : PFF_SW_MINB64)
+sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
+  static_assert(NB % (2 * SH) == 0, "two half-strips of SH rows must tile the brick");
+  constexpr int NSTRIP = NB / (2 * SH);
+  constexpr int NROW = SH + 2;                         // node rows per half
+  using P = typename VT<T>::T2;
+  constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
+  constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const unsigned FULL = 0xffffffffu;
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  SweepStage<T>* ring = reinterpret_cast<SweepStage<T>*>(smem_raw) + (threadIdx.x >> 5) * SW_DEPTH;
+  const int unit = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
+  if (unit >= a.lay.nbricks * NSTRIP) { pdl_wait(); return; }   // warp-uniform
+  const int bi = unit / NSTRIP;
+  const int r0 = (unit - bi * NSTRIP) * (2 * SH);
+  const BrickDesc* bd = a.lay.bricks + bi;
+  const int irr = __ldg(&bd->irr);
+  const LevGeom<T> g = geom<T>(a, __ldg(&bd->level));
+  const MatConst<T>& mc = matc<T>(a);
+  const int n = lane - 1;                              // window node column -1..30
+  const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
+  const int col = n - NB * dx;                         // its column in its brick
+  const int base_lo = __ldg(bd->nbr_base + dx + 1);    // the column's bricks below, beside, above
+  const int base_mid = __ldg(bd->nbr_base + dx + 4);
+  const int base_hi = __ldg(bd->nbr_base + dx + 7);
+  const int own_base = __ldg(bd->nbr_base + 4);
+  const int32_t* win = a.lay.win + (irr >= 0 ? irr : 0) * (WN * WN) + lane;
+  // window cell activity of an irregular brick: 31 words, word i held by lane i
+  const uint32_t cmw = (irr >= 0 && lane < 31) ? __ldg(a.lay.cellmask + irr * 31 + lane) : 0u;
+  T* yu = reinterpret_cast<T*>(a.yu);
+  T* yv = yu + a.n_slots;
+  T* yp = reinterpret_cast<T*>(a.yp);
+  // storage code of window node (n, r) of a regular brick, brick row r = -1..30;
+  // also the cell slot of cell (n, r) in any brick (its lower-left node position)
+  auto reg_code = [&](int r) -> int32_t {
+    return r < 0 ? base_lo + col + NB * (r + NB) : (r >= NB ? base_hi + col + NB * (r - NB) : base_mid + col + NB * r);
   };
-  bool pw_issue = build_codes(0);   // pairwise flag of the strip being issued
-  int k_issue = 0;
-  auto issue_stream = [&](int j) {
-    if (j < nstream) {
-      const int k = j / SREAD, i = j - k * SREAD;
-      if (k != k_issue) { pw_issue = build_codes(k); k_issue = k; }
-      issue_row<T, OP>(a, pw_issue, sm.code[k & 1][i][2 * hl], sm.code[k & 1][i][2 * hl + 1], sm.st[j % DEPTH], hl);
+  // window cell (n, c) is active (all 32 lanes call it: shuffle); the last
+  // lane's cell lies outside the window and reaches no owned node
+  auto cell_active = [&](int c) -> bool {
+    if (irr < 0) return true;
+    const int i = (c + 1) * NCW + (lane < 31 ? lane : 0);
+    const uint32_t w = __shfl_sync(FULL, cmw, (i >> 5) & 31);
+    return lane < 31 && ((w >> (i & 31)) & 1u);
+  };
+  // stream of node rows j = 0 .. NROW-1 per half: brick rows r0 - 1 + j (half 0)
+  // and r0 + SH - 1 + j (half 1); the codes of irregular bricks are read one row
+  // ahead of their copies
+  int32_t kn0 = 0, kn1 = 0;
+  if (irr >= 0) { kn0 = __ldg(win + WN * r0); kn1 = __ldg(win + WN * (r0 + SH)); }
+  auto issue_half = [&](SweepStage<T>& st, int h, int32_t k, int r) {
+    issue_node<T, OP>(a, k, st, h, lane);
+    if (a.ecell != nullptr) {
+      // modulus of cell (n, r), r <= 29, whose lower-left node this is
+      const bool act = r < NB && cell_active(r);
+      if (act) cp_one(&st.e[h][lane], reinterpret_cast<const T*>(a.ecell) + reg_code(r));
+    }
+    if (irr >= 0 && r >= 0 && r < NB && lane >= 1 && lane <= NB) {
+      const int o = irr * (NB * NB) + n + NB * r;
+      cp_async4(&st.part[h][lane], a.lay.own_part + o);
+      cp_async4(&st.actw[h][lane], reinterpret_cast<const uint32_t*>(a.lay.own_act + (o & ~3)));
+    }
+  };
+  auto issue = [&](int j) {
+    if (j < NROW) {
+      SweepStage<T>& st = ring[j % SW_DEPTH];
+      int32_t k0, k1;
+      if (irr >= 0) {
+        k0 = kn0;
+        k1 = kn1;
+        if (j + 1 < NROW) { kn0 = __ldg(win + WN * (r0 + j + 1)); kn1 = __ldg(win + WN * (r0 + SH + j + 1)); }
+      } else {
+        k0 = reg_code(r0 - 1 + j);
+        k1 = reg_code(r0 + SH - 1 + j);
+      }
+      issue_half(st, 0, k0, r0 - 1 + j);
+      issue_half(st, 1, k1, r0 + SH - 1 + j);
     }
     cp_async_commit();
   };
-#pragma unroll 1
-  for (int j = 0; j < DEPTH - 1; ++j) issue_stream(j);
+  // per-row values kept from consumption to completion (one step later)
+  struct RowExtra {
+    P e;
+    int32_t part0, part1;
+    uint32_t act0, act1;
+  };
+  auto row_extra = [&](const SweepStage<T>& st, RowExtra& x) {
+    x.e = pbc(T(1));
+    if (a.ecell != nullptr) { x.e.x = st.e[0][lane]; x.e.y = st.e[1][lane]; }
+    x.part0 = x.part1 = -1;
+    x.act0 = x.act1 = kActFinal;
+    if (irr >= 0 && lane >= 1 && lane <= NB) {
+      x.part0 = st.part[0][lane];
+      x.part1 = st.part[1][lane];
+      x.act0 = st.actw[0][lane];
+      x.act1 = st.actw[1][lane];
+    }
+  };
+#pragma unroll
+  for (int j = 0; j < SW_DEPTH - 1; ++j) issue(j);
 
-  // per-strip state of the strip being computed
-  bool valid = false, pairwise = false;
-  int irr = 0, r0 = 0, own_base = 0, cnbase = 0;
-  LevGeom<T> gq = geom<T>(a, 0);
-  uint8_t cmA = 0, cmB = 0;
+  NodeRaw<T> nr0, nr1;
+  cp_async_wait<SW_DEPTH - 2>();
+  read_node<T, OP>(a, ring[0], 0, lane, nr0);
+  read_node<T, OP>(a, ring[0], 1, lane, nr1);
+  RowExtra xb;                       // lower node row's extras
+  row_extra(ring[0], xb);
+  issue(SW_DEPTH - 1);
+  NodePair<T> ob, hb;                // lower node row of the current cell rows
+  uint32_t cb0 = nr0.cm, cb1 = nr1.cm;
+  make_row<T, OP>(nr0, nr1, ob, hb);
   P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
-#pragma unroll 1
-  for (int j = 0; j < nstream; ++j) {
-    const int k = j / SREAD, i = j - k * SREAD;
-    if (i == 0) {
-      const int unit = ubase0 + k * stride + half;
-      valid = unit < nunits;
-      const int b = valid ? unit / SSEG : 0;
-      r0 = valid ? (unit % SSEG) * SROWS : 0;
-      const BrickDesc* bd = a.lay.bricks + b;
-      irr = __ldg(&bd->irr);
-      own_base = __ldg(bd->nbr_base + 4);
-      cnbase = hl < 9 ? __ldg(bd->nbr_base + hl) : 0;
-      gq = geom<T>(a, __ldg(&bd->level));
-      pairwise = valid && irr < 0 && hl < 15;
+#pragma unroll 2
+  for (int s = 0; s <= SH; ++s) {
+    cp_async_wait<SW_DEPTH - 2>();
+    const SweepStage<T>& st = ring[(s + 1) % SW_DEPTH];
+    read_node<T, OP>(a, st, 0, lane, nr0);
+    read_node<T, OP>(a, st, 1, lane, nr1);
+    RowExtra xt;
+    row_extra(st, xt);
+    issue(s + SW_DEPTH);             // refills the stage of row s, read at the previous step
+    NodePair<T> ot, ht;              // upper node row
+    const uint32_t ct0 = nr0.cm, ct1 = nr1.cm;
+    make_row<T, OP>(nr0, nr1, ot, ht);
+    const int c0 = r0 - 1 + s, c1 = c0 + SH;   // cell rows (and completed node rows) of the halves
+    const bool act0 = cell_active(c0), act1 = cell_active(c1);
+    P out[12];
+    q1_cell_pair<T, OP>(ob, hb, ot, ht, mc, g, xb.e, out);
+    if (!act0 || !act1) {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        if (!act0) out[q].x = T(0);
+        if (!act1) out[q].y = T(0);
+      }
     }
-    cp_async_wait<DEPTH - 2>();
-    Stage<T>& si = sm.st[j % DEPTH];
-    const int32_t cA = sm.code[k & 1][i][2 * hl], cB = sm.code[k & 1][i][2 * hl + 1];
-    uint8_t nmA, nmB;
-    if (pairwise) {
-      const uint32_t w = si.cm[2 * hl];
-      nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, w, cA & 3);
-      nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, w, cB & 3);
-    } else {
-      nmA = settle_slot<T, OP>(a, cA, si, 2 * hl, si.cm[2 * hl], cA & 3);
-      nmB = settle_slot<T, OP>(a, cB, si, 2 * hl + 1, si.cm[2 * hl + 1], cB & 3);
-    }
-    if (i > 0) {
-      const int c = r0 - 2 + i;  // cell row between node rows c and c + 1
-      NodePair<T> v[4];
-      read_row<T, OP>(sm.st[(j - 1) % DEPTH], hl, right_lane, v[0], v[1]);
-      read_row<T, OP>(si, hl, right_lane, v[2], v[3]);
-      bool actA = hl < 15, actB = true;
-      if (irr >= 0) {
-        const uint32_t* cmw = a.lay.cellmask + irr * 31;
-        const int ib = (c + 1) * NCW + (nB + 1), ia = ib - 1;  // window cells of cells nA (if hl<15) and nB
-        actA = actA && ((__ldg(cmw + (ia >> 5)) >> (ia & 31)) & 1u);
-        actB = (__ldg(cmw + (ib >> 5)) >> (ib & 31)) & 1u;
-      }
-      // cell moduli: the cell slot of a cell is the slot of its lower-left node
-      // position in the bricks of this level (neighbour bricks for column/row -1)
-      P ec = pbc(T(1));
-      if (a.ecell != nullptr) {  // uniform: all 32 lanes take the shuffles in regular_code
-        const int32_t sA = regular_code(cnbase, nA, c), sB = regular_code(cnbase, nB, c);
-        const T* E = reinterpret_cast<const T*>(a.ecell);
-        if (valid && actA) ec.x = ldg(E + sA);
-        if (valid && actB) ec.y = ldg(E + sB);
-      }
-      P out[12];
-      q1_cell_pair<T, OP>(v, mc, gq, ec, out);
-      if (!actA || !actB) {
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-          if (!actA) out[q].x = T(0);
-          if (!actB) out[q].y = T(0);
-        }
-      }
-      if constexpr (OP == OP_VJP) {
-        // per-cell values of the cells owned by this strip (rows r0.., columns 0..29)
-        if (c >= r0 && hl < 15 && valid) {
-          T* co = reinterpret_cast<T*>(a.cell_out);
-          const int64_t sA = own_base + nA + NB * c;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            if (actA) co[q * a.n_slots + sA] = out[q].x;
-            if (actB) co[q * a.n_slots + sA + 1] = out[q].y;
-          }
-        }
-      } else {
-      // the left lane's cell B contributes BR to our node A (row c) and TR to node A (row c+1)
-      T brL[3], trL[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        brL[q] = __shfl_sync(FULL, out[3 + q].y, left_lane);
-        trL[q] = __shfl_sync(FULL, out[9 + q].y, left_lane);
-      }
-      if (c >= r0 && hl < 15 && valid) {
-        T yA[3], yB[3];
+    const bool owner = s >= 1 && lane >= 1 && lane <= NB;
+    if constexpr (OP == OP_VJP) {
+      // per-cell values of the cells this strip owns (lower-left node owned)
+      if (owner) {
+        T* co = reinterpret_cast<T*>(a.cell_out);
+        const int64_t sA = own_base + n + NB * c0, sB = own_base + n + NB * c1;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          yA[q] = (carry[q].x + brL[q]) + out[q].x;
-          yB[q] = (carry[q].y + out[3 + q].x) + out[q].y;
+          if (act0) co[q * a.n_slots + sA] = out[q].x;
+          if (act1) co[q * a.n_slots + sB] = out[q].y;
         }
-        if (irr < 0 && !(cmA | cmB)) {
-          // regular brick, unconstrained pair: one aligned pair store per output field
-          const int slot = own_base + nA + NB * c;
-          if (outU) {
-            *reinterpret_cast<P*>(yu + slot) = P{yA[0], yB[0]};
-            *reinterpret_cast<P*>(yv + slot) = P{yA[1], yB[1]};
-          }
-          if (outP) *reinterpret_cast<P*>(yp + slot) = P{yA[2], yB[2]};
+      }
+    } else {
+      P brL[3], trL[3];              // the left neighbour's lower-right and upper-right contributions
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        brL[q].x = __shfl_up_sync(FULL, out[3 + q].x, 1);
+        brL[q].y = __shfl_up_sync(FULL, out[3 + q].y, 1);
+        trL[q].x = __shfl_up_sync(FULL, out[9 + q].x, 1);
+        trL[q].y = __shfl_up_sync(FULL, out[9 + q].y, 1);
+      }
+      if (owner) {
+        P y[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) y[q] = padd(padd(carry[q], brL[q]), out[q]);
+        const int s0 = own_base + n + NB * c0, s1 = own_base + n + NB * c1;
+        if (irr < 0 && !(cb0 | cb1)) {
+          if (outU) { yu[s0] = y[0].x; yv[s0] = y[1].x; yu[s1] = y[0].y; yv[s1] = y[1].y; }
+          if (outP) { yp[s0] = y[2].x; yp[s1] = y[2].y; }
         } else {
-          write_node<T, OP>(a, irr, own_base, nA, c, cmA, yA[0], yA[1], yA[2]);
-          write_node<T, OP>(a, irr, own_base, nB, c, cmB, yB[0], yB[1], yB[2]);
+          const int o0 = irr >= 0 ? irr * (NB * NB) + n + NB * c0 : 0, o1 = o0 + NB * SH;
+          write_owned<T, OP>(a, s0, irr >= 0 ? int((xb.act0 >> (8 * (o0 & 3))) & 0xffu) : int(kActFinal),
+                             xb.part0, uint8_t(cb0), y[0].x, y[1].x, y[2].x);
+          write_owned<T, OP>(a, s1, irr >= 0 ? int((xb.act1 >> (8 * (o1 & 3))) & 0xffu) : int(kActFinal),
+                             xb.part1, uint8_t(cb1), y[0].y, y[1].y, y[2].y);
         }
       }
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        carry[q].x = out[6 + q].x + trL[q];
-        carry[q].y = out[6 + q].y + out[9 + q].x;
-      }
-      }
+      for (int q = 0; q < 3; ++q) carry[q] = padd(out[6 + q], trL[q]);
     }
-    cmA = nmA;
-    cmB = nmB;
-    // refill the stage of stream row j-1 (no longer read) with row j+DEPTH-1
-    issue_stream(j + DEPTH - 1);
+    ob = ot;
+    hb = ht;
+    cb0 = ct0;
+    cb1 = ct1;
+    xb = xt;
   }
   cp_async_wait<0>();
-  (void)isDiag;
+  pdl_wait();   // the launch this one depends on (if any) completes before this grid does
 }
 
+// C x on the hanging nodes (Q1 leaf): hx[f][h] = sum_b w_b x_f(parent_b), the
+// parents' fixed components zeroed under MODE_MASK_INPUT.  Runs before the
+// sweep, which may start early (programmatic dependent launch) and waits for
+// this grid only where it copies these values.
+template <typename T>
+__global__ void hang_x_kernel(const DevHanging* __restrict__ hang, int32_t nh, int np, const T* __restrict__ xu,
+                              const T* __restrict__ xp, int64_t n_slots, const uint8_t* __restrict__ cmask,
+                              int mode, T* __restrict__ hx) {
+  pdl_trigger();
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nh) return;
+  const bool mask = (mode & MODE_MASK_INPUT) != 0;
+  const DevHanging e = hang[h];
+  T v0 = 0, v1 = 0, vp = 0;
+  for (int b = 0; b < np; ++b) {
+    const int ps = e.parent[b];
+    const T w = T(e.weight[b]);
+    T p0 = __ldg(xu + ps), p1 = __ldg(xu + n_slots + ps), pp = __ldg(xp + ps);
+    if (mask) {
+      const uint8_t cm = __ldg(cmask + ps);
+      if (cm & 1) p0 = 0;
+      if (cm & 2) p1 = 0;
+      if (cm & 4) pp = 0;
+    }
+    v0 += w * p0; v1 += w * p1; vp += w * pp;
+  }
+  hx[h] = v0;
+  hx[int64_t(nh) + h] = v1;
+  hx[2 * int64_t(nh) + h] = vp;
+}
+
+// C^T on the interface nodes: y = sum of the node's partial sums (weights of
+// C), then its constraint rows.  Launched programmatically dependent on the
+// apply: everything but the partial sums is read before waiting for it.
 template <typename T>
 __global__ void fixup_kernel(const FixupArgs a) {
+  constexpr int PRE = 4;   // partials whose indices and weights are read before the wait
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ident = (a.mode & MODE_IDENTITY) != 0;
+  int slot = 0, e0 = 0, e1 = 0;
+  uint8_t cm = 0;
+  T xi[3] = {T(0), T(0), T(0)};
+  int pp[PRE];
+  T ww[PRE];
+  if (f < a.n) {
+    slot = a.slot[f];
+    e0 = a.ptr[f];
+    e1 = a.ptr[f + 1];
+    cm = a.cmask[slot];
+    if (cm && ident) {
+      const T* xu = reinterpret_cast<const T*>(a.xu);
+      xi[0] = xu[slot];
+      xi[1] = xu[a.n_slots + slot];
+      xi[2] = reinterpret_cast<const T*>(a.xp)[slot];
+    }
+#pragma unroll
+    for (int q = 0; q < PRE; ++q) {
+      pp[q] = e0 + q < e1 ? a.part[e0 + q] : 0;
+      ww[q] = e0 + q < e1 ? T(a.w[e0 + q]) : T(0);
+    }
+  }
+  pdl_wait();
   if (f >= a.n) return;
-  const int slot = a.slot[f];
   const T* ib = reinterpret_cast<const T*>(a.ibuf);
   T y0 = 0, y1 = 0, y2 = 0;
-  for (int e = a.ptr[f]; e < a.ptr[f + 1]; ++e) {
+#pragma unroll
+  for (int q = 0; q < PRE; ++q) {
+    if (e0 + q < e1) {
+      y0 += ww[q] * ib[3 * pp[q] + 0];
+      y1 += ww[q] * ib[3 * pp[q] + 1];
+      y2 += ww[q] * ib[3 * pp[q] + 2];
+    }
+  }
+  for (int e = e0 + PRE; e < e1; ++e) {
     const int p = a.part[e];
     const T w = T(a.w[e]);
     y0 += w * ib[3 * p + 0];
     y1 += w * ib[3 * p + 1];
     y2 += w * ib[3 * p + 2];
   }
-  const uint8_t cm = a.cmask[slot];
-  const T* xu = reinterpret_cast<const T*>(a.xu);
-  const T* xp = reinterpret_cast<const T*>(a.xp);
   if (cm) {
-    const bool ident = (a.mode & MODE_IDENTITY) != 0;
-    if (cm & 1) y0 = ident ? xu[slot] : T(0);
-    if (cm & 2) y1 = ident ? xu[a.n_slots + slot] : T(0);
-    if (cm & 4) y2 = ident ? xp[slot] : T(0);
+    if (cm & 1) y0 = ident ? xi[0] : T(0);
+    if (cm & 2) y1 = ident ? xi[1] : T(0);
+    if (cm & 4) y2 = ident ? xi[2] : T(0);
   }
   T* yu = reinterpret_cast<T*>(a.yu);
   yu[slot] = y0;
@@ -894,7 +998,7 @@ __global__ void set_lin_kernel(int64_t n, const double* __restrict__ u, const do
 }
 
 __global__ void set_lin_hanging_kernel(int32_t nh, int64_t n, const DevHanging* __restrict__ hang, int np,
-                                       double* lin64, float* lin32) {
+                                       double* lin64, float* lin32, double* hlin64, float* hlin32) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= nh) return;
   const DevHanging e = hang[h];
@@ -904,6 +1008,8 @@ __global__ void set_lin_hanging_kernel(int32_t nh, int64_t n, const DevHanging* 
     for (int b = 0; b < np; ++b) v += e.weight[b] * lin64[k * n + e.parent[b]];
     lin64[k * n + e.slot] = v;
     lin32[k * n + e.slot] = float(v);
+    if (hlin64) hlin64[k * int64_t(nh) + h] = v;
+    if (hlin32) hlin32[k * int64_t(nh) + h] = float(v);
   }
 }
 
@@ -977,73 +1083,121 @@ void fill_cell_constants(ApplyArgs& a, int nlevels) {
   }
 }
 
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  cache[dev] = sms;
+  return sms;
+}
+
+// Strip half-height of the column sweep: the Jacobian and the level block
+// operators come with SH = 15 (one strip per brick: 32 cell rows evaluated per
+// 30 owned rows), 5 and 1 (3 and 15 strips per brick: more, shorter warps for
+// small level meshes); the other operators with SH = 15.  a.sweep_sh forces one
+// of 15, 5, 1 where it exists; 0 picks the largest whose strips give every SM a
+// few warps.
+// Launch of kernel `fn` on stream s, programmatically dependent on the launch
+// before it in the stream when pdl is set (it may start once that grid has
+// triggered; it waits with griddepcontrol.wait where it reads that grid's output).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(bool pdl, void (*fn)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
+template <typename T, int OP>
+cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
+  using N = Needs<OP>;
+  constexpr bool multi = (OP == OP_FULL || OP == OP_UU || OP == OP_PP);
+  int sh = 15;
+  if (multi) {
+    if (a.sweep_sh == 15 || a.sweep_sh == 5 || a.sweep_sh == 1) {
+      sh = a.sweep_sh;
+    } else {
+      const int64_t want = int64_t(4) * sm_count();   // warps
+      sh = a.lay.nbricks >= want ? 15 : (3 * int64_t(a.lay.nbricks) >= want ? 5 : 1);
+    }
+  }
+  // hanging nodes' input: C x into a.hang_x first; the sweep may start before that
+  // grid ends and waits for it only where it copies those values
+  bool pdl = false;
+  if ((N::xu || N::xp) && a.nhang > 0 && a.hang != nullptr) {
+    if (a.hang_x == nullptr) return cudaErrorInvalidValue;
+    hang_x_kernel<T><<<(a.nhang + 127) / 128, 128, 0, s>>>(
+        a.hang, a.nhang, a.fe_degree + 1, reinterpret_cast<const T*>(a.xu), reinterpret_cast<const T*>(a.xp),
+        a.n_slots, a.cmask, a.mode, reinterpret_cast<T*>(a.hang_x));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pdl = true;
+  }
+  const unsigned blk = 32 * SW_WARPS;
+  const size_t smem = sizeof(SweepStage<T>) * SW_DEPTH * SW_WARPS;
+  auto grid = [&](int nstrip) { return unsigned((int64_t(a.lay.nbricks) * nstrip + SW_WARPS - 1) / SW_WARPS); };
+  auto go = [&](auto fn, int nstrip) {
+    resident_blocks(reinterpret_cast<const void*>(fn), int(blk), smem);   // sets the shared-memory limit once
+    return launch_ex(pdl, fn, grid(nstrip), blk, smem, s, a);
+  };
+  if constexpr (multi) {
+    if (sh == 5) return go(&sweep_q1_kernel<T, OP, 5>, 3);
+    if (sh == 1) return go(&sweep_q1_kernel<T, OP, 1>, 15);
+  }
+  return go(&sweep_q1_kernel<T, OP, 15>, 1);
+}
+
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
   if (a.fe_degree == 2) return launch_apply_q2<T>(a, op, s);
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
-  const unsigned blk = 32 * WARPS;
-  auto grid_of = [&](const void* fn, int strips_per_brick, size_t smem) -> unsigned {
-    const int units = (a.lay.nbricks * strips_per_brick + 1) / 2;  // two strips per warp
-    const int full = resident_blocks(fn, int(blk), smem);
-    const int need = (units + WARPS - 1) / WARPS;
-    return unsigned(need < full ? need : full);
-  };
-  const size_t smem = sizeof(HalfSmem<T, NROWS>) * 2 * WARPS;
-  // The level block operators of the V-cycle mostly run on small level meshes,
-  // where one wave of single-row strips covers the mesh: there the shorter
-  // per-strip chain (3 node rows read, 2 cell rows) gives the lower latency.
-  if (op == OP_UU || op == OP_PP) {
-    const size_t smem1 = sizeof(HalfSmem<T, 3>) * 2 * WARPS;
-    const void* fn = op == OP_UU ? reinterpret_cast<const void*>(&apply_q1_kernel<T, OP_UU, 1>)
-                                 : reinterpret_cast<const void*>(&apply_q1_kernel<T, OP_PP, 1>);
-    const int need = ((a.lay.nbricks * NB + 1) / 2 + WARPS - 1) / WARPS;
-    if (need <= resident_blocks(fn, int(blk), smem1)) {
-      const unsigned g = grid_of(fn, NB, smem1);
-      if (op == OP_UU) apply_q1_kernel<T, OP_UU, 1><<<g, blk, smem1, s>>>(a);
-      else apply_q1_kernel<T, OP_PP, 1><<<g, blk, smem1, s>>>(a);
-      return cudaGetLastError();
-    }
-  }
   switch (op) {
-#define PFF_LAUNCH(OPV)                                                                        \
-    case OPV: {                                                                                \
-      const void* fn = reinterpret_cast<const void*>(&apply_q1_kernel<T, OPV>);               \
-      apply_q1_kernel<T, OPV><<<grid_of(fn, NSEG, smem), blk, smem, s>>>(a);                   \
-      break;                                                                                   \
-    }
-    PFF_LAUNCH(OP_FULL)
-    PFF_LAUNCH(OP_FULL_T)
-    PFF_LAUNCH(OP_UU)
-    PFF_LAUNCH(OP_PP)
-    PFF_LAUNCH(OP_UU_DIAG)
-    PFF_LAUNCH(OP_PP_DIAG)
-    PFF_LAUNCH(OP_RESID)
-    PFF_LAUNCH(OP_MASS)
-    PFF_LAUNCH(OP_TCV)
-    PFF_LAUNCH(OP_TCV_GRAD)
-    PFF_LAUNCH(OP_VJP)
-    PFF_LAUNCH(OP_PHIT_VJP)
-#undef PFF_LAUNCH
+    case OP_FULL: return launch_sweep<T, OP_FULL>(a, s);
+    case OP_FULL_T: return launch_sweep<T, OP_FULL_T>(a, s);
+    case OP_UU: return launch_sweep<T, OP_UU>(a, s);
+    case OP_PP: return launch_sweep<T, OP_PP>(a, s);
+    case OP_UU_DIAG: return launch_sweep<T, OP_UU_DIAG>(a, s);
+    case OP_PP_DIAG: return launch_sweep<T, OP_PP_DIAG>(a, s);
+    case OP_RESID: return launch_sweep<T, OP_RESID>(a, s);
+    case OP_MASS: return launch_sweep<T, OP_MASS>(a, s);
+    case OP_TCV: return launch_sweep<T, OP_TCV>(a, s);
+    case OP_TCV_GRAD: return launch_sweep<T, OP_TCV_GRAD>(a, s);
+    case OP_VJP: return launch_sweep<T, OP_VJP>(a, s);
+    case OP_PHIT_VJP: return launch_sweep<T, OP_PHIT_VJP>(a, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fixup(const FixupArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  fixup_kernel<T><<<(a.n + 127) / 128, 128, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_ex(true, &fixup_kernel<T>, unsigned((a.n + 127) / 128), 128u, 0, s, a);
 }
 
 cudaError_t launch_set_lin(int64_t n_slots, const double* u, const double* phi, const double* phit,
                            const DevHanging* hang, int32_t nhang, int fe_degree,
-                           double* lin64, float* lin32, cudaStream_t s) {
+                           double* lin64, float* lin32, double* hlin64, float* hlin32, cudaStream_t s) {
   if (n_slots > 0)
     set_lin_kernel<<<unsigned((n_slots + 255) / 256), 256, 0, s>>>(n_slots, u, phi, phit, lin64, lin32);
   if (nhang > 0)
-    set_lin_hanging_kernel<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, n_slots, hang, fe_degree + 1, lin64, lin32);
+    set_lin_hanging_kernel<<<(nhang + 127) / 128, 128, 0, s>>>(nhang, n_slots, hang, fe_degree + 1, lin64, lin32,
+                                                               hlin64, hlin32);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,9 @@ struct ApplyArgs {
   void* yu;
   void* yp;
   void* ibuf;             // 3 T per partial slot
+  const void* hlin;       // Q1 leaf: 4 blocks of nhang T, the hanging nodes' linearisation
+  void* hang_x;           // Q1 leaf: 3 blocks of nhang T, scratch for the hanging nodes' input (C x)
+  int32_t nhang;
   const void* ecell;      // per-cell modulus E_K (T, cell-slot layout) or nullptr: constants carry E
   void* cell_out;         // OP_VJP: 3 blocks of n_slots T (E_K, p, G_c) at cell slots
   int64_t n_slots;
@@ -103,6 +106,7 @@ struct ApplyArgs {
   Q2Tab<double> q2d;
   int mode;
   int fe_degree;
+  int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (see launch_sweep)
 };
 
 struct FixupArgs {
@@ -124,7 +128,9 @@ struct FixupArgs {
 // fills mf / md / gf / gd from hx, hy and the material
 void fill_cell_constants(ApplyArgs& a, int nlevels);
 
-// launchers (return cudaError_t of the launch)
+// launchers (return cudaError_t of the launch).  launch_fixup must follow the
+// launch_apply whose partial sums it condenses directly on the same stream: it
+// is launched programmatically dependent on it.
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s);
 template <typename T>
@@ -132,8 +138,9 @@ cudaError_t launch_fixup(const FixupArgs& a, cudaStream_t s);
 
 // state conversion: lin64/lin32 blocks (u_x, u_y, phi, phi_t), hanging entries from parents;
 // u is the displacement in block layout (u_x block, u_y block)
+// hlin64/hlin32: the hanging nodes' linearisation again, 4 blocks of nhang (read by the Q1 sweep)
 cudaError_t launch_set_lin(int64_t n_slots, const double* u, const double* phi, const double* phit,
                            const DevHanging* hang, int32_t nhang, int fe_degree,
-                           double* lin64, float* lin32, cudaStream_t s);
+                           double* lin64, float* lin32, double* hlin64, float* hlin32, cudaStream_t s);
 
 }  // namespace pff

@@ -123,6 +123,7 @@ cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStr
   }
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
+  a.sweep_sh = pb.sweep_sh;
   a.mode = MODE_MASK_INPUT;
   return launch_apply<T>(a, op, s);
 }

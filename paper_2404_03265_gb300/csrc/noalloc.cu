@@ -1,23 +1,31 @@
-// pff_apply_noalloc: the leaf operator of pff_apply with its interface scratch
-// taken from a fixed device array of this file instead of the problem's buffers.
+// pff_apply_noalloc: the leaf operator of pff_apply with its scratch taken from
+// a fixed device array of this file instead of the problem's buffers.
 //
-// One apply writes one partial sum (3 values) per interface node of an irregular
-// brick, and the fix-up kernel that follows it in the same stream condenses them
-// (C^T).  pff_apply keeps those partials in buffers made by pff_problem_create.
-// This variant keeps them in `g_partials` below, a static device array that is
-// part of the library image and is reserved when the CUDA module is loaded.  No
-// call here allocates device or pinned memory, directly or through a library.
+// One apply of a Q1 mesh first writes the input resolved on each hanging node
+// (C x, 3 values per hanging node) and then one partial sum (3 values) per
+// interface node of an irregular brick; the fix-up kernel that follows in the
+// same stream condenses the partials (C^T).  pff_apply keeps both in buffers
+// made by pff_problem_create.  This variant keeps them in `g_partials` below, a
+// static device array that is part of the library image: the partials first,
+// the hanging inputs after them.  No call here allocates device or pinned
+// memory, directly or through a library.
 //
-// Set-up: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress and caches it per device.
-// That first call must be made outside any stream capture.
+// Set-up: pff_problem_create calls noalloc_prepare, which loads this file's
+// module on the problem's device and looks up the array's device address with
+// cudaGetSymbolAddress (the module may otherwise be loaded lazily, at the first
+// use of the array, which would reserve its memory inside the first call).  The
+// address is cached per device; a call on a device that was never prepared
+// looks it up itself, so make the first call there outside any stream capture.
+// The cache does not survive cudaDeviceReset, which also invalidates every
+// problem's device buffers.
 //
 // The array is shared by every problem and every stream on the device, and it
 // keeps the previous call's contents.  Nothing in it needs to start at zero:
-// the apply kernel writes every partial that the fix-up reads (each interface
-// node of an irregular brick is written once per call) before the fix-up runs.
-// Calls whose executions overlap on one device (different streams, no ordering
-// between them) race on the array; order them on one stream or with events.
+// every value that is read is written earlier in the same call (each hanging
+// input by the first kernel, each partial by the apply kernel before the
+// fix-up reads it).  Calls whose executions overlap on one device (different
+// streams, no ordering between them) race on the array; order them on one
+// stream or with events.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -31,8 +39,8 @@
 
 namespace {
 
-// 65536 partial sums x 3 components x 8 bytes = 1.5 MiB.  FP32 calls use the
-// same array as floats (the first half).
+// 65536 triples (partial sums and hanging inputs) x 8 bytes = 1.5 MiB.  FP32
+// calls use the same array as floats (the first half).
 constexpr int64_t kMaxPartials = PFF_NOALLOC_MAX_PARTIALS;
 constexpr int kMaxDevices = 64;
 
@@ -55,6 +63,22 @@ cudaError_t scratch_address(int dev, void** out) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+namespace pff {
+// Loads the module and caches the array's address on the current device.
+cudaError_t noalloc_prepare() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaSuccess;   // the call itself reports this
+  void* p = nullptr;
+  return scratch_address(dev, &p);
+}
+}  // namespace pff
+
+namespace {
+
 pff_status noalloc_fail(pff_status st, const std::string& msg) {
   pff::set_last_error(msg);
   return st;
@@ -71,10 +95,12 @@ extern "C" pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int3
     if (op < 0 || op > 2) return noalloc_fail(PFF_ERR_INVALID_ARG, "bad operator");
     const Mesh& M = pb->mesh->m;
     const DevMesh& D = pb->mesh->dev;
-    if (M.n_partials > kMaxPartials)
+    const int64_t nh = M.k == 1 ? int64_t(M.hang.size()) : 0;   // hanging inputs (Q1 only)
+    if (M.n_partials + nh > kMaxPartials)
       return noalloc_fail(PFF_ERR_INVALID_ARG,
                           "pff_apply_noalloc: the mesh has " + std::to_string(M.n_partials) +
-                              " interface partial sums, more than the fixed scratch holds (" +
+                              " interface partial sums and " + std::to_string(nh) +
+                              " hanging nodes, more triples than the fixed scratch holds (" +
                               std::to_string(kMaxPartials) + "); use pff_apply");
     if (!pb->has_state) return noalloc_fail(PFF_ERR_STATE, "pff_set_state has not been called");
     if (xu == yu || xp == yp) return noalloc_fail(PFF_ERR_INVALID_ARG, "x and y overlap");
@@ -96,6 +122,10 @@ extern "C" pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int3
     a.lin = precision == PFF_F64 ? static_cast<const void*>(pb->lin64) : static_cast<const void*>(pb->lin32);
     a.xu = xu; a.xp = xp; a.yu = yu; a.yp = yp;
     a.ibuf = scratch;
+    const size_t esz = precision == PFF_F64 ? sizeof(double) : sizeof(float);
+    a.hang_x = static_cast<char*>(scratch) + 3 * M.n_partials * esz;
+    a.hlin = precision == PFF_F64 ? static_cast<const void*>(pb->hlin64) : static_cast<const void*>(pb->hlin32);
+    a.nhang = D.nhang;
     a.n_slots = M.lay.n_slots;
     for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) {
       a.hx[l] = M.tree.hx(l);
@@ -104,6 +134,7 @@ extern "C" pff_status pff_apply_noalloc(pff_problem* pb, int32_t precision, int3
     leaf_modulus(*pb, precision, a);
     fill_cell_constants(a, M.Lf + 1);
     a.fe_degree = M.k;
+    a.sweep_sh = pb->sweep_sh;
     const int kop = op == PFF_OP_TRANSPOSE ? OP_FULL_T : OP_FULL;
     a.mode = op == PFF_OP_CONDENSED ? 0 : (MODE_MASK_INPUT | MODE_IDENTITY);
     FixupArgs f;

@@ -38,12 +38,16 @@ cudaError_t leaf_op(pff_problem& pb, int kop, int mode, const double* lin, const
   a.lin = lin;
   a.xu = xu; a.xp = xp; a.yu = yu; a.yp = yp;
   a.ibuf = pb.ibuf64;
+  a.hlin = lin == pb.lin64 ? pb.hlin64 : nullptr;   // other states hold their hanging values at the nodes' slots
+  a.hang_x = pb.hx64;
+  a.nhang = D.nhang;
   a.n_slots = M.lay.n_slots;
   for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) { a.hx[l] = M.tree.hx(l); a.hy[l] = M.tree.hy(l); }
   leaf_modulus(pb, PFF_F64, a);
   if (kop == OP_VJP) fill_material(pb.prm, a, true);
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
+  a.sweep_sh = pb.sweep_sh;
   a.mode = mode;
   a.cell_out = pb.cell_out;
   FixupArgs f;
@@ -294,7 +298,7 @@ cudaError_t newton_pdas_step(pff_problem& pb, pff_mg& mg, double* u, double* phi
     }
     if (k == o.max_newton) break;
     // linearisation, constraints, right-hand side with the inhomogeneous constraint on A
-    RET(launch_set_lin(n, u, phi, phit, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, s));
+    RET(launch_set_lin(n, u, phi, phit, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, pb.hlin64, pb.hlin32, s));
     pb.has_state = true;
     RET(launch_leaf_cmask(n, D.slot_flags, W.act, pb.cmask, s));
     RET(newton_du0(n, W.act, phi, phi_old, W.du0, s));

@@ -118,6 +118,11 @@ std::string alloc_problem(pff_problem& pb) {
   pb.cmask_dir = pb.bufs.alloc<uint8_t>(ns);
   pb.ibuf64 = pb.bufs.alloc<double>(3 * M.n_partials);
   pb.ibuf32 = pb.bufs.alloc<float>(3 * M.n_partials);
+  const int64_t nh = int64_t(M.hang.size());
+  pb.hlin64 = pb.bufs.alloc<double>(4 * nh);
+  pb.hlin32 = pb.bufs.alloc<float>(4 * nh);
+  pb.hx64 = pb.bufs.alloc<double>(3 * nh);
+  pb.hx32 = pb.bufs.alloc<float>(3 * nh);
   if (!pb.bufs.err.empty()) {
     std::string err = pb.bufs.err;
     pb.bufs.release();
@@ -162,6 +167,9 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
   a.lin = precision == PFF_F64 ? static_cast<const void*>(pb.lin64) : static_cast<const void*>(pb.lin32);
   a.xu = xu; a.xp = xp; a.yu = yu; a.yp = yp;
   a.ibuf = precision == PFF_F64 ? static_cast<void*>(pb.ibuf64) : static_cast<void*>(pb.ibuf32);
+  a.hlin = precision == PFF_F64 ? static_cast<const void*>(pb.hlin64) : static_cast<const void*>(pb.hlin32);
+  a.hang_x = precision == PFF_F64 ? static_cast<void*>(pb.hx64) : static_cast<void*>(pb.hx32);
+  a.nhang = D.nhang;
   a.n_slots = M.lay.n_slots;
   for (int l = 0; l <= M.Lf && l < kMaxLevels; ++l) {
     a.hx[l] = M.tree.hx(l);
@@ -170,6 +178,7 @@ cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, c
   leaf_modulus(pb, precision, a);
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
+  a.sweep_sh = pb.sweep_sh;
   int kop = OP_FULL;
   if (op == PFF_OP_JACOBIAN) { kop = OP_FULL; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }
   else if (op == PFF_OP_TRANSPOSE) { kop = OP_FULL_T; a.mode = MODE_MASK_INPUT | MODE_IDENTITY; }

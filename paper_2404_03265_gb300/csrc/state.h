@@ -142,6 +142,10 @@ struct pff_problem {
   pff::SolverWS ws;
   double* ibuf64 = nullptr;  // 3 per partial slot
   float* ibuf32 = nullptr;
+  double* hlin64 = nullptr;  // per hanging node: its resolved linearisation, 4 blocks of n_hang
+  float* hlin32 = nullptr;
+  double* hx64 = nullptr;    // per hanging node: the input resolved from its parents, 3 blocks of n_hang
+  float* hx32 = nullptr;
   bool has_state = false;
   // per-cell modulus E_K (cell-slot layout; levels concatenated like level vectors)
   bool has_ecell = false;
@@ -152,6 +156,7 @@ struct pff_problem {
   double* cell_out = nullptr;     // 3 * n_slots: per-cell VJP values
   double* adj_cell = nullptr;     // n_leaf_cells: per-step modulus gradient of the multi-step adjoint
   cudaEvent_t gm_ev[4] = {};      // GMRES phase timing (created on first use)
+  int sweep_sh = 0;               // Q1 cell-loop strip half-height (pff_set_cell_loop), 0 = by mesh size
 };
 
 namespace pff {
@@ -226,6 +231,9 @@ void set_last_error(const std::string& msg);
 // material constants; unit_E: elastic constants of E = 1 (a per-cell modulus is applied in the kernel)
 void fill_material(const pff_params& prm, ApplyArgs& a, bool unit_E = false);
 // modulus source of a leaf operator: unit-E constants + the cell array when a modulus field is set
+// pff_apply_noalloc's fixed scratch: loads its module and caches its address on
+// the current device (noalloc.cu).
+cudaError_t noalloc_prepare();
 void leaf_modulus(const pff_problem& pb, int precision, ApplyArgs& a);
 cudaError_t leaf_apply(pff_problem& pb, int precision, int op, const void* xu, const void* xp, void* yu,
                        void* yp, cudaStream_t s);

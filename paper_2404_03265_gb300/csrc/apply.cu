@@ -532,8 +532,12 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 #ifndef PFF_SW_DEPTH
 #define PFF_SW_DEPTH 4
 #endif
+#ifndef PFF_SW_UNROLL
+#define PFF_SW_UNROLL 2
+#endif
 constexpr int SW_WARPS = PFF_SW_WARPS;   // warps (strips) per block
 constexpr int SW_DEPTH = PFF_SW_DEPTH;   // ring stages per warp
+constexpr int SW_UNROLL = PFF_SW_UNROLL; // unrolled steps of the sweep loop
 
 // ---- asynchronous global -> shared copies (cp.async), per lane
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -557,111 +561,111 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
-// One node row of both halves in flight (per lane): node fields, the aligned
-// constraint-mask word holding each node's byte, the storage code, the modulus
-// of the cell whose lower-left node this is, and (irregular bricks) the owned
-// node's partial-sum slot and the word holding its storage action.
+// One node row of both halves in flight.  Every entry is a pair over the two
+// halves (lower half in .x, upper half in .y), so that a lane reads the pair of
+// its own node, and the pair of its right neighbour, with one shared load each.
+// Per lane: node fields (entry 32 pads the right-neighbour read of the last
+// lane), storage codes, the aligned constraint-mask words holding each node's
+// byte, the modulus of the cell whose lower-left node this is, and (irregular
+// bricks) the owned node's word (partial-sum slot + 1) | storage action << 30.
 template <typename T>
 struct __align__(16) SweepStage {
-  T f[NF][2][32];
-  T e[2][32];
-  uint32_t cm[2][32];
-  int32_t code[2][32];
-  int32_t part[2][32];
-  uint32_t actw[2][32];
+  typename VT<T>::T2 f[NF][33];
+  typename VT<T>::T2 e[32];
+  int2 code[32];
+  uint2 cm[32];
+  int2 own[32];
 };
 
-// One node of one half: its fields and constraint-mask byte.
 template <typename T>
-struct NodeRaw {
-  T f[NF];
-  uint32_t cm;
-};
+__device__ __forceinline__ T& half_of(typename VT<T>::T2& p, int h) { return h ? p.y : p.x; }
+__device__ __forceinline__ int32_t& half_of_i(int2& p, int h) { return h ? p.y : p.x; }
+__device__ __forceinline__ uint32_t& half_of_u(uint2& p, int h) { return h ? p.y : p.x; }
 
 // Issue the copies of the lane's node of half h.  A stored node (code >= 0)
 // copies its fields and constraint word from its slot.  A hanging node (code
 // <= -2, table entry -2 - code) copies its linearisation from a.hlin and its
 // input C x from a.hang_x (written by hang_x_kernel, the launch this one may
 // depend on), both indexed by the entry; without a.hlin the linearisation comes
-// from the node's own slot (resolved there by set_lin).
+// from the node's own slot (resolved there by set_lin).  Absent nodes are zero.
+// Hanging and absent nodes carry no constraint of their own.
 template <typename T, int OP>
 __device__ __forceinline__ void issue_node(const ApplyArgs& a, int32_t code, SweepStage<T>& st, int h, int lane) {
   using N = Needs<OP>;
-  st.code[h][lane] = code;
   if (code >= 0) {
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-      if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], field_ptr<T>(a, f) + code);
-    cp_async4(&st.cm[h][lane], reinterpret_cast<const uint32_t*>(a.cmask + (code & ~3)));
-  } else if (code != kAbsent) {
-    const int hi = -2 - code;
-    if (a.hlin != nullptr) {
-      const T* hl = reinterpret_cast<const T*>(a.hlin);
+      if (field_used<OP>(f)) cp_one(&half_of<T>(st.f[f][lane], h), field_ptr<T>(a, f) + code);
+    cp_async4(&half_of_u(st.cm[lane], h), reinterpret_cast<const uint32_t*>(a.cmask + (code & ~3)));
+    return;
+  }
+  half_of_u(st.cm[lane], h) = 0u;
+  if (code == kAbsent) {
 #pragma unroll
-      for (int f = F_LU; f < NF; ++f)
-        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], hl + (f - F_LU) * int64_t(a.nhang) + hi);
-    } else {
-      const int slot = __ldg(&a.hang[hi].slot);
+    for (int f = 0; f < NF; ++f)
+      if (field_used<OP>(f)) half_of<T>(st.f[f][lane], h) = T(0);
+    return;
+  }
+  const int hi = -2 - code;
+  if (a.hlin != nullptr) {
+    const T* hl = reinterpret_cast<const T*>(a.hlin);
 #pragma unroll
-      for (int f = F_LU; f < NF; ++f)
-        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], field_ptr<T>(a, f) + slot);
-    }
-    if (N::xu || N::xp) {
-      pdl_wait();
-      const T* hx = reinterpret_cast<const T*>(a.hang_x);
+    for (int f = F_LU; f < NF; ++f)
+      if (field_used<OP>(f)) cp_one(&half_of<T>(st.f[f][lane], h), hl + (f - F_LU) * int64_t(a.nhang) + hi);
+  } else {
+    const int slot = __ldg(&a.hang[hi].slot);
 #pragma unroll
-      for (int f = F_XU; f <= F_XP; ++f)
-        if (field_used<OP>(f)) cp_one(&st.f[f][h][lane], hx + f * int64_t(a.nhang) + hi);
-    }
+    for (int f = F_LU; f < NF; ++f)
+      if (field_used<OP>(f)) cp_one(&half_of<T>(st.f[f][lane], h), field_ptr<T>(a, f) + slot);
+  }
+  if (N::xu || N::xp) {
+    pdl_wait();
+    const T* hx = reinterpret_cast<const T*>(a.hang_x);
+#pragma unroll
+    for (int f = F_XU; f <= F_XP; ++f)
+      if (field_used<OP>(f)) cp_one(&half_of<T>(st.f[f][lane], h), hx + f * int64_t(a.nhang) + hi);
   }
 }
 
-// Read the lane's landed node of half h: fixed input components zeroed
-// (MODE_MASK_INPUT) on stored nodes; absent nodes are zero; hanging nodes carry
-// no constraint of their own.
+// Constraint bytes (lower, upper half) of the lane's node in a landed stage.
+template <typename T>
+__device__ __forceinline__ uint2 node_cm(const SweepStage<T>& st, int lane) {
+  const int2 k = st.code[lane];
+  const uint2 w = st.cm[lane];
+  return make_uint2((w.x >> (8 * (k.x & 3))) & 0xffu, (w.y >> (8 * (k.y & 3))) & 0xffu);
+}
+
+// Zero the fixed input components of the lane's node in a landed stage
+// (MODE_MASK_INPUT), so that the node and its left neighbour read masked values.
 template <typename T, int OP>
-__device__ __forceinline__ void read_node(const ApplyArgs& a, const SweepStage<T>& st, int h, int lane,
-                                          NodeRaw<T>& r) {
+__device__ __forceinline__ void mask_node(SweepStage<T>& st, int lane, uint2 cm) {
   using N = Needs<OP>;
-  const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
-  const int32_t code = st.code[h][lane];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) r.f[f] = T(0);
-  r.cm = 0;
-  if (code != kAbsent) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-      if (field_used<OP>(f)) r.f[f] = st.f[f][h][lane];
-  }
-  if (code >= 0) {
-    r.cm = (st.cm[h][lane] >> (8 * (code & 3))) & 0xffu;
-    if (mask && r.cm) {
-      if (N::xu && (r.cm & 1)) r.f[F_XU] = T(0);
-      if (N::xu && (r.cm & 2)) r.f[F_XV] = T(0);
-      if (N::xp && (r.cm & 4)) r.f[F_XP] = T(0);
+  if ((cm.x | cm.y) & 7u) {
+    if (N::xu) {
+      if (cm.x & 1) st.f[F_XU][lane].x = 0;
+      if (cm.y & 1) st.f[F_XU][lane].y = 0;
+      if (cm.x & 2) st.f[F_XV][lane].x = 0;
+      if (cm.y & 2) st.f[F_XV][lane].y = 0;
+    }
+    if (N::xp) {
+      if (cm.x & 4) st.f[F_XP][lane].x = 0;
+      if (cm.y & 4) st.f[F_XP][lane].y = 0;
     }
   }
 }
 
 // A node row of both halves as pairs: own values o and (right neighbour - own) h.
 template <typename T, int OP>
-__device__ __forceinline__ void make_row(const NodeRaw<T>& r0, const NodeRaw<T>& r1, NodePair<T>& o,
-                                         NodePair<T>& h) {
+__device__ __forceinline__ void load_row(const SweepStage<T>& st, int lane, NodePair<T>& o, NodePair<T>& h) {
   using P = typename VT<T>::T2;
-  const unsigned FULL = 0xffffffffu;
   P* po[NF] = {&o.x0, &o.x1, &o.xp, &o.lx, &o.ly, &o.lz, &o.lw};
   P* ph[NF] = {&h.x0, &h.x1, &h.xp, &h.lx, &h.ly, &h.lz, &h.lw};
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     if (field_used<OP>(f)) {
-      P v;
-      v.x = r0.f[f];
-      v.y = r1.f[f];
-      P rt;
-      rt.x = __shfl_down_sync(FULL, v.x, 1);
-      rt.y = __shfl_down_sync(FULL, v.y, 1);
+      const P v = st.f[f][lane];
       *po[f] = v;
-      *ph[f] = psub(rt, v);
+      *ph[f] = psub(st.f[f][lane + 1], v);
     } else {
       *po[f] = pbc(T(0));
       *ph[f] = pbc(T(0));
@@ -669,48 +673,40 @@ __device__ __forceinline__ void make_row(const NodeRaw<T>& r0, const NodeRaw<T>&
   }
 }
 
-// The stored value of an owned node of an irregular brick after the cell loop:
-// storage action (final value, zero, or none: another level's or the fix-up's),
-// partial sum, constraint rows.
+// Store of an owned node after the cell loop when it is constrained or lies in
+// an irregular brick: storage action (final value, zero, or none: another
+// level's or the fix-up's), partial sum, constraint rows (identity: y = the
+// original x of the node, read back from the input vectors).  Predicated rather
+// than branched: the lanes of a row take different actions.
 template <typename T, int OP>
-__device__ __forceinline__ void write_owned(const ApplyArgs& a, int slot, int act_s, int part, uint8_t cm, T y0,
-                                            T y1, T y2) {
+__device__ __forceinline__ void store_owned(const ApplyArgs& a, int slot, int act_s, int part, uint8_t cm, T y0, T y1,
+                                            T y2) {
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
-  T* yu = reinterpret_cast<T*>(a.yu);
-  T* yv = yu + a.n_slots;
-  T* yp = reinterpret_cast<T*>(a.yp);
   if (part >= 0) {
     T* ib = reinterpret_cast<T*>(a.ibuf) + 3 * int64_t(part);
     ib[0] = y0; ib[1] = y1; ib[2] = y2;
   }
-  if (act_s == kActFinal) {
-    if (isDiag) {
-      if (cm & 1) y0 = T(0);
-      if (cm & 2) y1 = T(0);
-      if (cm & 4) y2 = T(0);
-    } else if (cm) {
-      const bool ident = (a.mode & MODE_IDENTITY) != 0;
-      const T* xu = reinterpret_cast<const T*>(a.xu);
-      if (cm & 1) y0 = ident ? ldg(xu + slot) : T(0);
-      if (cm & 2) y1 = ident ? ldg(xu + a.n_slots + slot) : T(0);
-      if (cm & 4) y2 = ident ? ldg(reinterpret_cast<const T*>(a.xp) + slot) : T(0);
-    }
-    if (outU) { yu[slot] = y0; yv[slot] = y1; }
-    if (outP) yp[slot] = y2;
-  } else if (act_s == kActZero) {
-    if (outU) { yu[slot] = T(0); yv[slot] = T(0); }
-    if (outP) yp[slot] = T(0);
+  if (act_s == kActNone) return;
+  if (act_s == kActZero) {
+    y0 = y1 = y2 = T(0);
+  } else if (cm) {
+    const bool ident = !isDiag && (a.mode & MODE_IDENTITY) != 0;
+    const T* xu = reinterpret_cast<const T*>(a.xu);
+    if (cm & 1) y0 = ident ? ldg(xu + slot) : T(0);
+    if (cm & 2) y1 = ident ? ldg(xu + a.n_slots + slot) : T(0);
+    if (cm & 4) y2 = ident ? ldg(reinterpret_cast<const T*>(a.xp) + slot) : T(0);
   }
+  T* yu = reinterpret_cast<T*>(a.yu);
+  if (outU) { yu[slot] = y0; yu[a.n_slots + slot] = y1; }
+  if (outP) reinterpret_cast<T*>(a.yp)[slot] = y2;
 }
 
-template <typename T, int OP, int SH>
+template <typename T, int OP>
 __global__ void __launch_bounds__(32 * SW_WARPS, sizeof(T) == 4 ? PFF_SW_MINB : PFF_SW_MINB64)
-sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
-  static_assert(NB % (2 * SH) == 0, "two half-strips of SH rows must tile the brick");
-  constexpr int NSTRIP = NB / (2 * SH);
-  constexpr int NROW = SH + 2;                         // node rows per half
+sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__ units, int32_t nunits) {
+  static_assert(SW_DEPTH >= 3, "the ring holds the lower row, the upper row and at least one row in flight");
   using P = typename VT<T>::T2;
   constexpr bool outU = (OP != OP_PP && OP != OP_PP_DIAG && OP != OP_MASS && OP != OP_TCV && OP != OP_PHIT_VJP);
   constexpr bool outP = (OP != OP_UU && OP != OP_UU_DIAG);
@@ -720,13 +716,18 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
   const int lane = threadIdx.x & 31;
   SweepStage<T>* ring = reinterpret_cast<SweepStage<T>*>(smem_raw) + (threadIdx.x >> 5) * SW_DEPTH;
   const int unit = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
-  if (unit >= a.lay.nbricks * NSTRIP) { pdl_wait(); return; }   // warp-uniform
-  const int bi = unit / NSTRIP;
-  const int r0 = (unit - bi * NSTRIP) * (2 * SH);
+  if (unit >= nunits) { pdl_wait(); return; }   // warp-uniform
+  // the warp's strip: owned rows r0 .. r0 + 2 SH - 1 of brick bi
+  const int32_t uw = __ldg(units + unit);
+  const int bi = uw >> 8;
+  const int r0 = (uw >> 3) & 31;
+  const int SH = (0x0103050f >> (8 * (uw & 3))) & 0xff;   // 15, 5, 3, 1 for codes 0..3
+  const int NROW = SH + 2;                             // node rows per half
   const BrickDesc* bd = a.lay.bricks + bi;
   const int irr = __ldg(&bd->irr);
   const LevGeom<T> g = geom<T>(a, __ldg(&bd->level));
   const MatConst<T>& mc = matc<T>(a);
+  const bool mask = (a.mode & MODE_MASK_INPUT) != 0;
   const int n = lane - 1;                              // window node column -1..30
   const int dx = n < 0 ? -1 : (n >= NB ? 1 : 0);
   const int col = n - NB * dx;                         // its column in its brick
@@ -740,36 +741,37 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
   T* yu = reinterpret_cast<T*>(a.yu);
   T* yv = yu + a.n_slots;
   T* yp = reinterpret_cast<T*>(a.yp);
+  // the right-neighbour pad of every stage reads as zero
+  if (lane < NF)
+    for (int j = 0; j < SW_DEPTH; ++j) ring[j].f[lane][32] = pbc(T(0));
   // storage code of window node (n, r) of a regular brick, brick row r = -1..30;
   // also the cell slot of cell (n, r) in any brick (its lower-left node position)
   auto reg_code = [&](int r) -> int32_t {
     return r < 0 ? base_lo + col + NB * (r + NB) : (r >= NB ? base_hi + col + NB * (r - NB) : base_mid + col + NB * r);
   };
-  // window cell (n, c) is active (all 32 lanes call it: shuffle); the last
-  // lane's cell lies outside the window and reaches no owned node
+  // window cell (n, c) is active (all 32 lanes call it: shuffle).  The last
+  // lane's cell lies outside the window: its contributions reach only that
+  // lane's own (halo) node, so it is never masked.
   auto cell_active = [&](int c) -> bool {
     if (irr < 0) return true;
     const int i = (c + 1) * NCW + (lane < 31 ? lane : 0);
     const uint32_t w = __shfl_sync(FULL, cmw, (i >> 5) & 31);
-    return lane < 31 && ((w >> (i & 31)) & 1u);
+    return lane == 31 || ((w >> (i & 31)) & 1u);
   };
   // stream of node rows j = 0 .. NROW-1 per half: brick rows r0 - 1 + j (half 0)
   // and r0 + SH - 1 + j (half 1); the codes of irregular bricks are read one row
   // ahead of their copies
   int32_t kn0 = 0, kn1 = 0;
   if (irr >= 0) { kn0 = __ldg(win + WN * r0); kn1 = __ldg(win + WN * (r0 + SH)); }
-  auto issue_half = [&](SweepStage<T>& st, int h, int32_t k, int r) {
-    issue_node<T, OP>(a, k, st, h, lane);
+  auto issue_extra = [&](SweepStage<T>& st, int h, int r) {
     if (a.ecell != nullptr) {
-      // modulus of cell (n, r), r <= 29, whose lower-left node this is
-      const bool act = r < NB && cell_active(r);
-      if (act) cp_one(&st.e[h][lane], reinterpret_cast<const T*>(a.ecell) + reg_code(r));
+      // modulus of cell (n, r), r <= 29, whose lower-left node this is (the last
+      // lane's cell lies outside the window)
+      const bool act = r < NB && cell_active(r) && lane < 31;
+      if (act) cp_one(&half_of<T>(st.e[lane], h), reinterpret_cast<const T*>(a.ecell) + reg_code(r));
     }
-    if (irr >= 0 && r >= 0 && r < NB && lane >= 1 && lane <= NB) {
-      const int o = irr * (NB * NB) + n + NB * r;
-      cp_async4(&st.part[h][lane], a.lay.own_part + o);
-      cp_async4(&st.actw[h][lane], reinterpret_cast<const uint32_t*>(a.lay.own_act + (o & ~3)));
-    }
+    if (irr >= 0 && r >= 0 && r < NB && lane >= 1 && lane <= NB)
+      cp_async4(&half_of_i(st.own[lane], h), a.lay.own + irr * (NB * NB) + n + NB * r);
   };
   auto issue = [&](int j) {
     if (j < NROW) {
@@ -783,59 +785,46 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
         k0 = reg_code(r0 - 1 + j);
         k1 = reg_code(r0 + SH - 1 + j);
       }
-      issue_half(st, 0, k0, r0 - 1 + j);
-      issue_half(st, 1, k1, r0 + SH - 1 + j);
+      st.code[lane] = make_int2(k0, k1);
+      issue_node<T, OP>(a, k0, st, 0, lane);
+      issue_node<T, OP>(a, k1, st, 1, lane);
+      if (irr >= 0 || a.ecell != nullptr) {
+        issue_extra(st, 0, r0 - 1 + j);
+        issue_extra(st, 1, r0 + SH - 1 + j);
+      }
     }
     cp_async_commit();
   };
-  // per-row values kept from consumption to completion (one step later)
-  struct RowExtra {
-    P e;
-    int32_t part0, part1;
-    uint32_t act0, act1;
-  };
-  auto row_extra = [&](const SweepStage<T>& st, RowExtra& x) {
-    x.e = pbc(T(1));
-    if (a.ecell != nullptr) { x.e.x = st.e[0][lane]; x.e.y = st.e[1][lane]; }
-    x.part0 = x.part1 = -1;
-    x.act0 = x.act1 = kActFinal;
-    if (irr >= 0 && lane >= 1 && lane <= NB) {
-      x.part0 = st.part[0][lane];
-      x.part1 = st.part[1][lane];
-      x.act0 = st.actw[0][lane];
-      x.act1 = st.actw[1][lane];
-    }
-  };
+  // Ring: row j lives in stage j % SW_DEPTH from its issue until the step that
+  // completes it as the lower row; SW_DEPTH - 2 rows are in flight beyond the
+  // one being read.  A landed row is first masked by its owners; __syncwarp
+  // orders that before the left neighbours read it.
 #pragma unroll
   for (int j = 0; j < SW_DEPTH - 1; ++j) issue(j);
 
-  NodeRaw<T> nr0, nr1;
   cp_async_wait<SW_DEPTH - 2>();
-  read_node<T, OP>(a, ring[0], 0, lane, nr0);
-  read_node<T, OP>(a, ring[0], 1, lane, nr1);
-  RowExtra xb;                       // lower node row's extras
-  row_extra(ring[0], xb);
-  issue(SW_DEPTH - 1);
+  uint2 cb = node_cm(ring[0], lane);   // constraint bytes of the lower row's nodes
+  if (mask) mask_node<T, OP>(ring[0], lane, cb);
+  __syncwarp();
   NodePair<T> ob, hb;                // lower node row of the current cell rows
-  uint32_t cb0 = nr0.cm, cb1 = nr1.cm;
-  make_row<T, OP>(nr0, nr1, ob, hb);
+  load_row<T, OP>(ring[0], lane, ob, hb);
   P carry[3] = {pbc(T(0)), pbc(T(0)), pbc(T(0))};
-#pragma unroll 2
+#pragma unroll SW_UNROLL
   for (int s = 0; s <= SH; ++s) {
-    cp_async_wait<SW_DEPTH - 2>();
-    const SweepStage<T>& st = ring[(s + 1) % SW_DEPTH];
-    read_node<T, OP>(a, st, 0, lane, nr0);
-    read_node<T, OP>(a, st, 1, lane, nr1);
-    RowExtra xt;
-    row_extra(st, xt);
-    issue(s + SW_DEPTH);             // refills the stage of row s, read at the previous step
+    cp_async_wait<SW_DEPTH - 3>();
+    SweepStage<T>& sb = ring[s % SW_DEPTH];         // lower row: row s
+    SweepStage<T>& st = ring[(s + 1) % SW_DEPTH];   // upper row: row s + 1
+    const uint2 ct = node_cm(st, lane);
+    if (mask) mask_node<T, OP>(st, lane, ct);
+    __syncwarp();
+    issue(s + SW_DEPTH - 1);         // into the stage of row s - 1, completed at the previous step
     NodePair<T> ot, ht;              // upper node row
-    const uint32_t ct0 = nr0.cm, ct1 = nr1.cm;
-    make_row<T, OP>(nr0, nr1, ot, ht);
+    load_row<T, OP>(st, lane, ot, ht);
     const int c0 = r0 - 1 + s, c1 = c0 + SH;   // cell rows (and completed node rows) of the halves
     const bool act0 = cell_active(c0), act1 = cell_active(c1);
+    const P ec = a.ecell != nullptr ? sb.e[lane] : pbc(T(1));
     P out[12];
-    q1_cell_pair<T, OP>(ob, hb, ot, ht, mc, g, xb.e, out);
+    q1_cell_pair<T, OP>(ob, hb, ot, ht, mc, g, ec, out);
     if (!act0 || !act1) {
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
@@ -869,15 +858,21 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) y[q] = padd(padd(carry[q], brL[q]), out[q]);
         const int s0 = own_base + n + NB * c0, s1 = own_base + n + NB * c1;
-        if (irr < 0 && !(cb0 | cb1)) {
+        // storage action and partial sum of the two nodes (irregular bricks)
+        uint32_t w0 = uint32_t(kActFinal) << 30, w1 = w0;
+        if (irr >= 0) {
+          const int2 ow = sb.own[lane];
+          w0 = uint32_t(ow.x);
+          w1 = uint32_t(ow.y);
+        }
+        const bool plain0 = cb.x == 0 && w0 == (uint32_t(kActFinal) << 30);   // final value, no partial, free
+        const bool plain1 = cb.y == 0 && w1 == (uint32_t(kActFinal) << 30);
+        if (plain0 && plain1) {
           if (outU) { yu[s0] = y[0].x; yv[s0] = y[1].x; yu[s1] = y[0].y; yv[s1] = y[1].y; }
           if (outP) { yp[s0] = y[2].x; yp[s1] = y[2].y; }
         } else {
-          const int o0 = irr >= 0 ? irr * (NB * NB) + n + NB * c0 : 0, o1 = o0 + NB * SH;
-          write_owned<T, OP>(a, s0, irr >= 0 ? int((xb.act0 >> (8 * (o0 & 3))) & 0xffu) : int(kActFinal),
-                             xb.part0, uint8_t(cb0), y[0].x, y[1].x, y[2].x);
-          write_owned<T, OP>(a, s1, irr >= 0 ? int((xb.act1 >> (8 * (o1 & 3))) & 0xffu) : int(kActFinal),
-                             xb.part1, uint8_t(cb1), y[0].y, y[1].y, y[2].y);
+          store_owned<T, OP>(a, s0, int(w0 >> 30), int(w0 & 0x3fffffffu) - 1, uint8_t(cb.x), y[0].x, y[1].x, y[2].x);
+          store_owned<T, OP>(a, s1, int(w1 >> 30), int(w1 & 0x3fffffffu) - 1, uint8_t(cb.y), y[0].y, y[1].y, y[2].y);
         }
       }
 #pragma unroll
@@ -885,9 +880,7 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a) {
     }
     ob = ot;
     hb = ht;
-    cb0 = ct0;
-    cb1 = ct1;
-    xb = xt;
+    cb = ct;
   }
   cp_async_wait<0>();
   pdl_wait();   // the launch this one depends on (if any) completes before this grid does
@@ -1123,19 +1116,53 @@ cudaError_t launch_ex(bool pdl, void (*fn)(KArgs...), unsigned grid, unsigned bl
   return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
+// Work units of the Q1 cell loop (one warp each).  A strip of half-height SH
+// evaluates 2 (SH + 1) cell rows for its 2 SH owned rows and pays one pipeline
+// start; short strips give small meshes enough warps and even out the slower
+// irregular bricks.  Schedules: 0 by mesh size: on meshes with at least four
+// bricks per SM, regular bricks SH = 15 (one unit) and then irregular bricks
+// SH = 5 (three units), so that the blocks of the shorter irregular units fill
+// the slots the regular ones leave; on smaller meshes every brick SH = 5 if that
+// gives four warps per SM, else SH = 1; 1, 2, 3: every brick SH = 15, 5, 1.
+std::vector<int32_t> sweep_units(const std::vector<BrickDesc>& bricks, int32_t unit_off[5]) {
+  std::vector<int32_t> u;
+  const int nb = int(bricks.size());
+  auto add = [&](int b, int code) {
+    const int sh = code == 0 ? 15 : code == 1 ? 5 : code == 2 ? 3 : 1;
+    for (int r0 = 0; r0 < NB; r0 += 2 * sh) u.push_back(int32_t(b) << 8 | r0 << 3 | code);
+  };
+  const int64_t want = int64_t(4) * sm_count();
+  unit_off[0] = 0;
+  if (nb >= want) {
+    for (int b = 0; b < nb; ++b)
+      if (bricks[b].irr < 0) add(b, 0);
+    for (int b = 0; b < nb; ++b)
+      if (bricks[b].irr >= 0) add(b, 1);
+  } else {
+    const int code = 3 * int64_t(nb) >= want ? 1 : 3;
+    for (int b = 0; b < nb; ++b) add(b, code);
+  }
+  unit_off[1] = int32_t(u.size());
+  for (int b = 0; b < nb; ++b) add(b, 0);
+  unit_off[2] = int32_t(u.size());
+  for (int b = 0; b < nb; ++b) add(b, 1);
+  unit_off[3] = int32_t(u.size());
+  for (int b = 0; b < nb; ++b) add(b, 3);
+  unit_off[4] = int32_t(u.size());
+  return u;
+}
+
 template <typename T, int OP>
 cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
   using N = Needs<OP>;
-  constexpr bool multi = (OP == OP_FULL || OP == OP_UU || OP == OP_PP);
-  int sh = 15;
-  if (multi) {
-    if (a.sweep_sh == 15 || a.sweep_sh == 5 || a.sweep_sh == 1) {
-      sh = a.sweep_sh;
-    } else {
-      const int64_t want = int64_t(4) * sm_count();   // warps
-      sh = a.lay.nbricks >= want ? 15 : (3 * int64_t(a.lay.nbricks) >= want ? 5 : 1);
-    }
-  }
+  // FP64 is bound by its arithmetic rate: there the least work (one strip per
+  // brick) wins over the balanced schedule, except on small meshes
+  int sched = a.sweep_sh == 15 ? 1 : a.sweep_sh == 5 ? 2 : a.sweep_sh == 1 ? 3 : 0;
+  if (sched == 0 && sizeof(T) == 8 && a.lay.nbricks >= 4 * sm_count()) sched = 1;
+  if (a.lay.units == nullptr) return cudaErrorInvalidValue;
+  const int32_t* units = a.lay.units + a.lay.unit_off[sched];
+  const int32_t nunits = a.lay.unit_off[sched + 1] - a.lay.unit_off[sched];
+  if (nunits <= 0) return cudaSuccess;
   // hanging nodes' input: C x into a.hang_x first; the sweep may start before that
   // grid ends and waits for it only where it copies those values
   bool pdl = false;
@@ -1150,16 +1177,9 @@ cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
   }
   const unsigned blk = 32 * SW_WARPS;
   const size_t smem = sizeof(SweepStage<T>) * SW_DEPTH * SW_WARPS;
-  auto grid = [&](int nstrip) { return unsigned((int64_t(a.lay.nbricks) * nstrip + SW_WARPS - 1) / SW_WARPS); };
-  auto go = [&](auto fn, int nstrip) {
-    resident_blocks(reinterpret_cast<const void*>(fn), int(blk), smem);   // sets the shared-memory limit once
-    return launch_ex(pdl, fn, grid(nstrip), blk, smem, s, a);
-  };
-  if constexpr (multi) {
-    if (sh == 5) return go(&sweep_q1_kernel<T, OP, 5>, 3);
-    if (sh == 1) return go(&sweep_q1_kernel<T, OP, 1>, 15);
-  }
-  return go(&sweep_q1_kernel<T, OP, 15>, 1);
+  const auto fn = &sweep_q1_kernel<T, OP>;
+  resident_blocks(reinterpret_cast<const void*>(fn), int(blk), smem);   // sets the shared-memory limit once
+  return launch_ex(pdl, fn, unsigned((nunits + SW_WARPS - 1) / SW_WARPS), blk, smem, s, a, units, nunits);
 }
 
 template <typename T>

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "mesh.h"
 
@@ -47,6 +48,13 @@ struct DevLayout {
   const int32_t* win = nullptr;
   const int32_t* own_part = nullptr;
   const uint8_t* own_act = nullptr;
+  const int32_t* own = nullptr;      // both as one word: (own_part + 1) | own_act << 30
+  // Q1 cell-loop work units (one warp each): brick << 8 | first owned row << 3 |
+  // strip code (strip half-height 15, 5, 3, 1 for codes 0..3); four schedules
+  // one after the other (by mesh size; all 15; all 5; all 1), schedule p in
+  // units[unit_off[p] .. unit_off[p + 1])
+  const int32_t* units = nullptr;
+  int32_t unit_off[5] = {0, 0, 0, 0, 0};
   const uint32_t* cellmask = nullptr;
 };
 
@@ -106,7 +114,7 @@ struct ApplyArgs {
   Q2Tab<double> q2d;
   int mode;
   int fe_degree;
-  int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (see launch_sweep)
+  int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (schedules of DevLayout::units)
 };
 
 struct FixupArgs {
@@ -127,6 +135,11 @@ struct FixupArgs {
 
 // fills mf / md / gf / gd from hx, hy and the material
 void fill_cell_constants(ApplyArgs& a, int nlevels);
+
+// streaming multiprocessors of the current device (cached)
+int sm_count();
+// work units of the Q1 cell loop for a layout's bricks (see DevLayout::units)
+std::vector<int32_t> sweep_units(const std::vector<BrickDesc>& bricks, int32_t unit_off[5]);
 
 // launchers (return cudaError_t of the launch).  launch_fixup must follow the
 // launch_apply whose partial sums it condenses directly on the same stream: it

@@ -12,6 +12,12 @@ static DevLayout upload_layout(DevAllocs& mem, const Layout& L) {
   d.win = mem.upload(L.win);
   d.own_part = mem.upload(L.own_part);
   d.own_act = mem.upload(L.own_act);
+  std::vector<int32_t> own(L.own_part.size());
+  for (size_t i = 0; i < own.size(); ++i)
+    own[i] = int32_t(uint32_t(L.own_part[i] + 1) | (uint32_t(L.own_act[i]) << 30));
+  d.own = mem.upload(own);
+  const std::vector<int32_t> units = sweep_units(L.bricks, d.unit_off);
+  d.units = mem.upload(units);
   d.cellmask = mem.upload(L.cellmask);
   return d;
 }

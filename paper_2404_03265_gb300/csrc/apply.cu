@@ -362,6 +362,11 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T>& b, const NodePai
       }
   } else {
     P S11[2][2], S12[2][2], S22[2][2], fv[2][2];
+    // q = (1-kappa) sigma(u) + p I, so that the phi rows' coefficients are
+    //   (1-kappa) sigma(u):e(u) + 2 p div u + G_c/l = q : e(u) + p div u + G_c/l,
+    //   2 phi ((1-kappa) sigma(u) + p I) = 2 phi q
+    P oc2ml = zero, ocl = zero, ocm = zero;
+    if (N::linU) { oc2ml = pmul(omk, c2ml); ocl = pmul(omk, cl); ocm = pmul(omk, cm); }
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
@@ -369,17 +374,17 @@ __device__ __forceinline__ void q1_cell_pair(const NodePair<T>& b, const NodePai
         P gq = zero, T11 = zero, T22 = zero, T12 = zero, mq = zero;
         if (N::phit) gq = pfma(omk, pmul(phitq[q1][q2], phitq[q1][q2]), pbc(m.kap));
         if (N::linU) {
+          const P pp = pbc(m.p);
           const P ge12 = padd(uxy[q1], uyx[q2]);   // 2 e12
-          const P s11 = pfma(c2ml, e11[q2], pmul(cl, e22[q1]));
-          const P s22 = pfma(cl, e11[q2], pmul(c2ml, e22[q1]));
-          const P s12 = pmul(cm, ge12);
-          const P se = pfma(s11, e11[q2], pfma(s22, e22[q1], pmul(s12, ge12)));
-          mq = pfma(omk, se, pfma(pbc(m.p2), padd(e11[q2], e22[q1]), pbc(m.gcl)));
+          const P q11 = pfma(oc2ml, e11[q2], pfma(ocl, e22[q1], pp));
+          const P q22 = pfma(ocl, e11[q2], pfma(oc2ml, e22[q1], pp));
+          const P q12 = pmul(ocm, ge12);
+          mq = pfma(q11, e11[q2], pfma(q22, e22[q1], pfma(q12, ge12, pfma(pp, padd(e11[q2], e22[q1]), pbc(m.gcl)))));
           if (N::phi) {
             const P tp = padd(phiq[q1][q2], phiq[q1][q2]);
-            T11 = pmul(tp, pfma(omk, s11, pbc(m.p)));
-            T22 = pmul(tp, pfma(omk, s22, pbc(m.p)));
-            T12 = pmul(tp, pmul(omk, s12));
+            T11 = pmul(tp, q11);
+            T22 = pmul(tp, q22);
+            T12 = pmul(tp, q12);
           }
         }
         if (N::xu) {

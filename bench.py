@@ -27,6 +27,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Jacobian apply GDoF/s & %HBM peak; solve s/load step, FP32-MG vs FP64 MG"
+# FP64 FMA rate of a GB300 (CUDA cores), measured with an independent-chain DFMA
+# loop at 2.07 GHz; the FP64 apply is bound by it, not by HBM.
+FP64_PEAK_TFLOPS = 1.19
 WORKLOAD = "apply"
 L2_BYTES = 129 * 2 ** 20
 
@@ -156,13 +159,17 @@ def build_sets(mesh, n_sets, dtype, seed=0):
     return sets
 
 
-def time_applies(sets, steps, warmup, ws):
+def time_applies(sets, steps, warmup, ws, per_step=1):
+    """Seconds for `steps` timed steps of `per_step` applies each (rotating over
+    the input sets), after `warmup` untimed steps; CUDA events on the stream."""
     import torch
     from paper_2404_03265_gb300 import PFF_OP_JACOBIAN
     n = len(sets)
-    for i in range(warmup):
-        pb, xu, xp, yu, yp = sets[i % n]
+    k = 0
+    for i in range(warmup * per_step):
+        pb, xu, xp, yu, yp = sets[k % n]
         pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+        k += 1
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
@@ -170,14 +177,23 @@ def time_applies(sets, steps, warmup, ws):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for i in range(steps):
-        pb, xu, xp, yu, yp = sets[i % n]
+    for i in range(steps * per_step):
+        pb, xu, xp, yu, yp = sets[k % n]
         pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+        k += 1
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1) / 1e3
+
+
+def applies_per_step(sets, steps, min_seconds=1.0):
+    """Applies per timed step so that `steps` steps take at least min_seconds (at
+    least one): the headline's timed region is then long enough for the clock
+    sampler whatever --steps is.  From the duration of 50 untimed applies."""
+    t = time_applies(sets, 1, 1, 1, per_step=50) / 50
+    return max(1, int(np.ceil(min_seconds / (max(steps, 1) * t))))
 
 
 def time_e2e(mesh, dtype, steps, warmup):
@@ -231,7 +247,42 @@ def time_e2e(mesh, dtype, steps, warmup):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     nb = hxu.numel() * hxu.element_size() + hxp.numel() * hxp.element_size()
-    return t, nb, hy[0][0].numel() * hy[0][0].element_size() + hy[0][1].numel() * hy[0][1].element_size()
+    nbo = hy[0][0].numel() * hy[0][0].element_size() + hy[0][1].numel() * hy[0][1].element_size()
+    # the last step's y, copied out, against a plain apply of the same x on one stream
+    pb, xu, xp, yu, yp = sets[0]
+    xu.copy_(hxu)
+    xp.copy_(hxp)
+    yu.zero_()
+    yp.zero_()
+    pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+    torch.cuda.synchronize()
+    last = hy[(steps - 1) % 2]
+    ref = torch.cat([yu.reshape(-1), yp]).double().cpu()
+    got = torch.cat([last[0].reshape(-1), last[1]]).double()
+    rel = float((got - ref).norm() / ref.norm())
+    if not rel <= 1e-5:
+        raise RuntimeError("end-to-end leg: copied-out y differs from a plain apply (relative %.3g)" % rel)
+    # reference: the same pinned copies alone, in and out on their own streams
+    ci = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
+    co = torch.empty(nbo // 4, dtype=torch.float32, device="cuda")
+    hi = torch.empty(nb // 4, dtype=torch.float32).pin_memory()
+    ho = torch.empty(nbo // 4, dtype=torch.float32).pin_memory()
+    rates = {}
+    for name, (dst, src, st) in {"h2d": (ci, hi, s_in), "d2h": (ho, co, s_out)}.items():
+        for _ in range(3):
+            with torch.cuda.stream(st):
+                dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(20):
+            with torch.cuda.stream(st):
+                dst.copy_(src, non_blocking=True)
+        z.record(st)
+        torch.cuda.synchronize()
+        rates[name] = 20 * src.numel() * 4 / (a.elapsed_time(z) / 1e3) / 1e9
+    return t, nb, nbo, rel, rates
 
 
 SOLVE_LOADS = (1e-3, 1.5e-3, 2e-3)
@@ -528,25 +579,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def profiled_traffic():
-    """DRAM bytes (read + write) per launch of the FP32 apply kernel from the committed
-    ncu summary, or None when the kernel source has changed since it was captured."""
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the apply kernels' sources (the key under
+    which the committed ncu summaries record their counters)."""
     import hashlib
-    import re
-    prof = os.path.join(ROOT, "profiles", "apply_q1_f32_apply_workload_ncu.md")
-    if not os.path.exists(prof):
-        return None
-    with open(prof) as f:
-        text = f.read()
     h = hashlib.sha256()
     for name in ("apply.cu", "apply_q2.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2404_03265_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
-    m_hash = re.search(r"first 16 hex\): `([0-9a-f]{16})`", text)
-    m_bytes = re.search(r"^bytes_per_launch: (\d+)", text, re.M)
-    if not m_hash or not m_bytes or m_hash.group(1) != h.hexdigest()[:16]:
+    return h.hexdigest()[:16]
+
+
+def profiled(name, key):
+    """Counter `key` ("key: value" line) of the committed ncu summary profiles/<name>,
+    or None when the kernel sources have changed since it was captured."""
+    import re
+    prof = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(prof):
         return None
-    return int(m_bytes.group(1))
+    with open(prof) as f:
+        text = f.read()
+    m_hash = re.search(r"first 16 hex\): `([0-9a-f]{16})`", text)
+    m_val = re.search(r"^%s: ([0-9.eE+-]+)" % re.escape(key), text, re.M)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_val.group(1))
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch of the FP32 apply kernel from the committed
+    ncu summary, or None when the kernel source has changed since it was captured."""
+    v = profiled("apply_q1_f32_apply_workload_ncu.md", "bytes_per_launch")
+    return None if v is None else int(v)
 
 
 def main():
@@ -590,14 +654,16 @@ def main():
     n_sets = max(2, int(np.ceil(2.2 * L2_BYTES / per_set_bytes)))
     sets = build_sets(mesh, n_sets, torch.float32, seed=0)
 
+    per_step = applies_per_step(sets, args.steps)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
-    t = time_applies(sets, args.steps, args.warmup, ws)
+    t = time_applies(sets, args.steps, args.warmup, ws, per_step=per_step)
     clocks = sampler.stop() if sampler else None
     t = max_over_ranks(ws, t)
-    value = whole_job_rate(ws, dofs * args.steps, t) / 1e9
+    value = whole_job_rate(ws, dofs * args.steps * per_step, t) / 1e9
     ms = 1e3 * t / args.steps
+    t_apply = t / (args.steps * per_step)
     del sets
 
     # FP64 apply (FP64-ALU bound on GB300), fewer steps
@@ -606,6 +672,15 @@ def main():
     t64 = time_applies(sets64, k64, 3, 1)
     g64 = dofs * k64 / t64 / 1e9
     del sets64
+    # its arithmetic roof: FP64 flops of the cell-loop kernel per launch (ncu DFMA, DADD,
+    # DMUL counts of the committed capture) against the measured FP64 FMA rate
+    f64_flops = profiled("apply_q1_f64_apply_workload_flops.md", "fp64_flops_per_launch")
+    f64 = {"value": g64, "unit": "GDoF/s", "steps": k64, "us_per_apply": 1e6 * t64 / k64,
+           "hbm_frac": info["n_nodes"] * 80 / (t64 / k64) / 1e9 / load_peaks()[0],
+           "fp64_flops_per_launch": f64_flops,
+           "alu_peak_tflops": FP64_PEAK_TFLOPS,
+           "alu_frac": None if f64_flops is None else f64_flops / (t64 / k64) / 1e12 / FP64_PEAK_TFLOPS,
+           "bound": "alu (FP64 FMA rate)"}
 
     # Q2 u and phi on the same mesh (16,368,207 DoFs): FP32 and FP64 applies
     mesh2 = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(2)
@@ -626,14 +701,14 @@ def main():
           "f64": {"value": dofs2 * k2d / t2d / 1e9, "unit": "GDoF/s", "steps": k2d,
                   "us_per_apply": 1e6 * t2d / k2d}}
 
-    te, bi, bo = time_e2e(mesh, torch.float32, max(10, args.steps // 4), 3)
+    te, bi, bo, e2e_rel, copy_rates = time_e2e(mesh, torch.float32, max(10, args.steps // 4), 3)
     e2e = whole_job_rate(ws, dofs * max(10, args.steps // 4), max_over_ranks(ws, te)) / 1e9
 
     if rank != 0:
         return
     hbm, peak_kind = load_peaks()
     alg_bytes = info["n_nodes"] * 10 * 4  # x (3), y (3), linearisation (4) per node, FP32
-    achieved = alg_bytes / (t / args.steps) / 1e9
+    achieved = alg_bytes / t_apply / 1e9
     q2["f32"]["hbm_frac"] = info2["n_nodes"] * 40 / (t2 / k2) / 1e9 / hbm
     q2["f64"]["hbm_frac"] = info2["n_nodes"] * 80 / (t2d / k2d) / 1e9 / hbm
     traffic = profiled_traffic()
@@ -643,16 +718,23 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(apply_workload_config(dofs),
                        l2="%d rotating input sets of %.0f MB (> L2 129 MB)" % (n_sets, per_set_bytes / 1e6),
+                       step="%d applies of G~x, each on the next of the rotating input sets (the timed region is "
+                            "at least 1 s whatever --steps is)" % per_step,
+                       applies_per_step=per_step,
                        parallelism="replicas" if ws > 1 else "single GPU"),
+        "us_per_apply": 1e6 * t_apply,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "note": "achieved = 40 B/node x nodes per launch / avg pff_apply duration (apply kernel + "
-                             "interface fix-up kernel)"},
-        "f64_apply": {"value": g64, "unit": "GDoF/s", "steps": k64,
-                      "hbm_frac": info["n_nodes"] * 80 / (t64 / k64) / 1e9 / hbm},
+                     "note": "achieved = 40 B/node x nodes per launch / avg pff_apply duration (hanging-node "
+                             "pre-pass, cell-loop kernel and interface fix-up kernel, as one call)"},
+        "f64_apply": f64,
         "q2_apply": q2,
-        "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "verified_rel_l2": e2e_rel, "pinned_copy_gbs": copy_rates,
+                "note": "steps double-buffered over three streams (copy in, apply, copy out); the last step's "
+                        "copied-out y equals a plain apply of the same x (verified_rel_l2); pinned_copy_gbs: the "
+                        "same copies alone, the bound of this leg"},
+        "gpu_launches": 3 * args.steps * per_step,
         "clocks": clocks,
     }
     if not args.no_solve:

@@ -525,14 +525,16 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 // SW_DEPTH - 1 rows ahead of the arithmetic; each lane copies and reads only its
 // own column, so the ring needs no barrier.
 
+// One warp per block: the block scheduler then fills each SM's free warp slots
+// one unit at a time, which evens out the mix of long and short units per SM.
 #ifndef PFF_SW_WARPS
-#define PFF_SW_WARPS 4
+#define PFF_SW_WARPS 1
 #endif
 #ifndef PFF_SW_MINB
-#define PFF_SW_MINB 3
+#define PFF_SW_MINB 12
 #endif
 #ifndef PFF_SW_MINB64
-#define PFF_SW_MINB64 2
+#define PFF_SW_MINB64 8
 #endif
 #ifndef PFF_SW_DEPTH
 #define PFF_SW_DEPTH 4

@@ -2,7 +2,7 @@
 between the oracle's canonical node order and the library's slot layout.
 
 Mapping is by integer node coordinates only; no arithmetic of the method is
-shared.  Inputs come from ``paper_2404_03265_gb300.synth``.
+shared.  Inputs come from the top-level module ``synthetic``.
 """
 import numpy as np
 

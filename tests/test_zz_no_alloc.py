@@ -1,11 +1,14 @@
-"""pff_apply_noalloc (interface scratch in a fixed device array of the library)
-against pff_apply (scratch in the problem's buffers), both through the C-ABI.
+"""pff_apply_noalloc (scratch in a fixed device array of the library) against
+pff_apply (scratch in the problem's buffers), both through the C-ABI.
 
-Both run the same kernels in the same summation order, so the results agree to
-the parity tolerances of the apply (1e-12 FP64, 1e-5 FP32, relative 2-norm);
-in practice they are bit-identical.  Each case makes two no-alloc calls in a
-row with different inputs, on two meshes with different interface-partial
-counts, because the fixed array keeps the previous call's contents.  The file
+The scratch of one apply is the input resolved on the hanging nodes (Q1) and
+the interface partial sums.  Both calls run the same kernels in the same
+summation order, so the results agree to the parity tolerances of the apply
+(1e-12 FP64, 1e-5 FP32, relative 2-norm); in practice they are bit-identical.
+Each case makes two no-alloc calls in a row with different inputs, on meshes
+with different scratch sizes and both element degrees, because the fixed array
+keeps the previous call's contents.  A further test checks that repeated calls
+change neither the device's free memory nor torch's reserved memory.  The file
 is collected last so that the first no-alloc call of the process may come
 either first (run alone) or after every other GPU test.
 """
@@ -23,14 +26,14 @@ TOL = {0: 1e-12, 1: 1e-5}   # PFF_F64, PFF_F32
 _cases = {}
 
 
-def case(name):
+def case(name, k=1):
     """Mesh, problem with a random state and 10% active phi, and two inputs."""
-    if name in _cases:
-        return _cases[name]
+    if (name, k) in _cases:
+        return _cases[(name, k)]
     import torch
     from paper_2404_03265_gb300 import Mesh, Problem
     dev = torch.device("cuda:0")
-    m = Mesh.from_recipe(synth.recipe(name)).finalize(1)
+    m = Mesh.from_recipe(synth.recipe(name)).finalize(k)
     X, Y, F = m.slots()
     valid = np.nonzero((F & 1) == 1)[0]
     ns = len(X)
@@ -52,8 +55,8 @@ def case(name):
     for seed in (5, 6):
         v = slots(synth.vector(xv, yv, seed=seed))
         xs.append((torch.tensor(v[:, :2].T.copy(), device=dev), torch.tensor(v[:, 2].copy(), device=dev)))
-    _cases[name] = (m, pb, xs, ns)
-    return _cases[name]
+    _cases[(name, k)] = (m, pb, xs, ns)
+    return _cases[(name, k)]
 
 
 def call(fn, pb, prec, op, xu, xp, ns):
@@ -75,16 +78,41 @@ def rel(a, b):
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
 @pytest.mark.parametrize("op", [0, 1, 2], ids=["jacobian", "transpose", "condensed"])
-def test_noalloc_matches_apply(prec, op):
-    for name in ("solve", "small"):   # 39,296 and a few hundred interface partials
-        m, pb, xs, ns = case(name)
-        assert 0 < m.info["n_partials"] <= 65536
-        got = [call("pff_apply_noalloc", pb, prec, op, xu, xp, ns) for xu, xp in xs]   # two in a row
-        want = [call("pff_apply", pb, prec, op, xu, xp, ns) for xu, xp in xs]
-        for g, w in zip(got, want):
-            assert np.all(np.isfinite(g))
-            assert rel(g, w) <= TOL[prec], (name, rel(g, w))
-        assert rel(got[0], got[1]) > 0.1    # the two inputs give different results
+@pytest.mark.parametrize("name,k", [("solve", 1), ("small", 1), ("small", 2), ("adjoint", 2)])
+def test_noalloc_matches_apply(prec, op, name, k):
+    m, pb, xs, ns = case(name, k)
+    scratch = m.info["n_partials"] + (m.info["n_hanging"] if k == 1 else 0)
+    assert 0 < m.info["n_partials"] and scratch <= 65536
+    got = [call("pff_apply_noalloc", pb, prec, op, xu, xp, ns) for xu, xp in xs]   # two in a row
+    want = [call("pff_apply", pb, prec, op, xu, xp, ns) for xu, xp in xs]
+    for g, w in zip(got, want):
+        assert np.all(np.isfinite(g))
+        assert rel(g, w) <= TOL[prec], (name, k, rel(g, w))
+    assert rel(got[0], got[1]) > 0.1    # the two inputs give different results
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call, further calls leave the device's free memory (driver
+    view) and torch's reserved memory unchanged."""
+    import torch
+    m, pb, xs, ns = case("solve", 1)
+    dt = torch.float32
+    xu, xp = xs[0][0].to(dt), xs[0][1].to(dt)
+    yu = torch.empty((2, ns), dtype=dt, device=xu.device)
+    yp = torch.empty((ns,), dtype=dt, device=xu.device)
+    from paper_2404_03265_gb300 import _lib
+
+    def go():
+        _lib.check(_lib.lib().pff_apply_noalloc(pb._h, 1, 0, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(yu), _lib.ptr(yp),
+                                                _lib.stream_ptr(None)))
+    go()
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(5):
+        go()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
 
 
 def test_noalloc_rejects_oversized_mesh():

@@ -45,7 +45,8 @@ def build(verbose=False, extra=()):
         for _, log in res:
             if log.strip():
                 print(log)
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs
+    # --no-undefined: a symbol missing from the objects fails the link, not the first dlopen
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "--no-undefined", "-o", LIB] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (r.stdout, r.stderr))

@@ -23,6 +23,7 @@
 // partial sums; a small fix-up kernel condenses them (x_full = C x on input,
 // C^T y on output).  No atomics.
 #include "kernels.cuh"
+#include "pdl.cuh"
 
 #include <cmath>
 #include <mutex>
@@ -561,13 +562,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
-// ---- programmatic dependent launch (PTX griddepcontrol)
-// wait: until the grid this launch depends on has completed and its writes are
-// visible (no-op for a launch without the dependency); trigger: let the next
-// launch, if it is programmatically dependent, start scheduling.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
-
 // One node row of both halves in flight.  Every entry is a pair over the two
 // halves (lower half in .x, upper half in .y), so that a lane reads the pair of
 // its own node, and the pair of its right neighbour, with one shared load each.
@@ -720,6 +714,7 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned FULL = 0xffffffffu;
   pdl_trigger();
+  if (a.pdl_in) pdl_wait();
   const int lane = threadIdx.x & 31;
   SweepStage<T>* ring = reinterpret_cast<SweepStage<T>*>(smem_raw) + (threadIdx.x >> 5) * SW_DEPTH;
   const int unit = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
@@ -1104,25 +1099,6 @@ int sm_count() {
 // small level meshes); the other operators with SH = 15.  a.sweep_sh forces one
 // of 15, 5, 1 where it exists; 0 picks the largest whose strips give every SM a
 // few warps.
-// Launch of kernel `fn` on stream s, programmatically dependent on the launch
-// before it in the stream when pdl is set (it may start once that grid has
-// triggered; it waits with griddepcontrol.wait where it reads that grid's output).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(bool pdl, void (*fn)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
-                      Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
-}
-
 // Work units of the Q1 cell loop (one warp each).  A strip of half-height SH
 // evaluates 2 (SH + 1) cell rows for its 2 SH owned rows and pays one pipeline
 // start; short strips give small meshes enough warps and even out the slower
@@ -1172,7 +1148,7 @@ cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
   // hanging nodes' input: C x into a.hang_x first; the sweep may start before that
   // grid ends and waits for it only where it copies those values
-  bool pdl = false;
+  bool pdl = a.pdl_in != 0;
   if ((N::xu || N::xp) && a.nhang > 0 && a.hang != nullptr) {
     if (a.hang_x == nullptr) return cudaErrorInvalidValue;
     hang_x_kernel<T><<<(a.nhang + 127) / 128, 128, 0, s>>>(

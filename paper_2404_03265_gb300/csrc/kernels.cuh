@@ -115,6 +115,7 @@ struct ApplyArgs {
   int mode;
   int fe_degree;
   int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (schedules of DevLayout::units)
+  int pdl_in;             // Q1: launched dependent on the preceding kernel, which wrote x (pdl.cuh)
 };
 
 struct FixupArgs {

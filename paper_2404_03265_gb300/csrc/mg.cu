@@ -4,6 +4,7 @@
 // holes carry zeros; the inverse diagonal is zero off the interior, so the
 // Chebyshev updates leave edge and fixed entries untouched.
 #include "mg.cuh"
+#include "pdl.cuh"
 
 namespace pff {
 
@@ -21,6 +22,8 @@ inline unsigned blocks_for(int64_t n) {
 
 template <typename T>
 __global__ void k_cheb_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(i, n) {
     x[i] = c0 * dinv[i] * d[i];
     xprev[i] = T(0);
@@ -30,6 +33,8 @@ __global__ void k_cheb_first(int64_t n, T* x, T* xprev, const T* dinv, const T* 
 template <typename T>
 __global__ void k_cheb_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d, const T* ax,
                             T a, T b) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(i, n) {
     const T xi = x[i];
     xnew[i] = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
@@ -40,6 +45,8 @@ template <typename T>
 __global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* __restrict__ ptr,
                            const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ df,
                            const T* __restrict__ axf, T* dc, const uint8_t* __restrict__ cmask_c, int fixbits) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(y, nc) {
     const uint8_t cm = cmask_c[y];
     for (int c = 0; c < ncomp; ++c) {
@@ -58,6 +65,8 @@ template <typename T>
 __global__ void k_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const int32_t* __restrict__ ptr,
                           const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ xc,
                           T* xf, const uint8_t* __restrict__ cmask_f, int fixbits) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(z, nf) {
     const uint8_t cm = cmask_f[z];
     for (int c = 0; c < ncomp; ++c) {
@@ -88,6 +97,8 @@ template <typename T>
 __global__ void k_copy_out(int64_t nsl, int ncomp, DevHome home, const T* __restrict__ x,
                            const double* __restrict__ r, double* z, const uint8_t* __restrict__ lcm,
                            const uint8_t* __restrict__ lflags, int fixbits) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(s, nsl) {
     const uint8_t cm = lcm[s];
     const bool node = (lflags[s] & 1) && !(lflags[s] & 4);
@@ -106,6 +117,8 @@ __global__ void k_copy_out(int64_t nsl, int ncomp, DevHome home, const T* __rest
 template <typename T>
 __global__ void k_cheb_first_res(int64_t n, T* x, T* xprev, T* r, const T* __restrict__ dinv,
                                  const T* __restrict__ d, const T* __restrict__ ax, T c0, T* xadd) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(i, n) {
     const T ri = d[i] - ax[i];
     const T v = c0 * dinv[i] * ri;
@@ -123,6 +136,8 @@ template <typename T>
 __global__ void k_cheb_step_add(int64_t n, T* xadd, const T* __restrict__ x, const T* __restrict__ xprev,
                                 const T* __restrict__ dinv, const T* __restrict__ d, const T* __restrict__ ax, T a,
                                 T b) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(i, n) {
     const T xi = x[i];
     const T v = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
@@ -133,6 +148,8 @@ __global__ void k_cheb_step_add(int64_t n, T* xadd, const T* __restrict__ x, con
 // Dense FP64 coarse solve: tmp = d[idx] (to FP64), x[idx] = Ainv tmp; one block per row group.
 template <typename T>
 __global__ void k_coarse_gather(int32_t n, const int32_t* idx, const T* d, double* tmp) {
+  pdl_trigger();
+  pdl_wait();
   GRID_STRIDE(i, n) tmp[i] = double(d[idx[i]]);
 }
 
@@ -168,6 +185,8 @@ __global__ void k_gj_sweep(int32_t n, int32_t k, double* A, const double* __rest
 template <typename T>
 __global__ void k_coarse_matvec(int32_t n, const int32_t* idx, const double* __restrict__ A,
                                 const double* __restrict__ tmp, T* x) {
+  pdl_trigger();
+  pdl_wait();
   // one warp per row, lanes stride the columns, fixed-order warp reduction
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -347,29 +366,32 @@ __global__ void k_copy64(int64_t n, double* d, const double* s) { GRID_STRIDE(i,
 }  // namespace
 
 template <typename T>
-cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0, cudaStream_t s) {
-  if (n > 0) k_cheb_first<T><<<blocks_for(n), TPB, 0, s>>>(n, x, xprev, dinv, d, c0);
+cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0, cudaStream_t s, bool pdl) {
+  if (n > 0) return launch_ex(pdl, &k_cheb_first<T>, blocks_for(n), TPB, 0, s, n, x, xprev, dinv, d, c0);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d,
-                              const T* ax, T a, T b, cudaStream_t s) {
-  if (n > 0) k_cheb_step<T><<<blocks_for(n), TPB, 0, s>>>(n, xnew, x, xprev, dinv, d, ax, a, b);
+                              const T* ax, T a, T b, cudaStream_t s, bool pdl) {
+  if (n > 0) return launch_ex(pdl, &k_cheb_step<T>, blocks_for(n), TPB, 0, s, n, xnew, x, xprev, dinv, d, ax, a, b);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* ptr, const int32_t* col,
                         const float* val, const T* d_f, const T* ax_f, T* d_c, const uint8_t* cmask_c, int fixbits,
-                        cudaStream_t s) {
-  if (nc > 0) k_restrict<T><<<blocks_for(nc), TPB, 0, s>>>(nc, ncomp, ncs, nfs, ptr, col, val, d_f, ax_f, d_c,
-                                                           cmask_c, fixbits);
+                        cudaStream_t s, bool pdl) {
+  if (nc > 0)
+    return launch_ex(pdl, &k_restrict<T>, blocks_for(nc), TPB, 0, s, nc, ncomp, ncs, nfs, ptr, col, val, d_f, ax_f,
+                     d_c, cmask_c, fixbits);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const int32_t* ptr, const int32_t* col,
-                       const float* val, const T* x_c, T* x_f, const uint8_t* cmask_f, int fixbits, cudaStream_t s) {
-  if (nf > 0) k_prolong<T><<<blocks_for(nf), TPB, 0, s>>>(nf, ncomp, nfs, ncs, ptr, col, val, x_c, x_f, cmask_f,
-                                                          fixbits);
+                       const float* val, const T* x_c, T* x_f, const uint8_t* cmask_f, int fixbits, cudaStream_t s,
+                       bool pdl) {
+  if (nf > 0)
+    return launch_ex(pdl, &k_prolong<T>, blocks_for(nf), TPB, 0, s, nf, ncomp, nfs, ncs, ptr, col, val, x_c, x_f,
+                     cmask_f, fixbits);
   return cudaGetLastError();
 }
 template <typename T>
@@ -380,21 +402,24 @@ cudaError_t mg_copy_in(int64_t ns_leaf, int ncomp, DevHome home, const double* r
 }
 template <typename T>
 cudaError_t mg_copy_out(int64_t ns_leaf, int ncomp, DevHome home, const T* x, const double* r, double* z,
-                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s) {
+                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s, bool pdl) {
   if (ns_leaf > 0)
-    k_copy_out<T><<<blocks_for(ns_leaf), TPB, 0, s>>>(ns_leaf, ncomp, home, x, r, z, leaf_cmask, leaf_flags, fixbits);
+    return launch_ex(pdl, &k_copy_out<T>, blocks_for(ns_leaf), TPB, 0, s, ns_leaf, ncomp, home, x, r, z, leaf_cmask,
+                     leaf_flags, fixbits);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t mg_chebyshev_first_res(int64_t n, T* x, T* xprev, T* r, const T* dinv, const T* d, const T* ax, T c0,
-                                   T* xadd, cudaStream_t s) {
-  if (n > 0) k_cheb_first_res<T><<<blocks_for(n), TPB, 0, s>>>(n, x, xprev, r, dinv, d, ax, c0, xadd);
+                                   T* xadd, cudaStream_t s, bool pdl) {
+  if (n > 0)
+    return launch_ex(pdl, &k_cheb_first_res<T>, blocks_for(n), TPB, 0, s, n, x, xprev, r, dinv, d, ax, c0, xadd);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
-                                  const T* ax, T a, T b, cudaStream_t s) {
-  if (n > 0) k_cheb_step_add<T><<<blocks_for(n), TPB, 0, s>>>(n, xadd, x, xprev, dinv, d, ax, a, b);
+                                  const T* ax, T a, T b, cudaStream_t s, bool pdl) {
+  if (n > 0)
+    return launch_ex(pdl, &k_cheb_step_add<T>, blocks_for(n), TPB, 0, s, n, xadd, x, xprev, dinv, d, ax, a, b);
   return cudaGetLastError();
 }
 cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s) {
@@ -410,12 +435,13 @@ cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaSt
 
 template <typename T>
 cudaError_t mg_coarse(int32_t n, const int32_t* idx, const double* Ainv, const T* d, T* x, double* tmp,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool pdl) {
   if (n <= 0) return cudaSuccess;
-  k_coarse_gather<T><<<blocks_for(n), TPB, 0, s>>>(n, idx, d, tmp);
+  cudaError_t e = launch_ex(pdl, &k_coarse_gather<T>, blocks_for(n), TPB, 0, s, n, idx, d, tmp);
+  if (e != cudaSuccess) return e;
   const int warps_per_block = TPB / 32;
-  k_coarse_matvec<T><<<(n + warps_per_block - 1) / warps_per_block, TPB, 0, s>>>(n, idx, Ainv, tmp, x);
-  return cudaGetLastError();
+  return launch_ex(pdl, &k_coarse_matvec<T>, unsigned((n + warps_per_block - 1) / warps_per_block), TPB, 0, s, n, idx,
+                   Ainv, static_cast<const double*>(tmp), x);
 }
 
 cudaError_t mg_inject_lin(int32_t ns_l, const int32_t* slot_leaf, const double* lin64, int64_t ns_leaf,
@@ -478,21 +504,22 @@ cudaError_t copy64(int64_t n, double* dst, const double* src, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                                \
-  template cudaError_t mg_chebyshev_first<T>(int64_t, T*, T*, const T*, const T*, T, cudaStream_t);           \
+  template cudaError_t mg_chebyshev_first<T>(int64_t, T*, T*, const T*, const T*, T, cudaStream_t, bool);     \
   template cudaError_t mg_chebyshev_step<T>(int64_t, T*, const T*, const T*, const T*, const T*, const T*, T,  \
-                                            T, cudaStream_t);                                                  \
+                                            T, cudaStream_t, bool);                                            \
   template cudaError_t mg_restrict<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,          \
-                                      const float*, const T*, const T*, T*, const uint8_t*, int, cudaStream_t); \
+                                      const float*, const T*, const T*, T*, const uint8_t*, int, cudaStream_t, \
+                                      bool);                                                                   \
   template cudaError_t mg_prolong<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,           \
-                                     const float*, const T*, T*, const uint8_t*, int, cudaStream_t);           \
+                                     const float*, const T*, T*, const uint8_t*, int, cudaStream_t, bool);     \
   template cudaError_t mg_copy_in<T>(int64_t, int, DevHome, const double*, T*, const uint8_t*, int, cudaStream_t); \
   template cudaError_t mg_copy_out<T>(int64_t, int, DevHome, const T*, const double*, double*, const uint8_t*,     \
-                                      const uint8_t*, int, cudaStream_t);                                          \
+                                      const uint8_t*, int, cudaStream_t, bool);                                    \
   template cudaError_t mg_chebyshev_first_res<T>(int64_t, T*, T*, T*, const T*, const T*, const T*, T, T*,        \
-                                                 cudaStream_t);                                                    \
+                                                 cudaStream_t, bool);                                              \
   template cudaError_t mg_chebyshev_step_add<T>(int64_t, T*, const T*, const T*, const T*, const T*, const T*, T, \
-                                                T, cudaStream_t);                                                  \
-  template cudaError_t mg_coarse<T>(int32_t, const int32_t*, const double*, const T*, T*, double*, cudaStream_t);
+                                                T, cudaStream_t, bool);                                            \
+  template cudaError_t mg_coarse<T>(int32_t, const int32_t*, const double*, const T*, T*, double*, cudaStream_t, bool);
 INST(float)
 INST(double)
 #undef INST

@@ -33,21 +33,24 @@ struct DevHome {
 };
 
 // ---- elementwise / sparse kernels (T = float or double for the level vectors)
+// pdl: launch as a programmatic dependent launch (pdl.cuh): the kernel waits for
+// the preceding kernel of the stream at its start.
 template <typename T>
-cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0, cudaStream_t s);
+cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0, cudaStream_t s,
+                               bool pdl = false);
 template <typename T>
 cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d,
-                              const T* ax, T a, T b, cudaStream_t s);
+                              const T* ax, T a, T b, cudaStream_t s, bool pdl = false);
 // d_c[y] += sum_z R[y,z] (d_f[z] - ax_f[z]) over coarse slots; zero on coarse fixed rows
 template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t nc_stride, int64_t nf_stride, const int32_t* ptr,
                         const int32_t* col, const float* val, const T* d_f, const T* ax_f, T* d_c,
-                        const uint8_t* cmask_c, int fixbits, cudaStream_t s);
+                        const uint8_t* cmask_c, int fixbits, cudaStream_t s, bool pdl = false);
 // x_f[z] += sum_y P[z,y] x_c[y]; zero on fine fixed rows
 template <typename T>
 cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nf_stride, int64_t nc_stride, const int32_t* ptr,
                        const int32_t* col, const float* val, const T* x_c, T* x_f, const uint8_t* cmask_f,
-                       int fixbits, cudaStream_t s);
+                       int fixbits, cudaStream_t s, bool pdl = false);
 // Level vectors of a block: level l at ncomp * off_l, component c at + c * n_slots_l.
 // copy_in: d on each free leaf node's home level <- leaf r (double, ncomp blocks of
 // stride ns_leaf).  copy_out: z = r on fixed leaf node DoFs, the home-level value
@@ -57,16 +60,17 @@ cudaError_t mg_copy_in(int64_t ns_leaf, int ncomp, DevHome home, const double* r
                        int fixbits, cudaStream_t s);
 template <typename T>
 cudaError_t mg_copy_out(int64_t ns_leaf, int ncomp, DevHome home, const T* x, const double* r, double* z,
-                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s);
+                        const uint8_t* leaf_cmask, const uint8_t* leaf_flags, int fixbits, cudaStream_t s,
+                        bool pdl = false);
 // Post-smoothing pieces.  first_res: r = d - ax, x = c0 D^-1 r, xprev = 0; with
 // xadd != NULL (degree 1) instead xadd += c0 D^-1 (d - ax), nothing stored.
 // step_add: xadd += the Chebyshev step of mg_chebyshev_step (not stored).
 template <typename T>
 cudaError_t mg_chebyshev_first_res(int64_t n, T* x, T* xprev, T* r, const T* dinv, const T* d, const T* ax, T c0,
-                                   T* xadd, cudaStream_t s);
+                                   T* xadd, cudaStream_t s, bool pdl = false);
 template <typename T>
 cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
-                                  const T* ax, T a, T b, cudaStream_t s);
+                                  const T* ax, T a, T b, cudaStream_t s, bool pdl = false);
 // In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by Gauss-Jordan
 // sweeps without pivoting: the pivots are the diagonals of successive Schur
 // complements, positive for an SPD matrix.  rc: scratch of 4 n doubles.  *bad is
@@ -77,7 +81,7 @@ cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaSt
 // coarse solve x[idx] = Ainv (d[idx]) (dense FP64 inverse over the interior entries)
 template <typename T>
 cudaError_t mg_coarse(int32_t n, const int32_t* idx, const double* Ainv, const T* d, T* x, double* tmp,
-                      cudaStream_t s);
+                      cudaStream_t s, bool pdl = false);
 
 // ---- set-up kernels
 // level lin (4 blocks of ns_l, double and float) from leaf lin64 (4 blocks of ns_leaf)

@@ -101,8 +101,9 @@ int chebyshev_degree(double a, double b, double tol = 1e-3, int cap = 64) {
 
 }  // namespace
 
+// pdl: launched dependent on the preceding kernel of the stream (the V-cycle chain)
 template <typename T>
-cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s) {
+cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl) {
   pff_problem& pb = *mg.pb;
   const Mesh& M = pb.mesh->m;
   const DevMesh::Level& L = pb.mesh->dev.levels[level];
@@ -124,6 +125,7 @@ cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStr
   fill_cell_constants(a, M.Lf + 1);
   a.fe_degree = M.k;
   a.sweep_sh = pb.sweep_sh;
+  a.pdl_in = pdl ? 1 : 0;
   a.mode = MODE_MASK_INPUT;
   return launch_apply<T>(a, op, s);
 }
@@ -432,15 +434,16 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
       case 1: cur = w1; prev = w2; nxt = w0; break;
       default: cur = w1; prev = w0; nxt = w2; break;
     }
-    cudaError_t ee = mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s);
+    cudaError_t ee = mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s, true);
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
     for (int j = 1; j < degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
-      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s);
+      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
       if (ee != cudaSuccess) return ee;
       // next = cur + rho_n rho (cur - prev) + 2 rho_n / delta D^-1 (rhs - A cur)
-      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
+      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s,
+                                true);
       if (ee != cudaSuccess) return ee;
       T* old_prev = prev;
       prev = cur;
@@ -461,13 +464,13 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     const DevLevel& lc = D.levels[l - 1].lv;
     const int64_t o = nc * lv.off;
     VC(cheb(l, d + o, x + o));
-    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s));
+    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true));
     VC(mg_restrict<T>(lc.n_slots, nc, lc.n_slots, lv.n_slots, lv.R_ptr, lv.R_col, lv.R_val, d + o, t + o,
-                      d + nc * lc.off, mg.cmask + lc.off, B.fixbits, s));
+                      d + nc * lc.off, mg.cmask + lc.off, B.fixbits, s, true));
   }
   // coarse
   if (mg.coarse_mode == 1) VC(cheb_ab(0, d, x, B.c0_a, B.c0_b, B.c0_deg));
-  else VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s));
+  else VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s, true));
   // Post-smoothing on level l of the defect d - A x (t holds A x), from zero,
   // added to x: the first step forms the defect, the last adds instead of storing.
   // The level defect d is free once the first step has read it.
@@ -480,22 +483,24 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     const double a = mg.lo * lam, bb = mg.hi * lam;
     const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
     if (degree == 1)
-      return mg_chebyshev_first_res<T>(n, nullptr, nullptr, nullptr, dinv + o, d + o, t + o, T(1.0 / theta), x + o, s);
+      return mg_chebyshev_first_res<T>(n, nullptr, nullptr, nullptr, dinv + o, d + o, t + o, T(1.0 / theta), x + o, s,
+                                       true);
     T* cur = yp + o;
     T* prev = y + o;
     T* nxt = d + o;
     cudaError_t ee = mg_chebyshev_first_res<T>(n, cur, prev, rr + o, dinv + o, d + o, t + o, T(1.0 / theta),
-                                               nullptr, s);
+                                               nullptr, s, true);
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
     for (int j = 1; j < degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
-      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s);
+      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
       if (ee != cudaSuccess) return ee;
       if (j == degree - 1)
         return mg_chebyshev_step_add<T>(n, x + o, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho),
-                                        T(2.0 * rho_n / delta), s);
-      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s);
+                                        T(2.0 * rho_n / delta), s, true);
+      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s,
+                                true);
       if (ee != cudaSuccess) return ee;
       T* old_prev = prev;
       prev = cur;
@@ -511,11 +516,11 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     const DevLevel& lc = D.levels[l - 1].lv;
     const int64_t o = nc * lv.off;
     VC(mg_prolong<T>(lv.n_slots, nc, lv.n_slots, lc.n_slots, lv.P_ptr, lv.P_col, lv.P_val, x + nc * lc.off, x + o,
-                     mg.cmask + lv.off, B.fixbits, s));
-    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s));
+                     mg.cmask + lv.off, B.fixbits, s, true));
+    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true));
     VC(cheb_post(l));
   }
-  VC(mg_copy_out<T>(nsleaf, nc, D.home, x, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s));
+  VC(mg_copy_out<T>(nsleaf, nc, D.home, x, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s, true));
 #undef VC
   return cudaSuccess;
 }
@@ -609,7 +614,7 @@ cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s) {
   return e;
 }
 
-template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t);
-template cudaError_t level_apply<double>(pff_mg&, int, int, const double*, double*, cudaStream_t);
+template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t, bool);
+template cudaError_t level_apply<double>(pff_mg&, int, int, const double*, double*, cudaStream_t, bool);
 
 }  // namespace pff

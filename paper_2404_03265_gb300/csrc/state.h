@@ -285,6 +285,6 @@ cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStr
 cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s);
 // level operator y = A_l x of one block (op OP_UU / OP_PP / *_DIAG), precision of T
 template <typename T>
-cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s);
+cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl = false);
 
 }  // namespace pff

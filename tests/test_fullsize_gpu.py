@@ -102,6 +102,22 @@ def test_apply_fullsize_sampled():
     # identity rows on Dirichlet u
     d = np.nonzero(om.dirichlet)[0]
     assert np.array_equal(out["f64"][d, :2], x[d, :2])
+    # every strip schedule of the cell loop gives the same bits (the schedule by
+    # mesh size, taken above, runs regular bricks as one strip and irregular ones
+    # as three)
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        xu, xp = dv(xs[:, :2].T, dt), dv(xs[:, 2], dt)
+        ref_bits = None
+        for sched in (0, 15, 5, 1):
+            pb.set_cell_loop(sched)
+            yu, yp = torch.full_like(xu, float("nan")), torch.full_like(xp, float("nan"))
+            pb.apply(xu, xp, yu, yp, op=PFF_OP_JACOBIAN)
+            torch.cuda.synchronize()
+            bits = torch.cat([yu.reshape(-1), yp]).cpu().numpy()
+            if ref_bits is None:
+                ref_bits = bits
+            assert np.array_equal(bits, ref_bits), (name, sched)
+    pb.set_cell_loop(0)
 
 
 def solve_setup():
@@ -192,3 +208,44 @@ def test_vcycle_fullsize_symmetry(frac):
         l = float((c * za).sum())
         r = float((a * zc).sum())
         assert abs(l - r) <= 1e-10 * max(abs(l), abs(r)), (b, l, r)
+
+
+def test_vcycle_fullsize_schedules_bitwise():
+    """On the 1,043,811-DoF crack mesh (13 levels, from a few bricks to over a
+    thousand per level) the FP32 V-cycle of both blocks is bitwise the same under
+    every strip schedule of the level block operators, with a 5% active set."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Problem
+    mesh, valid, po, mat = solve_setup()
+    ns = mesh.info["n_slots"]
+    X, Y, F = mesh.slots()
+    Xv, Yv = X[valid], Y[valid]
+    info = mesh.info
+    u, phi, phit = synth.linearisation(Xv, Yv, info["x_max"], info["y_max"], seed=4, u_std=1e-3)
+
+    def slots(a):
+        o = np.zeros((ns,) + a.shape[1:])
+        o[valid] = a
+        return o
+
+    dv = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    rng = np.random.Generator(np.random.PCG64(9))
+    act = slots((rng.uniform(size=len(Xv)) < 0.05).astype(np.float64)).astype(np.uint8)
+    r = {0: dv(rng.normal(size=(2, ns))), 1: dv(rng.normal(size=ns))}
+    ref = {}
+    for sched in (0, 15, 5, 1):
+        pb = Problem(mesh, **mat)
+        pb.set_cell_loop(sched)
+        pb.set_state(dv(slots(u).T), dv(slots(phi)), dv(slots(phit)))
+        pb.set_active(dv(act))
+        mg = MG(pb, PFF_F32)
+        mg.setup()
+        for b in (0, 1):
+            z = torch.full_like(r[b], float("nan"))
+            mg.vcycle(b, r[b], z)
+            torch.cuda.synchronize()
+            zb = z.cpu().numpy()
+            assert np.all(np.isfinite(zb))
+            if b not in ref:
+                ref[b] = zb
+            assert np.array_equal(zb, ref[b]), (sched, b)

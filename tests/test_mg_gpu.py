@@ -132,3 +132,52 @@ def test_vcycle_chebyshev_coarse(name, frac, prec, tol):
         z = P.from_slots(zs.T if nc == 2 else zs[:, None])
         inf, two = rel_err(z, zref)
         assert inf < tol and two < tol, (blk, prec, inf, two)
+
+
+def lib_mg_schedule(P, mat, u, phi, phit, active, prec, sched):
+    """lib_mg with the Q1 cell loop forced to one strip schedule (before the set-up,
+    which captures the V-cycle)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, Problem
+    dev = torch.device("cuda:0")
+    pb = Problem(P.lm, **mat)
+    pb.set_cell_loop(sched)
+    pb.set_state(torch.tensor(P.to_slots(u).T.copy(), device=dev), torch.tensor(P.to_slots(phi), device=dev),
+                 torch.tensor(P.to_slots(phit), device=dev))
+    pb.set_active(torch.tensor(P.to_slots(active.astype(np.uint8)), device=dev))
+    mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
+    mg.setup()
+    return pb, mg
+
+
+@pytest.mark.parametrize("name,frac", [("small", 0.05), ("band4_2_4", 0.0)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_vcycle_parity_every_strip_schedule(name, frac, prec, tol):
+    """The level block operators (Sec. 3.2) under each strip schedule of the cell
+    loop (one, three or fifteen strips per brick): V-cycle output against the
+    oracle, and bitwise equal across the schedules (same arithmetic per cell and
+    the same summation order of every nodal sum)."""
+    import torch
+    P, mat, u, phi, phit, active, M = setup_pair(name, frac)
+    om = P.om
+    nn = om.nn
+    outs = {}
+    for sched in (15, 5, 1):
+        pb, mg = lib_mg_schedule(P, mat, u, phi, phit, active, prec, sched)
+        rng = np.random.default_rng(3)
+        for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
+            r = rng.normal(size=(nn, nc))
+            rs = P.to_slots(r)
+            rt = torch.tensor(rs.T.copy() if nc == 2 else rs[:, 0].copy(), device="cuda")
+            zt = torch.full_like(rt, float("nan"))
+            mg.vcycle(b, rt, zt)
+            torch.cuda.synchronize()
+            zs = zt.cpu().numpy()
+            outs.setdefault(b, []).append(zs)
+            zref = M.vcycle(blk, np.concatenate([r[:, c] for c in range(nc)]))
+            zref = np.stack([zref[c * nn:(c + 1) * nn] for c in range(nc)], 1)
+            z = P.from_slots(zs.T if nc == 2 else zs[:, None])
+            inf, two = rel_err(z, zref)
+            assert inf < tol and two < tol, (sched, blk, prec, inf, two)
+    for b, zs in outs.items():
+        assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2]), b

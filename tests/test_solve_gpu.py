@@ -101,11 +101,16 @@ def test_gmres_solves_constrained_system(prec):
     assert err < (1e-6 if prec == "f32" else 1e-7), err
 
 
-@pytest.mark.parametrize("name", ["small", "band4_3_3"])
-@pytest.mark.parametrize("prec", ["f32", "f64", "f32mv"])
-def test_newton_pdas_load_step(name, prec):
+_load_step_ref = {}
+
+
+@pytest.mark.parametrize("name,prec,sched", [(n, p, 0) for n in ("small", "band4_3_3") for p in ("f32", "f64", "f32mv")]
+                         + [("band4_3_3", "f32mv", s) for s in (15, 5, 1)])
+def test_newton_pdas_load_step(name, prec, sched):
     """Sneddon load step on the GPU against the oracle load step (Algorithm 2).
-    f32mv: FP32 V-cycle and FP32 Jacobian applies inside GMRES."""
+    f32mv: FP32 V-cycle and FP32 Jacobian applies inside GMRES.  sched: strip
+    schedule of the Q1 cell loop (0: by mesh size; 15, 5, 1 forced), which every
+    leaf and level operator of the step then runs."""
     import torch
     from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64, newton_step
     P = Pair(name, 1)
@@ -113,9 +118,12 @@ def test_newton_pdas_load_step(name, prec):
     h = om.h_min_diag()
     mat = P.material()
     u0, phi_old = solvers.sneddon_initial(om, h)
-    uo, po, ao, io = solvers.load_step(om, ops.Material(**mat), 1e4, u0, phi_old.copy(), phi_old)
+    if name not in _load_step_ref:
+        _load_step_ref[name] = solvers.load_step(om, ops.Material(**mat), 1e4, u0, phi_old.copy(), phi_old)
+    uo, po, ao, io = _load_step_ref[name]
     assert io.converged
     pb = problem(P, mat)
+    pb.set_cell_loop(sched)
     mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
     mv = PFF_F32 if prec == "f32mv" else PFF_F64
     us = dev(P.to_slots(u0).T)

@@ -141,6 +141,16 @@ pff_status pff_set_active(pff_problem* pb, const uint8_t* active, void* stream);
 pff_status pff_apply(pff_problem* pb, int32_t precision, int32_t op, const void* xu, const void* xp,
                      void* yu, void* yp, void* stream);
 
+/* phi_tilde of load step n by extrapolation (Sec. 2: the degradation of the
+ * u-equation uses phi_tilde, "the old incremental step solution or an
+ * extrapolation"): phi_tilde = clip(2 phi_prev - phi_prev2, 0, 1) per slot, the
+ * linear extrapolation in the step index from the two previous steps' converged
+ * phase fields, clipped to the phase field's range.  n_slots doubles each
+ * (device); phi_tilde may alias neither input.  Pass the result as
+ * pff_newton_opts.phi_tilde.  Errors: PFF_ERR_INVALID_ARG on NULL pointers.     */
+pff_status pff_extrapolate_phi(pff_problem* pb, const double* phi_prev, const double* phi_prev2,
+                               double* phi_tilde, void* stream);
+
 /* Shape of the Q1 cell loop (Sec. 3.3's matrix-free cell-by-cell evaluation;
  * the shape changes the schedule, not the arithmetic: every cell and every nodal
  * sum is evaluated in the same order, so results are bitwise the same).  A warp

@@ -189,6 +189,15 @@ def load_step(mesh, mat, c, u, phi, phi_old, active_prev=None, E_cells=None, tol
     return u, phi, A_prev, info
 
 
+def extrapolate_phi(phi_prev, phi_prev2):
+    """phi_tilde of load step n by extrapolation from the two previous steps (Sec. 2:
+    the u-equation's degradation uses phi_tilde, "the old incremental step solution
+    or an extrapolation").  Reading: linear extrapolation in the step index, which
+    is exact for equidistant load steps on which phi changes linearly, clipped to
+    the phase field's range [0, 1]: clip(2 phi^(n-1) - phi^(n-2), 0, 1) per node."""
+    return np.clip(2.0 * np.asarray(phi_prev, dtype=np.float64) - np.asarray(phi_prev2, dtype=np.float64), 0.0, 1.0)
+
+
 def sneddon_initial(mesh, h_min):
     """Initial crack phi_old (|x| <= 1, |y| <= h_min) and u = 0 (Sec. 4)."""
     import synthetic as synth

@@ -110,6 +110,11 @@ class Problem:
                                              _lib.stream_ptr(stream)))
         return nc.value, na.value, mg_.value
 
+    def extrapolate_phi(self, phi_prev, phi_prev2, phi_tilde, stream=None):
+        """phi_tilde = clip(2 phi_prev - phi_prev2, 0, 1) on the device (float64 (n_slots,) tensors)."""
+        _lib.check(_lib.lib().pff_extrapolate_phi(self._h, _lib.ptr(phi_prev), _lib.ptr(phi_prev2),
+                                                  _lib.ptr(phi_tilde), _lib.stream_ptr(stream)))
+
     def set_cell_loop(self, strip_half_rows):
         """Q1 cell-loop strip half-height: 15, 5, 1, or 0 (by mesh size)."""
         _lib.check(_lib.lib().pff_set_cell_loop(self._h, strip_half_rows))

@@ -96,6 +96,7 @@ _SIGS = [
     ("pff_mg_destroy", None, [_P]),
     ("pff_set_pressure", ctypes.c_int32, [_P, ctypes.c_double]),
     ("pff_set_cell_loop", ctypes.c_int32, [_P, ctypes.c_int32]),
+    ("pff_extrapolate_phi", ctypes.c_int32, [_P, _P, _P, _P, _P]),
     ("pff_residual", ctypes.c_int32, [_P, _P, _P, _P, _P, _P]),
     ("pff_lumped_mass", ctypes.c_int32, [_P, _P, _P]),
     ("pff_tcv", ctypes.c_int32, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),

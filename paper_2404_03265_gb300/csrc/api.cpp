@@ -350,6 +350,15 @@ extern "C" void pff_mg_destroy(pff_mg* mg) {
   delete mg;
 }
 
+extern "C" pff_status pff_extrapolate_phi(pff_problem* pb, const double* phi_prev, const double* phi_prev2,
+                                          double* phi_tilde, void* stream) {
+  PFF_TRY({
+    if (!pb || !phi_prev || !phi_prev2 || !phi_tilde) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    PFF_CUDA(extrapolate_phi(pb->mesh->m.lay.n_slots, phi_prev, phi_prev2, phi_tilde, cudaStream_t(stream)));
+    return PFF_OK;
+  })
+}
+
 extern "C" pff_status pff_set_cell_loop(pff_problem* pb, int32_t strip_half_rows) {
   PFF_TRY({
     if (!pb) return fail(PFF_ERR_INVALID_ARG, "NULL argument");

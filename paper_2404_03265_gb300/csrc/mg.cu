@@ -156,29 +156,92 @@ __global__ void k_coarse_gather(int32_t n, const int32_t* idx, const T* d, doubl
 // Gauss-Jordan sweep k: row[] and col[] are row k and column k before the sweep;
 // the sweep writes row k+1 and column k+1 after it into row_n[] and col_n[], so
 // no thread reads an entry another thread of the same sweep writes.
-__global__ void k_gj_init(int32_t n, const double* __restrict__ A, double* rc) {
-  GRID_STRIDE(i, n) {
-    rc[i] = A[i];
-    rc[n + i] = A[i * n];
+// Blocked Gauss-Jordan inversion in place, panels of GJB pivots.  With P the
+// panel's rows/columns and R the others, eliminating the pivots of P gives
+//   A_PP <- X = A_PP^-1,  A_PR <- X A_PR,  A_RP <- -A_RP X,  A_RR <- A_RR - A_RP X A_PR
+// (old A_RP, A_PR on the right), the same as GJB scalar Gauss-Jordan steps.  A_PP
+// is then a Schur complement of an SPD matrix, so no pivoting is needed; its
+// inversion (one block, scalar steps in shared memory) flags a non-positive pivot.
+constexpr int GJB = 32;
+
+// X = A_PP^-1 in place (one block of GJB x GJB threads' worth of work)
+__global__ void k_gj_panel(int32_t n, int32_t k0, int32_t b, double* A, int32_t* bad) {
+  __shared__ double T[GJB][GJB + 1];
+  __shared__ double prow[GJB], pcol[GJB];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    T[i][j] = A[int64_t(k0 + i) * n + k0 + j];
+  }
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    for (int e = threadIdx.x; e < b; e += blockDim.x) {
+      prow[e] = T[k][e];
+      pcol[e] = T[e][k];
+    }
+    __syncthreads();
+    const double p = prow[k];
+    if (!(p > 0.0) && threadIdx.x == 0) *bad = 1;
+    const double ip = 1.0 / p;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+      const int i = e / b, j = e - i * b;
+      double v;
+      if (i == k) v = j == k ? ip : prow[j] * ip;
+      else if (j == k) v = -pcol[i] * ip;
+      else v = T[i][j] - pcol[i] * prow[j] * ip;
+      T[i][j] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    A[int64_t(k0 + i) * n + k0 + j] = T[i][j];
   }
 }
 
-__global__ void k_gj_sweep(int32_t n, int32_t k, double* A, const double* __restrict__ rc, double* __restrict__ rcn,
-                           int32_t* bad) {
-  const double* row = rc;
-  const double* col = rc + n;
-  const double p = row[k];
-  if (!(p > 0.0) && blockIdx.x == 0 && threadIdx.x == 0) *bad = 1;
-  const double ip = 1.0 / p;
-  GRID_STRIDE(e, int64_t(n) * n) {
-    const int32_t i = int32_t(e / n), j = int32_t(e - int64_t(i) * n);
-    double v;
-    if (i == k) v = j == k ? ip : row[j] * ip;
-    else if (j == k) v = -col[i] * ip;
-    else v = A[e] - col[i] * row[j] * ip;
-    A[e] = v;
-    if (i == k + 1) rcn[j] = v;
-    if (j == k + 1) rcn[n + i] = v;
+// A_PR <- X A_PR: one thread per column j outside the panel
+__global__ void k_gj_rows(int32_t n, int32_t k0, int32_t b, double* A) {
+  __shared__ double X[GJB][GJB];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) X[e / b][e % b] = A[int64_t(k0 + e / b) * n + k0 + e % b];
+  __syncthreads();
+  GRID_STRIDE(jj, n - b) {
+    const int j = int(jj) < k0 ? int(jj) : int(jj) + b;
+    double c[GJB];
+#pragma unroll
+    for (int k = 0; k < GJB; ++k) c[k] = k < b ? A[int64_t(k0 + k) * n + j] : 0.0;
+    for (int i = 0; i < b; ++i) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < GJB; ++k) v += X[i][k] * c[k];
+      A[int64_t(k0 + i) * n + j] = v;
+    }
+  }
+}
+
+// rows i outside the panel, one warp each: A_iR -= A_iP (new A_PR), then A_iP <- -A_iP X
+__global__ void k_gj_rest(int32_t n, int32_t k0, int32_t b, double* A) {
+  __shared__ double X[GJB][GJB];
+  __shared__ double rowp[8][GJB];   // old A_iP of each warp's row (blockDim.x <= 256)
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) X[e / b][e % b] = A[int64_t(k0 + e / b) * n + k0 + e % b];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = (blockDim.x >> 5);
+  for (int ii = blockIdx.x * nw + w; ii < n - b; ii += gridDim.x * nw) {
+    const int i = ii < k0 ? ii : ii + b;
+    double* Ai = A + int64_t(i) * n;
+    if (lane < b) rowp[w][lane] = Ai[k0 + lane];
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+      if (j >= k0 && j < k0 + b) continue;
+      double v = Ai[j];
+      for (int k = 0; k < b; ++k) v -= rowp[w][k] * A[int64_t(k0 + k) * n + j];
+      Ai[j] = v;
+    }
+    if (lane < b) {
+      double v = 0.0;
+      for (int k = 0; k < b; ++k) v += rowp[w][k] * X[k][lane];
+      Ai[k0 + lane] = -v;
+    }
+    __syncwarp();
   }
 }
 
@@ -425,10 +488,14 @@ cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev
 cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
   if (e != cudaSuccess || n <= 0) return e;
-  k_gj_init<<<blocks_for(n), TPB, 0, s>>>(n, A, rc);
-  const unsigned nb = blocks_for(int64_t(n) * n);
-  for (int32_t k = 0; k < n; ++k) {
-    k_gj_sweep<<<nb, TPB, 0, s>>>(n, k, A, rc + (k & 1) * 2 * int64_t(n), rc + ((k + 1) & 1) * 2 * int64_t(n), bad);
+  (void)rc;
+  for (int32_t k0 = 0; k0 < n; k0 += GJB) {
+    const int32_t b = n - k0 < GJB ? n - k0 : GJB;
+    k_gj_panel<<<1, TPB, 0, s>>>(n, k0, b, A, bad);
+    if (n > b) {
+      k_gj_rows<<<blocks_for(n - b), TPB, 0, s>>>(n, k0, b, A);
+      k_gj_rest<<<unsigned((n - b + (TPB / 32) - 1) / (TPB / 32)), TPB, 0, s>>>(n, k0, b, A);
+    }
   }
   return cudaGetLastError();
 }

@@ -71,11 +71,12 @@ cudaError_t mg_chebyshev_first_res(int64_t n, T* x, T* xprev, T* r, const T* din
 template <typename T>
 cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
                                   const T* ax, T a, T b, cudaStream_t s, bool pdl = false);
-// In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by Gauss-Jordan
-// sweeps without pivoting: the pivots are the diagonals of successive Schur
-// complements, positive for an SPD matrix.  rc: scratch of 4 n doubles.  *bad is
-// set to 1 when a pivot is not positive (the matrix is then not SPD and A holds
-// no inverse); it is cleared first.
+// In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by blocked
+// Gauss-Jordan elimination without pivoting (panels of 32 pivots, three launches
+// each): the pivots are the diagonals of successive Schur complements, positive
+// for an SPD matrix.  rc: unused (4 n doubles).  *bad is set to 1 when a pivot
+// is not positive (the matrix is then not SPD and A holds no inverse); it is
+// cleared first.
 cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s);
 
 // coarse solve x[idx] = Ainv (d[idx]) (dense FP64 inverse over the interior entries)

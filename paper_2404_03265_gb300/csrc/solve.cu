@@ -157,6 +157,12 @@ __global__ void k_axpby(int64_t n, double* out, const double* __restrict__ x, do
   GRID_STRIDE(i, n) out[i] = a * x[i] + b * y[i];
 }
 
+// phi_tilde = clip(2 phi^(n-1) - phi^(n-2), 0, 1)
+__global__ void k_extrapolate_phi(int64_t n, const double* __restrict__ p1, const double* __restrict__ p2,
+                                  double* out) {
+  GRID_STRIDE(i, n) out[i] = fmin(fmax(2.0 * p1[i] - p2[i], 0.0), 1.0);
+}
+
 
 // Krylov basis storage: rows in blocks of kBasisBlock; block r holds the rows
 // r kBasisBlock .. of every basis vector j contiguously, at r ldb + j kBasisBlock.
@@ -371,6 +377,11 @@ cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const dou
 cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
                         cudaStream_t s) {
   if (n > 0) k_store_basis<<<blocks_for(n), TPB, 0, s>>>(n, V, ldb, j, x, a, vc);
+  return cudaGetLastError();
+}
+
+cudaError_t extrapolate_phi(int64_t n, const double* p1, const double* p2, double* out, cudaStream_t s) {
+  if (n > 0) k_extrapolate_phi<<<blocks_for(n), TPB, 0, s>>>(n, p1, p2, out);
   return cudaGetLastError();
 }
 

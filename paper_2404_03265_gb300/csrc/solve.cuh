@@ -51,6 +51,8 @@ cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const dou
 cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
                         cudaStream_t s);
 cudaError_t vsum(int64_t n, const double* a, double* partial, double* out, cudaStream_t s);
+// phi_tilde = clip(2 phi^(n-1) - phi^(n-2), 0, 1) per slot
+cudaError_t extrapolate_phi(int64_t n, const double* p1, const double* p2, double* out, cudaStream_t s);
 cudaError_t all_finite(int64_t n, const double* a, int* bad, cudaStream_t s);
 
 }  // namespace pff

@@ -422,3 +422,77 @@ def test_multi_step_adjoint_vs_oracle_and_differences():
     Em[c] -= hh
     fd = (Jfd({}, ps, Ep) - Jfd({}, ps, Em)) / (2 * hh)
     assert abs(fd - gEn[c]) <= 1e-5 * abs(fd), (c, fd, gEn[c])
+
+
+def test_autograd_load_steps_three():
+    """J = TCV after three load steps (p = 0.1, 0.15, 0.2, lognormal E_K) through the
+    several-step torch wrapper: J.backward() against the oracle's checkpointed
+    adjoint (1e-6) and central differences of three-step GPU solves (1e-5) for the
+    first pressure, G_c and the largest E_K gradient."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Problem
+    from paper_2404_03265_gb300.autograd import tcv_load_steps
+    P = pair("small")
+    om = P.om
+    E = cell_E(P)
+    ps = [0.1, 0.15, 0.2]
+    base = P.material()
+    _, po = solvers.sneddon_initial(om, om.h_min_diag())
+    mats, ous, ophis, oacts = [], [np.zeros((om.nn, 2))], [po], []
+    u, phi, act = ous[0], po.copy(), None
+    for p in ps:
+        mat = ops.Material(**dict(base, p=p))
+        u, phi_n, act, info = solvers.load_step(om, mat, 1e4, u, phi.copy(), phi, active_prev=act, E_cells=E,
+                                                tol=1e-12, atol=1e-15)
+        assert info.converged
+        phi = phi_n
+        mats.append(mat)
+        ous.append(u)
+        ophis.append(phi)
+        oacts.append(act)
+    go = adj.tcv_adjoint_steps(om, mats, ous, ophis, oacts, E)
+    Jo = ops.tcv(om, ops.State(om, ous[-1], ophis[-1], ophis[-1]))
+
+    pb = Problem(P.lm, **base)
+    mg = MG(pb, PFF_F32)
+    pt = torch.tensor(ps, dtype=torch.float64, requires_grad=True)
+    gct = torch.tensor(base["Gc"], dtype=torch.float64, requires_grad=True)
+    Et = dev(E).requires_grad_(True)
+    u0 = torch.zeros((2, P.n_slots), dtype=torch.float64, device="cuda")
+    phi0 = dev(P.to_slots(po))
+    out = {}
+    J = tcv_load_steps(pb, mg, pt, gct, Et, u0, phi0, newton_kw=dict(tol=1e-12, atol=1e-15),
+                       adjoint_kw=dict(rtol=1e-12), out=out)
+    assert abs(J.item() - Jo) <= 1e-7 * abs(Jo), (J.item(), Jo)
+    for a_g, a_o in zip(out["active"], oacts):
+        assert np.array_equal(P.from_slots(a_g.cpu().numpy()).astype(bool), a_o)
+    J.backward()
+    gp = pt.grad.numpy()
+    for n in range(len(ps)):
+        assert close(gp[n], go["p"][n], 1e-6, 0.0), (n, gp[n], go["p"][n])
+    assert close(gct.grad.item(), go["Gc"], 1e-6, 1e-10 * Jo / base["Gc"]), (gct.grad.item(), go["Gc"])
+    gE = Et.grad.cpu().numpy()
+    inf, two = rel_err(gE, go["E"])
+    assert inf < 1e-6 and two < 1e-6, (inf, two)
+
+    # central differences of three-step GPU solves, through the same wrapper's forward
+    def Jfd(pss, gc, Ec):
+        with torch.no_grad():
+            return tcv_load_steps(pb, mg, torch.tensor(pss, dtype=torch.float64),
+                                  torch.tensor(gc, dtype=torch.float64), dev(Ec), u0,
+                                  phi0, newton_kw=dict(tol=1e-12, atol=1e-15)).item()
+
+    rel = 1e-6
+    hh = rel * ps[0]
+    fd = (Jfd([ps[0] + hh] + ps[1:], base["Gc"], E) - Jfd([ps[0] - hh] + ps[1:], base["Gc"], E)) / (2 * hh)
+    assert abs(fd - gp[0]) <= 1e-5 * abs(fd), (fd, gp[0])
+    hh = rel * base["Gc"]
+    fd = (Jfd(ps, base["Gc"] + hh, E) - Jfd(ps, base["Gc"] - hh, E)) / (2 * hh)
+    assert abs(fd - gct.grad.item()) <= 1e-5 * abs(fd), (fd, gct.grad.item())
+    c = int(np.argmax(np.abs(gE)))
+    hh = rel * E[c]
+    Ep, Em = E.copy(), E.copy()
+    Ep[c] += hh
+    Em[c] -= hh
+    fd = (Jfd(ps, base["Gc"], Ep) - Jfd(ps, base["Gc"], Em)) / (2 * hh)
+    assert abs(fd - gE[c]) <= 1e-5 * abs(fd), (c, fd, gE[c])

@@ -133,3 +133,17 @@ def test_adaptive_pdas_constant_same_solution():
     assert np.array_equal(a1, a2)
     assert np.linalg.norm(u1 - u2) <= 1e-7 * np.linalg.norm(u1)
     assert np.linalg.norm(p1 - p2) <= 1e-7 * np.linalg.norm(p1)
+
+
+def test_extrapolated_phi_tilde():
+    """Linear extrapolation in the step index: exact on data linear in the step
+    (phi^n = a + b n), clipped to [0, 1]; phi_tilde = phi^(n-1) when phi did not
+    change between the two previous steps."""
+    rng = np.random.default_rng(4)
+    a, b = rng.uniform(0.3, 0.6, 50), rng.uniform(-0.1, 0.1, 50)
+    phi = [a + b * n for n in range(3)]
+    assert np.allclose(solvers.extrapolate_phi(phi[1], phi[0]), phi[2], rtol=0, atol=1e-15)
+    same = rng.uniform(0, 1, 50)
+    assert np.array_equal(solvers.extrapolate_phi(same, same), same)
+    lo_hi = solvers.extrapolate_phi(np.array([0.1, 0.9, 0.5]), np.array([0.5, 0.1, 0.5]))
+    assert np.array_equal(lo_hi, np.array([0.0, 1.0, 0.5]))

@@ -268,3 +268,52 @@ def test_propagating_crack_sequence():
         lengths.append(np.abs(x[pg < 0.5]).max())
         phio = phin
     assert lengths[-1] > lengths[0] + 0.3, lengths
+
+
+def test_extrapolated_phi_tilde_two_steps():
+    """phi_tilde by extrapolation from the two previous steps (Sec. 2): the library's
+    device extrapolation equals the oracle's bit for bit on the same inputs, and a
+    second load step with it matches the oracle's (u, phi within 1e-7, active set
+    identical)."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, newton_step
+    P = Pair("small", 1)
+    om = P.om
+    mat = P.material(kappa=1e-3)
+    u0, phi0 = solvers.sneddon_initial(om, om.h_min_diag())
+    ps = (0.2, 0.3)
+    m1 = ops.Material(**dict(mat, p=ps[0]))
+    u1, p1, a1, i1 = solvers.load_step(om, m1, 1e4, u0, phi0.copy(), phi0, tol=1e-12, atol=1e-15)
+    assert i1.converged
+    pt_o = solvers.extrapolate_phi(p1, phi0)
+    assert np.abs(pt_o - p1).max() > 1e-6          # phi moved in the first step
+    m2 = ops.Material(**dict(mat, p=ps[1]))
+    u2, p2, a2, i2 = solvers.load_step(om, m2, 1e4, u1, p1.copy(), p1, active_prev=a1, tol=1e-12, atol=1e-15,
+                                       phi_tilde=pt_o)
+    assert i2.converged
+    pb = problem(P, mat)
+    mg = MG(pb, PFF_F32)
+    # the device extrapolation on the oracle's phases
+    pt = torch.empty(P.n_slots, dtype=torch.float64, device="cuda")
+    pb.extrapolate_phi(dev(P.to_slots(p1)), dev(P.to_slots(phi0)), pt)
+    torch.cuda.synchronize()
+    assert np.array_equal(P.from_slots(pt.cpu().numpy()), pt_o)
+    # two load steps on the GPU, the second with the extrapolated phi_tilde
+    us = dev(P.to_slots(u0).T)
+    ph0 = dev(P.to_slots(phi0))
+    ps_ = ph0.clone()
+    act = torch.zeros(P.n_slots, dtype=torch.uint8, device="cuda")
+    pb.set_pressure(ps[0])
+    info = newton_step(pb, mg, us, ps_, ph0, act, tol=1e-12, atol=1e-15)
+    assert info["converged"]
+    ph1 = ps_.clone()
+    pb.extrapolate_phi(ph1, ph0, pt)
+    pb.set_pressure(ps[1])
+    info = newton_step(pb, mg, us, ps_, ph1, act, tol=1e-12, atol=1e-15, phi_tilde=pt)
+    assert info["converged"]
+    ag = P.from_slots(act.cpu().numpy()).astype(bool)
+    assert np.array_equal(ag, a2)
+    ug = P.from_slots(us.cpu().numpy().T)
+    pg = P.from_slots(ps_.cpu().numpy())
+    assert np.linalg.norm(ug - u2) / np.linalg.norm(u2) < 1e-7
+    assert np.linalg.norm(pg - p2) / np.linalg.norm(p2) < 1e-7

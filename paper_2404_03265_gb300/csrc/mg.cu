@@ -4,6 +4,9 @@
 // holes carry zeros; the inverse diagonal is zero off the interior, so the
 // Chebyshev updates leave edge and fixed entries untouched.
 #include "mg.cuh"
+
+#include <algorithm>
+
 #include "pdl.cuh"
 
 namespace pff {
@@ -153,95 +156,153 @@ __global__ void k_coarse_gather(int32_t n, const int32_t* idx, const T* d, doubl
   GRID_STRIDE(i, n) tmp[i] = double(d[idx[i]]);
 }
 
-// Gauss-Jordan sweep k: row[] and col[] are row k and column k before the sweep;
-// the sweep writes row k+1 and column k+1 after it into row_n[] and col_n[], so
-// no thread reads an entry another thread of the same sweep writes.
 // Blocked Gauss-Jordan inversion in place, panels of GJB pivots.  With P the
 // panel's rows/columns and R the others, eliminating the pivots of P gives
 //   A_PP <- X = A_PP^-1,  A_PR <- X A_PR,  A_RP <- -A_RP X,  A_RR <- A_RR - A_RP X A_PR
 // (old A_RP, A_PR on the right), the same as GJB scalar Gauss-Jordan steps.  A_PP
 // is then a Schur complement of an SPD matrix, so no pivoting is needed; its
 // inversion (one block, scalar steps in shared memory) flags a non-positive pivot.
+// Two launches per panel: k_gj_panel inverts A_PP and copies the old A_RP and
+// A_PR to scratch; k_gj_update then owns every entry it writes, so no block reads
+// an entry another block of the same launch writes.
+// Scratch layout (double): X (GJB x GJB, zero beyond b), then Cp ((n - b) x GJB:
+// old A_RP by compact row index, zero beyond b), then Rp (GJB x n: old A_PR, zero
+// in the panel's columns and beyond b).
 constexpr int GJB = 32;
+constexpr int GJ_ROWS = 128;   // rows of a k_gj_update tile (its columns: GJB)
 
-// X = A_PP^-1 in place (one block of GJB x GJB threads' worth of work)
-__global__ void k_gj_panel(int32_t n, int32_t k0, int32_t b, double* A, int32_t* bad) {
-  __shared__ double T[GJB][GJB + 1];
-  __shared__ double prow[GJB], pcol[GJB];
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e - i * b;
-    T[i][j] = A[int64_t(k0 + i) * n + k0 + j];
-  }
-  __syncthreads();
-  for (int k = 0; k < b; ++k) {
-    for (int e = threadIdx.x; e < b; e += blockDim.x) {
-      prow[e] = T[k][e];
-      pcol[e] = T[e][k];
+__device__ __forceinline__ int gj_row(int ii, int k0, int b) { return ii < k0 ? ii : ii + b; }
+
+// block 0: X = A_PP^-1 (padded with the identity to GJB x GJB); the others copy
+// the old pivot columns and rows
+__global__ void __launch_bounds__(TPB) k_gj_panel(int32_t n, int32_t k0, int32_t b, double* A, double* scr,
+                                                  int32_t* bad) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (blockIdx.x == 0) {
+    // one reciprocal per step: the thread that writes the next pivot inverts it
+    __shared__ double T[GJB][GJB + 1];
+    __shared__ double ipiv[2];
+#pragma unroll
+    for (int r = 0; r < GJB / 8; ++r) {
+      const int i = w + 8 * r;
+      T[i][lane] = (i < b && lane < b) ? A[int64_t(k0 + i) * n + k0 + lane] : (i == lane ? 1.0 : 0.0);
     }
     __syncthreads();
-    const double p = prow[k];
-    if (!(p > 0.0) && threadIdx.x == 0) *bad = 1;
-    const double ip = 1.0 / p;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-      const int i = e / b, j = e - i * b;
-      double v;
-      if (i == k) v = j == k ? ip : prow[j] * ip;
-      else if (j == k) v = -pcol[i] * ip;
-      else v = T[i][j] - pcol[i] * prow[j] * ip;
-      T[i][j] = v;
+    if (threadIdx.x == 0) {
+      if (!(T[0][0] > 0.0)) *bad = 1;
+      ipiv[0] = 1.0 / T[0][0];
     }
     __syncthreads();
+    for (int k = 0; k < GJB; ++k) {
+      const double ip = ipiv[k & 1];
+      const double sk = T[k][lane] * ip;   // row k scaled by the pivot's reciprocal
+      double v[GJB / 8];
+#pragma unroll
+      for (int r = 0; r < GJB / 8; ++r) {
+        const int i = w + 8 * r;
+        const double pc = T[i][k];
+        if (i == k) v[r] = lane == k ? ip : sk;
+        else if (lane == k) v[r] = -pc * ip;
+        else v[r] = fma(-pc, sk, T[i][lane]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < GJB / 8; ++r) {
+        const int i = w + 8 * r;
+        T[i][lane] = v[r];
+        if (i == k + 1 && lane == k + 1) {
+          if (!(v[r] > 0.0)) *bad = 1;
+          ipiv[(k + 1) & 1] = 1.0 / v[r];
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < GJB / 8; ++r) {
+      const int i = w + 8 * r;
+      const bool in = i < b && lane < b;
+      scr[i * GJB + lane] = in ? T[i][lane] : 0.0;
+      if (in) A[int64_t(k0 + i) * n + k0 + lane] = T[i][lane];
+    }
+    return;
   }
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e - i * b;
-    A[int64_t(k0 + i) * n + k0 + j] = T[i][j];
+  double* Cp = scr + GJB * GJB;
+  double* Rp = Cp + int64_t(n - b) * GJB;
+  const int64_t nc = int64_t(n - b) * GJB, nr = int64_t(GJB) * n;
+  const int64_t stride = int64_t(gridDim.x - 1) * blockDim.x;
+  for (int64_t e = int64_t(blockIdx.x - 1) * blockDim.x + threadIdx.x; e < nc + nr; e += stride) {
+    if (e < nc) {
+      const int ii = int(e / GJB), k = int(e % GJB);
+      Cp[e] = k < b ? A[int64_t(gj_row(ii, k0, b)) * n + k0 + k] : 0.0;
+    } else {
+      const int64_t f = e - nc;
+      const int k = int(f / n), j = int(f % n);
+      Rp[f] = (k < b && (j < k0 || j >= k0 + b)) ? A[int64_t(k0 + k) * n + j] : 0.0;
+    }
   }
 }
 
-// A_PR <- X A_PR: one thread per column j outside the panel
-__global__ void k_gj_rows(int32_t n, int32_t k0, int32_t b, double* A) {
-  __shared__ double X[GJB][GJB];
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) X[e / b][e % b] = A[int64_t(k0 + e / b) * n + k0 + e % b];
-  __syncthreads();
-  GRID_STRIDE(jj, n - b) {
-    const int j = int(jj) < k0 ? int(jj) : int(jj) + b;
-    double c[GJB];
+// tile (GJ_ROWS rows outside P) x (GJB columns): the panel's columns get
+// -A_RP X; any other column tile forms X A_PR for its columns (written back by
+// the first row tile) and subtracts A_RP (X A_PR) from its rows
+__global__ void __launch_bounds__(TPB) k_gj_update(int32_t n, int32_t k0, int32_t b, double* A,
+                                                   const double* scr) {
+  __shared__ double Xs[GJB][GJB];
+  __shared__ double Ps[GJB][GJB];       // old A_PR tile, then X A_PR
+  __shared__ double Cs[GJ_ROWS][GJB];   // old A_RP rows of the tile
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double* Cp = scr + GJB * GJB;
+  const double* Rp = Cp + int64_t(n - b) * GJB;
+  const int ii0 = int(blockIdx.y) * GJ_ROWS;
+  const int nrow = min(GJ_ROWS, n - b - ii0);
+  const int j0 = int(blockIdx.x) * GJB;
+  const int j = j0 + lane;
+  const bool panel = j0 == k0;
 #pragma unroll
-    for (int k = 0; k < GJB; ++k) c[k] = k < b ? A[int64_t(k0 + k) * n + j] : 0.0;
-    for (int i = 0; i < b; ++i) {
-      double v = 0.0;
+  for (int r = 0; r < GJB / 8; ++r) Xs[w + 8 * r][lane] = scr[(w + 8 * r) * GJB + lane];
+  for (int r = w; r < GJ_ROWS; r += TPB / 32) Cs[r][lane] = r < nrow ? Cp[int64_t(ii0 + r) * GJB + lane] : 0.0;
+  if (!panel) {
 #pragma unroll
-      for (int k = 0; k < GJB; ++k) v += X[i][k] * c[k];
-      A[int64_t(k0 + i) * n + j] = v;
-    }
+    for (int r = 0; r < GJB / 8; ++r) Ps[w + 8 * r][lane] = j < n ? Rp[int64_t(w + 8 * r) * n + j] : 0.0;
   }
-}
-
-// rows i outside the panel, one warp each: A_iR -= A_iP (new A_PR), then A_iP <- -A_iP X
-__global__ void k_gj_rest(int32_t n, int32_t k0, int32_t b, double* A) {
-  __shared__ double X[GJB][GJB];
-  __shared__ double rowp[8][GJB];   // old A_iP of each warp's row (blockDim.x <= 256)
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) X[e / b][e % b] = A[int64_t(k0 + e / b) * n + k0 + e % b];
   __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = (blockDim.x >> 5);
-  for (int ii = blockIdx.x * nw + w; ii < n - b; ii += gridDim.x * nw) {
-    const int i = ii < k0 ? ii : ii + b;
-    double* Ai = A + int64_t(i) * n;
-    if (lane < b) rowp[w][lane] = Ai[k0 + lane];
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-      if (j >= k0 && j < k0 + b) continue;
-      double v = Ai[j];
-      for (int k = 0; k < b; ++k) v -= rowp[w][k] * A[int64_t(k0 + k) * n + j];
-      Ai[j] = v;
+  if (panel) {
+    // A_RP <- -A_RP X
+    for (int r = w; r < nrow; r += TPB / 32) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < GJB; ++k) acc = fma(Cs[r][k], Xs[k][lane], acc);
+      if (lane < b) A[int64_t(gj_row(ii0 + r, k0, b)) * n + j] = -acc;
     }
-    if (lane < b) {
-      double v = 0.0;
-      for (int k = 0; k < b; ++k) v += rowp[w][k] * X[k][lane];
-      Ai[k0 + lane] = -v;
-    }
-    __syncwarp();
+    return;
+  }
+  double pr[GJB / 8];
+#pragma unroll
+  for (int r = 0; r < GJB / 8; ++r) {
+    const int k = w + 8 * r;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < GJB; ++m) acc = fma(Xs[k][m], Ps[m][lane], acc);
+    pr[r] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < GJB / 8; ++r) {
+    const int k = w + 8 * r;
+    Ps[k][lane] = pr[r];
+    if (blockIdx.y == 0 && k < b && j < n) A[int64_t(k0 + k) * n + j] = pr[r];
+  }
+  __syncthreads();
+  if (j >= n) return;
+  double pc[GJB];
+#pragma unroll
+  for (int k = 0; k < GJB; ++k) pc[k] = Ps[k][lane];
+  for (int r = w; r < nrow; r += TPB / 32) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < GJB; ++k) acc = fma(Cs[r][k], pc[k], acc);
+    double* a = A + int64_t(gj_row(ii0 + r, k0, b)) * n + j;
+    *a = *a - acc;
   }
 }
 
@@ -485,16 +546,19 @@ cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev
     return launch_ex(pdl, &k_cheb_step_add<T>, blocks_for(n), TPB, 0, s, n, xadd, x, xprev, dinv, d, ax, a, b);
   return cudaGetLastError();
 }
-cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s) {
+int64_t mg_spd_scratch(int32_t cap) { return int64_t(GJB) * GJB + 2 * int64_t(GJB) * cap; }
+
+cudaError_t mg_spd_invert(int32_t n, double* A, double* scr, int32_t* bad, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
   if (e != cudaSuccess || n <= 0) return e;
-  (void)rc;
   for (int32_t k0 = 0; k0 < n; k0 += GJB) {
     const int32_t b = n - k0 < GJB ? n - k0 : GJB;
-    k_gj_panel<<<1, TPB, 0, s>>>(n, k0, b, A, bad);
+    const int64_t copies = int64_t(n - b) * GJB + int64_t(GJB) * n;
+    const unsigned cb = n > b ? unsigned(std::min<int64_t>((copies + TPB - 1) / TPB, 64)) : 0u;
+    k_gj_panel<<<1 + cb, TPB, 0, s>>>(n, k0, b, A, scr, bad);
     if (n > b) {
-      k_gj_rows<<<blocks_for(n - b), TPB, 0, s>>>(n, k0, b, A);
-      k_gj_rest<<<unsigned((n - b + (TPB / 32) - 1) / (TPB / 32)), TPB, 0, s>>>(n, k0, b, A);
+      const dim3 grid(unsigned((n + GJB - 1) / GJB), unsigned((n - b + GJ_ROWS - 1) / GJ_ROWS));
+      k_gj_update<<<grid, TPB, 0, s>>>(n, k0, b, A, scr);
     }
   }
   return cudaGetLastError();

@@ -72,12 +72,13 @@ template <typename T>
 cudaError_t mg_chebyshev_step_add(int64_t n, T* xadd, const T* x, const T* xprev, const T* dinv, const T* d,
                                   const T* ax, T a, T b, cudaStream_t s, bool pdl = false);
 // In-place inverse of a dense SPD matrix (n x n, row-major, FP64) by blocked
-// Gauss-Jordan elimination without pivoting (panels of 32 pivots, three launches
+// Gauss-Jordan elimination without pivoting (panels of 32 pivots, two launches
 // each): the pivots are the diagonals of successive Schur complements, positive
-// for an SPD matrix.  rc: unused (4 n doubles).  *bad is set to 1 when a pivot
-// is not positive (the matrix is then not SPD and A holds no inverse); it is
-// cleared first.
-cudaError_t mg_spd_invert(int32_t n, double* A, double* rc, int32_t* bad, cudaStream_t s);
+// for an SPD matrix.  scr: device scratch of mg_spd_scratch(cap) doubles for any
+// n <= cap.  *bad is set to 1 when a pivot is not positive (the matrix is then
+// not SPD and A holds no inverse); it is cleared first.
+int64_t mg_spd_scratch(int32_t cap);
+cudaError_t mg_spd_invert(int32_t n, double* A, double* scr, int32_t* bad, cudaStream_t s);
 
 // coarse solve x[idx] = Ainv (d[idx]) (dense FP64 inverse over the interior entries)
 template <typename T>

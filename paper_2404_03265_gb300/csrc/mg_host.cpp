@@ -355,7 +355,7 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
         B.coarse_idx = mg.mem.alloc<int32_t>(cap);
         B.coarse_inv = mg.mem.alloc<double>(int64_t(cap) * cap);
         B.coarse_tmp = mg.mem.alloc<double>(cap);
-        B.coarse_rc = mg.mem.alloc<double>(4 * int64_t(cap));
+        B.coarse_rc = mg.mem.alloc<double>(mg_spd_scratch(cap));
         if (!mg.mem.err.empty()) return mg.mem.err;
         B.coarse_cap = cap;
       }

@@ -171,48 +171,63 @@ __device__ __forceinline__ int64_t basis_row(int64_t i, int64_t ldb) {
 }
 
 // partial[b * k + j] = sum over this block's rows of V_j . w.  The basis vectors
-// go in chunks of MD_J; a thread visits its rows i = t, t + S, t + 2 S, ...
-// (S = the grid's thread count) in that order, as a plain grid-stride dot does,
-// but issues the loads of MD_R consecutive visits (w and MD_J basis entries each)
-// together.  It keeps MD_J sums, and the block reduces all of them in one
-// shared-memory tree (fixed order).
+// go in chunks of MD_J (the last one of k mod MD_J, its own instantiation, so no
+// multiply is spent on padding); a thread visits its rows i = t, t + S, t + 2 S,
+// ... (S = the grid's thread count) in that order, as a plain grid-stride dot
+// does, but issues the loads of MD_R consecutive visits (w and the chunk's basis
+// entries each) together.  It keeps one sum per vector of the chunk, and the
+// block reduces them in one shared-memory tree (fixed order).
 constexpr int MD_J = 8;
 constexpr int MD_R = 4;
+template <int JN>
+__device__ __forceinline__ void md_chunk(int64_t n, const double* __restrict__ Vc, int64_t ldb,
+                                         const double* __restrict__ w, double (&sh)[MD_J][TPB]) {
+  const int64_t S = int64_t(gridDim.x) * TPB;
+  double acc[JN];
+#pragma unroll
+  for (int q = 0; q < JN; ++q) acc[q] = 0.0;
+  for (int64_t i0 = int64_t(blockIdx.x) * TPB + threadIdx.x; i0 < n; i0 += MD_R * S) {
+    double wv[MD_R], vv[JN][MD_R];
+#pragma unroll
+    for (int e = 0; e < MD_R; ++e) {
+      const int64_t i = i0 + e * S;
+      const int64_t bi = basis_row(i, ldb);
+      wv[e] = i < n ? w[i] : 0.0;
+#pragma unroll
+      for (int q = 0; q < JN; ++q) vv[q][e] = i < n ? Vc[bi + q * kBasisBlock] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < MD_R; ++e) {
+      if (i0 + e * S < n) {
+#pragma unroll
+        for (int q = 0; q < JN; ++q) acc[q] += vv[q][e] * wv[e];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < JN; ++q) sh[q][threadIdx.x] = acc[q];
+}
+
 __global__ void k_multidot_partial(int64_t n, int k, const double* __restrict__ V, int64_t ldb,
                                    const double* __restrict__ w, double* partial) {
   __shared__ double sh[MD_J][TPB];
-  const int64_t S = int64_t(gridDim.x) * TPB;
   for (int j0 = 0; j0 < k; j0 += MD_J) {
     const int jn = k - j0 < MD_J ? k - j0 : MD_J;
-    double acc[MD_J];
-#pragma unroll
-    for (int q = 0; q < MD_J; ++q) acc[q] = 0.0;
     const double* Vc = V + int64_t(j0) * kBasisBlock;
-    for (int64_t i0 = int64_t(blockIdx.x) * TPB + threadIdx.x; i0 < n; i0 += MD_R * S) {
-      double wv[MD_R], vv[MD_J][MD_R];
-#pragma unroll
-      for (int e = 0; e < MD_R; ++e) {
-        const int64_t i = i0 + e * S;
-        const int64_t bi = basis_row(i, ldb);
-        wv[e] = i < n ? w[i] : 0.0;
-#pragma unroll
-        for (int q = 0; q < MD_J; ++q) vv[q][e] = (q < jn && i < n) ? Vc[bi + q * kBasisBlock] : 0.0;
-      }
-#pragma unroll
-      for (int e = 0; e < MD_R; ++e) {
-        if (i0 + e * S < n) {
-#pragma unroll
-          for (int q = 0; q < MD_J; ++q) acc[q] += vv[q][e] * wv[e];
-        }
-      }
+    switch (jn) {
+      case 1: md_chunk<1>(n, Vc, ldb, w, sh); break;
+      case 2: md_chunk<2>(n, Vc, ldb, w, sh); break;
+      case 3: md_chunk<3>(n, Vc, ldb, w, sh); break;
+      case 4: md_chunk<4>(n, Vc, ldb, w, sh); break;
+      case 5: md_chunk<5>(n, Vc, ldb, w, sh); break;
+      case 6: md_chunk<6>(n, Vc, ldb, w, sh); break;
+      case 7: md_chunk<7>(n, Vc, ldb, w, sh); break;
+      default: md_chunk<8>(n, Vc, ldb, w, sh); break;
     }
-#pragma unroll
-    for (int q = 0; q < MD_J; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
     for (int o = TPB / 2; o > 0; o >>= 1) {
       if (threadIdx.x < o) {
-#pragma unroll
-        for (int q = 0; q < MD_J; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+        for (int q = 0; q < jn; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
       }
       __syncthreads();
     }
@@ -235,11 +250,12 @@ __global__ void k_multidot_final(int nb, int k, const double* __restrict__ parti
   if (threadIdx.x == 0) out[j] = sh[0];
 }
 
-// w += sign * sum_j h_j V_j (the sum in the order j = 0, 1, ...; loads of four
-// basis entries are issued together; h staged in shared memory)
+// w[map(i)] += sign * sum_j h_j V_j[i] (the sum in the order j = 0, 1, ...; loads
+// of four basis entries are issued together; h staged in shared memory; map(i) = i
+// without a map)
 constexpr int MAX_BASIS = 512;
 __global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int64_t ldb, const double* __restrict__ h,
-                             double sign, double* w) {
+                             double sign, double* w, const int32_t* __restrict__ map) {
   __shared__ double hs[MAX_BASIS];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
@@ -256,17 +272,24 @@ __global__ void k_multi_axpy(int64_t n, int k, const double* __restrict__ V, int
       acc += hs[j + 3] * v3;
     }
     for (; j < k; ++j) acc += hs[j] * Vi[j * kBasisBlock];
-    w[i] += sign * acc;
+    const int64_t o = map ? int64_t(map[i]) : i;
+    w[o] += sign * acc;
   }
 }
 
-// basis vector j = a x, also written contiguously to vc (x may be vc)
-__global__ void k_store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc) {
+// basis vector j = a x, also written to vc[map(i)] (map(i) = i without a map; x may
+// be vc when there is no map)
+__global__ void k_store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
+                              const int32_t* __restrict__ map) {
   GRID_STRIDE(i, n) {
     const double v = a * x[i];
     V[basis_row(i, ldb) + int64_t(j) * kBasisBlock] = v;
-    vc[i] = v;
+    vc[map ? int64_t(map[i]) : i] = v;
   }
+}
+
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ map, const double* __restrict__ x, double* out) {
+  GRID_STRIDE(i, n) out[i] = x[map[i]];
 }
 
 __global__ void k_sum_partial(int64_t n, const double* __restrict__ a, double* part) {
@@ -368,15 +391,20 @@ cudaError_t multidot(int64_t n, int k, const double* V, int64_t ldb, const doubl
 }
 
 cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const double* h, double sign, double* w,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int32_t* map) {
   if (k > MAX_BASIS) return cudaErrorInvalidValue;
-  if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ldb, h, sign, w);
+  if (n > 0 && k > 0) k_multi_axpy<<<blocks_for(n), TPB, 0, s>>>(n, k, V, ldb, h, sign, w, map);
   return cudaGetLastError();
 }
 
 cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
-                        cudaStream_t s) {
-  if (n > 0) k_store_basis<<<blocks_for(n), TPB, 0, s>>>(n, V, ldb, j, x, a, vc);
+                        cudaStream_t s, const int32_t* map) {
+  if (n > 0) k_store_basis<<<blocks_for(n), TPB, 0, s>>>(n, V, ldb, j, x, a, vc, map);
+  return cudaGetLastError();
+}
+
+cudaError_t gather(int64_t n, const int32_t* map, const double* x, double* out, cudaStream_t s) {
+  if (n > 0) k_gather<<<blocks_for(n), TPB, 0, s>>>(n, map, x, out);
   return cudaGetLastError();
 }
 

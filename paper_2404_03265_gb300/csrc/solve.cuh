@@ -44,12 +44,14 @@ inline int64_t basis_blocks(int64_t n) { return (n + kBasisBlock - 1) / kBasisBl
 // out[j] = V_j . w, j < k
 cudaError_t multidot(int64_t n, int k, const double* V, int64_t ldb, const double* w, double* partial, double* out,
                      cudaStream_t s);
-// w += sign * sum_j h[j] V_j  (h on the device)
+// w[map[i]] += sign * sum_j h[j] V_j[i]  (h on the device; map[i] = i when map is null)
 cudaError_t multi_axpy(int64_t n, int k, const double* V, int64_t ldb, const double* h, double sign, double* w,
-                       cudaStream_t s);
-// V_j = a x, and vc = a x contiguously (x may be vc)
+                       cudaStream_t s, const int32_t* map = nullptr);
+// V_j = a x, and vc[map[i]] = a x[i] (map[i] = i when map is null; x may then be vc)
 cudaError_t store_basis(int64_t n, double* V, int64_t ldb, int j, const double* x, double a, double* vc,
-                        cudaStream_t s);
+                        cudaStream_t s, const int32_t* map = nullptr);
+// out[i] = x[map[i]], i < n
+cudaError_t gather(int64_t n, const int32_t* map, const double* x, double* out, cudaStream_t s);
 cudaError_t vsum(int64_t n, const double* a, double* partial, double* out, cudaStream_t s);
 // phi_tilde = clip(2 phi^(n-1) - phi^(n-2), 0, 1) per slot
 cudaError_t extrapolate_phi(int64_t n, const double* p1, const double* p2, double* out, cudaStream_t s);

@@ -66,7 +66,18 @@ std::string ensure_workspace(pff_problem& pb, int restart) {
   W = SolverWS();
   W.restart = restart;
   const int64_t n3 = 3 * n;
-  W.V = W.mem.alloc<double>(size_t(basis_blocks(n3)) * size_t(restart + 1) * kBasisBlock);
+  {
+    // node rows of the three blocks: the other slots are zero in every Krylov vector
+    const std::vector<uint8_t>& F = pb.mesh->m.slot_flags;
+    std::vector<int32_t> map;
+    for (int c = 0; c < 3; ++c)
+      for (int64_t i = 0; i < n; ++i)
+        if (F[size_t(i)] & 1) map.push_back(int32_t(c * n + i));
+    W.nc = int64_t(map.size());
+    W.map = W.mem.upload(map);
+  }
+  W.V = W.mem.alloc<double>(size_t(basis_blocks(W.nc)) * size_t(restart + 1) * kBasisBlock);
+  W.wc = W.mem.alloc<double>(W.nc);
   W.vc = W.mem.alloc<double>(n3);
   W.w = W.mem.alloc<double>(n3);
   W.tmp = W.mem.alloc<double>(n3);
@@ -89,6 +100,7 @@ std::string ensure_workspace(pff_problem& pb, int restart) {
   W.x32 = W.mem.alloc<float>(n3);
   W.y32 = W.mem.alloc<float>(n3);
   if (!W.mem.err.empty()) return W.mem.err;
+  if (cudaMemset(W.vc, 0, n3 * sizeof(double)) != cudaSuccess) return "workspace: cudaMemset failed";
   W.ready = true;
   return "";
 }
@@ -127,9 +139,11 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
   cudaEvent_t* ev = pb.gm_ev;
   RET(cudaMemsetAsync(x, 0, n3 * sizeof(double), s));
   const int64_t ldb = int64_t(restart + 1) * kBasisBlock;   // row-block stride of the basis
-  RET(precond(mg, b, W.vc, s));
+  const int64_t nc = W.nc;
+  RET(precond(mg, b, W.w, s));
+  RET(gather(nc, W.map, W.w, W.wc, s));
   double beta = 0.0;
-  RET(norm2(pb, n3, W.vc, &beta, s));
+  RET(norm2(pb, nc, W.wc, &beta, s));
   res = GmresResult();
   res.initial = beta;
   if (!(beta > 0.0)) {
@@ -148,23 +162,24 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
-    RET(store_basis(n3, W.V, ldb, 0, W.vc, 1.0 / beta, W.vc, s));
+    RET(store_basis(nc, W.V, ldb, 0, W.wc, 1.0 / beta, W.vc, s, W.map));
     int jd = 0;
     bool conv = false;
     for (int j = 0; j < restart; ++j) {
-      // W.vc holds V_j contiguously
+      // W.vc holds V_j in slot layout
       RET(cudaEventRecord(ev[0], s));
       RET(A(W.vc, W.tmp));
       RET(cudaEventRecord(ev[1], s));
       RET(precond(mg, W.tmp, W.w, s));
       RET(cudaEventRecord(ev[2], s));
-      // classical Gram-Schmidt, twice; the coefficients stay on the device until
-      // one copy brings both passes and |w|^2 to the host
-      RET(multidot(n3, j + 1, W.V, ldb, W.w, W.partial, h1d, s));
-      RET(multi_axpy(n3, j + 1, W.V, ldb, h1d, -1.0, W.w, s));
-      RET(multidot(n3, j + 1, W.V, ldb, W.w, W.partial, h2d, s));
-      RET(multi_axpy(n3, j + 1, W.V, ldb, h2d, -1.0, W.w, s));
-      RET(dot64(n3, W.w, W.w, W.partial, nwd, s));
+      // classical Gram-Schmidt, twice, on the node rows; the coefficients stay on
+      // the device until one copy brings both passes and |w|^2 to the host
+      RET(gather(nc, W.map, W.w, W.wc, s));
+      RET(multidot(nc, j + 1, W.V, ldb, W.wc, W.partial, h1d, s));
+      RET(multi_axpy(nc, j + 1, W.V, ldb, h1d, -1.0, W.wc, s));
+      RET(multidot(nc, j + 1, W.V, ldb, W.wc, W.partial, h2d, s));
+      RET(multi_axpy(nc, j + 1, W.V, ldb, h2d, -1.0, W.wc, s));
+      RET(dot64(nc, W.wc, W.wc, W.partial, nwd, s));
       RET(cudaEventRecord(ev[3], s));
       RET(cudaMemcpyAsync(hh.data(), W.hh, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       RET(cudaStreamSynchronize(s));
@@ -198,7 +213,7 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
         conv = std::fabs(g[j + 1]) <= target || hn == 0.0;
         break;
       }
-      RET(store_basis(n3, W.V, ldb, j + 1, W.w, 1.0 / hn, W.vc, s));
+      RET(store_basis(nc, W.V, ldb, j + 1, W.wc, 1.0 / hn, W.vc, s, W.map));
     }
     // y = H^-1 g (upper triangular), x += V y
     std::vector<double> y(jd, 0.0);
@@ -209,7 +224,7 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     }
     if (jd > 0) {
       RET(cudaMemcpyAsync(W.h, y.data(), jd * sizeof(double), cudaMemcpyHostToDevice, s));
-      RET(multi_axpy(n3, jd, W.V, ldb, W.h, 1.0, x, s));
+      RET(multi_axpy(nc, jd, W.V, ldb, W.h, 1.0, x, s, W.map));
     }
     res.iterations = it;
     res.estimate = std::fabs(g[jd]);
@@ -218,8 +233,9 @@ cudaError_t gmres_solve(pff_problem& pb, pff_mg& mg, int transpose, const double
     // restart from the true preconditioned residual
     RET(A(x, W.tmp));
     RET(axpby(n3, W.tmp, b, 1.0, W.tmp, -1.0, s));
-    RET(precond(mg, W.tmp, W.vc, s));
-    RET(norm2(pb, n3, W.vc, &beta, s));
+    RET(precond(mg, W.tmp, W.w, s));
+    RET(gather(nc, W.map, W.w, W.wc, s));
+    RET(norm2(pb, nc, W.wc, &beta, s));
     res.estimate = beta;
     if (beta <= target) { res.converged = true; return cudaSuccess; }
   }

@@ -86,7 +86,12 @@ struct SolverWS {
   bool ready = false;
   int restart = 0;
   double *V = nullptr, *w = nullptr, *tmp = nullptr, *rhs = nullptr, *R = nullptr, *res = nullptr;
-  double* vc = nullptr;   // the newest basis vector, contiguous (V is stored in row blocks)
+  double* vc = nullptr;   // the newest basis vector in slot layout (zero off the node slots)
+  // GMRES keeps its Krylov basis on the node rows only: row i of a basis vector is
+  // entry map[i] of the slot-layout vector (3 blocks of n_slots), nc rows
+  int32_t* map = nullptr;
+  int64_t nc = 0;
+  double* wc = nullptr;   // the Arnoldi vector on those rows
   double *dU = nullptr, *du0 = nullptr, *st = nullptr, *ut = nullptr, *B = nullptr;
   uint8_t *act = nullptr, *act_prev = nullptr;
   unsigned long long* stats = nullptr;
@@ -179,7 +184,7 @@ struct MGBlock {
   int32_t* coarse_idx = nullptr;   // level-0 entries (comp * n_0 + slot) of the coarse interior
   double* coarse_inv = nullptr;    // dense FP64 inverse, n_coarse^2
   double* coarse_tmp = nullptr;
-  double* coarse_rc = nullptr;     // 4 n_coarse: pivot rows and columns of the inversion
+  double* coarse_rc = nullptr;     // scratch of the inversion: panel inverse, old pivot columns and rows
 };
 
 }  // namespace pff

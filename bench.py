@@ -625,12 +625,30 @@ def main():
                     help="add the 16.5M-DoF Q2 five-load-step solve and its checkpointed adjoint")
     ap.add_argument("--ref-seconds", type=float, default=90.0,
                     help="reference arm: the W + K oracle steps are sized to take about this long")
+    ap.add_argument("--profile-apply", action="store_true",
+                    help="a small case for ncu: one input set of the apply workload, three FP32 and one FP64 applies "
+                         "(Q1), then one FP32 Q2 apply; prints nothing but a short line")
     ap.add_argument("--solve-only", action="store_true",
                     help="run only the first load step of the solve leg (FP32 V-cycle, FP32 GMRES applies) and "
                          "print its record: a small case for profiling the set-up, V-cycle and GMRES kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_apply:
+        import torch
+        from paper_2404_03265_gb300 import Mesh
+        import synthetic as synth
+        mesh = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(1)
+        sets = build_sets(mesh, 1, torch.float32, seed=0)
+        time_applies(sets, 3, 0, 1)
+        sets = build_sets(mesh, 1, torch.float64, seed=0)
+        time_applies(sets, 1, 0, 1)
+        del sets
+        mesh2 = Mesh.from_recipe(synth.recipe(WORKLOAD)).finalize(2)
+        time_applies(build_sets(mesh2, 1, torch.float32, seed=0), 1, 0, 1)
+        torch.cuda.synchronize()
+        print("profile-apply done")
         return
     if args.solve_only:
         from paper_2404_03265_gb300 import PFF_F32

@@ -192,6 +192,11 @@ class MG:
     def setup(self, stream=None):
         _lib.check(_lib.lib().pff_mg_setup(self._h, _lib.stream_ptr(stream)))
 
+    def set_fused_smoother(self, on):
+        """Q1: Chebyshev steps as the stores of the level applies (True, the default)
+        or as separate kernels (False)."""
+        _lib.check(_lib.lib().pff_mg_set_fused_smoother(self._h, 1 if on else 0))
+
     def vcycle(self, block, r, z, stream=None):
         """z = MG(r); block 0: r, z float64 (2, n_slots); block 1: (n_slots,)."""
         _lib.check(_lib.lib().pff_vcycle(self._h, block, _lib.ptr(r), _lib.ptr(z), _lib.stream_ptr(stream)))

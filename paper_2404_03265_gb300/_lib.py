@@ -91,6 +91,7 @@ _SIGS = [
     ("pff_mg_create", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("pff_mg_setup", ctypes.c_int32, [_P, _P]),
     ("pff_mg_set_coarse", ctypes.c_int32, [_P, ctypes.c_int32]),
+    ("pff_mg_set_fused_smoother", ctypes.c_int32, [_P, ctypes.c_int32]),
     ("pff_vcycle", ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
     ("pff_mg_lambda", ctypes.c_int32, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     ("pff_mg_destroy", None, [_P]),

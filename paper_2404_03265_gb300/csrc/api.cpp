@@ -676,6 +676,16 @@ extern "C" pff_status pff_mg_set_coarse(pff_mg* mg, int32_t mode) {
   })
 }
 
+extern "C" pff_status pff_mg_set_fused_smoother(pff_mg* mg, int32_t on) {
+  PFF_TRY({
+    if (!mg) return fail(PFF_ERR_INVALID_ARG, "NULL argument");
+    if (on != 0 && on != 1) return fail(PFF_ERR_INVALID_ARG, "bad fused-smoother flag");
+    mg->fused = on;
+    mg_release_graphs(*mg);
+    return PFF_OK;
+  })
+}
+
 extern "C" pff_status pff_cod(pff_problem* pb, const double* u, const double* phi, const double* x_host, int32_t n_x,
                               double* cod_host, void* stream) {
   PFF_TRY({

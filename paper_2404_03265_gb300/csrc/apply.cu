@@ -23,6 +23,7 @@
 // partial sums; a small fix-up kernel condenses them (x_full = C x on input,
 // C^T y on output).  No atomics.
 #include "kernels.cuh"
+#include "cheb.cuh"
 #include "pdl.cuh"
 
 #include <cmath>
@@ -704,6 +705,59 @@ __device__ __forceinline__ void store_owned(const ApplyArgs& a, int slot, int ac
   if (outP) reinterpret_cast<T*>(a.yp)[slot] = y2;
 }
 
+// Fused Chebyshev store of a level node (OP_UU: components u_x, u_y; OP_PP: phi):
+// the value a plain store would write (zero on absent slots and constrained
+// components) enters the smoother update of ChebEpi instead of being stored.
+// The operands are loaded at the start of the row step that stores the node, so
+// their latency overlaps the step's cell arithmetic.
+template <typename T, int OP>
+struct ChebOps {
+  static constexpr int NC = OP == OP_UU ? 2 : 1;
+  T x[NC], prev[NC], dinv[NC], rhs[NC], out[NC];
+};
+
+template <typename T, int OP>
+__device__ __forceinline__ void cheb_load(const ApplyArgs& a, int slot, ChebOps<T, OP>& o) {
+  const ChebEpi& ch = a.ch;
+  const T* x = reinterpret_cast<const T*>(OP == OP_UU ? a.xu : a.xp);
+#pragma unroll
+  for (int c = 0; c < ChebOps<T, OP>::NC; ++c) {
+    const int64_t i = c * a.n_slots + slot;
+    o.dinv[c] = ldg(reinterpret_cast<const T*>(ch.dinv) + i);
+    o.rhs[c] = ldg(reinterpret_cast<const T*>(ch.rhs) + i);
+    if (ch.mode != CHEB_FIRST_RES) {
+      o.x[c] = ldg(x + i);
+      o.prev[c] = ldg(reinterpret_cast<const T*>(ch.prev) + i);
+    }
+    if (ch.mode == CHEB_STEP_ADD) o.out[c] = reinterpret_cast<const T*>(ch.out)[i];
+  }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void cheb_store(const ApplyArgs& a, int slot, int act_s, uint8_t cm, T y0, T y1, T y2,
+                                           const ChebOps<T, OP>& o) {
+  const ChebEpi& ch = a.ch;
+  const T ca = sizeof(T) == 4 ? T(ch.af) : T(ch.ad);
+  const T cb = sizeof(T) == 4 ? T(ch.bf) : T(ch.bd);
+  T* out = reinterpret_cast<T*>(ch.out);
+#pragma unroll
+  for (int c = 0; c < ChebOps<T, OP>::NC; ++c) {
+    const int bit = OP == OP_UU ? (1 << c) : 4;
+    const T y = OP == OP_UU ? (c == 0 ? y0 : y1) : y2;
+    const T ye = (act_s == kActZero || (cm & bit)) ? T(0) : y;
+    const int64_t i = c * a.n_slots + slot;
+    if (ch.mode == CHEB_FIRST_RES) {
+      const T ri = o.rhs[c] - ye;
+      reinterpret_cast<T*>(ch.r)[i] = ri;
+      out[i] = cheb_first_of(ca, o.dinv[c], ri);
+      reinterpret_cast<T*>(ch.xprev)[i] = T(0);
+    } else {
+      const T v = cheb_next(o.x[c], o.prev[c], o.dinv[c], o.rhs[c], ye, ca, cb);
+      out[i] = ch.mode == CHEB_STEP_ADD ? o.out[c] + v : v;
+    }
+  }
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(32 * SW_WARPS, sizeof(T) == 4 ? PFF_SW_MINB : PFF_SW_MINB64)
 sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__ units, int32_t nunits) {
@@ -714,7 +768,6 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned FULL = 0xffffffffu;
   pdl_trigger();
-  if (a.pdl_in) pdl_wait();
   const int lane = threadIdx.x & 31;
   SweepStage<T>* ring = reinterpret_cast<SweepStage<T>*>(smem_raw) + (threadIdx.x >> 5) * SW_DEPTH;
   const int unit = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
@@ -801,6 +854,9 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
   // completes it as the lower row; SW_DEPTH - 2 rows are in flight beyond the
   // one being read.  A landed row is first masked by its owners; __syncwarp
   // orders that before the left neighbours read it.
+  // Everything above reads tables that no kernel of a chain writes; the input
+  // vector is the preceding kernel's output
+  if (a.pdl_in) pdl_wait();
 #pragma unroll
   for (int j = 0; j < SW_DEPTH - 1; ++j) issue(j);
 
@@ -820,9 +876,17 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
     if (mask) mask_node<T, OP>(st, lane, ct);
     __syncwarp();
     issue(s + SW_DEPTH - 1);         // into the stage of row s - 1, completed at the previous step
+    const int c0 = r0 - 1 + s, c1 = c0 + SH;   // cell rows (and completed node rows) of the halves
+    const bool owner = s >= 1 && lane >= 1 && lane <= NB;
+    ChebOps<T, OP> ch0, ch1;         // fused Chebyshev store: operands of the two nodes this step stores
+    if constexpr (OP == OP_UU || OP == OP_PP) {
+      if (a.ch.mode != CHEB_OFF && owner) {
+        cheb_load<T, OP>(a, own_base + n + NB * c0, ch0);
+        cheb_load<T, OP>(a, own_base + n + NB * c1, ch1);
+      }
+    }
     NodePair<T> ot, ht;              // upper node row
     load_row<T, OP>(st, lane, ot, ht);
-    const int c0 = r0 - 1 + s, c1 = c0 + SH;   // cell rows (and completed node rows) of the halves
     const bool act0 = cell_active(c0), act1 = cell_active(c1);
     const P ec = a.ecell != nullptr ? sb.e[lane] : pbc(T(1));
     P out[12];
@@ -834,7 +898,6 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
         if (!act1) out[q].y = T(0);
       }
     }
-    const bool owner = s >= 1 && lane >= 1 && lane <= NB;
     if constexpr (OP == OP_VJP) {
       // per-cell values of the cells this strip owns (lower-left node owned)
       if (owner) {
@@ -869,7 +932,12 @@ sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__
         }
         const bool plain0 = cb.x == 0 && w0 == (uint32_t(kActFinal) << 30);   // final value, no partial, free
         const bool plain1 = cb.y == 0 && w1 == (uint32_t(kActFinal) << 30);
-        if (plain0 && plain1) {
+        bool fused = false;
+        if constexpr (OP == OP_UU || OP == OP_PP) fused = a.ch.mode != CHEB_OFF;
+        if (fused) {
+          cheb_store<T, OP>(a, s0, int(w0 >> 30), uint8_t(cb.x), y[0].x, y[1].x, y[2].x, ch0);
+          cheb_store<T, OP>(a, s1, int(w1 >> 30), uint8_t(cb.y), y[0].y, y[1].y, y[2].y, ch1);
+        } else if (plain0 && plain1) {
           if (outU) { yu[s0] = y[0].x; yv[s0] = y[1].x; yu[s1] = y[0].y; yv[s1] = y[1].y; }
           if (outP) { yp[s0] = y[2].x; yp[s1] = y[2].y; }
         } else {
@@ -1168,6 +1236,8 @@ cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
+  // the fused Chebyshev store exists in the Q1 sweep's level operators only
+  if (a.ch.mode != CHEB_OFF && (a.fe_degree != 1 || (op != OP_UU && op != OP_PP))) return cudaErrorInvalidValue;
   if (a.fe_degree == 2) return launch_apply_q2<T>(a, op, s);
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
   switch (op) {

@@ -86,6 +86,25 @@ struct Q2Tab {
   T w[3];
 };
 
+// Chebyshev step fused into the store of a Q1 level apply (OP_UU, OP_PP): instead
+// of y = A x the sweep writes, per level entry i (component blocks of n_slots):
+//   CHEB_STEP       out[i]  = x + a (x - prev) + b dinv (rhs - A x)
+//   CHEB_STEP_ADD   out[i] += the same value
+//   CHEB_FIRST_RES  r[i] = rhs - A x, out[i] = c0 dinv r[i] (c0 in a), xprev[i] = 0
+// with x the apply's input.  No output may alias the input, prev, dinv or rhs.
+enum ChebMode : int { CHEB_OFF = 0, CHEB_STEP = 1, CHEB_STEP_ADD = 2, CHEB_FIRST_RES = 3 };
+struct ChebEpi {
+  int mode;
+  const void* prev;
+  const void* dinv;
+  const void* rhs;
+  void* out;
+  void* r;
+  void* xprev;
+  float af, bf;      // a (or c0) and b in the kernel's precision
+  double ad, bd;
+};
+
 struct ApplyArgs {
   DevLayout lay;
   const DevHanging* hang;
@@ -116,6 +135,7 @@ struct ApplyArgs {
   int fe_degree;
   int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (schedules of DevLayout::units)
   int pdl_in;             // Q1: launched dependent on the preceding kernel, which wrote x (pdl.cuh)
+  ChebEpi ch;             // Q1 level applies: fused Chebyshev store (mode CHEB_OFF: plain y = A x)
 };
 
 struct FixupArgs {

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "cheb.cuh"
 #include "pdl.cuh"
 
 namespace pff {
@@ -28,7 +29,7 @@ __global__ void k_cheb_first(int64_t n, T* x, T* xprev, const T* dinv, const T* 
   pdl_trigger();
   pdl_wait();
   GRID_STRIDE(i, n) {
-    x[i] = c0 * dinv[i] * d[i];
+    x[i] = cheb_first_of(c0, dinv[i], d[i]);
     xprev[i] = T(0);
   }
 }
@@ -39,15 +40,15 @@ __global__ void k_cheb_step(int64_t n, T* xnew, const T* x, const T* xprev, cons
   pdl_trigger();
   pdl_wait();
   GRID_STRIDE(i, n) {
-    const T xi = x[i];
-    xnew[i] = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
+    xnew[i] = cheb_next(x[i], xprev[i], dinv[i], d[i], ax[i], a, b);
   }
 }
 
 template <typename T>
 __global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* __restrict__ ptr,
                            const int32_t* __restrict__ col, const float* __restrict__ val, const T* __restrict__ df,
-                           const T* __restrict__ axf, T* dc, const uint8_t* __restrict__ cmask_c, int fixbits) {
+                           const T* __restrict__ axf, T* dc, const uint8_t* __restrict__ cmask_c, int fixbits,
+                           const T* __restrict__ dinv_c, T* cur_c, T* prev_c, T c0) {
   pdl_trigger();
   pdl_wait();
   GRID_STRIDE(y, nc) {
@@ -59,7 +60,12 @@ __global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, cons
         const int z = col[e];
         acc += T(val[e]) * (df[c * nfs + z] - axf[c * nfs + z]);
       }
-      dc[c * ncs + y] = (cm & bit) ? T(0) : acc;
+      const T v = (cm & bit) ? T(0) : acc;
+      dc[c * ncs + y] = v;
+      if (cur_c != nullptr) {
+        cur_c[c * ncs + y] = cheb_first_of(c0, dinv_c[c * ncs + y], v);
+        prev_c[c * ncs + y] = T(0);
+      }
     }
   }
 }
@@ -124,7 +130,7 @@ __global__ void k_cheb_first_res(int64_t n, T* x, T* xprev, T* r, const T* __res
   pdl_wait();
   GRID_STRIDE(i, n) {
     const T ri = d[i] - ax[i];
-    const T v = c0 * dinv[i] * ri;
+    const T v = cheb_first_of(c0, dinv[i], ri);
     if (xadd != nullptr) {
       xadd[i] += v;
     } else {
@@ -142,9 +148,7 @@ __global__ void k_cheb_step_add(int64_t n, T* xadd, const T* __restrict__ x, con
   pdl_trigger();
   pdl_wait();
   GRID_STRIDE(i, n) {
-    const T xi = x[i];
-    const T v = xi + a * (xi - xprev[i]) + b * dinv[i] * (d[i] - ax[i]);
-    xadd[i] += v;
+    xadd[i] += cheb_next(x[i], xprev[i], dinv[i], d[i], ax[i], a, b);
   }
 }
 
@@ -503,10 +507,10 @@ cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, co
 template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, const int32_t* ptr, const int32_t* col,
                         const float* val, const T* d_f, const T* ax_f, T* d_c, const uint8_t* cmask_c, int fixbits,
-                        cudaStream_t s, bool pdl) {
+                        cudaStream_t s, bool pdl, const T* dinv_c, T* cur_c, T* prev_c, T c0) {
   if (nc > 0)
     return launch_ex(pdl, &k_restrict<T>, blocks_for(nc), TPB, 0, s, nc, ncomp, ncs, nfs, ptr, col, val, d_f, ax_f,
-                     d_c, cmask_c, fixbits);
+                     d_c, cmask_c, fixbits, dinv_c, cur_c, prev_c, c0);
   return cudaGetLastError();
 }
 template <typename T>
@@ -640,7 +644,7 @@ cudaError_t copy64(int64_t n, double* dst, const double* src, cudaStream_t s) {
                                             T, cudaStream_t, bool);                                            \
   template cudaError_t mg_restrict<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,          \
                                       const float*, const T*, const T*, T*, const uint8_t*, int, cudaStream_t, \
-                                      bool);                                                                   \
+                                      bool, const T*, T*, T*, T);                                              \
   template cudaError_t mg_prolong<T>(int32_t, int, int64_t, int64_t, const int32_t*, const int32_t*,           \
                                      const float*, const T*, T*, const uint8_t*, int, cudaStream_t, bool);     \
   template cudaError_t mg_copy_in<T>(int64_t, int, DevHome, const double*, T*, const uint8_t*, int, cudaStream_t); \

@@ -41,11 +41,14 @@ cudaError_t mg_chebyshev_first(int64_t n, T* x, T* xprev, const T* dinv, const T
 template <typename T>
 cudaError_t mg_chebyshev_step(int64_t n, T* xnew, const T* x, const T* xprev, const T* dinv, const T* d,
                               const T* ax, T a, T b, cudaStream_t s, bool pdl = false);
-// d_c[y] += sum_z R[y,z] (d_f[z] - ax_f[z]) over coarse slots; zero on coarse fixed rows
+// d_c[y] += sum_z R[y,z] (d_f[z] - ax_f[z]) over coarse slots; zero on coarse fixed rows.
+// With cur_c set, also the coarse level's first Chebyshev iterate (as
+// mg_chebyshev_first): cur_c = c0 dinv_c d_c, prev_c = 0.
 template <typename T>
 cudaError_t mg_restrict(int32_t nc, int ncomp, int64_t nc_stride, int64_t nf_stride, const int32_t* ptr,
                         const int32_t* col, const float* val, const T* d_f, const T* ax_f, T* d_c,
-                        const uint8_t* cmask_c, int fixbits, cudaStream_t s, bool pdl = false);
+                        const uint8_t* cmask_c, int fixbits, cudaStream_t s, bool pdl = false,
+                        const T* dinv_c = nullptr, T* cur_c = nullptr, T* prev_c = nullptr, T c0 = T(0));
 // x_f[z] += sum_y P[z,y] x_c[y]; zero on fine fixed rows
 template <typename T>
 cudaError_t mg_prolong(int32_t nf, int ncomp, int64_t nf_stride, int64_t nc_stride, const int32_t* ptr,

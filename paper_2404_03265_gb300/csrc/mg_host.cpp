@@ -103,7 +103,8 @@ int chebyshev_degree(double a, double b, double tol = 1e-3, int cap = 64) {
 
 // pdl: launched dependent on the preceding kernel of the stream (the V-cycle chain)
 template <typename T>
-cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl) {
+cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl,
+                        const ChebEpi* ch) {
   pff_problem& pb = *mg.pb;
   const Mesh& M = pb.mesh->m;
   const DevMesh::Level& L = pb.mesh->dev.levels[level];
@@ -127,6 +128,7 @@ cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStr
   a.sweep_sh = pb.sweep_sh;
   a.pdl_in = pdl ? 1 : 0;
   a.mode = MODE_MASK_INPUT;
+  if (ch) a.ch = *ch;
   return launch_apply<T>(a, op, s);
 }
 
@@ -412,38 +414,57 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
   const T* dinv = sizeof(T) == 8 ? reinterpret_cast<const T*>(B.dinv64) : reinterpret_cast<const T*>(B.dinv32);
   cudaError_t e;
 #define VC(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+  // Q1 levels: each Chebyshev step is the store of the level sweep that applies A
+  const bool fuse = mg.fused != 0 && M.k == 1;
+  auto epi = [&](int mode, const T* prev, const T* dinv_l, const T* rhs, T* out, T* r_out, T* xprev_out, double ca,
+                 double cb) {
+    ChebEpi c;
+    std::memset(&c, 0, sizeof(c));
+    c.mode = mode; c.prev = prev; c.dinv = dinv_l; c.rhs = rhs; c.out = out; c.r = r_out; c.xprev = xprev_out;
+    c.af = float(T(ca)); c.bf = float(T(cb)); c.ad = double(T(ca)); c.bd = double(T(cb));
+    return c;
+  };
   VC(cudaMemsetAsync(d, 0, nc * N * sizeof(T), s));
   VC(cudaMemsetAsync(x, 0, nc * N * sizeof(T), s));
   VC(mg_copy_in<T>(nsleaf, nc, D.home, r, d, pb.cmask, B.fixbits, s));
   // Chebyshev on level l over [a, bb], `degree` applications of D^-1: solve A v = rhs
-  // from v = 0 into out (buffers yp, y, t)
-  auto cheb_ab = [&](int l, const T* rhs, T* out, double a, double bb, int degree) -> cudaError_t {
-    const DevLevel& lv = D.levels[l].lv;
-    const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
-    if (!(bb > 0) || degree < 1) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
-    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
-    // three iterates (current, previous, next) rotate roles each step; the start is
-    // chosen so that the last step writes `out`
-    const int steps = degree - 1;
+  // from v = 0 into out (buffers yp, y, t).  The three iterates (current,
+  // previous, next) rotate roles each step; the start is chosen so that the last
+  // step writes `out`.
+  auto cheb_bufs = [&](int64_t o, T* out, int degree, T*& cur, T*& prev, T*& nxt) {
     T* w0 = out;
     T* w1 = yp + o;
     T* w2 = y + o;
-    T *cur, *prev, *nxt;   // each step maps (cur, prev, nxt) to (nxt, cur, prev)
-    switch (steps % 3) {
+    switch ((degree - 1) % 3) {   // each step maps (cur, prev, nxt) to (nxt, cur, prev)
       case 0: cur = w0; prev = w1; nxt = w2; break;
       case 1: cur = w1; prev = w2; nxt = w0; break;
       default: cur = w1; prev = w0; nxt = w2; break;
     }
-    cudaError_t ee = mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s, true);
+  };
+  // first_done: the first iterate was formed with the level's defect (mg_restrict)
+  auto cheb_ab = [&](int l, const T* rhs, T* out, double a, double bb, int degree, bool first_done) -> cudaError_t {
+    const DevLevel& lv = D.levels[l].lv;
+    const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
+    if (!(bb > 0) || degree < 1) return cudaMemsetAsync(out, 0, n * sizeof(T), s);
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    T *cur, *prev, *nxt;
+    cheb_bufs(o, out, degree, cur, prev, nxt);
+    cudaError_t ee = first_done ? cudaSuccess
+                                : mg_chebyshev_first<T>(n, cur, prev, dinv + o, rhs, T(1.0 / theta), s, true);
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
     for (int j = 1; j < degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
-      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
-      if (ee != cudaSuccess) return ee;
       // next = cur + rho_n rho (cur - prev) + 2 rho_n / delta D^-1 (rhs - A cur)
-      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s,
-                                true);
+      if (fuse) {
+        const ChebEpi c = epi(CHEB_STEP, prev, dinv + o, rhs, nxt, nullptr, nullptr, rho_n * rho, 2.0 * rho_n / delta);
+        ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true, &c);
+      } else {
+        ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
+        if (ee == cudaSuccess)
+          ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rhs, t + o, T(rho_n * rho), T(2.0 * rho_n / delta),
+                                    s, true);
+      }
       if (ee != cudaSuccess) return ee;
       T* old_prev = prev;
       prev = cur;
@@ -454,26 +475,38 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     return cudaSuccess;
   };
   // smoothing on level l >= 1: degree mg.degree on [lo, hi] * lambda_max
-  auto cheb = [&](int l, const T* rhs, T* out) -> cudaError_t {
+  auto smooths = [&](int l) { return l >= 1 && B.lam[l] > 0 && mg.degree >= 1; };
+  auto cheb = [&](int l, const T* rhs, T* out, bool first_done) -> cudaError_t {
     const double lam = B.lam[l];
-    return cheb_ab(l, rhs, out, mg.lo * lam, mg.hi * lam, lam > 0 ? mg.degree : 0);
+    return cheb_ab(l, rhs, out, mg.lo * lam, mg.hi * lam, lam > 0 ? mg.degree : 0, first_done);
   };
-  // down sweep
+  // down sweep; with the fused smoother the restriction also forms the coarser
+  // level's first Chebyshev iterate
+  bool first_done = false;
   for (int l = nl - 1; l >= 1; --l) {
     const DevLevel& lv = D.levels[l].lv;
     const DevLevel& lc = D.levels[l - 1].lv;
-    const int64_t o = nc * lv.off;
-    VC(cheb(l, d + o, x + o));
+    const int64_t o = nc * lv.off, oc = nc * lc.off;
+    VC(cheb(l, d + o, x + o, first_done));
     VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true));
-    VC(mg_restrict<T>(lc.n_slots, nc, lc.n_slots, lv.n_slots, lv.R_ptr, lv.R_col, lv.R_val, d + o, t + o,
-                      d + nc * lc.off, mg.cmask + lc.off, B.fixbits, s, true));
+    first_done = fuse && smooths(l - 1);
+    if (first_done) {
+      const double lam = B.lam[l - 1], theta = 0.5 * (mg.lo * lam + mg.hi * lam);
+      T *cur, *prev, *nxt;
+      cheb_bufs(oc, x + oc, mg.degree, cur, prev, nxt);
+      VC(mg_restrict<T>(lc.n_slots, nc, lc.n_slots, lv.n_slots, lv.R_ptr, lv.R_col, lv.R_val, d + o, t + o, d + oc,
+                        mg.cmask + lc.off, B.fixbits, s, true, dinv + oc, cur, prev, T(1.0 / theta)));
+    } else {
+      VC(mg_restrict<T>(lc.n_slots, nc, lc.n_slots, lv.n_slots, lv.R_ptr, lv.R_col, lv.R_val, d + o, t + o, d + oc,
+                        mg.cmask + lc.off, B.fixbits, s, true));
+    }
   }
   // coarse
-  if (mg.coarse_mode == 1) VC(cheb_ab(0, d, x, B.c0_a, B.c0_b, B.c0_deg));
+  if (mg.coarse_mode == 1) VC(cheb_ab(0, d, x, B.c0_a, B.c0_b, B.c0_deg, false));
   else VC(mg_coarse<T>(B.n_coarse, B.coarse_idx, B.coarse_inv, d, x, B.coarse_tmp, s, true));
-  // Post-smoothing on level l of the defect d - A x (t holds A x), from zero,
-  // added to x: the first step forms the defect, the last adds instead of storing.
-  // The level defect d is free once the first step has read it.
+  // Post-smoothing on level l of the defect d - A x, from zero, added to x: the
+  // first step applies A to x and forms the defect, the last adds instead of
+  // storing.  The level defect d is free once the first step has read it.
   auto cheb_post = [&](int l) -> cudaError_t {
     const DevLevel& lv = D.levels[l].lv;
     const int64_t n = nc * int64_t(lv.n_slots), o = nc * lv.off;
@@ -482,26 +515,46 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     if (!(lam > 0) || degree < 1) return cudaSuccess;   // a zero correction
     const double a = mg.lo * lam, bb = mg.hi * lam;
     const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
-    if (degree == 1)
+    cudaError_t ee;
+    if (degree == 1) {
+      // x += c0 D^-1 (d - A x) reads and writes x: never fused
+      ee = level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true);
+      if (ee != cudaSuccess) return ee;
       return mg_chebyshev_first_res<T>(n, nullptr, nullptr, nullptr, dinv + o, d + o, t + o, T(1.0 / theta), x + o, s,
                                        true);
+    }
     T* cur = yp + o;
     T* prev = y + o;
     T* nxt = d + o;
-    cudaError_t ee = mg_chebyshev_first_res<T>(n, cur, prev, rr + o, dinv + o, d + o, t + o, T(1.0 / theta),
-                                               nullptr, s, true);
+    if (fuse) {
+      const ChebEpi c = epi(CHEB_FIRST_RES, nullptr, dinv + o, d + o, cur, rr + o, prev, 1.0 / theta, 0.0);
+      ee = level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true, &c);
+    } else {
+      ee = level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true);
+      if (ee == cudaSuccess)
+        ee = mg_chebyshev_first_res<T>(n, cur, prev, rr + o, dinv + o, d + o, t + o, T(1.0 / theta), nullptr, s,
+                                       true);
+    }
     if (ee != cudaSuccess) return ee;
     double rho = 1.0 / sigma;
     for (int j = 1; j < degree; ++j) {
       const double rho_n = 1.0 / (2.0 * sigma - rho);
-      ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
-      if (ee != cudaSuccess) return ee;
-      if (j == degree - 1)
-        return mg_chebyshev_step_add<T>(n, x + o, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho),
-                                        T(2.0 * rho_n / delta), s, true);
-      ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho), T(2.0 * rho_n / delta), s,
-                                true);
-      if (ee != cudaSuccess) return ee;
+      const bool last = j == degree - 1;
+      if (fuse) {
+        const ChebEpi c = epi(last ? CHEB_STEP_ADD : CHEB_STEP, prev, dinv + o, rr + o, last ? x + o : nxt, nullptr,
+                              nullptr, rho_n * rho, 2.0 * rho_n / delta);
+        ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true, &c);
+        if (ee != cudaSuccess || last) return ee;
+      } else {
+        ee = level_apply<T>(mg, l, block_op(b), cur, t + o, s, true);
+        if (ee != cudaSuccess) return ee;
+        if (last)
+          return mg_chebyshev_step_add<T>(n, x + o, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho),
+                                          T(2.0 * rho_n / delta), s, true);
+        ee = mg_chebyshev_step<T>(n, nxt, cur, prev, dinv + o, rr + o, t + o, T(rho_n * rho), T(2.0 * rho_n / delta),
+                                  s, true);
+        if (ee != cudaSuccess) return ee;
+      }
       T* old_prev = prev;
       prev = cur;
       cur = nxt;
@@ -517,7 +570,6 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
     const int64_t o = nc * lv.off;
     VC(mg_prolong<T>(lv.n_slots, nc, lv.n_slots, lc.n_slots, lv.P_ptr, lv.P_col, lv.P_val, x + nc * lc.off, x + o,
                      mg.cmask + lv.off, B.fixbits, s, true));
-    VC(level_apply<T>(mg, l, block_op(b), x + o, t + o, s, true));
     VC(cheb_post(l));
   }
   VC(mg_copy_out<T>(nsleaf, nc, D.home, x, r, z, pb.cmask, pb.mesh->dev.slot_flags, B.fixbits, s, true));
@@ -614,7 +666,8 @@ cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s) {
   return e;
 }
 
-template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t, bool);
-template cudaError_t level_apply<double>(pff_mg&, int, int, const double*, double*, cudaStream_t, bool);
+template cudaError_t level_apply<float>(pff_mg&, int, int, const float*, float*, cudaStream_t, bool, const ChebEpi*);
+template cudaError_t level_apply<double>(pff_mg&, int, int, const double*, double*, cudaStream_t, bool,
+                                         const ChebEpi*);
 
 }  // namespace pff

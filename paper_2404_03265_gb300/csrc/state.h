@@ -195,6 +195,7 @@ struct pff_mg {
   int degree = 3;                  // Chebyshev degree
   int lanczos_steps = 12;
   int coarse_mode = 0;             // 0: direct FP64 solve on level 0, 1: Chebyshev-Jacobi (Sec. 3.2)
+  int fused = 1;                   // Q1: Chebyshev steps fused into the level sweeps' stores
   double lo = 0.08, hi = 1.2;      // smoothing range [lo, hi] * lambda_max
   pff::DevAllocs mem;
   double* lin64 = nullptr;         // 4 * lev_total (level linearisation)
@@ -290,6 +291,7 @@ cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStr
 cudaError_t mg_precond(pff_mg& mg, const double* v, double* z, cudaStream_t s);
 // level operator y = A_l x of one block (op OP_UU / OP_PP / *_DIAG), precision of T
 template <typename T>
-cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl = false);
+cudaError_t level_apply(pff_mg& mg, int level, int op, const T* x, T* y, cudaStream_t s, bool pdl = false,
+                        const ChebEpi* ch = nullptr);
 
 }  // namespace pff

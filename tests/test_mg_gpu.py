@@ -51,10 +51,14 @@ def test_lambda_estimates(name, frac):
 
 @pytest.mark.parametrize("name,frac", [("tiny", 0.0), ("small", 0.0), ("small", 0.05), ("band4_2_4", 0.0)])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
-def test_vcycle_parity(name, frac, prec, tol):
+@pytest.mark.parametrize("fused", [True, False])
+def test_vcycle_parity(name, frac, prec, tol, fused):
+    """Both smoother paths: Chebyshev steps fused into the level sweeps' stores, and
+    apply and update as separate kernels."""
     import torch
     P, mat, u, phi, phit, active, M = setup_pair(name, frac)
     pb, mg = lib_mg(P, mat, u, phi, phit, active, prec)
+    mg.set_fused_smoother(fused)
     om = P.om
     nn = om.nn
     rng = np.random.default_rng(3)

@@ -532,6 +532,14 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 #ifndef PFF_SW_WARPS
 #define PFF_SW_WARPS 1
 #endif
+// Resident one-warp blocks per SM the compiler must allow (the register cap):
+// 16 (128 registers) for the FP32 leaf Jacobian, whose few spilled bytes cost
+// less than the extra warps gain; 12 for the other FP32 operators, which spill
+// more under that cap; 8 in FP64.  A 3-stage ring keeps 16 warps within the
+// shared memory of an SM.
+#ifndef PFF_SW_MINB_LEAF
+#define PFF_SW_MINB_LEAF 16
+#endif
 #ifndef PFF_SW_MINB
 #define PFF_SW_MINB 12
 #endif
@@ -539,7 +547,7 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 #define PFF_SW_MINB64 8
 #endif
 #ifndef PFF_SW_DEPTH
-#define PFF_SW_DEPTH 4
+#define PFF_SW_DEPTH 3
 #endif
 #ifndef PFF_SW_UNROLL
 #define PFF_SW_UNROLL 2
@@ -547,6 +555,10 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 constexpr int SW_WARPS = PFF_SW_WARPS;   // warps (strips) per block
 constexpr int SW_DEPTH = PFF_SW_DEPTH;   // ring stages per warp
 constexpr int SW_UNROLL = PFF_SW_UNROLL; // unrolled steps of the sweep loop
+template <typename T, int OP>
+constexpr int sw_min_blocks() {
+  return sizeof(T) == 8 ? PFF_SW_MINB64 : (OP == OP_FULL || OP == OP_FULL_T) ? PFF_SW_MINB_LEAF : PFF_SW_MINB;
+}
 
 // ---- asynchronous global -> shared copies (cp.async), per lane
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -759,7 +771,7 @@ __device__ __forceinline__ void cheb_store(const ApplyArgs& a, int slot, int act
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(32 * SW_WARPS, sizeof(T) == 4 ? PFF_SW_MINB : PFF_SW_MINB64)
+__global__ void __launch_bounds__(32 * SW_WARPS, (sw_min_blocks<T, OP>()))
 sweep_q1_kernel(const __grid_constant__ ApplyArgs a, const int32_t* __restrict__ units, int32_t nunits) {
   static_assert(SW_DEPTH >= 3, "the ring holds the lower row, the upper row and at least one row in flight");
   using P = typename VT<T>::T2;

@@ -384,6 +384,9 @@ pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const d
  * for.  Outputs: gp_host[k-1] = dJ/dp_k (host, n_steps), *gGc_host = dJ/dG_c,
  * gE_cells (device, n_leaf_cells, may be NULL) = dJ/dE_K.  Leaves the problem's
  * state, active set and multigrid at step 1; restores the pressure.
+ * The steps must have been solved with phi_tilde = phi[k-1] (the default of
+ * pff_newton_opts); the extrapolated phi_tilde of pff_extrapolate_phi is not
+ * differentiated (its clip makes the step map non-smooth).
  * Synchronises.  Errors as pff_tcv_adjoint.                                  */
 pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t n_steps, const double* const* u,
                                  const double* const* phi, const uint8_t* const* active, const double* p_host,

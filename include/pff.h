@@ -199,13 +199,13 @@ pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam_host, int3
  * lambda_max]; the degree is the smallest with a Chebyshev error bound of 1e-3,
  * at most 64).  Takes effect at the next pff_mg_setup.                         */
 pff_status pff_mg_set_coarse(pff_mg* mg, int32_t mode);
-/* Fused smoother (on = 1, the default): on Q1 meshes each Chebyshev step of the
- * V-cycle (Sec. 3.2) is the store of the level apply that it needs, one launch
- * instead of two; on = 0 runs the apply and the update as separate kernels.  The
- * two round the same expressions; they may differ in the last bit where the
- * compiler contracts the update differently.  Q2 meshes always take the separate
- * kernels.  No paper counterpart: a launch-count choice.  Takes effect at the
- * next V-cycle; PFF_ERR_INVALID_ARG for other values of on.                     */
+/* Fused smoother (on = 1, the default): each Chebyshev step of the V-cycle
+ * (Sec. 3.2) is the store of the level apply that it needs, one launch instead
+ * of two (Q1 and Q2); on = 0 runs the apply and the update as separate kernels.
+ * The two round the same expressions; they may differ in the last bit where the
+ * compiler contracts the update differently.  No paper counterpart: a
+ * launch-count choice.  Takes effect at the next V-cycle; PFF_ERR_INVALID_ARG
+ * for other values of on.                                                      */
 pff_status pff_mg_set_fused_smoother(pff_mg* mg, int32_t on);
 void pff_mg_destroy(pff_mg* mg);
 

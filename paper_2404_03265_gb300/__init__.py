@@ -193,7 +193,7 @@ class MG:
         _lib.check(_lib.lib().pff_mg_setup(self._h, _lib.stream_ptr(stream)))
 
     def set_fused_smoother(self, on):
-        """Q1: Chebyshev steps as the stores of the level applies (True, the default)
+        """Chebyshev steps as the stores of the level applies (True, the default)
         or as separate kernels (False)."""
         _lib.check(_lib.lib().pff_mg_set_fused_smoother(self._h, 1 if on else 0))
 

@@ -1248,8 +1248,8 @@ cudaError_t launch_sweep(const ApplyArgs& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs& a, int op, cudaStream_t s) {
   if (a.lay.nbricks <= 0) return cudaSuccess;
-  // the fused Chebyshev store exists in the Q1 sweep's level operators only
-  if (a.ch.mode != CHEB_OFF && (a.fe_degree != 1 || (op != OP_UU && op != OP_PP))) return cudaErrorInvalidValue;
+  // the fused Chebyshev store exists in the level block operators only
+  if (a.ch.mode != CHEB_OFF && op != OP_UU && op != OP_PP) return cudaErrorInvalidValue;
   if (a.fe_degree == 2) return launch_apply_q2<T>(a, op, s);
   if (a.fe_degree != 1) return cudaErrorInvalidValue;
   switch (op) {

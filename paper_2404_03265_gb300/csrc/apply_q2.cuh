@@ -17,7 +17,8 @@
 //   3. the cells' nodal contributions are added into a shared tile in four
 //      colour phases (cells of equal (i, j) parity share no node), so every
 //      nodal sum has a fixed order;
-//   4. the owned nodes are written (constraint rows, partial sums, holes).
+//   4. the owned nodes are written (constraint rows, partial sums, holes), or
+//      for the level block operators the fused Chebyshev step of ChebEpi.
 
 constexpr int Q2NB = 30;          // owned node slots per side
 constexpr int Q2W = 33;           // window nodes per side (-2..30)
@@ -343,11 +344,20 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
         }
         __syncthreads();
       }
-      // 4. owned nodes
+      // 4. owned nodes (level block operators: or the fused Chebyshev store)
       const int own_base = sm.nb[4];
       for (int o = tid; o < Q2NB * Q2NB; o += Q2T) {
         const int oi = o % Q2NB, oj = o / Q2NB;
         const int w = (oi + 2) + Q2W * (oj + 2);
+        if constexpr (OP == OP_UU || OP == OP_PP) {
+          if (a.ch.mode != CHEB_OFF) {
+            const int act_s = irr >= 0 ? int(__ldg(a.lay.own_act + irr * (Q2NB * Q2NB) + o)) : int(kActFinal);
+            ChebOps<T, OP> co;
+            cheb_load<T, OP>(a, own_base + o, co);
+            cheb_store<T, OP>(a, own_base + o, act_s, sm.cm[w], sm.y[0][w], sm.y[1][w], sm.y[2][w], co);
+            continue;
+          }
+        }
         write_node<T, OP>(a, irr, own_base, oi, oj, sm.cm[w], sm.y[0][w], sm.y[1][w], sm.y[2][w]);
       }
     }

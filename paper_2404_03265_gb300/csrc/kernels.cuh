@@ -86,7 +86,7 @@ struct Q2Tab {
   T w[3];
 };
 
-// Chebyshev step fused into the store of a Q1 level apply (OP_UU, OP_PP): instead
+// Chebyshev step fused into the store of a level apply (OP_UU, OP_PP): instead
 // of y = A x the sweep writes, per level entry i (component blocks of n_slots):
 //   CHEB_STEP       out[i]  = x + a (x - prev) + b dinv (rhs - A x)
 //   CHEB_STEP_ADD   out[i] += the same value
@@ -135,7 +135,7 @@ struct ApplyArgs {
   int fe_degree;
   int sweep_sh;           // Q1 strip half-height: 0 = by mesh size, else 15, 5 or 1 (schedules of DevLayout::units)
   int pdl_in;             // Q1: launched dependent on the preceding kernel, which wrote x (pdl.cuh)
-  ChebEpi ch;             // Q1 level applies: fused Chebyshev store (mode CHEB_OFF: plain y = A x)
+  ChebEpi ch;             // level applies: fused Chebyshev store (mode CHEB_OFF: plain y = A x)
 };
 
 struct FixupArgs {

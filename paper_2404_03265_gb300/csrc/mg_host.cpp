@@ -414,8 +414,8 @@ cudaError_t vcycle_t(pff_mg& mg, int b, const double* r, double* z, cudaStream_t
   const T* dinv = sizeof(T) == 8 ? reinterpret_cast<const T*>(B.dinv64) : reinterpret_cast<const T*>(B.dinv32);
   cudaError_t e;
 #define VC(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
-  // Q1 levels: each Chebyshev step is the store of the level sweep that applies A
-  const bool fuse = mg.fused != 0 && M.k == 1;
+  // each Chebyshev step is the store of the level apply that applies A
+  const bool fuse = mg.fused != 0;
   auto epi = [&](int mode, const T* prev, const T* dinv_l, const T* rhs, T* out, T* r_out, T* xprev_out, double ca,
                  double cb) {
     ChebEpi c;

@@ -195,7 +195,7 @@ struct pff_mg {
   int degree = 3;                  // Chebyshev degree
   int lanczos_steps = 12;
   int coarse_mode = 0;             // 0: direct FP64 solve on level 0, 1: Chebyshev-Jacobi (Sec. 3.2)
-  int fused = 1;                   // Q1: Chebyshev steps fused into the level sweeps' stores
+  int fused = 1;                   // Chebyshev steps fused into the level applies' stores
   double lo = 0.08, hi = 1.2;      // smoothing range [lo, hi] * lambda_max
   pff::DevAllocs mem;
   double* lin64 = nullptr;         // 4 * lev_total (level linearisation)

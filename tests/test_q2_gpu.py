@@ -127,7 +127,10 @@ def test_q2_residual_mass_tcv_gradient_vjp(name):
 
 @pytest.mark.parametrize("name,frac", [("tiny", 0.0), ("small", 0.0), ("band4_2_4", 0.0)])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
-def test_q2_vcycle(name, frac, prec, tol):
+@pytest.mark.parametrize("fused", [True, False])
+def test_q2_vcycle(name, frac, prec, tol, fused):
+    """Q2 V-cycle against the oracle's, with the Chebyshev steps fused into the level
+    applies' stores and as separate kernels."""
     import torch
     from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64
     P = pair(name)
@@ -140,6 +143,7 @@ def test_q2_vcycle(name, frac, prec, tol):
     pb = lib_problem(P, mat, u, phi, phit, active)
     mg = MG(pb, PFF_F64 if prec == "f64" else PFF_F32)
     mg.setup()
+    mg.set_fused_smoother(fused)
     rng = np.random.default_rng(3)
     for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
         lam = mg.lam(b)

@@ -26,12 +26,18 @@ constexpr int Q2C = 16;           // window cells per side (-1..14)
 constexpr int Q2T = Q2C * Q2C;    // threads per block: one per window cell
 constexpr int Q2WW = Q2W * Q2W;
 
+// FP32 keeps two window buffers: while a block computes one brick, the window
+// of its next brick, when regular, streams into the other with cp.async.  FP64
+// (twice the bytes per field) keeps one and gathers each brick in turn.
 template <typename T>
 struct Q2Smem {
-  T f[NF][Q2WW];     // node fields of the window
-  T y[3][Q2WW];      // nodal sums
-  int32_t nb[9];     // storage bases of the 3x3 neighbour bricks
-  uint8_t cm[Q2WW];  // constraint-mask byte of each window node
+  static constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
+  T f[NBUF][NF][Q2WW];      // node fields of the window
+  T y[3][Q2WW];             // nodal sums
+  uint32_t cmw[NBUF][Q2WW]; // prefetch: the aligned word holding each node's constraint byte
+  int32_t nb[NBUF][9];      // storage bases of the 3x3 neighbour bricks
+  uint8_t cmsh[NBUF][Q2WW]; // prefetch: byte position of the constraint byte in its word
+  uint8_t cm[Q2WW];         // constraint-mask byte of each window node of the current brick
 };
 
 // Storage slot of node (n, r) (brick-relative, -2..30) of a brick whose
@@ -135,7 +141,7 @@ __device__ __forceinline__ void q2_point(const Q2Point<T>& q, const MatConst<T>&
 // base + a + Q2W * b.  r[3 * (a + 3 b) + c]: contribution to node (a, b),
 // component c.  cell[]: per-cell values (OP_VJP).
 template <typename T, int OP>
-__device__ __forceinline__ void q2_cell(const Q2Smem<T>& sm, int base, const MatConst<T>& m, const LevGeom<T>& g,
+__device__ __forceinline__ void q2_cell(const T (*fb)[Q2WW], int base, const MatConst<T>& m, const LevGeom<T>& g,
                                         const Q2Tab<T>& tb, T ec, T r[27], T cell[3]) {
   using N = Needs<OP>;
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
@@ -153,7 +159,7 @@ __device__ __forceinline__ void q2_cell(const Q2Smem<T>& sm, int base, const Mat
     for (int fi = 0; fi < 7; ++fi) {
       const int f = FIELDS[fi];
       if (!field_used<OP>(f)) continue;
-      const T* fl = sm.f[f] + base;
+      const T* fl = fb[f] + base;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T v0 = fl[a], v1 = fl[a + Q2W], v2 = fl[a + 2 * Q2W];
@@ -255,6 +261,7 @@ template <> __device__ __forceinline__ const Q2Tab<double>& q2tab<double>(const 
 template <typename T, int OP>
 __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ ApplyArgs a) {
   constexpr bool isVjp = (OP == OP_VJP);
+  constexpr int NBUF = Q2Smem<T>::NBUF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Q2Smem<T>& sm = *reinterpret_cast<Q2Smem<T>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -263,53 +270,102 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
   const Q2Tab<T>& tb = q2tab<T>(a);
   const int ci = tid % Q2C, cj = tid / Q2C;          // window cell (cell ci - 1, cj - 1)
   const int cbase = 2 * ci + Q2W * 2 * cj;            // window node (0, 0) of the cell
+  const int G = int(gridDim.x);
+  // window of regular brick bn into buffer bu: cp.async of every used field and of
+  // the word holding each node's constraint byte; committed as one group
+  auto prefetch = [&](int bn, int bu) {
+    const BrickDesc* bdn = a.lay.bricks + bn;
+    int32_t nbv[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) nbv[i] = __ldg(bdn->nbr_base + i);
+    if (tid < 9) sm.nb[bu][tid] = nbv[tid];
+    for (int w = tid; w < Q2WW; w += Q2T) {
+      const int32_t code = q2_slot(nbv, w % Q2W - 2, w / Q2W - 2);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if (field_used<OP>(f)) cp_one(&sm.f[bu][f][w], field_ptr<T>(a, f) + code);
+      cp_async4(&sm.cmw[bu][w], a.cmask + (code & ~3));
+      sm.cmsh[bu][w] = uint8_t(code & 3);
+    }
+    cp_async_commit();
+  };
+  auto regular = [&](int bn) { return __ldg(&a.lay.bricks[bn].irr) < 0; };
+  int cur = 0;
+  bool pending = false;   // buffer cur holds a prefetch of brick b not yet waited for
+  if (NBUF == 2 && int(blockIdx.x) < a.lay.nbricks && regular(blockIdx.x)) {
+    prefetch(blockIdx.x, 0);
+    pending = true;
+  }
 #pragma unroll 1
-  for (int b = blockIdx.x; b < a.lay.nbricks; b += gridDim.x) {
+  for (int b = blockIdx.x; b < a.lay.nbricks; b += G) {
     const BrickDesc* bd = a.lay.bricks + b;
     const int irr = __ldg(&bd->irr);
     const int level = __ldg(&bd->level);
+    T (*fb)[Q2WW] = sm.f[cur];
+    const int32_t* nbc = sm.nb[cur];
     __syncthreads();   // the previous brick's tiles are no longer read
-    if (tid < 9) sm.nb[tid] = __ldg(bd->nbr_base + tid);
-    __syncthreads();
-    // 1. window node fields (and a zero output tile)
-    for (int w = tid; w < Q2WW; w += Q2T) {
-      const int wx = w % Q2W, wy = w / Q2W;
-      const int32_t code = irr < 0 ? q2_slot(sm.nb, wx - 2, wy - 2) : __ldg(a.lay.win + int64_t(irr) * Q2WW + w);
-      T v[NF];
+    if (pending) {
+      // 1a. the prefetched window: constraint bytes, masked input components, a zero output tile
+      cp_async_wait<0>();
+      for (int w = tid; w < Q2WW; w += Q2T) {
+        const uint8_t cmw = uint8_t((sm.cmw[cur][w] >> (8 * sm.cmsh[cur][w])) & 0xffu);
+        sm.cm[w] = cmw;
+        if (mask && cmw) {
+          if (cmw & 1) fb[F_XU][w] = T(0);
+          if (cmw & 2) fb[F_XV][w] = T(0);
+          if (cmw & 4) fb[F_XP][w] = T(0);
+        }
+        if (!isVjp) { sm.y[0][w] = T(0); sm.y[1][w] = T(0); sm.y[2][w] = T(0); }
+      }
+    } else {
+      if (tid < 9) sm.nb[cur][tid] = __ldg(bd->nbr_base + tid);
+      __syncthreads();
+      // 1b. window node fields (and a zero output tile)
+      for (int w = tid; w < Q2WW; w += Q2T) {
+        const int wx = w % Q2W, wy = w / Q2W;
+        const int32_t code = irr < 0 ? q2_slot(nbc, wx - 2, wy - 2) : __ldg(a.lay.win + int64_t(irr) * Q2WW + w);
+        T v[NF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) v[f] = T(0);
-      uint8_t cmw = 0;
-      if (code >= 0) {
-        cmw = __ldg(a.cmask + code);
+        for (int f = 0; f < NF; ++f) v[f] = T(0);
+        uint8_t cmw = 0;
+        if (code >= 0) {
+          cmw = __ldg(a.cmask + code);
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            if (field_used<OP>(f)) v[f] = ldg(field_ptr<T>(a, f) + code);
+          if (mask && cmw) {
+            if (cmw & 1) v[F_XU] = T(0);
+            if (cmw & 2) v[F_XV] = T(0);
+            if (cmw & 4) v[F_XP] = T(0);
+          }
+        } else if (code != kAbsent) {
+          const DevHanging& h = a.hang[-2 - code];
+#pragma unroll
+          for (int f = F_LU; f < NF; ++f)
+            if (field_used<OP>(f)) v[f] = ldg(field_ptr<T>(a, f) + h.slot);
+          for (int p = 0; p < 3; ++p) {
+            const int ps = h.parent[p];
+            const T wgt = T(h.weight[p]);
+            const uint8_t pc = mask ? __ldg(a.cmask + ps) : uint8_t(0);
+#pragma unroll
+            for (int f = F_XU; f <= F_XP; ++f)
+              if (field_used<OP>(f) && !(pc & (1 << f))) v[f] += wgt * ldg(field_ptr<T>(a, f) + ps);
+          }
+        }
 #pragma unroll
         for (int f = 0; f < NF; ++f)
-          if (field_used<OP>(f)) v[f] = ldg(field_ptr<T>(a, f) + code);
-        if (mask && cmw) {
-          if (cmw & 1) v[F_XU] = T(0);
-          if (cmw & 2) v[F_XV] = T(0);
-          if (cmw & 4) v[F_XP] = T(0);
-        }
-      } else if (code != kAbsent) {
-        const DevHanging& h = a.hang[-2 - code];
-#pragma unroll
-        for (int f = F_LU; f < NF; ++f)
-          if (field_used<OP>(f)) v[f] = ldg(field_ptr<T>(a, f) + h.slot);
-        for (int p = 0; p < 3; ++p) {
-          const int ps = h.parent[p];
-          const T wgt = T(h.weight[p]);
-          const uint8_t pc = mask ? __ldg(a.cmask + ps) : uint8_t(0);
-#pragma unroll
-          for (int f = F_XU; f <= F_XP; ++f)
-            if (field_used<OP>(f) && !(pc & (1 << f))) v[f] += wgt * ldg(field_ptr<T>(a, f) + ps);
-        }
+          if (field_used<OP>(f)) fb[f][w] = v[f];
+        sm.cm[w] = cmw;
+        if (!isVjp) { sm.y[0][w] = T(0); sm.y[1][w] = T(0); sm.y[2][w] = T(0); }
       }
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if (field_used<OP>(f)) sm.f[f][w] = v[f];
-      sm.cm[w] = cmw;
-      if (!isVjp) { sm.y[0][w] = T(0); sm.y[1][w] = T(0); sm.y[2][w] = T(0); }
     }
     __syncthreads();
+    // the next brick's window streams in while this one computes
+    bool next_pending = false;
+    if (NBUF == 2 && b + G < a.lay.nbricks && regular(b + G)) {
+      prefetch(b + G, cur ^ 1);
+      next_pending = true;
+    }
     // 2. one cell per thread
     bool act = true;
     if (irr >= 0) {
@@ -317,14 +373,14 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
       act = (__ldg(a.lay.cellmask + irr * ((Q2T + 31) / 32) + (c >> 5)) >> (c & 31)) & 1u;
     }
     T ec = T(1);
-    if (a.ecell != nullptr && act) ec = ldg(reinterpret_cast<const T*>(a.ecell) + q2_slot(sm.nb, 2 * ci - 2, 2 * cj - 2));
+    if (a.ecell != nullptr && act) ec = ldg(reinterpret_cast<const T*>(a.ecell) + q2_slot(nbc, 2 * ci - 2, 2 * cj - 2));
     T r[27], cell[3];
-    if (act) q2_cell<T, OP>(sm, cbase, mc, geom<T>(a, level), tb, ec, r, cell);
+    if (act) q2_cell<T, OP>(fb, cbase, mc, geom<T>(a, level), tb, ec, r, cell);
     if constexpr (isVjp) {
       // the brick owns the cells whose lower-left node it owns (cells 0..14)
       if (act && ci >= 1 && cj >= 1) {
         T* co = reinterpret_cast<T*>(a.cell_out);
-        const int64_t s = int64_t(sm.nb[4]) + 2 * (ci - 1) + Q2NB * 2 * (cj - 1);
+        const int64_t s = int64_t(nbc[4]) + 2 * (ci - 1) + Q2NB * 2 * (cj - 1);
 #pragma unroll
         for (int q = 0; q < 3; ++q) co[q * a.n_slots + s] = cell[q];
       }
@@ -345,7 +401,7 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
         __syncthreads();
       }
       // 4. owned nodes (level block operators: or the fused Chebyshev store)
-      const int own_base = sm.nb[4];
+      const int own_base = nbc[4];
       for (int o = tid; o < Q2NB * Q2NB; o += Q2T) {
         const int oi = o % Q2NB, oj = o / Q2NB;
         const int w = (oi + 2) + Q2W * (oj + 2);
@@ -361,7 +417,10 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
         write_node<T, OP>(a, irr, own_base, oi, oj, sm.cm[w], sm.y[0][w], sm.y[1][w], sm.y[2][w]);
       }
     }
+    if (NBUF == 2) cur ^= 1;
+    pending = next_pending;
   }
+  cp_async_wait<0>();
 }
 
 template <typename T>

@@ -24,6 +24,8 @@ inline unsigned blocks_for(int64_t n) {
 
 #define GRID_STRIDE(i, n) for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
 
+constexpr int TB = 8;   // transfer-row entries whose loads are issued together
+
 template <typename T>
 __global__ void k_cheb_first(int64_t n, T* x, T* xprev, const T* dinv, const T* d, T c0) {
   pdl_trigger();
@@ -53,14 +55,33 @@ __global__ void k_restrict(int32_t nc, int ncomp, int64_t ncs, int64_t nfs, cons
   pdl_wait();
   GRID_STRIDE(y, nc) {
     const uint8_t cm = cmask_c[y];
+    const int e0 = ptr[y], e1 = ptr[y + 1];
+    // ncomp is 1 or 2: the second sum is acc1
+    T acc0 = dc[y], acc1 = ncomp > 1 ? dc[ncs + y] : T(0);
+    // the row in batches of TB entries: indices and weights, then values, then the
+    // sums in entry order (as one entry at a time)
+    for (int eb = e0; eb < e1; eb += TB) {
+      int z[TB];
+      T w[TB];
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        z[q] = eb + q < e1 ? col[eb + q] : 0;
+        w[q] = eb + q < e1 ? T(val[eb + q]) : T(0);
+      }
+      for (int c = 0; c < ncomp; ++c) {
+        T d[TB];
+#pragma unroll
+        for (int q = 0; q < TB; ++q) d[q] = eb + q < e1 ? df[c * nfs + z[q]] - axf[c * nfs + z[q]] : T(0);
+        T a = c == 0 ? acc0 : acc1;
+#pragma unroll
+        for (int q = 0; q < TB; ++q)
+          if (eb + q < e1) a += w[q] * d[q];
+        if (c == 0) acc0 = a; else acc1 = a;
+      }
+    }
     for (int c = 0; c < ncomp; ++c) {
       const int bit = (fixbits == 4) ? 4 : (1 << c);
-      T acc = dc[c * ncs + y];
-      for (int e = ptr[y]; e < ptr[y + 1]; ++e) {
-        const int z = col[e];
-        acc += T(val[e]) * (df[c * nfs + z] - axf[c * nfs + z]);
-      }
-      const T v = (cm & bit) ? T(0) : acc;
+      const T v = (cm & bit) ? T(0) : (c == 0 ? acc0 : acc1);
       dc[c * ncs + y] = v;
       if (cur_c != nullptr) {
         cur_c[c * ncs + y] = cheb_first_of(c0, dinv_c[c * ncs + y], v);
@@ -78,11 +99,30 @@ __global__ void k_prolong(int32_t nf, int ncomp, int64_t nfs, int64_t ncs, const
   pdl_wait();
   GRID_STRIDE(z, nf) {
     const uint8_t cm = cmask_f[z];
+    const int e0 = ptr[z], e1 = ptr[z + 1];
+    T acc0 = xf[z], acc1 = ncomp > 1 ? xf[nfs + z] : T(0);
+    for (int eb = e0; eb < e1; eb += TB) {
+      int yy[TB];
+      T w[TB];
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        yy[q] = eb + q < e1 ? col[eb + q] : 0;
+        w[q] = eb + q < e1 ? T(val[eb + q]) : T(0);
+      }
+      for (int c = 0; c < ncomp; ++c) {
+        T v[TB];
+#pragma unroll
+        for (int q = 0; q < TB; ++q) v[q] = eb + q < e1 ? xc[c * ncs + yy[q]] : T(0);
+        T a = c == 0 ? acc0 : acc1;
+#pragma unroll
+        for (int q = 0; q < TB; ++q)
+          if (eb + q < e1) a += w[q] * v[q];
+        if (c == 0) acc0 = a; else acc1 = a;
+      }
+    }
     for (int c = 0; c < ncomp; ++c) {
       const int bit = (fixbits == 4) ? 4 : (1 << c);
-      T acc = xf[c * nfs + z];
-      for (int e = ptr[z]; e < ptr[z + 1]; ++e) acc += T(val[e]) * xc[c * ncs + col[e]];
-      xf[c * nfs + z] = (cm & bit) ? T(0) : acc;
+      xf[c * nfs + z] = (cm & bit) ? T(0) : (c == 0 ? acc0 : acc1);
     }
   }
 }

@@ -169,9 +169,10 @@ pff_status pff_set_cell_loop(pff_problem* pb, int32_t strip_half_rows);
  * 2*n_slots doubles), block 1 = phi-phi (n_slots doubles).  Levels are all cells
  * of one refinement level (local smoothing); Chebyshev-accelerated Jacobi
  * smoothing of degree 3 on [0.08, 1.2] * lambda_max, lambda_max from 12 steps of
- * Jacobi-preconditioned CG (FP64); inverse diagonal from cell-local assembly;
- * direct FP64 solve on level 0.  precision selects the V-cycle arithmetic
- * (PFF_F32: applies, smoothing and transfers in FP32).
+ * Jacobi-preconditioned CG (FP64 vectors and coefficients; its operator applies
+ * in the V-cycle's precision on levels >= 1); inverse diagonal from cell-local
+ * assembly (FP64); direct FP64 solve on level 0.  precision selects the V-cycle
+ * arithmetic (PFF_F32: applies, smoothing and transfers in FP32).
  * pff_mg_setup uses the problem's current state and active set (call it after
  * pff_set_state / pff_set_active); it synchronises the stream.  Its per-level
  * work (inverse diagonals, eigenvalue estimates) runs on an internal pool of

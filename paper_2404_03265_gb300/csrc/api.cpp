@@ -337,6 +337,9 @@ extern "C" pff_status pff_mg_lambda(const pff_mg* mg, int32_t block, double* lam
 extern "C" void pff_mg_destroy(pff_mg* mg) {
   if (!mg) return;
   mg_release_graphs(*mg);
+  mg_release_setup_graph(*mg);
+  if (mg->su_side) cudaStreamDestroy(mg->su_side);
+  if (mg->su_chains) cudaEventDestroy(mg->su_chains);
   if (mg->cap_stream) cudaStreamDestroy(mg->cap_stream);
   if (mg->cap_stream2) cudaStreamDestroy(mg->cap_stream2);
   if (mg->ev_fork) cudaEventDestroy(mg->ev_fork);

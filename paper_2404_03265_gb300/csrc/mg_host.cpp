@@ -18,6 +18,7 @@
 #include <cstring>
 #include <unordered_map>
 
+#include "solve.cuh"
 #include "state.h"
 
 namespace pff {
@@ -175,6 +176,138 @@ void mg_release_graphs(pff_mg& mg) {
   if (mg.vc_both) { cudaGraphExecDestroy(mg.vc_both); mg.vc_both = nullptr; }
 }
 
+void mg_release_setup_graph(pff_mg& mg) {
+  if (mg.su_exec) { cudaGraphExecDestroy(mg.su_exec); mg.su_exec = nullptr; }
+  mg.su_key.clear();
+}
+
+// The CG run of one (block, level) chain on stream t.  Its vectors, dot products
+// and coefficients are FP64; the level apply q = A p runs in the V-cycle's
+// precision.  In FP32, p is rounded into and q converted out of two FP32
+// vectors that take the chain's diagonal slot (free once the inverse diagonal is
+// formed): the apply's rounding is relative to its operands, so the small
+// residuals of a converging run keep their accuracy.
+static cudaError_t setup_cg(pff_mg& mg, int b, int l, bool f32, cudaStream_t t) {
+  const DevMesh& D = mg.pb->mesh->dev;
+  const int nl = int(D.levels.size());
+  const int64_t N = D.lev_total;
+  MGBlock& B = mg.blk[b];
+  const DevLevel& lv = D.levels[l].lv;
+  const int64_t nn = B.ncomp * int64_t(lv.n_slots), o = B.ncomp * lv.off, vs = B.ncomp * N;
+  double* r = mg.su_vec[b] + vs + o;
+  double* z = mg.su_vec[b] + 2 * vs + o;
+  double* p = mg.su_vec[b] + 3 * vs + o;
+  double* q = mg.su_vec[b] + 4 * vs + o;
+  float* p32 = reinterpret_cast<float*>(mg.su_vec[b] + o);
+  float* q32 = p32 + nn;
+  const int c = b * nl + l;
+  double* part = mg.su_partial + int64_t(c) * mg_dot_partials();
+  double* sc = mg.su_sc + 8 * c;
+  double* hist = mg.su_hist + 2 * kMaxLanczos * c;
+  const double* dinv = B.dinv64 + o;
+  cudaError_t e = cudaSuccess;
+#define SC(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+  SC(mg_start_vector(lv.n_slots, B.ncomp, D.levels[l].gx, D.levels[l].gy, dinv, r, t));
+  SC(fill64(nn, q, 0.0, t));
+  // z = D^-1 r, rz = r.z, p = z
+  SC(cg_init_scalars(sc, t));
+  SC(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
+  SC(cg_dot_final(part, sc, 0, hist, 0, t));
+  SC(copy64(nn, p, z, t));
+  for (int j = 0; j < mg.lanczos_steps; ++j) {
+    // q = A p; pq, alpha; r -= alpha q, z = D^-1 r, rz_new, beta; p = z + beta p
+    if (f32) {
+      SC(f64_to_f32(nn, p, p32, t));
+      SC(level_apply<float>(mg, l, block_op(b), p32, q32, t));
+      SC(f32_to_f64(nn, q32, q, t));
+    } else {
+      SC(level_apply<double>(mg, l, block_op(b), p, q, t));
+    }
+    SC(dot_partial64(nn, p, q, part, t));
+    SC(cg_dot_final(part, sc, 1, hist, j, t));
+    SC(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
+    SC(cg_dot_final(part, sc, 2, hist, j, t));
+    SC(cg_update_p(nn, p, z, sc, t));
+  }
+#undef SC
+  return e;
+}
+
+// Launches of the set-up chains (section 1 of mg_setup) on the first K pool
+// streams: one chain per (block, level), finest levels first: the inverse
+// diagonal (FP64, cast to both precisions), then the CG run (its applies in the
+// V-cycle's precision; level 0: FP64).
+static cudaError_t launch_setup_chains(pff_mg& mg) {
+  pff_problem& pb = *mg.pb;
+  const DevMesh& D = pb.mesh->dev;
+  const int nl = int(D.levels.size());
+  constexpr int K = pff_mg::kSetupStreams;
+  cudaError_t e = cudaSuccess;
+  int chain = 0;
+  for (int l = nl - 1; l >= 0; --l)
+    for (int b = 0; b < 2; ++b, ++chain) {
+      cudaStream_t t = mg.su_stream[chain % K];
+      MGBlock& B = mg.blk[b];
+      const DevLevel& lv = D.levels[l].lv;
+      const int64_t o = B.ncomp * lv.off;
+      double* diag = mg.su_vec[b] + o;
+      e = level_apply<double>(mg, l, block_diag_op(b), diag, diag, t);
+      if (e == cudaSuccess)
+        e = mg_invert_diag(lv.n_slots, B.ncomp, diag, lv.flags, mg.cmask + lv.off, B.fixbits, B.dinv64 + o,
+                           B.dinv32 + o, t);
+      if (e != cudaSuccess) return e;
+      if (l == 0 && mg.coarse_mode == 0) continue;
+      // level 0 (the Chebyshev coarse solver's interval and degree) applies in FP64
+      e = setup_cg(mg, b, l, mg.precision == PFF_F32 && l > 0, t);
+      if (e != cudaSuccess) return e;
+    }
+  return e;
+}
+
+// What the chains' captured launches depend on besides fixed buffers
+static std::vector<unsigned char> setup_key(const pff_mg& mg) {
+  const pff_problem& pb = *mg.pb;
+  std::vector<unsigned char> k;
+  auto put = [&](const void* v, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(v);
+    k.insert(k.end(), c, c + n);
+  };
+  put(&pb.prm, sizeof(pb.prm));
+  put(&pb.has_ecell, sizeof(pb.has_ecell));
+  put(&pb.lev_ecell64, sizeof(pb.lev_ecell64));
+  put(&pb.lev_ecell32, sizeof(pb.lev_ecell32));
+  put(&pb.sweep_sh, sizeof(pb.sweep_sh));
+  put(&mg.coarse_mode, sizeof(mg.coarse_mode));
+  put(&mg.lanczos_steps, sizeof(mg.lanczos_steps));
+  put(&mg.precision, sizeof(mg.precision));
+  return k;
+}
+
+// Capture the chains: a fork from the capture stream to the pool, the chains, a
+// join back; false (no graph) if any step fails
+static bool capture_setup_chains(pff_mg& mg) {
+  constexpr int K = pff_mg::kSetupStreams;
+  if (!mg.cap_stream && cudaStreamCreateWithFlags(&mg.cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaStreamBeginCapture(mg.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  cudaError_t e = cudaEventRecord(mg.su_start, mg.cap_stream);
+  for (int i = 0; i < K && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(mg.su_stream[i], mg.su_start, 0);
+  if (e == cudaSuccess) e = launch_setup_chains(mg);
+  for (int i = 0; i < K && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(mg.su_done[i], mg.su_stream[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(mg.cap_stream, mg.su_done[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(mg.cap_stream, &g);
+  bool ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+  if (ok) ok = cudaGraphInstantiate(&mg.su_exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    mg.su_exec = nullptr;
+    cudaGetLastError();   // clear a capture error; the chains are launched directly
+  }
+  return ok;
+}
+
 // Lambda_max (and on level 0 the Chebyshev interval) of one (block, level) from
 // the CG coefficients alpha_j, beta_j of its chain: the Lanczos tridiagonal
 // d_j = 1/alpha_j + beta_{j-1}/alpha_{j-1}, e_j = sqrt(beta_j)/alpha_j.
@@ -220,56 +353,45 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
   // 1. One chain per (block, level), finest levels first, spread over the stream
   //    pool: inverse diagonal, then the Jacobi-preconditioned CG run whose
   //    coefficients give lambda_max of D^-1 A on the interior (level 0: only for
-  //    the Chebyshev coarse solver).  The chains share no buffer.
+  //    the Chebyshev coarse solver).  The chains share no buffer.  From the
+  //    second set-up on they replay as one graph on su_side (re-captured when
+  //    their arguments change); the extra pool stream K takes the second coarse
+  //    inversion below either way.
   constexpr int K = pff_mg::kSetupStreams;
   if (!mg.su_start) CK(cudaEventCreateWithFlags(&mg.su_start, cudaEventDisableTiming));
+  if (!mg.su_chains) CK(cudaEventCreateWithFlags(&mg.su_chains, cudaEventDisableTiming));
+  if (!mg.su_side) CK(cudaStreamCreateWithFlags(&mg.su_side, cudaStreamNonBlocking));
   for (int i = 0; i <= K; ++i) {
     if (!mg.su_stream[i]) CK(cudaStreamCreateWithFlags(&mg.su_stream[i], cudaStreamNonBlocking));
     if (!mg.su_done[i]) CK(cudaEventCreateWithFlags(&mg.su_done[i], cudaEventDisableTiming));
   }
-  CK(cudaEventRecord(mg.su_start, s));
-  for (int i = 0; i <= K; ++i) CK(cudaStreamWaitEvent(mg.su_stream[i], mg.su_start, 0));
-  const int np = mg_dot_partials();
-  int chain = 0;
-  for (int l = nl - 1; l >= 0; --l)
-    for (int b = 0; b < 2; ++b, ++chain) {
-      cudaStream_t t = mg.su_stream[chain % K];
-      MGBlock& B = mg.blk[b];
-      const DevLevel& lv = D.levels[l].lv;
-      const int64_t nn = B.ncomp * int64_t(lv.n_slots), o = B.ncomp * lv.off, vs = B.ncomp * N;
-      double* diag = mg.su_vec[b] + o;
-      double* r = mg.su_vec[b] + vs + o;
-      double* z = mg.su_vec[b] + 2 * vs + o;
-      double* p = mg.su_vec[b] + 3 * vs + o;
-      double* q = mg.su_vec[b] + 4 * vs + o;
-      const int c = b * nl + l;
-      double* part = mg.su_partial + int64_t(c) * np;
-      double* sc = mg.su_sc + 8 * c;
-      double* hist = mg.su_hist + 2 * kMaxLanczos * c;
-      CK(level_apply<double>(mg, l, block_diag_op(b), diag, diag, t));
-      CK(mg_invert_diag(lv.n_slots, B.ncomp, diag, lv.flags, mg.cmask + lv.off, B.fixbits, B.dinv64 + o,
-                        B.dinv32 + o, t));
-      B.lam[l] = 0.0;
-      if (l == 0) { B.c0_a = B.c0_b = 0.0; B.c0_deg = 0; }
-      if (l == 0 && mg.coarse_mode == 0) continue;
-      const double* dinv = B.dinv64 + o;
-      CK(mg_start_vector(lv.n_slots, B.ncomp, D.levels[l].gx, D.levels[l].gy, dinv, r, t));
-      CK(fill64(nn, q, 0.0, t));
-      // z = D^-1 r, rz = r.z, p = z
-      CK(cg_init_scalars(sc, t));
-      CK(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
-      CK(cg_dot_final(part, sc, 0, hist, 0, t));
-      CK(copy64(nn, p, z, t));
-      for (int j = 0; j < mg.lanczos_steps; ++j) {
-        // q = A p; pq, alpha; r -= alpha q, z = D^-1 r, rz_new, beta; p = z + beta p
-        CK(level_apply<double>(mg, l, block_op(b), p, q, t));
-        CK(dot_partial64(nn, p, q, part, t));
-        CK(cg_dot_final(part, sc, 1, hist, j, t));
-        CK(cg_update_r_dot(nn, r, z, q, dinv, sc, part, t));
-        CK(cg_dot_final(part, sc, 2, hist, j, t));
-        CK(cg_update_p(nn, p, z, sc, t));
-      }
+  for (int b = 0; b < 2; ++b) {
+    MGBlock& B = mg.blk[b];
+    for (int l = 0; l < nl; ++l) B.lam[l] = 0.0;
+    B.c0_a = B.c0_b = 0.0;
+    B.c0_deg = 0;
+  }
+  bool replay = false;
+  if (mg.su_graph_ok && mg.su_setups > 0) {
+    std::vector<unsigned char> key = setup_key(mg);
+    if (mg.su_exec && key != mg.su_key) mg_release_setup_graph(mg);
+    if (!mg.su_exec) {
+      if (capture_setup_chains(mg)) mg.su_key = key;
+      else mg.su_graph_ok = false;
     }
+    replay = mg.su_exec != nullptr;
+  }
+  ++mg.su_setups;
+  CK(cudaEventRecord(mg.su_start, s));
+  CK(cudaStreamWaitEvent(mg.su_stream[K], mg.su_start, 0));
+  if (replay) {
+    CK(cudaStreamWaitEvent(mg.su_side, mg.su_start, 0));
+    CK(cudaGraphLaunch(mg.su_exec, mg.su_side));
+    CK(cudaEventRecord(mg.su_chains, mg.su_side));
+  } else {
+    for (int i = 0; i < K; ++i) CK(cudaStreamWaitEvent(mg.su_stream[i], mg.su_start, 0));
+    CK(launch_setup_chains(mg));
+  }
   // 2. Direct coarse solve: the dense level-0 block of each block by probing with
   //    (2k+1)^2 colours per component (all probes applied in one batch on s, beside
   //    the chains), assembled on the host and inverted on the device.
@@ -374,10 +496,16 @@ std::string mg_setup(pff_mg& mg, cudaStream_t s) {
       CK(mg_spd_invert(B.n_coarse, B.coarse_inv, B.coarse_rc, mg.spd_bad + b, t));
     }
   }
-  // 3. join the pool, read the CG coefficients (and coarse status) once
-  for (int i = 0; i <= K; ++i) {
-    CK(cudaEventRecord(mg.su_done[i], mg.su_stream[i]));
-    CK(cudaStreamWaitEvent(s, mg.su_done[i], 0));
+  // 3. join the chains and the pool, read the CG coefficients (and coarse status) once
+  if (replay) {
+    CK(cudaStreamWaitEvent(s, mg.su_chains, 0));
+    CK(cudaEventRecord(mg.su_done[K], mg.su_stream[K]));
+    CK(cudaStreamWaitEvent(s, mg.su_done[K], 0));
+  } else {
+    for (int i = 0; i <= K; ++i) {
+      CK(cudaEventRecord(mg.su_done[i], mg.su_stream[i]));
+      CK(cudaStreamWaitEvent(s, mg.su_done[i], 0));
+    }
   }
   std::vector<double> hist(size_t(2) * nl * 2 * kMaxLanczos);
   int32_t bad[2] = {0, 0};

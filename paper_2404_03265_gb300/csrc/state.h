@@ -210,6 +210,15 @@ struct pff_mg {
   cudaStream_t su_stream[kSetupStreams + 1] = {};
   cudaEvent_t su_done[kSetupStreams + 1] = {};
   cudaEvent_t su_start = nullptr;
+  // The chains' launches are captured once as a graph and replayed by later
+  // set-ups on su_side while their arguments hold (su_key: the material, the
+  // modulus buffers, the cell-loop schedule and the coarse mode they bake in).
+  cudaGraphExec_t su_exec = nullptr;
+  std::vector<unsigned char> su_key;
+  cudaStream_t su_side = nullptr;
+  cudaEvent_t su_chains = nullptr;
+  int su_setups = 0;               // set-ups run so far (the first one launches directly)
+  bool su_graph_ok = true;
   double* su_vec[2] = {nullptr, nullptr};
   double *su_partial = nullptr, *su_sc = nullptr, *su_hist = nullptr;
   // coarse probing: all colours of both blocks at once (in and out, probe_len doubles each)
@@ -285,6 +294,8 @@ cudaError_t cells_gather(int32_t n, const double* in, const int32_t* slot, doubl
 // multigrid (mg_host.cpp)
 std::string mg_alloc(pff_mg& mg);
 void mg_release_graphs(pff_mg& mg);
+// the set-up chains' graph (re-captured at the next set-up)
+void mg_release_setup_graph(pff_mg& mg);
 std::string mg_setup(pff_mg& mg, cudaStream_t s);
 cudaError_t mg_vcycle(pff_mg& mg, int block, const double* r, double* z, cudaStream_t s);
 // both blocks of the preconditioner on the full vector (u_x | u_y | phi)

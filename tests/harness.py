@@ -92,3 +92,9 @@ def rel_err(a, b):
     inf = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
     two = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
     return inf, two
+
+
+# lambda_max parity: the FP64 V-cycle's estimates come from FP64 CG runs (the
+# oracle's arithmetic); the FP32 V-cycle's CG applies its level operators (levels
+# >= 1) in FP32, which moves lambda by FP32 rounding of the operator
+LAMBDA_RTOL = {"f64": 1e-9, "f32": 5e-6}

@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 import synthetic as synth
-from harness import Pair, oracle_apply, random_active, random_linearisation, rel_err
+from harness import LAMBDA_RTOL, Pair, oracle_apply, random_active, random_linearisation, rel_err
 from oracle import adjoint as adj
 from oracle import mg as omg
 from oracle import operators as ops
@@ -133,7 +133,7 @@ def test_vcycle_with_cell_modulus(name, prec, tol):
     for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
         lam = mg.lam(b)
         ref = np.array([0.0] + [M.B[blk][l].lam for l in range(1, len(M.B[blk]))])
-        assert np.allclose(lam[1:], ref[1:], rtol=1e-9, atol=1e-300), (blk, lam, ref)
+        assert np.allclose(lam[1:], ref[1:], rtol=LAMBDA_RTOL[prec], atol=1e-300), (blk, lam, ref)
         r = rng.normal(size=(nn, nc))
         zref = M.vcycle(blk, np.concatenate([r[:, c] for c in range(nc)]))
         zref = np.stack([zref[c * nn:(c + 1) * nn] for c in range(nc)], 1)

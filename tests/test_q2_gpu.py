@@ -1,13 +1,13 @@
 """Parity of the Q2 (k = 2) operators through the C-ABI with the oracle: leaf
 Jacobian, transpose and condensed apply (1e-12 FP64, 1e-5 FP32), residual,
 lumped mass and TCV (1e-12), cell modulus, TCV gradient and parameter VJP
-(1e-12), the block V-cycle (lambda_max 1e-9, V-cycle 1e-10 FP64, 1e-5 FP32) and
+(1e-12), the block V-cycle (lambda_max 1e-9 FP64 and LAMBDA_RTOL FP32, V-cycle 1e-10 FP64, 1e-5 FP32) and
 a Sneddon load step of Algorithm 2 (same active set, u and phi within 1e-7)."""
 import numpy as np
 import pytest
 
 import synthetic as synth
-from harness import Pair, oracle_apply, random_active, random_linearisation, rel_err
+from harness import LAMBDA_RTOL, Pair, oracle_apply, random_active, random_linearisation, rel_err
 from oracle import adjoint as adj
 from oracle import mg as omg
 from oracle import operators as ops
@@ -148,7 +148,7 @@ def test_q2_vcycle(name, frac, prec, tol, fused):
     for b, blk, nc in ((0, "uu", 2), (1, "pp", 1)):
         lam = mg.lam(b)
         ref = np.array([0.0] + [M.B[blk][l].lam for l in range(1, len(M.B[blk]))])
-        assert np.allclose(lam[1:], ref[1:], rtol=1e-9, atol=1e-300), (blk, lam, ref)
+        assert np.allclose(lam[1:], ref[1:], rtol=LAMBDA_RTOL[prec], atol=1e-300), (blk, lam, ref)
         r = rng.normal(size=(nn, nc))
         zref = M.vcycle(blk, np.concatenate([r[:, c] for c in range(nc)]))
         zref = np.stack([zref[c * nn:(c + 1) * nn] for c in range(nc)], 1)

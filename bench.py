@@ -768,8 +768,9 @@ def main():
             "unit": "s/load step", "newton_tol": 1e-8, "gmres_rtol": 1e-6,
             "fp32_mg": r32, "fp32_mg_fp64_matvec": r32d, "fp32_mg_chebyshev_coarse": r32c, "fp64_mg": r64,
             "note": "fp32_mg: V-cycle and the Jacobian applies inside GMRES in FP32 (Krylov basis, "
-                    "orthogonalisation, Givens, residual, line search, active set, lambda_max and coarse solve in "
-                    "FP64); fp32_mg_fp64_matvec: FP32 V-cycle only; fp32_mg_chebyshev_coarse: the same with the "
+                    "orthogonalisation, Givens, residual, line search, active set and coarse solve in FP64; the "
+                    "lambda_max CG in FP64 with FP32 level applies); fp32_mg_fp64_matvec: FP32 V-cycle only; "
+                    "fp32_mg_chebyshev_coarse: the same with the "
                     "Chebyshev-Jacobi coarse solver instead of the direct one; fp64_mg: everything in FP64. "
                     "Per step: s_mg_setup and s_gmres are host wall seconds; s_gmres_apply, s_gmres_vcycle and "
                     "s_gmres_orth are device seconds (CUDA events) of the operator applies, block V-cycles and "

@@ -176,8 +176,11 @@ pff_status pff_set_cell_loop(pff_problem* pb, int32_t strip_half_rows);
  * pff_mg_setup uses the problem's current state and active set (call it after
  * pff_set_state / pff_set_active); it synchronises the stream.  Its per-level
  * work (inverse diagonals, eigenvalue estimates) runs on an internal pool of
- * streams that is joined back into `stream` before it returns; the level-0
- * blocks are assembled by probing and inverted on the device.
+ * streams that is joined back into `stream` before it returns (from the second
+ * set-up on, replayed as one captured graph while the material, the modulus, the
+ * cell-loop shape and the coarse mode are unchanged); the level-0 blocks are
+ * assembled by probing and inverted on the device (blocked Gauss-Jordan, two
+ * launches per 32 pivots).
  * pff_vcycle: z = MG(r) for one block; fixed leaf DoFs (Dirichlet u, active phi)
  * get z = r, hanging entries and holes 0.  r and z are device vectors.          */
 pff_status pff_mg_create(pff_problem* pb, int32_t precision, pff_mg** out);
@@ -316,7 +319,9 @@ pff_status pff_tcv(pff_problem* pb, const double* u, const double* phi, double* 
 pff_status pff_cod(pff_problem* pb, const double* u, const double* phi, const double* x_host, int32_t n_x,
                    double* cod_host, void* stream);
 /* Left-preconditioned GMRES on G~ x = rhs (transpose != 0: G~^T) with the block
- * V-cycle preconditioner of mg, x0 = 0; synchronises.  Errors:
+ * V-cycle preconditioner of mg, x0 = 0; synchronises.  The Krylov basis (FP64,
+ * restart + 1 vectors) holds the node rows only; rhs and x are slot-layout
+ * vectors (x is 0 on holes).  Errors:
  * PFF_ERR_NOT_CONVERGED, PFF_ERR_GMRES_BREAKDOWN, PFF_ERR_NONFINITE (info filled). */
 pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
                            double rtol, int32_t restart, int32_t maxiter, pff_solve_info* info, void* stream);

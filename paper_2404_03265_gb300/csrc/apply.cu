@@ -15,10 +15,12 @@
 // lower and upper halves advance one cell row per step side by side, so every
 // sum-factorised 2x2 Gauss operation of the two cells is one paired FP32
 // instruction (FFMA2 / FADD2 / FMUL2) with no per-member index arithmetic.
-// Neighbouring lanes exchange node values and nodal contributions with
-// shuffles; there is no block barrier and no shared memory.  Input x has its
-// hanging-node constraints resolved on the fly and fixed components masked.
-// Each owned node is written once, by one lane, in a fixed summation order.
+// Node rows stream into a per-warp cp.async ring in shared memory; a lane reads
+// its right neighbour's node values there and receives its left neighbour's
+// nodal contributions by shuffle; there is no block barrier.  Fixed input
+// components are masked in the ring; the input of hanging nodes (C x) comes from
+// a pre-pass kernel.  Each owned node is written once, by one lane, in a fixed
+// summation order.
 // Nodes shared with another level, hanging nodes and their parents write
 // partial sums; a small fix-up kernel condenses them (x_full = C x on input,
 // C^T y on output).  No atomics.
@@ -518,14 +520,14 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 // r0+2SH-1) are swept upwards side by side, one cell row each per step: they are
 // the two members of every packed operation.  A half needs SH + 1 cell rows (its
 // own and the one below), so a step reads one new node row per half.  The right
-// neighbour's node values come by shuffle; the contributions of the left
-// neighbour's cell by shuffle, those of the cell row below as a carry in
+// neighbour's node values are read from the ring; the contributions of the left
+// neighbour's cell come by shuffle, those of the cell row below as a carry in
 // registers.  Each owned node is completed once, by its own lane, in the fixed
 // order ((carry + left lower-right) + own lower-left); the carry is (own
 // upper-left + left upper-right).
 // Node rows stream HBM -> shared memory through a per-warp cp.async ring,
-// SW_DEPTH - 1 rows ahead of the arithmetic; each lane copies and reads only its
-// own column, so the ring needs no barrier.
+// SW_DEPTH - 1 rows ahead of the arithmetic; each lane copies its own column,
+// and __syncwarp orders its in-place masking before its left neighbour reads it.
 
 // One warp per block: the block scheduler then fills each SM's free warp slots
 // one unit at a time, which evens out the mix of long and short units per SM.
@@ -533,9 +535,8 @@ __device__ __forceinline__ void write_node(const ApplyArgs& a, int irr, int own_
 #define PFF_SW_WARPS 1
 #endif
 // Resident one-warp blocks per SM the compiler must allow (the register cap):
-// 16 (128 registers) for the FP32 leaf Jacobian, whose few spilled bytes cost
-// less than the extra warps gain; 12 for the other FP32 operators, which spill
-// more under that cap; 8 in FP64.  A 3-stage ring keeps 16 warps within the
+// 16 (128 registers) for the FP32 leaf Jacobian, which fits them; 12 for the
+// other FP32 operators, which would spill under that cap; 8 in FP64.  A 3-stage ring keeps 16 warps within the
 // shared memory of an SM.
 #ifndef PFF_SW_MINB_LEAF
 #define PFF_SW_MINB_LEAF 16

@@ -114,3 +114,8 @@ def test_invalid_arguments_are_reported():
     assert L.pff_apply(pb._h, 0, 0, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(xu), _lib.ptr(yp), None) == INVALID_ARG
     assert L.pff_set_cell_loop(pb._h, 4) == INVALID_ARG
     assert L.pff_apply(pb._h, 0, 0, _lib.ptr(xu), _lib.ptr(xp), _lib.ptr(yu), _lib.ptr(yp), None) == 0
+    from paper_2404_03265_gb300 import MG, PFF_F32
+    mg = MG(pb, PFF_F32)
+    assert L.pff_mg_set_fused_smoother(mg._h, 2) == INVALID_ARG
+    assert L.pff_mg_set_coarse(mg._h, 5) == INVALID_ARG
+    assert L.pff_mg_set_fused_smoother(mg._h, 0) == 0

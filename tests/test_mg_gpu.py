@@ -189,3 +189,41 @@ def test_vcycle_parity_every_strip_schedule(name, frac, prec, tol):
             assert inf < tol and two < tol, (sched, blk, prec, inf, two)
     for b, zs in outs.items():
         assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2]), b
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_setup_graph_replay(prec):
+    """From its second set-up on, an MG replays its set-up chains as a captured graph,
+    re-captured when the pressure (a constant baked into the launches) changes.  After
+    a pressure change the replaying MG gives bitwise the lambda estimates and V-cycle
+    outputs of a fresh MG set up directly at the new pressure, and a further replay
+    gives them again."""
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, PFF_F64
+    P, mat, u, phi, phit, active, M = setup_pair("small", 0.05)
+    pb, mg = lib_mg(P, mat, u, phi, phit, active, prec)   # first set-up: direct launches
+    p2 = 0.5 * mat["p"]
+    pb.set_pressure(p2)
+    mg.setup()                                              # key changed: capture, then replay
+
+    def state(m):
+        nn = P.om.nn
+        rng = np.random.default_rng(7)
+        out = [m.lam(0), m.lam(1)]
+        for b, nc in ((0, 2), (1, 1)):
+            rs = P.to_slots(rng.normal(size=(nn, nc)))
+            rt = torch.tensor(rs.T.copy() if nc == 2 else rs[:, 0].copy(), device="cuda")
+            zt = torch.full_like(rt, float("nan"))
+            m.vcycle(b, rt, zt)
+            torch.cuda.synchronize()
+            out.append(zt.cpu().numpy())
+        return out
+
+    a = state(mg)
+    mg.setup()                                              # same key: replay
+    b = state(mg)
+    mat2 = dict(mat, p=p2)
+    pb2, mg2 = lib_mg(P, mat2, u, phi, phit, active, prec)
+    c = state(mg2)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)

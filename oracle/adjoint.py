@@ -146,10 +146,26 @@ def phit_vjp(mesh, mat, st, w):
     return mesh.C.T @ out
 
 
-def tcv_adjoint_steps(mesh, mats, us, phis, actives, E_cells=None):
+def extrapolated_phit(phis, n):
+    """phi_tilde of step n >= 2 by linear extrapolation in the step index, clipped
+    to [0, 1] (the reading of Sec. 2's "extrapolation"; oracle/solvers.extrapolate_phi
+    restated here so that this module keeps its own arithmetic), and the mask chi
+    of its nodes strictly inside (0, 1), where its derivatives in phi^(n-1) and
+    phi^(n-2) are 2 and -1 (0 where the clip acts)."""
+    raw = 2.0 * phis[n - 1] - phis[n - 2]
+    return np.clip(raw, 0.0, 1.0), ((raw > 0.0) & (raw < 1.0)).astype(np.float64)
+
+
+def tcv_adjoint_steps(mesh, mats, us, phis, actives, E_cells=None, extrapolate=False):
     """Gradient of J = TCV(U^N) after N load steps (Algorithm 2, phi_tilde and the
     obstacle of step n are phi^(n-1)) with respect to each step's pressure p_n,
     G_c and E_K.
+
+    extrapolate: phi_tilde of step n >= 2 is clip(2 phi^(n-1) - phi^(n-2), 0, 1)
+    instead (step 1 keeps phi^0; the obstacle stays phi^(n-1)).  The phi_tilde
+    sensitivity v^n = C^T (dA/dphi~)^T C M_f mu^n then reaches step n-1 as
+    -2 chi v^n and step n-2 as +chi v^n (chi: the unclipped nodes); what reaches
+    phi^0 is dropped (the initial state does not depend on the parameters).
 
     mats[n-1]: Material of step n; us[n], phis[n]: converged state of step n
     (n = 0: the initial state, u = 0 and phi = phi^0, independent of the
@@ -166,17 +182,25 @@ def tcv_adjoint_steps(mesh, mats, us, phis, actives, E_cells=None):
     nn = mesh.nn
     N = len(mats)
     C = ops.C3(mesh)
-    st = ops.State(mesh, us[N], phis[N], phis[N - 1], E_cells)
+
+    def phit_of(n):
+        if extrapolate and n >= 2:
+            return extrapolated_phit(phis, n)
+        return phis[n - 1], None
+
+    st = ops.State(mesh, us[N], phis[N], phit_of(N)[0], E_cells)
     gbar = C.T @ tcv_gradient(mesh, st)
     gbar[:nn][mesh.dirichlet] = 0.0
     gbar[nn:2 * nn][mesh.dirichlet] = 0.0
     g_p = np.zeros(N)
     g_gc = 0.0
     g_e = np.zeros(len(mesh.cells))
+    pend = None   # phi sensitivity from step n + 1 that reaches step n - 1
     for n in range(N, 0, -1):
         mat = mats[n - 1]
         act = np.asarray(actives[n - 1], bool)
-        st = ops.State(mesh, us[n], phis[n], phis[n - 1], E_cells)
+        phit, chi = phit_of(n)
+        st = ops.State(mesh, us[n], phis[n], phit, E_cells)
         K = (C.T @ ops.assemble_jacobian(mesh, mat, st) @ C).tocsc()
         free = ops.free_dofs(mesh, act)
         fixed = ops.fixed_dofs(mesh, act)
@@ -191,7 +215,11 @@ def tcv_adjoint_steps(mesh, mats, us, phis, actives, E_cells=None):
         g_gc += b
         g_e += c
         if n > 1:
+            v = phit_vjp(mesh, mat, st, wf)
             gbar = np.zeros(3 * nn)
-            gbar[2 * nn:] = -phit_vjp(mesh, mat, st, wf)
+            gbar[2 * nn:] = -v if chi is None else -2.0 * chi * v
             gbar[2 * nn:][act] += mu[2 * nn:][act]
+            if pend is not None:
+                gbar[2 * nn:] += pend
+            pend = chi * v if (chi is not None and n - 2 >= 1) else None
     return dict(p=g_p, Gc=g_gc, E=g_e)

@@ -222,3 +222,67 @@ def test_multi_step_adjoint_central_difference():
         Em[c] -= hh
         fd = (J(base, ps, Ep) - J(base, ps, Em)) / (2 * hh)
         assert abs(fd - g["E"][c]) <= 1e-5 * abs(fd), (c, fd, g["E"][c])
+
+
+def sneddon_steps_extrapolated(om, base, E, ps, tol=1e-13):
+    """sneddon_steps with phi_tilde of step n >= 2 extrapolated from the two previous
+    steps (clip(2 phi^(n-1) - phi^(n-2), 0, 1), oracle/solvers.extrapolate_phi);
+    returns mats, us, phis, actives and the clip masks of steps 2..N."""
+    h = om.h_min_diag()
+    u0, po = solvers.sneddon_initial(om, h)
+    mats, us, phis, acts, chis = [], [u0], [po], [], []
+    u, phi, act = u0, po.copy(), None
+    for n, p in enumerate(ps, start=1):
+        mat = ops.Material(**dict(base, p=p))
+        phit = None
+        if n >= 2:
+            phit = solvers.extrapolate_phi(phis[-1], phis[-2])
+            raw = 2.0 * phis[-1] - phis[-2]
+            chis.append((raw > 0.0) & (raw < 1.0))
+        u, phi_new, act, info = solvers.load_step(om, mat, 1e4, u, phi.copy(), phi, active_prev=act, E_cells=E,
+                                                  tol=tol, atol=1e-15, gmres_rtol=1e-12, phi_tilde=phit)
+        assert info.converged
+        phi = phi_new
+        mats.append(mat)
+        us.append(u)
+        phis.append(phi)
+        acts.append(act)
+    return mats, us, phis, acts, chis
+
+
+def test_multi_step_adjoint_extrapolated_phi_tilde():
+    """Three load steps whose phi_tilde (Sec. 2) is extrapolated from the two previous
+    steps: dJ/dp_n and dJ/dG_c of the final TCV from one backward sweep against central
+    differences of three-step solves (relative step 1e-6, bound 1e-5), active sets and
+    clip pattern unchanged under the perturbations.  The gradient differs from the one
+    with phi_tilde = phi_old of the same states (the extrapolation's two-step coupling
+    matters)."""
+    om = mesh("tiny")
+    E = cell_E(om)
+    base = dict(E=1.0, nu=0.2, Gc=1.0, eps=2.0 * om.h_min_diag(), kappa=1e-10)
+    ps = [0.1, 0.15, 0.2]
+    mats, us, phis, acts, chis = sneddon_steps_extrapolated(om, base, E, ps)
+    assert all(c.any() for c in chis)
+    g = adj.tcv_adjoint_steps(om, mats, us, phis, acts, E, extrapolate=True)
+    g_old = adj.tcv_adjoint_steps(om, mats, us, phis, acts, E)
+    assert np.max(np.abs(g["p"] - g_old["p"])) > 1e-2 * np.max(np.abs(g["p"]))
+
+    def J(bkw, pss):
+        _, uu, pp, aa, cc = sneddon_steps_extrapolated(om, bkw, E, pss)
+        for a0, a1 in zip(aa, acts):
+            assert np.array_equal(a0, a1), "active set changed under the perturbation"
+        for c0, c1 in zip(cc, chis):
+            assert np.array_equal(c0, c1), "clip pattern changed under the perturbation"
+        return ops.tcv(om, ops.State(om, uu[-1], pp[-1], pp[-1]))
+
+    rel = 1e-6
+    for n in range(len(ps)):
+        hh = rel * ps[n]
+        pp_, pm_ = list(ps), list(ps)
+        pp_[n] += hh
+        pm_[n] -= hh
+        fd = (J(base, pp_) - J(base, pm_)) / (2 * hh)
+        assert abs(fd - g["p"][n]) <= 1e-5 * abs(fd), (n, fd, g["p"][n])
+    hh = rel * base["Gc"]
+    fd = (J(dict(base, Gc=base["Gc"] + hh), ps) - J(dict(base, Gc=base["Gc"] - hh), ps)) / (2 * hh)
+    assert abs(fd - g["Gc"]) <= 1e-5 * abs(fd), (fd, g["Gc"])

@@ -377,9 +377,16 @@ pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const d
                            const uint8_t* active, double rtol, int32_t restart, int32_t maxiter, double* gE_cells,
                            double* g_host, pff_solve_info* info, void* stream);
 
+/* phi_tilde of the load steps that pff_tcv_adjoint_steps differentiates. */
+#define PFF_PHIT_PREVIOUS 0     /* phi_tilde of step k = phi[k-1] (the obstacle)          */
+#define PFF_PHIT_EXTRAPOLATED 1 /* step k >= 2: clip(2 phi[k-1] - phi[k-2], 0, 1), as
+                                   pff_extrapolate_phi; step 1: phi[0]                     */
+
 /* Checkpointed adjoint of J = TCV(U^N) over n_steps load steps of Algorithm 2,
- * step k (1..N) solved from phi_old = phi_tilde = phi[k-1] at pressure
- * p_host[k-1] with final active set active[k-1]:
+ * step k (1..N) solved from phi_old = phi[k-1] (its obstacle) at pressure
+ * p_host[k-1] with final active set active[k-1], and phi_tilde per
+ * phi_tilde_mode (PFF_PHIT_PREVIOUS or PFF_PHIT_EXTRAPOLATED, the choice the
+ * steps were solved with; Sec. 2 allows the old step or an extrapolation):
  *   u[k], phi[k] (k = 0..N): host arrays of device pointers to the converged
  *   states (u: 2*n_slots, phi: n_slots doubles; k = 0 is the initial state);
  *   active[k] (k = 0..N-1): host array of device pointers (n_slots bytes).
@@ -387,17 +394,20 @@ pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double* u, const d
  * to the previous one through phi_tilde (the degradation and pressure terms of
  * the u-equation) and through its active rows (obstacle phi[k-1]); the free rows
  * of a step still see the active values, which the active-row adjoint accounts
- * for.  Outputs: gp_host[k-1] = dJ/dp_k (host, n_steps), *gGc_host = dJ/dG_c,
+ * for.  Extrapolated, the phi_tilde share reaches step k-1 with weight 2 and step
+ * k-2 with weight -1 on the slots strictly inside the clip (the derivative of
+ * the clip there; 0 on clipped slots, the one-sided choice at the kinks); the
+ * share that reaches phi[0] is dropped (the initial state is parameter-free).
+ * Outputs: gp_host[k-1] = dJ/dp_k (host, n_steps), *gGc_host = dJ/dG_c,
  * gE_cells (device, n_leaf_cells, may be NULL) = dJ/dE_K.  Leaves the problem's
  * state, active set and multigrid at step 1; restores the pressure.
- * The steps must have been solved with phi_tilde = phi[k-1] (the default of
- * pff_newton_opts); the extrapolated phi_tilde of pff_extrapolate_phi is not
- * differentiated (its clip makes the step map non-smooth).
- * Synchronises.  Errors as pff_tcv_adjoint.                                  */
+ * Synchronises.  Errors as pff_tcv_adjoint; PFF_ERR_INVALID_ARG on another
+ * phi_tilde_mode.                                                            */
 pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t n_steps, const double* const* u,
                                  const double* const* phi, const uint8_t* const* active, const double* p_host,
-                                 double rtol, int32_t restart, int32_t maxiter, double* gE_cells, double* gp_host,
-                                 double* gGc_host, pff_solve_info* info, void* stream);
+                                 int32_t phi_tilde_mode, double rtol, int32_t restart, int32_t maxiter,
+                                 double* gE_cells, double* gp_host, double* gGc_host, pff_solve_info* info,
+                                 void* stream);
 
 #ifdef __cplusplus
 }

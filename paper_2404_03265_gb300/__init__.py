@@ -8,7 +8,8 @@ arguments; torch supplies device memory and streams.
 import numpy as np
 
 from . import _lib
-from ._lib import PFF_F32, PFF_F64, PFF_OP_CONDENSED, PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, PffError
+from ._lib import (PFF_F32, PFF_F64, PFF_OP_CONDENSED, PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, PFF_PHIT_EXTRAPOLATED,
+                   PFF_PHIT_PREVIOUS, PffError)
 
 
 class Mesh:
@@ -274,13 +275,15 @@ def tcv_adjoint(problem, mg, u, phi, phi_old, active, gE=None, rtol=1e-10, resta
                 status=st)
 
 
-def tcv_adjoint_steps(problem, mg, us, phis, actives, ps, gE=None, rtol=1e-10, restart=50, maxiter=2000,
-                      stream=None, check=True):
+def tcv_adjoint_steps(problem, mg, us, phis, actives, ps, gE=None, extrapolated=False, rtol=1e-10, restart=50,
+                      maxiter=2000, stream=None, check=True):
     """dJ/dp_k (k = 1..N), dJ/dG_c (and dJ/dE_K into gE) of J = TCV after N load steps.
 
     us, phis: N + 1 converged states (index 0 the initial state) as device tensors
     (u (2, n_slots), phi (n_slots,) float64); actives: N uint8 device tensors;
-    ps: the N pressures."""
+    ps: the N pressures; extrapolated: the steps k >= 2 were solved with
+    phi_tilde = clip(2 phi^(k-1) - phi^(k-2), 0, 1) (Problem.extrapolate_phi), else
+    with phi_tilde = phi^(k-1)."""
     N = len(ps)
     assert len(us) == N + 1 and len(phis) == N + 1 and len(actives) == N
     VP = _lib.ctypes.c_void_p
@@ -291,8 +294,9 @@ def tcv_adjoint_steps(problem, mg, us, phis, actives, ps, gE=None, rtol=1e-10, r
     gp = np.zeros(N)
     ggc = np.zeros(1)
     info = _lib.SolveInfo()
-    st = _lib.lib().pff_tcv_adjoint_steps(problem._h, mg._h, N, ua, pa, aa, _lib.ptr(p_host), rtol, restart, maxiter,
-                                          None if gE is None else _lib.ptr(gE), _lib.ptr(gp), _lib.ptr(ggc),
+    mode = _lib.PFF_PHIT_EXTRAPOLATED if extrapolated else _lib.PFF_PHIT_PREVIOUS
+    st = _lib.lib().pff_tcv_adjoint_steps(problem._h, mg._h, N, ua, pa, aa, _lib.ptr(p_host), mode, rtol, restart,
+                                          maxiter, None if gE is None else _lib.ptr(gE), _lib.ptr(gp), _lib.ptr(ggc),
                                           _lib.ctypes.byref(info), _lib.stream_ptr(stream))
     if check:
         _lib.check(st)

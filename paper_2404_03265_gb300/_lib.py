@@ -15,6 +15,7 @@ LIBPATH = os.environ.get("PFF_LIBPATH") or os.path.join(HERE, "libpff.so")
 PFF_OK = 0
 PFF_F64, PFF_F32 = 0, 1
 PFF_OP_JACOBIAN, PFF_OP_TRANSPOSE, PFF_OP_CONDENSED = 0, 1, 2
+PFF_PHIT_PREVIOUS, PFF_PHIT_EXTRAPOLATED = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "GMRES_BREAKDOWN",
                 6: "NONFINITE", 7: "LINESEARCH", 8: "TIMEOUT", 9: "STATE"}
 
@@ -116,8 +117,8 @@ _SIGS = [
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), _P]),
     ("pff_inverse_diagonal", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64), _P]),
-    ("pff_tcv_adjoint_steps", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
-                                               ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+    ("pff_tcv_adjoint_steps", ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32,
+                                               ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                                ctypes.POINTER(SolveInfo), _P]),
 ]
 

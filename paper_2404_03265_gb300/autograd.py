@@ -8,12 +8,14 @@ forward  runs the Newton / PDAS load step (pff_newton_pdas_step) and keeps the
 backward runs one adjoint solve at that state (pff_tcv_adjoint: transposed
          constrained Jacobian, GMRES with the block V-cycle, then the VJP of the
          residual with respect to the parameters).
-Several steps (TCVLoadSteps), step n from phi_old = phi_tilde = phi^(n-1):
+Several steps (TCVLoadSteps), step n from phi_old = phi^(n-1) with phi_tilde =
+phi^(n-1), or extrapolated (Sec. 2) as clip(2 phi^(n-1) - phi^(n-2), 0, 1) for n >= 2:
 forward  runs the N load steps and keeps every step's converged state (u^n,
          phi^n, active set A^n) as the checkpoints;
 backward runs the checkpointed adjoint chain (pff_tcv_adjoint_steps): one
          adjoint solve per step, last to first, each passing its phi-sensitivity
-         to the step before through phi_tilde and the active rows.
+         to the steps before through phi_tilde (one step back, or two when
+         extrapolated) and the active rows.
 """
 import torch
 
@@ -62,7 +64,7 @@ class TCVLoadSteps(torch.autograd.Function):
     """J = TCV(U^N) after N load steps; see ``tcv_load_steps``."""
 
     @staticmethod
-    def forward(ctx, ps, Gc, E_cells, problem, mg, u0, phi0, newton_kw, adjoint_kw, out):
+    def forward(ctx, ps, Gc, E_cells, problem, mg, u0, phi0, newton_kw, adjoint_kw, out, extrapolated):
         problem.set_params(Gc=float(Gc))
         problem.set_cell_modulus(None if E_cells is None else E_cells.detach().contiguous())
         pl = [float(v) for v in ps.detach().cpu().reshape(-1)]
@@ -71,16 +73,21 @@ class TCVLoadSteps(torch.autograd.Function):
         acts = []
         act = torch.zeros(phi0.numel(), dtype=torch.uint8, device=phi0.device)
         infos = []
-        for p in pl:
+        phit = torch.empty_like(phi0) if extrapolated and len(pl) >= 2 else None
+        for n, p in enumerate(pl, start=1):
             problem.set_pressure(p)
             u = us[-1].clone()
             phi = phis[-1].clone()
-            infos.append(newton_step(problem, mg, u, phi, phis[-1], act, **newton_kw))
+            kw = dict(newton_kw)
+            if extrapolated and n >= 2:
+                problem.extrapolate_phi(phis[-1], phis[-2], phit)
+                kw["phi_tilde"] = phit
+            infos.append(newton_step(problem, mg, u, phi, phis[-1], act, **kw))
             us.append(u)
             phis.append(phi)
             acts.append(act.clone())
         J = problem.tcv(us[-1], phis[-1])
-        ctx.problem, ctx.mg, ctx.adjoint_kw = problem, mg, adjoint_kw
+        ctx.problem, ctx.mg, ctx.adjoint_kw, ctx.extrapolated = problem, mg, adjoint_kw, extrapolated
         ctx.checkpoints = (us, phis, acts, pl)
         ctx.has_E = E_cells is not None
         ctx.dev_p, ctx.dev_gc = ps.device, Gc.device if torch.is_tensor(Gc) else torch.device("cpu")
@@ -94,21 +101,25 @@ class TCVLoadSteps(torch.autograd.Function):
         dev = phis[0].device
         gE = torch.empty(ctx.problem.mesh.info["n_leaf_cells"], dtype=torch.float64, device=dev) \
             if ctx.has_E else None
-        r = tcv_adjoint_steps(ctx.problem, ctx.mg, us, phis, acts, pl, gE=gE, **ctx.adjoint_kw)
+        r = tcv_adjoint_steps(ctx.problem, ctx.mg, us, phis, acts, pl, gE=gE, extrapolated=ctx.extrapolated,
+                              **ctx.adjoint_kw)
         ctx.adjoint = r
         g_ps = (gJ.cpu() * torch.tensor(r["p"], dtype=torch.float64)).to(ctx.dev_p)
         g_gc = (gJ * r["Gc"]).to(ctx.dev_gc)
         g_e = gJ * gE if gE is not None else None
-        return g_ps, g_gc, g_e, None, None, None, None, None, None, None
+        return g_ps, g_gc, g_e, None, None, None, None, None, None, None, None
 
 
-def tcv_load_steps(problem, mg, ps, Gc, E_cells, u0, phi0, newton_kw=None, adjoint_kw=None, out=None):
+def tcv_load_steps(problem, mg, ps, Gc, E_cells, u0, phi0, newton_kw=None, adjoint_kw=None, out=None,
+                   extrapolated=False):
     """Differentiable J = integral of u . grad phi after len(ps) load steps.
 
     ps: float64 tensor of the N pressures (CPU); Gc: 0-dim float64 tensor; E_cells:
     float64 device tensor (n_leaf_cells, leaf order) or None; u0 (2, n_slots) and
     phi0 (n_slots,): the initial state (phi0 also the first step's obstacle).
     out (dict, optional) receives the step states (u, phi, active lists) and the
-    Newton infos.  The backward pass leaves the problem's state, active set and
-    multigrid at the first step."""
-    return TCVLoadSteps.apply(ps, Gc, E_cells, problem, mg, u0, phi0, newton_kw or {}, adjoint_kw or {}, out)
+    Newton infos.  extrapolated: phi_tilde of steps n >= 2 is clip(2 phi^(n-1) -
+    phi^(n-2), 0, 1) (Problem.extrapolate_phi) instead of phi^(n-1).  The backward
+    pass leaves the problem's state, active set and multigrid at the first step."""
+    return TCVLoadSteps.apply(ps, Gc, E_cells, problem, mg, u0, phi0, newton_kw or {}, adjoint_kw or {}, out,
+                              bool(extrapolated))

@@ -111,18 +111,23 @@ cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const doub
 namespace pff {
 
 // Checkpointed adjoint over n_steps load steps (see the header of this file):
-// step k (1..N) has state (u[k], phi[k]), phi_tilde = obstacle = phi[k-1],
-// active set active[k-1] and pressure p[k-1].  Backwards from
-// gbar^N = C^T dJ/dU^N (Dirichlet rows 0):
+// step k (1..N) has state (u[k], phi[k]), obstacle phi[k-1], active set
+// active[k-1], pressure p[k-1] and phi_tilde = phi[k-1], or, when extrapolated,
+// phi_tilde = clip(2 phi[k-1] - phi[k-2], 0, 1) for k >= 2 (Sec. 2).  Backwards
+// from gbar^N = C^T dJ/dU^N (Dirichlet rows 0):
 //   G~_k^T mu = gbar^k (GMRES; the fixed rows of mu equal gbar there),
 //   dJ/dtheta += (C M_f mu) . dR_k/dtheta,
-//   gbar^(k-1) = (0, 0, -(dA/dphi~)^T C M_f mu + [mu - K^T C M_f mu] on the active rows),
+//   v^k = (dA/dphi~)^T C M_f mu,
+//   gbar^(k-1) = (0, 0, -v^k + [mu - K^T C M_f mu] on the active rows),
 // the bracket being the active-row adjoint of the full step Jacobian, whose free
-// rows still see the active values (K = C^T G C).
+// rows still see the active values (K = C^T G C).  Extrapolated: d phi~/d phi^(k-1)
+// = 2 chi and d phi~/d phi^(k-2) = -chi (chi = 1 strictly inside the clip), so
+// -2 chi v^k enters gbar^(k-1) and +chi v^k waits (adj_pend) for gbar^(k-2); the
+// share that would reach phi^0 is dropped (the initial state is parameter-free).
 cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* const* u, const double* const* phi,
-                              const uint8_t* const* active, const double* p, double rtol, int restart, int maxiter,
-                              double* gE, double* gp_host, double* ggc_host, AdjointStats& st, std::string& err,
-                              cudaStream_t s) {
+                              const uint8_t* const* active, const double* p, bool extrapolated, double rtol,
+                              int restart, int maxiter, double* gE, double* gp_host, double* ggc_host,
+                              AdjointStats& st, std::string& err, cudaStream_t s) {
   const Mesh& M = pb.mesh->m;
   const DevMesh& D = pb.mesh->dev;
   SolverWS& W = pb.ws;
@@ -130,6 +135,11 @@ cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* 
   if (gE && !pb.adj_cell) {
     pb.adj_cell = pb.bufs.alloc<double>(D.n_leaf_cells);
     if (!pb.adj_cell) return cudaErrorMemoryAllocation;
+  }
+  if (extrapolated && N >= 2 && !pb.adj_phit) {
+    pb.adj_phit = pb.bufs.alloc<double>(n);
+    pb.adj_pend = pb.bufs.alloc<double>(n);
+    if (!pb.adj_phit || !pb.adj_pend) return cudaErrorMemoryAllocation;
   }
   const double p_saved = pb.prm.p;
   struct Restore {
@@ -139,8 +149,15 @@ cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* 
   RET(tcv_gradient(pb, u[N], phi[N], W.rhs, s, pb.cmask_dir));
   if (gE) RET(cudaMemsetAsync(gE, 0, D.n_leaf_cells * sizeof(double), s));
   *ggc_host = 0.0;
+  bool pend = false;  // adj_pend holds a share for the step being carried into
   for (int k = N; k >= 1; --k) {
-    RET(launch_set_lin(n, u[k], phi[k], phi[k - 1], D.hang, D.nhang, M.k, pb.lin64, pb.lin32, pb.hlin64, pb.hlin32, s));
+    const bool ex = extrapolated && k >= 2;
+    const double* phit = phi[k - 1];
+    if (ex) {
+      RET(extrapolate_phi(n, phi[k - 1], phi[k - 2], pb.adj_phit, s));
+      phit = pb.adj_phit;
+    }
+    RET(launch_set_lin(n, u[k], phi[k], phit, D.hang, D.nhang, M.k, pb.lin64, pb.lin32, pb.hlin64, pb.hlin32, s));
     pb.has_state = true;
     RET(launch_leaf_cmask(n, D.slot_flags, active[k - 1], pb.cmask, s));
     pb.prm.p = p[k - 1];
@@ -162,7 +179,14 @@ cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* 
       // t1 = C^T G^T C (M_f mu) on every row but Dirichlet u; t2 = (dA/dphi~)^T (M_f mu)
       RET(leaf_op(pb, OP_FULL_T, MODE_MASK_INPUT, pb.lin64, pb.cmask_dir, W.tmp, W.tmp + 2 * n, W.R, W.R + 2 * n, s));
       RET(leaf_op(pb, OP_PHIT_VJP, MODE_MASK_INPUT, pb.lin64, pb.cmask_dir, W.tmp, W.tmp + 2 * n, W.du0, W.res, s));
-      RET(adj_carry(n, active[k - 1], W.dU, W.R, W.res, W.rhs, s));
+      if (ex) {
+        const bool out = k - 2 >= 1;
+        RET(adj_carry(n, active[k - 1], W.dU, W.R, W.res, W.rhs, s, phi[k - 1], phi[k - 2],
+                      pend ? pb.adj_pend : nullptr, out ? pb.adj_pend : nullptr));
+        pend = out;
+      } else {
+        RET(adj_carry(n, active[k - 1], W.dU, W.R, W.res, W.rhs, s));
+      }
     }
   }
   return cudaStreamSynchronize(s);

@@ -572,9 +572,9 @@ extern "C" pff_status pff_tcv_adjoint(pff_problem* pb, pff_mg* mg, const double*
 
 extern "C" pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t n_steps, const double* const* u,
                                             const double* const* phi, const uint8_t* const* active,
-                                            const double* p_host, double rtol, int32_t restart, int32_t maxiter,
-                                            double* gE_cells, double* gp_host, double* gGc_host,
-                                            pff_solve_info* info, void* stream) {
+                                            const double* p_host, int32_t phi_tilde_mode, double rtol,
+                                            int32_t restart, int32_t maxiter, double* gE_cells, double* gp_host,
+                                            double* gGc_host, pff_solve_info* info, void* stream) {
   PFF_TRY({
     if (!pb || !mg || !u || !phi || !active || !p_host || !gp_host || !gGc_host)
       return fail(PFF_ERR_INVALID_ARG, "NULL argument");
@@ -585,11 +585,14 @@ extern "C" pff_status pff_tcv_adjoint_steps(pff_problem* pb, pff_mg* mg, int32_t
       if (!active[k]) return fail(PFF_ERR_INVALID_ARG, "NULL active-set pointer");
     if (mg->pb != pb) return fail(PFF_ERR_INVALID_ARG, "multigrid object of another problem");
     if (restart < 1 || restart > 500 || maxiter < 1 || !(rtol > 0)) return fail(PFF_ERR_INVALID_ARG, "bad options");
+    if (phi_tilde_mode != PFF_PHIT_PREVIOUS && phi_tilde_mode != PFF_PHIT_EXTRAPOLATED)
+      return fail(PFF_ERR_INVALID_ARG, "phi_tilde_mode must be PFF_PHIT_PREVIOUS or PFF_PHIT_EXTRAPOLATED");
     std::string e = ensure_workspace(*pb, restart);
     if (!e.empty()) return fail(PFF_ERR_OOM, e);
     AdjointStats st;
     std::string err;
-    const cudaError_t ce = tcv_adjoint_steps(*pb, *mg, n_steps, u, phi, active, p_host, rtol, restart, maxiter,
+    const cudaError_t ce = tcv_adjoint_steps(*pb, *mg, n_steps, u, phi, active, p_host,
+                                             phi_tilde_mode == PFF_PHIT_EXTRAPOLATED, rtol, restart, maxiter,
                                              gE_cells, gp_host, gGc_host, st, err, cudaStream_t(stream));
     if (info) {
       std::memset(info, 0, sizeof(*info));

@@ -143,12 +143,29 @@ __global__ void k_copy_fixed(int64_t n, const uint8_t* __restrict__ cmask, const
 }
 
 // adjoint carry to the previous load step: g = (0, 0, -t2 + act (mu_phi - t1_phi))
+// g = (0, 0, -w t2 + act (mu_phi - t1_phi) + pend_in).  phi_tilde = phi^(k-1)
+// (p1 null): w = 1.  Extrapolated phi_tilde = clip(2 p1 - p2, 0, 1): w = 2 chi on
+// the slots strictly inside the clip (chi = 1, else 0), and pend_out = chi t2 is
+// the share that reaches the step before the previous one (weight -1 there, so
+// +chi t2 on its right-hand side).  pend_in may alias pend_out.
 __global__ void k_adj_carry(int64_t n, const uint8_t* __restrict__ act, const double* __restrict__ mu,
-                            const double* __restrict__ t1, const double* __restrict__ t2, double* g) {
+                            const double* __restrict__ t1, const double* __restrict__ t2,
+                            const double* __restrict__ p1, const double* __restrict__ p2, const double* pend_in,
+                            double* pend_out, double* g) {
   GRID_STRIDE(s, n) {
+    const double v = t2[s];
+    double w = 1.0, chi = 0.0;
+    if (p1) {
+      const double raw = 2.0 * p1[s] - p2[s];
+      chi = (raw > 0.0 && raw < 1.0) ? 1.0 : 0.0;
+      w = 2.0 * chi;
+    }
+    double gp = -w * v + (act[s] ? mu[2 * n + s] - t1[2 * n + s] : 0.0);
+    if (pend_in) gp += pend_in[s];
     g[s] = 0.0;
     g[n + s] = 0.0;
-    g[2 * n + s] = -t2[s] + (act[s] ? mu[2 * n + s] - t1[2 * n + s] : 0.0);
+    g[2 * n + s] = gp;
+    if (pend_out) pend_out[s] = chi * v;
   }
 }
 
@@ -369,8 +386,9 @@ cudaError_t copy_fixed(int64_t n, const uint8_t* cmask, const double* x, double*
 }
 
 cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
-                      cudaStream_t s) {
-  if (n > 0) k_adj_carry<<<blocks_for(n), TPB, 0, s>>>(n, act, mu, t1, t2, g);
+                      cudaStream_t s, const double* p1, const double* p2, const double* pend_in, double* pend_out) {
+  if ((p1 == nullptr) != (p2 == nullptr)) return cudaErrorInvalidValue;
+  if (n > 0) k_adj_carry<<<blocks_for(n), TPB, 0, s>>>(n, act, mu, t1, t2, p1, p2, pend_in, pend_out, g);
   return cudaGetLastError();
 }
 

@@ -31,9 +31,13 @@ cudaError_t f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t s);
 cudaError_t mask_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
 // out = x on the rows cmask marks fixed; the other rows of out are left as they are
 cudaError_t copy_fixed(int64_t n, const uint8_t* cmask, const double* x, double* out, cudaStream_t s);
-// g = (0, 0, -t2 + act * (mu_phi - t1_phi)): adjoint right-hand side of the previous load step
+// g = (0, 0, -t2 + act * (mu_phi - t1_phi)): adjoint right-hand side of the previous load step.
+// With p1 = phi^(k-1), p2 = phi^(k-2) (extrapolated phi_tilde of step k): -2 chi t2 in
+// place of -t2 (chi: 1 where 2 p1 - p2 lies strictly inside (0, 1)), pend_in (may be
+// null) added, and pend_out = chi t2 (may be null; may alias pend_in) for step k - 2.
 cudaError_t adj_carry(int64_t n, const uint8_t* act, const double* mu, const double* t1, const double* t2, double* g,
-                      cudaStream_t s);
+                      cudaStream_t s, const double* p1 = nullptr, const double* p2 = nullptr,
+                      const double* pend_in = nullptr, double* pend_out = nullptr);
 cudaError_t axpby(int64_t n, double* out, const double* x, double a, const double* y, double b, cudaStream_t s);
 int reduction_partials();
 // Krylov basis V in row blocks: entry i of basis vector j at

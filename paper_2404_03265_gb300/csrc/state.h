@@ -160,6 +160,8 @@ struct pff_problem {
   float* lev_ecell32 = nullptr;
   double* cell_out = nullptr;     // 3 * n_slots: per-cell VJP values
   double* adj_cell = nullptr;     // n_leaf_cells: per-step modulus gradient of the multi-step adjoint
+  double* adj_phit = nullptr;     // n_slots: extrapolated phi_tilde of the step the multi-step adjoint is at
+  double* adj_pend = nullptr;     // n_slots: phi share of step k's adjoint that reaches step k - 2
   cudaEvent_t gm_ev[4] = {};      // GMRES phase timing (created on first use)
   int sweep_sh = 0;               // Q1 cell-loop strip half-height (pff_set_cell_loop), 0 = by mesh size
 };
@@ -275,9 +277,9 @@ struct AdjointStats {
   GmresResult last;
 };
 cudaError_t tcv_adjoint_steps(pff_problem& pb, pff_mg& mg, int N, const double* const* u, const double* const* phi,
-                              const uint8_t* const* active, const double* p, double rtol, int restart, int maxiter,
-                              double* gE, double* gp_host, double* ggc_host, AdjointStats& st, std::string& err,
-                              cudaStream_t s);
+                              const uint8_t* const* active, const double* p, bool extrapolated, double rtol,
+                              int restart, int maxiter, double* gE, double* gp_host, double* ggc_host,
+                              AdjointStats& st, std::string& err, cudaStream_t s);
 cudaError_t param_vjp(pff_problem& pb, const double* w, double* gE_cells, double* g_host, cudaStream_t s);
 cudaError_t tcv_adjoint(pff_problem& pb, pff_mg& mg, const double* u, const double* phi, const double* phi_old,
                         const uint8_t* active, double rtol, int restart, int maxiter, double* gE, double* g_host,

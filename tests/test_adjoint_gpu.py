@@ -496,3 +496,125 @@ def test_autograd_load_steps_three():
     Em[c] -= hh
     fd = (Jfd(ps, base["Gc"], Ep) - Jfd(ps, base["Gc"], Em)) / (2 * hh)
     assert abs(fd - gE[c]) <= 1e-5 * abs(fd), (c, fd, gE[c])
+
+
+def oracle_steps_extrapolated(om, base, E, po, ps):
+    """Oracle load steps from (u = 0, phi^0 = po), phi_tilde of step n >= 2 extrapolated
+    (clip(2 phi^(n-1) - phi^(n-2), 0, 1), Sec. 2); the clip masks of steps 2..N."""
+    mats, us, phis, acts, chis = [], [np.zeros((om.nn, 2))], [po], [], []
+    u, phi, act = us[0], po.copy(), None
+    for n, p in enumerate(ps, start=1):
+        mat = ops.Material(**dict(base, p=p))
+        phit = None
+        if n >= 2:
+            phit = solvers.extrapolate_phi(phis[-1], phis[-2])
+            raw = 2.0 * phis[-1] - phis[-2]
+            chis.append((raw > 0.0) & (raw < 1.0))
+        u, phi_n, act, info = solvers.load_step(om, mat, 1e4, u, phi.copy(), phi, active_prev=act, E_cells=E,
+                                                tol=1e-12, atol=1e-15, phi_tilde=phit)
+        assert info.converged
+        phi = phi_n
+        mats.append(mat)
+        us.append(u)
+        phis.append(phi)
+        acts.append(act)
+    return mats, us, phis, acts, chis
+
+
+def test_load_steps_extrapolated_phi_tilde_gradient():
+    """Three load steps (p = 0.1, 0.15, 0.2, lognormal E_K, 4,293 DoFs) whose phi_tilde
+    of steps 2 and 3 is extrapolated from the two previous steps (Sec. 2), through the
+    several-step torch wrapper: J and the GPU states' active sets and clip masks equal
+    the oracle's; J.backward() (pff_tcv_adjoint_steps, PFF_PHIT_EXTRAPOLATED) against
+    the oracle's extrapolated adjoint (1e-6) and central differences of three-step GPU
+    solves (1e-5) for p_1, p_2, G_c and the largest E_K gradient; another
+    phi_tilde_mode is refused."""
+    import ctypes
+    import torch
+    from paper_2404_03265_gb300 import MG, PFF_F32, Problem, _lib, tcv_adjoint_steps
+    from paper_2404_03265_gb300.autograd import tcv_load_steps
+    P = pair("small")
+    om = P.om
+    E = cell_E(P)
+    ps = [0.1, 0.15, 0.2]
+    base = P.material()
+    _, po = solvers.sneddon_initial(om, om.h_min_diag())
+    mats, ous, ophis, oacts, ochis = oracle_steps_extrapolated(om, base, E, po, ps)
+    go = adj.tcv_adjoint_steps(om, mats, ous, ophis, oacts, E, extrapolate=True)
+    Jo = ops.tcv(om, ops.State(om, ous[-1], ophis[-1], ophis[-1]))
+
+    pb = Problem(P.lm, **base)
+    mg = MG(pb, PFF_F32)
+    pt = torch.tensor(ps, dtype=torch.float64, requires_grad=True)
+    gct = torch.tensor(base["Gc"], dtype=torch.float64, requires_grad=True)
+    Et = dev(E).requires_grad_(True)
+    u0 = torch.zeros((2, P.n_slots), dtype=torch.float64, device="cuda")
+    phi0 = dev(P.to_slots(po))
+    out = {}
+    kw = dict(newton_kw=dict(tol=1e-12, atol=1e-15), extrapolated=True)
+    J = tcv_load_steps(pb, mg, pt, gct, Et, u0, phi0, adjoint_kw=dict(rtol=1e-12), out=out, **kw)
+    assert abs(J.item() - Jo) <= 1e-7 * abs(Jo), (J.item(), Jo)
+    for a_g, a_o in zip(out["active"], oacts):
+        assert np.array_equal(P.from_slots(a_g.cpu().numpy()).astype(bool), a_o)
+    gphis = [P.from_slots(t.cpu().numpy()) for t in out["phi"]]
+    for n, c_o in enumerate(ochis, start=2):
+        raw = 2.0 * gphis[n - 1] - gphis[n - 2]
+        assert np.array_equal((raw > 0.0) & (raw < 1.0), c_o), n
+    J.backward()
+    gp = pt.grad.numpy()
+    for n in range(len(ps)):
+        assert close(gp[n], go["p"][n], 1e-6, 0.0), (n, gp[n], go["p"][n])
+    assert close(gct.grad.item(), go["Gc"], 1e-6, 1e-10 * Jo / base["Gc"]), (gct.grad.item(), go["Gc"])
+    gE = Et.grad.cpu().numpy()
+    inf, two = rel_err(gE, go["E"])
+    assert inf < 1e-6 and two < 1e-6, (inf, two)
+
+    # the same checkpoints with phi_tilde = phi^(k-1) give another gradient
+    pb.set_cell_modulus(dev(E))
+    r_prev = tcv_adjoint_steps(pb, mg, out["u"], out["phi"], out["active"], ps, rtol=1e-12)
+    assert np.max(np.abs(r_prev["p"] - gp)) > 1e-2 * np.max(np.abs(gp))
+
+    # phi_tilde_mode other than PFF_PHIT_PREVIOUS / PFF_PHIT_EXTRAPOLATED
+    VP = ctypes.c_void_p
+    N = len(ps)
+    ua = (VP * (N + 1))(*[_lib.ptr(t) for t in out["u"]])
+    pa = (VP * (N + 1))(*[_lib.ptr(t) for t in out["phi"]])
+    aa = (VP * N)(*[_lib.ptr(t) for t in out["active"]])
+    p_host = np.asarray(ps, dtype=np.float64)
+    gpo, ggc = np.zeros(N), np.zeros(1)
+    st = _lib.lib().pff_tcv_adjoint_steps(pb._h, mg._h, N, ua, pa, aa, _lib.ptr(p_host), 2, 1e-12, 50, 2000, None,
+                                          _lib.ptr(gpo), _lib.ptr(ggc), None, _lib.stream_ptr())
+    assert st == 1 and b"phi_tilde_mode" in _lib.lib().pff_last_error()
+
+    # central differences of three-step GPU solves, through the same wrapper's forward
+    def Jfd(pss, gc, Ec):
+        with torch.no_grad():
+            o = {}
+            v = tcv_load_steps(pb, mg, torch.tensor(pss, dtype=torch.float64), torch.tensor(gc, dtype=torch.float64),
+                               dev(Ec), u0, phi0, out=o, **kw).item()
+        for x0, x1 in zip(o["active"], out["active"]):
+            assert torch.equal(x0, x1), "active set changed under the perturbation"
+        for n in range(2, len(pss) + 1):
+            c0 = (lambda r: (r > 0) & (r < 1))(2.0 * o["phi"][n - 1] - o["phi"][n - 2])
+            c1 = (lambda r: (r > 0) & (r < 1))(2.0 * out["phi"][n - 1] - out["phi"][n - 2])
+            assert torch.equal(c0, c1), "clip pattern changed under the perturbation"
+        return v
+
+    rel = 1e-6
+    for n in (0, 1):
+        hh = rel * ps[n]
+        pp_, pm_ = list(ps), list(ps)
+        pp_[n] += hh
+        pm_[n] -= hh
+        fd = (Jfd(pp_, base["Gc"], E) - Jfd(pm_, base["Gc"], E)) / (2 * hh)
+        assert abs(fd - gp[n]) <= 1e-5 * abs(fd), (n, fd, gp[n])
+    hh = rel * base["Gc"]
+    fd = (Jfd(ps, base["Gc"] + hh, E) - Jfd(ps, base["Gc"] - hh, E)) / (2 * hh)
+    assert abs(fd - gct.grad.item()) <= 1e-5 * abs(fd), (fd, gct.grad.item())
+    c = int(np.argmax(np.abs(gE)))
+    hh = rel * E[c]
+    Ep, Em = E.copy(), E.copy()
+    Ep[c] += hh
+    Em[c] -= hh
+    fd = (Jfd(ps, base["Gc"], Ep) - Jfd(ps, base["Gc"], Em)) / (2 * hh)
+    assert abs(fd - gE[c]) <= 1e-5 * abs(fd), (c, fd, gE[c])

@@ -32,6 +32,42 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) <= set(_lib.exported_names()) | {"pff_params_default"}
 
 
+def declared_prototypes():
+    """name -> number of parameters of every function prototype in include/pff.h."""
+    txt = open(os.path.join(ROOT, "include", "pff.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(pff_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes signature of the binding passes as many arguments as the
+    header's prototype of the same function declares."""
+    from paper_2404_03265_gb300 import _lib
+    protos = declared_prototypes()
+    for name, _, args in _lib._SIGS:
+        assert name in protos, name
+        assert len(args) == protos[name], (name, len(args), protos[name])
+
+
+def test_binding_constants_match_header():
+    """Every PFF_* integer constant the binding names has the header's value (a
+    #define or an enumerator)."""
+    from paper_2404_03265_gb300 import _lib
+    txt = open(os.path.join(ROOT, "include", "pff.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(PFF_[A-Z0-9_]+)\s+(-?\d+)\b", txt)}
+    defs.update({k: int(v) for k, v in re.findall(r"\b(PFF_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)})
+    named = [k for k in dir(_lib) if k.startswith("PFF_") and isinstance(getattr(_lib, k), int)]
+    assert {"PFF_PHIT_PREVIOUS", "PFF_PHIT_EXTRAPOLATED", "PFF_F32"} <= set(named)
+    for k in named:
+        assert k in defs, k
+        assert getattr(_lib, k) == defs[k], (k, getattr(_lib, k), defs[k])
+
+
 @pytest.mark.parametrize("name,k", [("tiny", 1), ("small", 1), ("tiny", 2), ("small", 2), ("band4_2_4", 1),
                                     ("band4_2_4", 2)])
 def test_mesh_matches_oracle(name, k):

@@ -13,7 +13,10 @@
 //      parents, fixed input components masked, absent nodes zero);
 //   2. each thread evaluates one cell, sum-factorised: per Gauss row eta_q2 the
 //      3x3 nodal values collapse to three column values, then to the row's
-//      three Gauss points; the test runs the same two steps backwards;
+//      three Gauss points; the test runs the same two steps backwards.  Fields
+//      that take the same contractions travel as pairs (u_x with u_y of the
+//      input and of the linearisation, the input dphi with phi), one paired
+//      FP32 instruction for both, and the shared tiles interleave each pair;
 //   3. the cells' nodal contributions are added into a shared tile in four
 //      colour phases (cells of equal (i, j) parity share no node), so every
 //      nodal sum has a fixed order;
@@ -26,19 +29,40 @@ constexpr int Q2C = 16;           // window cells per side (-1..14)
 constexpr int Q2T = Q2C * Q2C;    // threads per block: one per window cell
 constexpr int Q2WW = Q2W * Q2W;
 
+// Field pairs of the window tiles: pair 0 (u_x, u_y of the input), 1 (u_x, u_y
+// of the linearisation), 2 (input dphi, phi), 3 (phi_tilde, unused).
+constexpr int Q2NP = 4;
+__host__ __device__ constexpr int q2_pair(int f) {
+  return f == F_XU || f == F_XV ? 0 : f == F_LU || f == F_LV ? 1 : f == F_XP || f == F_LP ? 2 : 3;
+}
+__host__ __device__ constexpr int q2_half(int f) { return f == F_XV || f == F_LV || f == F_LP ? 1 : 0; }
+template <int OP>
+__device__ __forceinline__ constexpr bool q2_pair_used(int k) {
+  return k == 0 ? field_used<OP>(F_XU) || field_used<OP>(F_XV)
+       : k == 1 ? field_used<OP>(F_LU) || field_used<OP>(F_LV)
+       : k == 2 ? field_used<OP>(F_XP) || field_used<OP>(F_LP) : field_used<OP>(F_LT);
+}
+
 // FP32 keeps two window buffers: while a block computes one brick, the window
 // of its next brick, when regular, streams into the other with cp.async.  FP64
 // (twice the bytes per field) keeps one and gathers each brick in turn.
 template <typename T>
 struct Q2Smem {
+  using P = typename VT<T>::T2;
   static constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
-  T f[NBUF][NF][Q2WW];      // node fields of the window
-  T y[3][Q2WW];             // nodal sums
+  P f[NBUF][Q2NP][Q2WW];    // node fields of the window, as pairs (q2_pair, q2_half)
+  P yu[Q2WW];               // nodal sums, u_x and u_y
+  T yp[Q2WW];               // nodal sums, phi
   uint32_t cmw[NBUF][Q2WW]; // prefetch: the aligned word holding each node's constraint byte
   int32_t nb[NBUF][9];      // storage bases of the 3x3 neighbour bricks
   uint8_t cmsh[NBUF][Q2WW]; // prefetch: byte position of the constraint byte in its word
   uint8_t cm[Q2WW];         // constraint-mask byte of each window node of the current brick
 };
+
+template <typename T>
+__device__ __forceinline__ T& q2_field(typename VT<T>::T2 (*fb)[Q2WW], int f, int w) {
+  return half_of<T>(fb[q2_pair(f)][w], q2_half(f));
+}
 
 // Storage slot of node (n, r) (brick-relative, -2..30) of a brick whose
 // neighbour bases are nb; the caller guarantees the neighbour exists.
@@ -138,58 +162,74 @@ __device__ __forceinline__ void q2_point(const Q2Point<T>& q, const MatConst<T>&
 }
 
 // One Q2 cell: node (a, b) of the cell (a along x, b along y) is window node
-// base + a + Q2W * b.  r[3 * (a + 3 b) + c]: contribution to node (a, b),
-// component c.  cell[]: per-cell values (OP_VJP).
+// base + a + Q2W * b.  Contributions to node A = a + 3 b: ru[A] (components u_x,
+// u_y) and rp[A] (phi).  cell[]: per-cell values (OP_VJP).
 template <typename T, int OP>
-__device__ __forceinline__ void q2_cell(const T (*fb)[Q2WW], int base, const MatConst<T>& m, const LevGeom<T>& g,
-                                        const Q2Tab<T>& tb, T ec, T r[27], T cell[3]) {
+__device__ __forceinline__ void q2_cell(const typename VT<T>::T2 (*fb)[Q2WW], int base, const MatConst<T>& m,
+                                        const LevGeom<T>& g, const Q2Tab<T>& tb, T ec, typename VT<T>::T2 ru[9],
+                                        T rp[9], T cell[3]) {
   using N = Needs<OP>;
+  using P = typename VT<T>::T2;
   constexpr bool isDiag = (OP == OP_UU_DIAG || OP == OP_PP_DIAG);
   const T c2ml = m.c2ml * ec, cl = m.cl * ec, cm = m.cm * ec;
   const T area = T(4) * g.jxw;   // hx hy
 #pragma unroll
-  for (int k = 0; k < 27; ++k) r[k] = T(0);
+  for (int k = 0; k < 9; ++k) { ru[k] = pbc(T(0)); rp[k] = T(0); }
   cell[0] = cell[1] = cell[2] = T(0);
-  constexpr int FIELDS[7] = {F_XU, F_XV, F_XP, F_LU, F_LV, F_LP, F_LT};
 #pragma unroll
   for (int q2 = 0; q2 < 3; ++q2) {
-    // collapse every used field along eta: V[a] = sum_b l_b(eta) v_ab, E[a] = sum_b l_b'(eta) v_ab
-    T V[7][3], E[7][3];
+    // collapse every used pair along eta: V[a] = sum_b l_b(eta) v_ab, E[a] = sum_b l_b'(eta) v_ab
+    // (pair 3 holds phi_tilde alone, whose value is all the point needs: no E)
+    P V[Q2NP][3], E[Q2NP - 1][3];
 #pragma unroll
-    for (int fi = 0; fi < 7; ++fi) {
-      const int f = FIELDS[fi];
-      if (!field_used<OP>(f)) continue;
-      const T* fl = fb[f] + base;
+    for (int k = 0; k < Q2NP; ++k) {
+      if (!q2_pair_used<OP>(k)) continue;
+      const P* fl = fb[k] + base;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const T v0 = fl[a], v1 = fl[a + Q2W], v2 = fl[a + 2 * Q2W];
-        V[fi][a] = tb.L[0][q2] * v0 + tb.L[1][q2] * v1 + tb.L[2][q2] * v2;
-        E[fi][a] = tb.D[0][q2] * v0 + tb.D[1][q2] * v1 + tb.D[2][q2] * v2;
+        const P v0 = fl[a], v1 = fl[a + Q2W], v2 = fl[a + 2 * Q2W];
+        V[k][a] = pfma(pbc(tb.L[2][q2]), v2, pfma(pbc(tb.L[1][q2]), v1, pmul(pbc(tb.L[0][q2]), v0)));
+        if (k < Q2NP - 1)
+          E[k][a] = pfma(pbc(tb.D[2][q2]), v2, pfma(pbc(tb.D[1][q2]), v1, pmul(pbc(tb.D[0][q2]), v0)));
       }
     }
-    T Rv[3][3], Re[3][3];   // [component][a]: value/x-gradient part, y-gradient part
+    // test sums per node column a: value/x-gradient part and y-gradient part
+    P RvU[3], ReU[3];
+    T Rvp[3], Rep[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) { Rv[c][a] = T(0); Re[c][a] = T(0); }
+    for (int a = 0; a < 3; ++a) { RvU[a] = pbc(T(0)); ReU[a] = pbc(T(0)); Rvp[a] = T(0); Rep[a] = T(0); }
 #pragma unroll
     for (int q1 = 0; q1 < 3; ++q1) {
-      auto val = [&](int fi) { return tb.L[0][q1] * V[fi][0] + tb.L[1][q1] * V[fi][1] + tb.L[2][q1] * V[fi][2]; };
-      auto ddx = [&](int fi) {
-        return (tb.D[0][q1] * V[fi][0] + tb.D[1][q1] * V[fi][1] + tb.D[2][q1] * V[fi][2]) * g.ihx;
+      auto val = [&](int k) {
+        return pfma(pbc(tb.L[2][q1]), V[k][2], pfma(pbc(tb.L[1][q1]), V[k][1], pmul(pbc(tb.L[0][q1]), V[k][0])));
       };
-      auto ddy = [&](int fi) {
-        return (tb.L[0][q1] * E[fi][0] + tb.L[1][q1] * E[fi][1] + tb.L[2][q1] * E[fi][2]) * g.ihy;
+      auto ddx = [&](int k) {
+        return pmul(pfma(pbc(tb.D[2][q1]), V[k][2], pfma(pbc(tb.D[1][q1]), V[k][1], pmul(pbc(tb.D[0][q1]), V[k][0]))),
+                    pbc(g.ihx));
+      };
+      auto ddy = [&](int k) {
+        return pmul(pfma(pbc(tb.L[2][q1]), E[k][2], pfma(pbc(tb.L[1][q1]), E[k][1], pmul(pbc(tb.L[0][q1]), E[k][0]))),
+                    pbc(g.ihy));
       };
       Q2Point<T> q{};
-      if (N::xu) { q.ax = ddx(0); q.bxy = ddy(0); q.cyx = ddx(1); q.dy = ddy(1); }
-      if (N::xp) { q.xp = val(2); q.xpx = ddx(2); q.xpy = ddy(2); }
-      if (N::linU) {
-        q.uxx = ddx(3); q.uxy = ddy(3); q.uyx = ddx(4); q.uyy = ddy(4);
-        if (OP == OP_TCV || OP == OP_TCV_GRAD) { q.ux = val(3); q.uy = val(4); }
+      if (N::xu) {
+        const P dx = ddx(0), dy = ddy(0);
+        q.ax = dx.x; q.bxy = dy.x; q.cyx = dx.y; q.dy = dy.y;
       }
-      if (N::phi) { q.phi = val(5); q.phix = ddx(5); q.phiy = ddy(5); }
-      if (N::phit) q.phit = val(6);
+      if (N::xp || N::phi) {
+        const P v = val(2), dx = ddx(2), dy = ddy(2);
+        if (N::xp) { q.xp = v.x; q.xpx = dx.x; q.xpy = dy.x; }
+        if (N::phi) { q.phi = v.y; q.phix = dx.y; q.phiy = dy.y; }
+      }
+      if (N::linU) {
+        const P dx = ddx(1), dy = ddy(1);
+        q.uxx = dx.x; q.uxy = dy.x; q.uyx = dx.y; q.uyy = dy.y;
+        if (OP == OP_TCV || OP == OP_TCV_GRAD) {
+          const P v = val(1);
+          q.ux = v.x; q.uy = v.y;
+        }
+      }
+      if (N::phit) q.phit = val(3).x;
       const T W = area * tb.w[q1] * tb.w[q2];
       if constexpr (isDiag) {
         // diagonal of the element matrix of the block
@@ -208,10 +248,10 @@ __device__ __forceinline__ void q2_cell(const T (*fb)[Q2WW], int base, const Mat
             const T dxn = tb.D[a][q1] * tb.L[b][q2] * g.ihx, dyn = tb.L[a][q1] * tb.D[b][q2] * g.ihy;
             const int A = a + 3 * b;
             if (OP == OP_UU_DIAG) {
-              r[3 * A + 0] += W * gq * (c2ml * dxn * dxn + cm * dyn * dyn);
-              r[3 * A + 1] += W * gq * (cm * dxn * dxn + c2ml * dyn * dyn);
+              ru[A].x += W * gq * (c2ml * dxn * dxn + cm * dyn * dyn);
+              ru[A].y += W * gq * (cm * dxn * dxn + c2ml * dyn * dyn);
             } else {
-              r[3 * A + 2] += W * (mq * Nv * Nv + m.gcL * (dxn * dxn + dyn * dyn));
+              rp[A] += W * (mq * Nv * Nv + m.gcL * (dxn * dxn + dyn * dyn));
             }
           }
       } else if constexpr (OP == OP_VJP) {
@@ -225,14 +265,18 @@ __device__ __forceinline__ void q2_cell(const T (*fb)[Q2WW], int base, const Mat
         Q2Coef<T> cf;
         T cv[3];
         q2_point<T, OP>(q, m, c2ml, cl, cm, cf, cv);
+        const T wx = W * g.ihx, wy = W * g.ihy;
+        P f0u, fxu, fyu;
+        f0u.x = W * cf.f0[0]; f0u.y = W * cf.f0[1];
+        fxu.x = wx * cf.fx[0]; fxu.y = wx * cf.fx[1];
+        fyu.x = wy * cf.fy[0]; fyu.y = wy * cf.fy[1];
+        const T f0p = W * cf.f0[2], fxp = wx * cf.fx[2], fyp = wy * cf.fy[2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T f0 = W * cf.f0[c], fx = W * g.ihx * cf.fx[c], fy = W * g.ihy * cf.fy[c];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            Rv[c][a] += tb.L[a][q1] * f0 + tb.D[a][q1] * fx;
-            Re[c][a] += tb.L[a][q1] * fy;
-          }
+        for (int a = 0; a < 3; ++a) {
+          RvU[a] = pfma(pbc(tb.L[a][q1]), f0u, pfma(pbc(tb.D[a][q1]), fxu, RvU[a]));
+          ReU[a] = pfma(pbc(tb.L[a][q1]), fyu, ReU[a]);
+          Rvp[a] += tb.L[a][q1] * f0p + tb.D[a][q1] * fxp;
+          Rep[a] += tb.L[a][q1] * fyp;
         }
       }
     }
@@ -240,14 +284,16 @@ __device__ __forceinline__ void q2_cell(const T (*fb)[Q2WW], int base, const Mat
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) r[3 * (a + 3 * b) + c] += tb.L[b][q2] * Rv[c][a] + tb.D[b][q2] * Re[c][a];
+        for (int a = 0; a < 3; ++a) {
+          const int A = a + 3 * b;
+          ru[A] = pfma(pbc(tb.L[b][q2]), RvU[a], pfma(pbc(tb.D[b][q2]), ReU[a], ru[A]));
+          rp[A] += tb.L[b][q2] * Rvp[a] + tb.D[b][q2] * Rep[a];
+        }
     }
   }
   if constexpr (OP == OP_RESID) {
 #pragma unroll
-    for (int k = 0; k < 27; ++k) r[k] = -r[k];
+    for (int k = 0; k < 9; ++k) { ru[k] = pmul(pbc(T(-1)), ru[k]); rp[k] = -rp[k]; }
   }
   if constexpr (OP == OP_VJP) {
     cell[0] = -cell[0]; cell[1] = -cell[1]; cell[2] = -cell[2];
@@ -259,7 +305,8 @@ template <> __device__ __forceinline__ const Q2Tab<float>& q2tab<float>(const Ap
 template <> __device__ __forceinline__ const Q2Tab<double>& q2tab<double>(const ApplyArgs& a) { return a.q2d; }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ ApplyArgs a) {
+__global__ void __launch_bounds__(Q2T, sizeof(T) == 4 ? 2 : 1) apply_q2_kernel(const __grid_constant__ ApplyArgs a) {
+  using P = typename VT<T>::T2;
   constexpr bool isVjp = (OP == OP_VJP);
   constexpr int NBUF = Q2Smem<T>::NBUF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,7 +330,7 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
       const int32_t code = q2_slot(nbv, w % Q2W - 2, w / Q2W - 2);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        if (field_used<OP>(f)) cp_one(&sm.f[bu][f][w], field_ptr<T>(a, f) + code);
+        if (field_used<OP>(f)) cp_one(&q2_field<T>(sm.f[bu], f, w), field_ptr<T>(a, f) + code);
       cp_async4(&sm.cmw[bu][w], a.cmask + (code & ~3));
       sm.cmsh[bu][w] = uint8_t(code & 3);
     }
@@ -301,7 +348,7 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
     const BrickDesc* bd = a.lay.bricks + b;
     const int irr = __ldg(&bd->irr);
     const int level = __ldg(&bd->level);
-    T (*fb)[Q2WW] = sm.f[cur];
+    P (*fb)[Q2WW] = sm.f[cur];
     const int32_t* nbc = sm.nb[cur];
     __syncthreads();   // the previous brick's tiles are no longer read
     if (pending) {
@@ -311,11 +358,11 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
         const uint8_t cmw = uint8_t((sm.cmw[cur][w] >> (8 * sm.cmsh[cur][w])) & 0xffu);
         sm.cm[w] = cmw;
         if (mask && cmw) {
-          if (cmw & 1) fb[F_XU][w] = T(0);
-          if (cmw & 2) fb[F_XV][w] = T(0);
-          if (cmw & 4) fb[F_XP][w] = T(0);
+          if (cmw & 1) q2_field<T>(fb, F_XU, w) = T(0);
+          if (cmw & 2) q2_field<T>(fb, F_XV, w) = T(0);
+          if (cmw & 4) q2_field<T>(fb, F_XP, w) = T(0);
         }
-        if (!isVjp) { sm.y[0][w] = T(0); sm.y[1][w] = T(0); sm.y[2][w] = T(0); }
+        if (!isVjp) { sm.yu[w] = pbc(T(0)); sm.yp[w] = T(0); }
       }
     } else {
       if (tid < 9) sm.nb[cur][tid] = __ldg(bd->nbr_base + tid);
@@ -354,9 +401,9 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f)
-          if (field_used<OP>(f)) fb[f][w] = v[f];
+          if (field_used<OP>(f)) q2_field<T>(fb, f, w) = v[f];
         sm.cm[w] = cmw;
-        if (!isVjp) { sm.y[0][w] = T(0); sm.y[1][w] = T(0); sm.y[2][w] = T(0); }
+        if (!isVjp) { sm.yu[w] = pbc(T(0)); sm.yp[w] = T(0); }
       }
     }
     __syncthreads();
@@ -374,8 +421,9 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
     }
     T ec = T(1);
     if (a.ecell != nullptr && act) ec = ldg(reinterpret_cast<const T*>(a.ecell) + q2_slot(nbc, 2 * ci - 2, 2 * cj - 2));
-    T r[27], cell[3];
-    if (act) q2_cell<T, OP>(fb, cbase, mc, geom<T>(a, level), tb, ec, r, cell);
+    P ru[9];
+    T rp[9], cell[3];
+    if (act) q2_cell<T, OP>(fb, cbase, mc, geom<T>(a, level), tb, ec, ru, rp, cell);
     if constexpr (isVjp) {
       // the brick owns the cells whose lower-left node it owns (cells 0..14)
       if (act && ci >= 1 && cj >= 1) {
@@ -394,8 +442,8 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
               const int w = cbase + aa + Q2W * bb;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) sm.y[c][w] += r[3 * (aa + 3 * bb) + c];
+              sm.yu[w] = padd(sm.yu[w], ru[aa + 3 * bb]);
+              sm.yp[w] += rp[aa + 3 * bb];
             }
         }
         __syncthreads();
@@ -410,11 +458,11 @@ __global__ void __launch_bounds__(Q2T) apply_q2_kernel(const __grid_constant__ A
             const int act_s = irr >= 0 ? int(__ldg(a.lay.own_act + irr * (Q2NB * Q2NB) + o)) : int(kActFinal);
             ChebOps<T, OP> co;
             cheb_load<T, OP>(a, own_base + o, co);
-            cheb_store<T, OP>(a, own_base + o, act_s, sm.cm[w], sm.y[0][w], sm.y[1][w], sm.y[2][w], co);
+            cheb_store<T, OP>(a, own_base + o, act_s, sm.cm[w], sm.yu[w].x, sm.yu[w].y, sm.yp[w], co);
             continue;
           }
         }
-        write_node<T, OP>(a, irr, own_base, oi, oj, sm.cm[w], sm.y[0][w], sm.y[1][w], sm.y[2][w]);
+        write_node<T, OP>(a, irr, own_base, oi, oj, sm.cm[w], sm.yu[w].x, sm.yu[w].y, sm.yp[w]);
       }
     }
     if (NBUF == 2) cur ^= 1;

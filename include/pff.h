@@ -326,8 +326,9 @@ pff_status pff_cod(pff_problem* pb, const double* u, const double* phi, const do
 pff_status pff_gmres_solve(pff_problem* pb, pff_mg* mg, int32_t transpose, const double* rhs, double* x,
                            double rtol, int32_t restart, int32_t maxiter, pff_solve_info* info, void* stream);
 /* One load step of Algorithm 2 at the problem's pressure: Newton iterations with
- * the primal-dual active set, multigrid-preconditioned GMRES and line search,
- * phi_tilde = phi_old.  u, phi: updated in place; active: n_slots bytes, the
+ * the primal-dual active set, multigrid-preconditioned GMRES and line search;
+ * phi_tilde = opts->phi_tilde when set (e.g. from pff_extrapolate_phi), else
+ * phi_old.  u, phi: updated in place; active: n_slots bytes, the
  * previous step's final set on input, this step's on output.  opts may be NULL
  * (defaults above).  Synchronises.  Errors: PFF_ERR_NOT_CONVERGED,
  * PFF_ERR_NONFINITE, PFF_ERR_GMRES_BREAKDOWN (info filled).                   */

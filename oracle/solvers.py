@@ -19,7 +19,8 @@ Test infrastructure only (see ``oracle/__init__``).
     6. line search U + omega^(l-1) dU, l = 1..l_max, accept the first trial whose
        ||R~|| (same active set) is below the current one (else the last trial).
   R~ is the Newton residual: R on free rows, phi_old - phi on active rows, 0 on
-  Dirichlet and hanging rows.  phi_tilde = phi_old = phi^{n-1} for the step.
+  Dirichlet and hanging rows.  phi_tilde = phi_old = phi^{n-1} for the step
+  unless a phi_tilde is given (e.g. extrapolate_phi of the two previous steps).
 
 Pinned by tests/test_oracle_solvers.py: GMRES against a dense solve, KKT
 conditions at convergence, the pure-elasticity limit, and the Sneddon crack

@@ -142,7 +142,7 @@ __global__ void k_copy_fixed(int64_t n, const uint8_t* __restrict__ cmask, const
   }
 }
 
-// adjoint carry to the previous load step: g = (0, 0, -t2 + act (mu_phi - t1_phi))
+// Adjoint carry to the previous load step:
 // g = (0, 0, -w t2 + act (mu_phi - t1_phi) + pend_in).  phi_tilde = phi^(k-1)
 // (p1 null): w = 1.  Extrapolated phi_tilde = clip(2 p1 - p2, 0, 1): w = 2 chi on
 // the slots strictly inside the clip (chi = 1, else 0), and pend_out = chi t2 is
